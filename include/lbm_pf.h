@@ -1,0 +1,180 @@
+/*
+ * lbm_pf.h -- C ABI of the B300 lattice Boltzmann phase-field solver for
+ * two-phase flow with phase change (Verdier, Kestener & Cartalade,
+ * arXiv:2003.06342).
+ *
+ * One handle owns one lattice: the three coupled distribution sets of the
+ * paper (Sec. 3) -- f for incompressible Navier-Stokes (Sec. 3.1), g for the
+ * conservative Allen-Cahn phase field with the interfacial production source
+ * (Sec. 3.2), s for the temperature with the latent-heat source (Sec. 3.3) --
+ * advanced by one fused CUDA kernel per time step that also evaluates the
+ * finite-difference gradient, Laplacian and chemical-potential stencils
+ * (Sec. 3.4).
+ *
+ * Conventions for every call:
+ *  - Lattice units, dx = dt = 1.  Fields are dense arrays of nx*ny*nz values,
+ *    x fastest, then y, then z: index (z*ny + y)*nx + x.  2D runs use nz = 1.
+ *  - All calls return LBM_OK (0) or a negative LBM_E* code; none aborts,
+ *    throws or exits.  lbm_strerror() names the code.
+ *  - Device work is queued on the handle's CUDA stream and is asynchronous
+ *    unless a call says it synchronises.  Errors raised by a kernel surface at
+ *    the next synchronising call (lbm_sync, lbm_reduce, host-side
+ *    lbm_get_fields / lbm_get_state) as LBM_ECUDA.
+ *  - The caller owns all memory: the workspace passed to lbm_create (device
+ *    memory, kept by the handle until lbm_destroy) and every field, state and
+ *    map buffer.  The library itself never calls cudaMalloc.
+ *  - A handle is not thread-safe; different handles are independent.
+ */
+#ifndef LBM_PF_H
+#define LBM_PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LBM_OK            0
+#define LBM_EINVAL       -1   /* bad argument: size, pointer, parameter range   */
+#define LBM_ENOMEM       -2   /* workspace or caller buffer too small            */
+#define LBM_ECUDA        -3   /* a CUDA runtime call or kernel launch failed     */
+#define LBM_ENONFINITE   -4   /* a reduction found NaN or Inf in the fields      */
+#define LBM_ETIMEOUT     -5   /* reserved: no kernel of this library waits       */
+#define LBM_EUNSUPPORTED -6   /* combination not built (e.g. lattice/storage)    */
+
+/* ---- lattices (Sec. 3, lattice definitions) ----------------------------- */
+#define LBM_D2Q9        0     /* 2D: D2Q9 for f, g and s                         */
+#define LBM_D3Q19_D3Q7  1     /* 3D: D3Q19 for f and s, D3Q7 for g               */
+
+/* ---- population storage -------------------------------------------------- */
+#define LBM_STORE_FP32  0     /* 32-bit deviations  d_i = theta_i - w_i*ref      */
+#define LBM_STORE_FP16  1     /* 16-bit deviations  d_i = (theta_i/w_i - ref)*scale */
+#define LBM_STORE_BF16  2     /* bfloat16, same encoding as FP16                 */
+
+typedef struct lbm_handle lbm_handle;
+
+/* Grid.  nz = 1 selects 2D.  periodic[a] != 0 makes axis a periodic; at most
+ * one axis may be non-periodic: it carries two half-way walls, at -1/2 and at
+ * n_a - 1/2, with no-slip bounce-back for f and anti-bounce-back Dirichlet
+ * values for g and s (Sec. 3.3, Sec. 4.1). */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t periodic[3];
+} lbm_grid;
+
+/* Model parameters, lattice units (Table tab:FilmBoiling_Parameters after
+ * conversion).  Index 0/1 of phi_wall and T_wall is the low/high wall of the
+ * non-periodic axis. */
+typedef struct {
+    double rho_l, rho_g;          /* phase densities, Eq. Density                */
+    double nu_l, nu_g;            /* kinematic viscosities, Eq. Viscosity        */
+    double alpha_l, alpha_g;      /* thermal diffusivities                       */
+    double sigma, W;              /* surface tension, interface width, Eq. Def_K-H */
+    double M_phi;                 /* mobility, tau_g = M_phi / cs^2              */
+    double A;                     /* coefficient of Eq. ProductionRate (10/48)   */
+    double theta_I;               /* dimensionless interface temperature         */
+    double L, Cp, T_sat;          /* latent heat, specific heat, saturation T    */
+    double gravity[3];            /* gravity vector; F_v = (rho - rho_l) gravity */
+    double body_force[3];         /* constant force density added to F_tot       */
+    double phi_wall[2];           /* Dirichlet phi at the low / high wall        */
+    double T_wall[2];             /* Dirichlet T at the low / high wall          */
+    double normal_eps;            /* n = grad phi / max(|grad phi|, normal_eps)  */
+    double store_ref[3];          /* storage reference per set (f, g, s)         */
+    double store_scale[3];        /* 16-bit storage scale per set (f, g, s)      */
+    int32_t source_on;            /* 0: mdot''' = 0                              */
+    int32_t visc_interp;          /* 0: harmonic Eq. Viscosity, 1: linear Eq. Visco_lin */
+    int32_t alpha_interp;         /* 0: linear in phi, 1: harmonic               */
+    int32_t storage;              /* LBM_STORE_*                                 */
+} lbm_params;
+
+/* Macroscopic fields.  Any pointer may be NULL (that field is skipped on
+ * output; on input NULL means zero, except phi and T, which are required).
+ * uz is ignored in 2D.  on_device: 1 for device pointers, 0 for host
+ * pointers (host transfers are synchronous).  dtype: 0 float32, 1 float64. */
+typedef struct {
+    void *phi, *T, *ux, *uy, *uz, *p;
+    int32_t on_device;
+    int32_t dtype;
+} lbm_fields;
+
+/* Device workspace needed by lbm_create for this grid, lattice and storage:
+ * two population buffers (read/write per step), phi^{n-1}, two lagged-source
+ * buffers, moment and reduction scratch.  Returns LBM_EINVAL on an invalid
+ * grid or parameter set. */
+int lbm_workspace_bytes(const lbm_grid *grid, int32_t lattice, const lbm_params *params,
+                        size_t *bytes);
+
+/* Validate grid and parameters (tau_f, tau_g, tau_s > 0, W > 0, densities > 0,
+ * at most one wall axis) and build a handle over the caller's device
+ * workspace (256-byte aligned, at least lbm_workspace_bytes).  stream is a
+ * cudaStream_t (NULL: the legacy default stream).  The state is undefined
+ * until lbm_init or lbm_set_state.  Errors: LBM_EINVAL, LBM_ENOMEM,
+ * LBM_EUNSUPPORTED, LBM_ECUDA. */
+int lbm_create(const lbm_grid *grid, int32_t lattice, const lbm_params *params,
+               void *workspace, size_t workspace_bytes, void *stream, lbm_handle **out);
+
+/* Queue later work on another cudaStream_t. */
+int lbm_set_stream(lbm_handle *h, void *stream);
+
+/* Set the populations to the barred equilibria of the given fields,
+ * theta_bar_i = theta_eq_i - S_i/2 (App. C, Eq. VariableChange_feq), with
+ * phi^{n-1} = phi_0 and the lagged source evaluated from (phi_0, T_0), so that
+ * lbm_get_fields returns the input fields.  Resets the step counter. */
+int lbm_init(lbm_handle *h, const lbm_fields *in);
+
+/* Advance n >= 0 time steps: per step one fused kernel computing the moments
+ * (Eqs. Moment_Phi, Velocity, Pressure, Moment_Temp), the phi stencils (Eqs.
+ * Grad, Laplacian, ChemicalPotential), the production rate (Eq.
+ * ProductionRate), the three BGK collisions with sources (Eq. LBE) and the
+ * streaming with boundary links.  Asynchronous. */
+int lbm_step(lbm_handle *h, int32_t n);
+
+/* Write phi, u, p and T of the current state (the moments of the step
+ * above).  Device outputs are asynchronous; host outputs synchronise. */
+int lbm_get_fields(lbm_handle *h, lbm_fields *out);
+
+/* Global phase-field mass sum(phi) and enthalpy sum(rho (Cp T + phi L))
+ * (Eq. Conservation_Enthalpie with H = Cp T + phi L), accumulated in FP64.
+ * Synchronises; returns LBM_ENONFINITE if either sum is not finite. */
+int lbm_reduce(lbm_handle *h, double *phi_mass, double *energy);
+
+/* Same reduction, asynchronous: two doubles written to device memory d_out. */
+int lbm_reduce_async(lbm_handle *h, double *d_out);
+
+/* Checkpoint / resume: the state is the populations, phi^{n-1} and the lagged
+ * source (bytes from lbm_state_bytes).  on_device selects the buffer's side.
+ * Restoring a saved state and stepping reproduces the uninterrupted run bit
+ * for bit. */
+int lbm_state_bytes(const lbm_handle *h, size_t *bytes);
+int lbm_get_state(lbm_handle *h, void *dst, size_t bytes, int32_t on_device);
+int lbm_set_state(lbm_handle *h, const void *src, size_t bytes, int32_t on_device);
+
+/* Test hook: the streaming map of one step as executed by the step kernel,
+ * in pull form.  set 0 = the f/s lattice, 1 = the g lattice.  For direction i
+ * and destination cell x, src_index[i*N + x] = cell the value comes from and
+ * kind[i*N + x] = 0 interior, 1 wrapped over a periodic axis, 2 bounced at the
+ * low wall, 3 bounced at the high wall (a bounced value comes from x itself,
+ * opposite direction).  Both buffers are device memory of Q*N entries. */
+int lbm_stream_map(lbm_handle *h, int32_t set, int32_t *src_index, int8_t *kind);
+
+/* Number of time steps since lbm_init / lbm_set_state. */
+int lbm_steps_done(const lbm_handle *h, int64_t *steps);
+
+/* Kernel launches queued by the last lbm_step call. */
+int lbm_last_launches(const lbm_handle *h, int32_t *launches);
+
+/* Wait for the handle's stream; report any pending CUDA error. */
+int lbm_sync(lbm_handle *h);
+
+/* Release the handle (not the workspace, which the caller owns). */
+void lbm_destroy(lbm_handle *h);
+
+const char *lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_PF_H */

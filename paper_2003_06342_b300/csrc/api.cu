@@ -1,0 +1,461 @@
+// C ABI of the phase-field LB solver (declarations and contracts in
+// include/lbm_pf.h).  Host-side validation, workspace carving, dispatch to the
+// 2D / 3D kernels and host <-> device transfers.  No cudaMalloc anywhere: the
+// caller provides the device workspace.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm_pf.h"
+#include "lbm_kernels.h"
+#include "lbm3d.h"
+
+using namespace lbm;
+
+struct lbm_handle {
+    lbm_grid grid;
+    int32_t lattice;
+    lbm_params params;
+    DevParams dp;
+    cudaStream_t stream;
+    int dim, Qf, Qg, Qtot;
+    size_t elem;             // bytes per stored population value
+    size_t N;
+    void *pops[2];
+    float *phi_prev;
+    float *q[2];
+    float *scratch;          // 6 planes of N floats
+    double *partial;         // 2 doubles per reduction block
+    double *red_out;         // 2 doubles
+    int red_blocks;
+    int cur;
+    int64_t steps;
+    int32_t last_launches;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t pops, phi, q, scratch, partial, red, total;
+    int red_blocks;
+};
+
+int lattice_dims(int32_t lattice, int *dim, int *Qf, int *Qg) {
+    if (lattice == LBM_D2Q9) { *dim = 2; *Qf = 9; *Qg = 9; return LBM_OK; }
+    if (lattice == LBM_D3Q19_D3Q7) { *dim = 3; *Qf = 19; *Qg = 7; return LBM_OK; }
+    return LBM_EINVAL;
+}
+
+size_t elem_size(int32_t storage) { return storage == LBM_STORE_FP32 ? 4 : 2; }
+
+int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
+    if (!g || !p) return LBM_EINVAL;
+    int dim, Qf, Qg;
+    if (lattice_dims(lattice, &dim, &Qf, &Qg) != LBM_OK) return LBM_EINVAL;
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return LBM_EINVAL;
+    if (dim == 2 && g->nz != 1) return LBM_EINVAL;
+    const double N = (double)g->nx * g->ny * g->nz;
+    if (N >= 2147483647.0) return LBM_EINVAL;          // int32 stream-map indices
+    int walls = 0;
+    for (int a = 0; a < dim; ++a) walls += g->periodic[a] ? 0 : 1;
+    if (walls > 1) return LBM_EINVAL;
+    if (!(p->rho_l > 0 && p->rho_g > 0 && p->nu_l > 0 && p->nu_g > 0 && p->alpha_l > 0 &&
+          p->alpha_g > 0 && p->W > 0 && p->M_phi > 0 && p->A != 0 && p->L != 0 && p->Cp != 0 &&
+          p->sigma >= 0 && p->normal_eps > 0))
+        return LBM_EINVAL;
+    if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16) return LBM_EINVAL;
+    const double vals[] = {p->rho_l, p->rho_g, p->nu_l, p->nu_g, p->alpha_l, p->alpha_g, p->sigma,
+                           p->W, p->M_phi, p->A, p->theta_I, p->L, p->Cp, p->T_sat,
+                           p->gravity[0], p->gravity[1], p->gravity[2], p->body_force[0],
+                           p->body_force[1], p->body_force[2], p->phi_wall[0], p->phi_wall[1],
+                           p->T_wall[0], p->T_wall[1], p->normal_eps};
+    for (double v : vals)
+        if (!std::isfinite(v)) return LBM_EINVAL;
+    return LBM_OK;
+}
+
+Layout layout(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
+    int dim, Qf, Qg;
+    lattice_dims(lattice, &dim, &Qf, &Qg);
+    const size_t N = (size_t)g->nx * g->ny * g->nz;
+    const size_t Qtot = (size_t)(2 * Qf + Qg);
+    Layout L;
+    L.pops = align_up(Qtot * N * elem_size(p->storage));
+    L.phi = align_up(N * sizeof(float));
+    L.q = align_up(N * sizeof(float));
+    L.scratch = align_up(6 * N * sizeof(float));
+    L.red_blocks = (int)((N + 255) / 256);
+    L.partial = align_up((size_t)L.red_blocks * 2 * sizeof(double));
+    L.red = align_up(2 * sizeof(double));
+    L.total = 2 * L.pops + L.phi + 2 * L.q + L.scratch + L.partial + L.red;
+    return L;
+}
+
+void fill_devparams(lbm_handle *h) {
+    const lbm_params &p = h->params;
+    DevParams &d = h->dp;
+    std::memset(&d, 0, sizeof(d));
+    d.n[0] = h->grid.nx; d.n[1] = h->grid.ny; d.n[2] = h->grid.nz;
+    d.wall_axis = -1;
+    for (int a = 0; a < 3; ++a) {
+        d.periodic[a] = (a < h->dim) ? (h->grid.periodic[a] ? 1 : 0) : 1;
+        if (!d.periodic[a]) d.wall_axis = a;
+    }
+    d.N = (long long)h->N;
+    d.rho_l = (float)p.rho_l; d.rho_g = (float)p.rho_g; d.drho = (float)(p.rho_g - p.rho_l);
+    d.nu_l = (float)p.nu_l; d.nu_g = (float)p.nu_g;
+    d.alpha_l = (float)p.alpha_l; d.alpha_g = (float)p.alpha_g;
+    d.K = (float)(1.5 * p.W * p.sigma);
+    d.H = (float)(12.0 * p.sigma / p.W);
+    d.four_over_W = (float)(4.0 / p.W);
+    d.prod_coef = (float)(4.0 / (p.A * p.W * p.W));
+    d.theta_I = (float)p.theta_I;
+    d.L_over_Cp = (float)(p.L / p.Cp);
+    d.Cp_over_L = (float)(p.Cp / p.L);
+    d.T_sat = (float)p.T_sat;
+    const double cs2_g = h->dim == 2 ? 1.0 / 3.0 : 0.25;
+    d.tau_g = (float)(p.M_phi / cs2_g);
+    d.kappa = (float)(1.0 - p.rho_g / p.rho_l);
+    d.eps2 = (float)(p.normal_eps * p.normal_eps);
+    for (int a = 0; a < 3; ++a) { d.gravity[a] = (float)p.gravity[a]; d.body[a] = (float)p.body_force[a]; }
+    for (int k = 0; k < 2; ++k) { d.phi_wall[k] = (float)p.phi_wall[k]; d.T_wall[k] = (float)p.T_wall[k]; }
+    d.source_on = p.source_on ? 1 : 0;
+    d.visc_interp = p.visc_interp;
+    d.alpha_interp = p.alpha_interp;
+    d.storage = p.storage;
+    // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
+    int k = 0;
+    for (int set = 0; set < 3; ++set) {
+        const int Q = set == 1 ? h->Qg : h->Qf;
+        const double scale = p.store_scale[set] != 0.0 ? p.store_scale[set] : 1.0;
+        for (int i = 0; i < Q; ++i, ++k) {
+            double w;   // exact lattice weights in double
+            if (h->dim == 2) w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+            else if (set == 1) w = i == 0 ? 0.25 : 0.125;
+            else w = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+            d.enc_c[k] = (float)(w * p.store_ref[set]);
+            if (p.storage == LBM_STORE_FP32) { d.enc_s[k] = 1.0f; d.dec_s[k] = 1.0f; }
+            else { d.enc_s[k] = (float)(scale / w); d.dec_s[k] = (float)(w / scale); }
+        }
+    }
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+// ---- dispatch on storage type and dimension
+int do_step(lbm_handle *h) {
+    const int nxt = h->cur ^ 1;
+    cudaError_t e;
+    if (h->dim == 2) {
+        switch (h->params.storage) {
+        case LBM_STORE_FP32: e = launch_step2d<float>(h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->dp, h->stream); break;
+        case LBM_STORE_FP16: e = launch_step2d<__half>(h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->dp, h->stream); break;
+        default: e = launch_step2d<__nv_bfloat16>(h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->dp, h->stream); break;
+        }
+    } else {
+        switch (h->params.storage) {
+        case LBM_STORE_FP32: e = launch_step3d<float>(h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->dp, h->stream); break;
+        case LBM_STORE_FP16: e = launch_step3d<__half>(h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->dp, h->stream); break;
+        default: e = launch_step3d<__nv_bfloat16>(h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->dp, h->stream); break;
+        }
+    }
+    if (e != cudaSuccess) return LBM_ECUDA;
+    h->cur = nxt;
+    return LBM_OK;
+}
+
+int do_macro(lbm_handle *h, float *o_phi, float *o_T, float *o_u[3], float *o_p, double *partial) {
+    float *phi_tmp = h->scratch;   // plane 0 of the scratch
+    const double Cp = h->params.Cp, Lh = h->params.L;
+    cudaError_t e;
+    if (h->dim == 2) {
+        switch (h->params.storage) {
+        case LBM_STORE_FP32: e = launch_macro2d<float>(h->pops[h->cur], phi_tmp, h->phi_prev, h->q[h->cur], o_phi, o_T, o_u[0], o_u[1], o_p, partial, Cp, Lh, h->dp, h->stream); break;
+        case LBM_STORE_FP16: e = launch_macro2d<__half>(h->pops[h->cur], phi_tmp, h->phi_prev, h->q[h->cur], o_phi, o_T, o_u[0], o_u[1], o_p, partial, Cp, Lh, h->dp, h->stream); break;
+        default: e = launch_macro2d<__nv_bfloat16>(h->pops[h->cur], phi_tmp, h->phi_prev, h->q[h->cur], o_phi, o_T, o_u[0], o_u[1], o_p, partial, Cp, Lh, h->dp, h->stream); break;
+        }
+    } else {
+        switch (h->params.storage) {
+        case LBM_STORE_FP32: e = launch_macro3d<float>(h->pops[h->cur], phi_tmp, h->phi_prev, h->q[h->cur], o_phi, o_T, o_u, o_p, partial, Cp, Lh, h->dp, h->stream); break;
+        case LBM_STORE_FP16: e = launch_macro3d<__half>(h->pops[h->cur], phi_tmp, h->phi_prev, h->q[h->cur], o_phi, o_T, o_u, o_p, partial, Cp, Lh, h->dp, h->stream); break;
+        default: e = launch_macro3d<__nv_bfloat16>(h->pops[h->cur], phi_tmp, h->phi_prev, h->q[h->cur], o_phi, o_T, o_u, o_p, partial, Cp, Lh, h->dp, h->stream); break;
+        }
+    }
+    return cuda_status(e);
+}
+
+int do_init(lbm_handle *h, const float *phi0, const float *T0, const float *u0[3], const float *p0) {
+    cudaError_t e;
+    if (h->dim == 2) {
+        switch (h->params.storage) {
+        case LBM_STORE_FP32: e = launch_init2d<float>(phi0, T0, u0[0], u0[1], p0, h->pops[h->cur], h->phi_prev, h->q[h->cur], h->dp, h->stream); break;
+        case LBM_STORE_FP16: e = launch_init2d<__half>(phi0, T0, u0[0], u0[1], p0, h->pops[h->cur], h->phi_prev, h->q[h->cur], h->dp, h->stream); break;
+        default: e = launch_init2d<__nv_bfloat16>(phi0, T0, u0[0], u0[1], p0, h->pops[h->cur], h->phi_prev, h->q[h->cur], h->dp, h->stream); break;
+        }
+    } else {
+        switch (h->params.storage) {
+        case LBM_STORE_FP32: e = launch_init3d<float>(phi0, T0, u0, p0, h->pops[h->cur], h->phi_prev, h->q[h->cur], h->dp, h->stream); break;
+        case LBM_STORE_FP16: e = launch_init3d<__half>(phi0, T0, u0, p0, h->pops[h->cur], h->phi_prev, h->q[h->cur], h->dp, h->stream); break;
+        default: e = launch_init3d<__nv_bfloat16>(phi0, T0, u0, p0, h->pops[h->cur], h->phi_prev, h->q[h->cur], h->dp, h->stream); break;
+        }
+    }
+    return cuda_status(e);
+}
+
+// Stage one input field as float32 on the device (scratch plane `slot`).
+int stage_in(lbm_handle *h, const void *src, int on_device, int dtype, int slot, const float **out) {
+    *out = nullptr;
+    if (!src) return LBM_OK;
+    float *dst = h->scratch + (size_t)slot * h->N;
+    const size_t N = h->N;
+    if (on_device) {
+        if (dtype == 0) { *out = (const float *)src; return LBM_OK; }
+        if (dtype != 1) return LBM_EINVAL;
+        if (launch_convert_f64_to_f32((const double *)src, dst, N, h->stream) != cudaSuccess) return LBM_ECUDA;
+    } else {
+        if (dtype == 0) {
+            if (cudaMemcpyAsync(dst, src, N * sizeof(float), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return LBM_ECUDA;
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+        } else if (dtype == 1) {
+            std::vector<float> tmp(N);
+            const double *s = (const double *)src;
+            for (size_t i = 0; i < N; ++i) tmp[i] = (float)s[i];
+            if (cudaMemcpyAsync(dst, tmp.data(), N * sizeof(float), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return LBM_ECUDA;
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+        } else return LBM_EINVAL;
+    }
+    *out = dst;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_strerror(int code) {
+    switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "workspace or buffer too small";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ENONFINITE: return "non-finite value in the fields";
+    case LBM_ETIMEOUT: return "timeout";
+    case LBM_EUNSUPPORTED: return "unsupported combination";
+    default: return "unknown error";
+    }
+}
+
+int lbm_workspace_bytes(const lbm_grid *grid, int32_t lattice, const lbm_params *params, size_t *bytes) {
+    if (!bytes) return LBM_EINVAL;
+    const int v = validate(grid, lattice, params);
+    if (v != LBM_OK) return v;
+    *bytes = layout(grid, lattice, params).total;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_grid *grid, int32_t lattice, const lbm_params *params, void *workspace,
+               size_t workspace_bytes, void *stream, lbm_handle **out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    const int v = validate(grid, lattice, params);
+    if (v != LBM_OK) return v;
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0) return LBM_EINVAL;
+    const Layout L = layout(grid, lattice, params);
+    if (workspace_bytes < L.total) return LBM_ENOMEM;
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ENOMEM;
+    h->grid = *grid;
+    if (lattice == LBM_D2Q9) { h->grid.nz = 1; h->grid.periodic[2] = 1; }
+    h->lattice = lattice;
+    h->params = *params;
+    lattice_dims(lattice, &h->dim, &h->Qf, &h->Qg);
+    h->Qtot = 2 * h->Qf + h->Qg;
+    h->elem = elem_size(params->storage);
+    h->N = (size_t)grid->nx * grid->ny * grid->nz;
+    h->stream = (cudaStream_t)stream;
+    char *p = (char *)workspace;
+    h->pops[0] = p; p += L.pops;
+    h->pops[1] = p; p += L.pops;
+    h->phi_prev = (float *)p; p += L.phi;
+    h->q[0] = (float *)p; p += L.q;
+    h->q[1] = (float *)p; p += L.q;
+    h->scratch = (float *)p; p += L.scratch;
+    h->partial = (double *)p; p += L.partial;
+    h->red_out = (double *)p; p += L.red;
+    h->red_blocks = L.red_blocks;
+    h->cur = 0;
+    h->steps = 0;
+    h->last_launches = 0;
+    fill_devparams(h);
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle *h, void *stream) {
+    if (!h) return LBM_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_handle *h, const lbm_fields *in) {
+    if (!h || !in || !in->phi || !in->T) return LBM_EINVAL;
+    const float *phi0, *T0, *p0, *u0[3] = {nullptr, nullptr, nullptr};
+    int r;
+    if ((r = stage_in(h, in->phi, in->on_device, in->dtype, 0, &phi0)) != LBM_OK) return r;
+    if ((r = stage_in(h, in->T, in->on_device, in->dtype, 1, &T0)) != LBM_OK) return r;
+    if ((r = stage_in(h, in->ux, in->on_device, in->dtype, 2, &u0[0])) != LBM_OK) return r;
+    if ((r = stage_in(h, in->uy, in->on_device, in->dtype, 3, &u0[1])) != LBM_OK) return r;
+    if (h->dim == 3 && (r = stage_in(h, in->uz, in->on_device, in->dtype, 4, &u0[2])) != LBM_OK) return r;
+    if ((r = stage_in(h, in->p, in->on_device, in->dtype, 5, &p0)) != LBM_OK) return r;
+    h->cur = 0;
+    h->steps = 0;
+    return do_init(h, phi0, T0, u0, p0);
+}
+
+int lbm_step(lbm_handle *h, int32_t n) {
+    if (!h || n < 0) return LBM_EINVAL;
+    h->last_launches = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        const int r = do_step(h);
+        if (r != LBM_OK) return r;
+        ++h->steps;
+        ++h->last_launches;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_handle *h, lbm_fields *out) {
+    if (!h || !out) return LBM_EINVAL;
+    if (out->dtype != 0 && out->dtype != 1) return LBM_EINVAL;
+    void *dsts[6] = {out->phi, out->T, out->ux, out->uy, h->dim == 3 ? out->uz : nullptr, out->p};
+    float *dev[6];
+    const bool direct = out->on_device && out->dtype == 0;
+    // scratch plane 0 holds phi_tmp; planes 1..5 stage outputs (phi shares plane 1
+    // with T only when both requested, so phi staging uses the destination or plane 5)
+    float *stage[6] = {nullptr, h->scratch + 1 * h->N, h->scratch + 2 * h->N, h->scratch + 3 * h->N,
+                       h->scratch + 4 * h->N, h->scratch + 5 * h->N};
+    for (int k = 0; k < 6; ++k) {
+        if (!dsts[k]) { dev[k] = nullptr; continue; }
+        dev[k] = direct ? (float *)dsts[k] : (k == 0 ? nullptr : stage[k]);
+    }
+    // phi output: staged through phi_tmp itself (plane 0 holds the moment phi)
+    float *o_phi = (dsts[0] && direct) ? (float *)dsts[0] : nullptr;
+    float *o_u[3] = {dev[2], dev[3], dev[4]};
+    int r = do_macro(h, o_phi, dev[1], o_u, dev[5], nullptr);
+    if (r != LBM_OK) return r;
+    if (direct) return LBM_OK;
+    dev[0] = dsts[0] ? h->scratch : nullptr;   // phi moment lives in plane 0
+    const size_t N = h->N;
+    for (int k = 0; k < 6; ++k) {
+        if (!dsts[k]) continue;
+        if (out->on_device) {   // float64 device output
+            if (launch_convert_f32_to_f64(dev[k], (double *)dsts[k], N, h->stream) != cudaSuccess) return LBM_ECUDA;
+        } else if (out->dtype == 0) {
+            if (cudaMemcpyAsync(dsts[k], dev[k], N * sizeof(float), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return LBM_ECUDA;
+        } else {
+            std::vector<float> tmp(N);
+            if (cudaMemcpyAsync(tmp.data(), dev[k], N * sizeof(float), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return LBM_ECUDA;
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+            double *d = (double *)dsts[k];
+            for (size_t i = 0; i < N; ++i) d[i] = tmp[i];
+        }
+    }
+    if (!out->on_device && cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+    return LBM_OK;
+}
+
+int lbm_reduce_async(lbm_handle *h, double *d_out) {
+    if (!h || !d_out) return LBM_EINVAL;
+    float *none[3] = {nullptr, nullptr, nullptr};
+    const int r = do_macro(h, nullptr, nullptr, none, nullptr, h->partial);
+    if (r != LBM_OK) return r;
+    return cuda_status(launch_final_sum2(h->partial, h->red_blocks, d_out, h->stream));
+}
+
+int lbm_reduce(lbm_handle *h, double *phi_mass, double *energy) {
+    if (!h) return LBM_EINVAL;
+    int r = lbm_reduce_async(h, h->red_out);
+    if (r != LBM_OK) return r;
+    double host[2];
+    if (cudaMemcpyAsync(host, h->red_out, sizeof(host), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return LBM_ECUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+    if (phi_mass) *phi_mass = host[0];
+    if (energy) *energy = host[1];
+    if (!std::isfinite(host[0]) || !std::isfinite(host[1])) return LBM_ENONFINITE;
+    return LBM_OK;
+}
+
+int lbm_state_bytes(const lbm_handle *h, size_t *bytes) {
+    if (!h || !bytes) return LBM_EINVAL;
+    *bytes = (size_t)h->Qtot * h->N * h->elem + 2 * h->N * sizeof(float);
+    return LBM_OK;
+}
+
+static int copy_state(lbm_handle *h, void *buf, size_t bytes, int32_t on_device, bool save) {
+    size_t need;
+    lbm_state_bytes(h, &need);
+    if (!buf) return LBM_EINVAL;
+    if (bytes < need) return LBM_ENOMEM;
+    const size_t pb = (size_t)h->Qtot * h->N * h->elem, sb = h->N * sizeof(float);
+    char *b = (char *)buf;
+    void *dev[3] = {h->pops[h->cur], h->phi_prev, h->q[h->cur]};
+    const size_t sz[3] = {pb, sb, sb};
+    size_t off = 0;
+    cudaMemcpyKind kind = save ? (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost)
+                               : (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e = save ? cudaMemcpyAsync(b + off, dev[k], sz[k], kind, h->stream)
+                             : cudaMemcpyAsync(dev[k], b + off, sz[k], kind, h->stream);
+        if (e != cudaSuccess) return LBM_ECUDA;
+        off += sz[k];
+    }
+    if (!on_device && cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle *h, void *dst, size_t bytes, int32_t on_device) {
+    if (!h) return LBM_EINVAL;
+    return copy_state(h, dst, bytes, on_device, true);
+}
+
+int lbm_set_state(lbm_handle *h, const void *src, size_t bytes, int32_t on_device) {
+    if (!h) return LBM_EINVAL;
+    const int r = copy_state(h, const_cast<void *>(src), bytes, on_device, false);
+    if (r == LBM_OK) h->steps = 0;
+    return r;
+}
+
+int lbm_stream_map(lbm_handle *h, int32_t set, int32_t *src_index, int8_t *kind) {
+    if (!h || !src_index || !kind || set < 0 || set > 1) return LBM_EINVAL;
+    cudaError_t e;
+    if (h->dim == 2) e = launch_streammap2d(src_index, kind, h->dp, h->stream);
+    else e = launch_streammap3d(set, src_index, kind, h->dp, h->stream);
+    return cuda_status(e);
+}
+
+int lbm_steps_done(const lbm_handle *h, int64_t *steps) {
+    if (!h || !steps) return LBM_EINVAL;
+    *steps = h->steps;
+    return LBM_OK;
+}
+
+int lbm_last_launches(const lbm_handle *h, int32_t *launches) {
+    if (!h || !launches) return LBM_EINVAL;
+    *launches = h->last_launches;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle *h) {
+    if (!h) return LBM_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+    return cuda_status(cudaGetLastError());
+}
+
+void lbm_destroy(lbm_handle *h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Shared device-side definitions of the B300 phase-field LB kernels.
+//
+// Lattices (Sec. 3): D2Q9 e0=(0,0), e1..4 = +x,+y,-x,-y, e5..8 = (1,1),
+// (-1,1), (-1,-1), (1,-1); D3Q7 = rest + six axis vectors in the order
+// +x,+y,+z,-x,-y,-z; D3Q19 = D3Q7's vectors + face diagonals (+-1,1,0),
+// (+-1,-1,0), (+-1,0,1), (+-1,0,-1), (0,+-1,1), (0,+-1,-1).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------- lattices
+struct D2Q9L {
+    static constexpr int Q = 9;
+    static __host__ __device__ constexpr int ex(int i) {
+        return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+    }
+    static __host__ __device__ constexpr int ey(int i) {
+        return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+    }
+    static __host__ __device__ constexpr int ez(int) { return 0; }
+    static __host__ __device__ constexpr int opp(int i) {
+        return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+    }
+    static __host__ __device__ constexpr float w(int i) {
+        return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+    }
+    static constexpr float cs2 = 1.0f / 3.0f;
+    static constexpr float inv_cs2 = 3.0f;
+};
+
+// axis part shared by D3Q7 and D3Q19: 1..6 = +x,+y,+z,-x,-y,-z
+__host__ __device__ constexpr int axis_e(int i, int a) {
+    return (i >= 1 && i <= 6) ? ((i - 1) % 3 == a ? (i <= 3 ? 1 : -1) : 0) : 0;
+}
+
+struct D3Q7L {
+    static constexpr int Q = 7;
+    static __host__ __device__ constexpr int ex(int i) { return axis_e(i, 0); }
+    static __host__ __device__ constexpr int ey(int i) { return axis_e(i, 1); }
+    static __host__ __device__ constexpr int ez(int i) { return axis_e(i, 2); }
+    static __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 3 ? i + 3 : i - 3); }
+    static __host__ __device__ constexpr float w(int i) { return i == 0 ? 0.25f : 0.125f; }
+    static constexpr float cs2 = 0.25f;
+    static constexpr float inv_cs2 = 4.0f;
+};
+
+struct D3Q19L {
+    static constexpr int Q = 19;
+    // diagonals 7..18 as (a, b) sign pairs on an axis pair
+    static __host__ __device__ constexpr int ex(int i) {
+        return i <= 6 ? axis_e(i, 0) : (i <= 14 ? ((i % 2) ? 1 : -1) : 0);
+    }
+    static __host__ __device__ constexpr int ey(int i) {
+        return i <= 6 ? axis_e(i, 1)
+             : (i <= 8 ? 1 : (i <= 10 ? -1 : (i <= 14 ? 0 : ((i % 2) ? 1 : -1))));
+    }
+    static __host__ __device__ constexpr int ez(int i) {
+        return i <= 6 ? axis_e(i, 2)
+             : (i <= 10 ? 0 : (i <= 12 ? 1 : (i <= 14 ? -1 : (i <= 16 ? 1 : -1))));
+    }
+    static __host__ __device__ constexpr int opp(int i) {
+        // pairs (7,10) (8,9) (11,14) (12,13) (15,18) (16,17)
+        return i == 0 ? 0 : (i <= 6 ? (i <= 3 ? i + 3 : i - 3)
+             : (i == 7 ? 10 : i == 8 ? 9 : i == 9 ? 8 : i == 10 ? 7
+             : i == 11 ? 14 : i == 12 ? 13 : i == 13 ? 12 : i == 14 ? 11
+             : i == 15 ? 18 : i == 16 ? 17 : i == 17 ? 16 : 15));
+    }
+    static __host__ __device__ constexpr float w(int i) {
+        return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+    }
+    static constexpr float cs2 = 1.0f / 3.0f;
+    static constexpr float inv_cs2 = 3.0f;
+};
+
+// ---------------------------------------------------------------- parameters
+constexpr int MAXQ_TOTAL = 45;   // 19 + 7 + 19
+
+// Everything a kernel needs, precomputed on the host in float.
+struct DevParams {
+    int n[3];            // nx, ny, nz
+    int periodic[3];
+    int wall_axis;       // -1 when every axis is periodic
+    long long N;         // cells
+    float rho_l, rho_g, drho;          // drho = rho_g - rho_l
+    float nu_l, nu_g, alpha_l, alpha_g;
+    float K, H;                        // Eq. Def_K-H
+    float four_over_W;                 // 4/W
+    float prod_coef;                   // 4 / (A W^2)
+    float theta_I, L_over_Cp, Cp_over_L, T_sat;
+    float tau_g;                       // M_phi / cs^2 of the phase-field lattice
+    float kappa;                       // 1 - rho_g/rho_l
+    float eps2;                        // normal_eps^2
+    float gravity[3], body[3];
+    float phi_wall[2], T_wall[2];
+    int source_on, visc_interp, alpha_interp, storage;
+    // storage codec per population plane k (f planes, then g, then s):
+    // FP32: theta = d + enc_c[k];  16-bit: theta = enc_c[k] + x * dec_s[k],
+    // x = (theta - enc_c[k]) * enc_s[k]
+    float enc_c[MAXQ_TOTAL], enc_s[MAXQ_TOTAL], dec_s[MAXQ_TOTAL];
+};
+
+// ---------------------------------------------------------------- storage
+template <typename S> struct Codec;
+
+template <> struct Codec<float> {
+    static __device__ __forceinline__ float load(const float *p, int k, const DevParams &P) {
+        return __ldg(p) + P.enc_c[k];
+    }
+    static __device__ __forceinline__ void store(float *p, float v, int k, const DevParams &P) {
+        *p = v - P.enc_c[k];
+    }
+};
+
+template <> struct Codec<__half> {
+    static __device__ __forceinline__ float load(const __half *p, int k, const DevParams &P) {
+        return fmaf(__half2float(__ldg(p)), P.dec_s[k], P.enc_c[k]);
+    }
+    static __device__ __forceinline__ void store(__half *p, float v, int k, const DevParams &P) {
+        *p = __float2half_rn((v - P.enc_c[k]) * P.enc_s[k]);
+    }
+};
+
+template <> struct Codec<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16 *p, int k, const DevParams &P) {
+        return fmaf(__bfloat162float(__ldg(p)), P.dec_s[k], P.enc_c[k]);
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v, int k, const DevParams &P) {
+        *p = __float2bfloat16_rn((v - P.enc_c[k]) * P.enc_s[k]);
+    }
+};
+
+// ---------------------------------------------------------------- closures
+__device__ __forceinline__ float viscosity(float phi, const DevParams &P) {
+    return P.visc_interp == 0 ? P.nu_l * P.nu_g / (phi * P.nu_l + (1.0f - phi) * P.nu_g)
+                              : (1.0f - phi) * P.nu_l + phi * P.nu_g;
+}
+
+__device__ __forceinline__ float diffusivity(float phi, const DevParams &P) {
+    return P.alpha_interp == 0 ? phi * P.alpha_g + (1.0f - phi) * P.alpha_l
+                               : P.alpha_l * P.alpha_g / (phi * P.alpha_l + (1.0f - phi) * P.alpha_g);
+}
+
+// mdot'''/rho_g of Eq. ProductionRate
+__device__ __forceinline__ float production(float phi, float T, const DevParams &P) {
+    if (!P.source_on) return 0.0f;
+    const float theta = P.Cp_over_L * (T - P.T_sat);
+    return -(P.prod_coef * diffusivity(phi, P)) * (P.theta_I - theta) * phi * (1.0f - phi);
+}
+
+// Periodic wrap / wall test of one coordinate.  Returns 0 in range, 1 wrapped,
+// 2 beyond the low wall, 3 beyond the high wall (c is wrapped in place).
+__device__ __forceinline__ int wrap_coord(int &c, int n, int periodic) {
+    if (c >= 0 && c < n) return 0;
+    if (periodic) { c = c < 0 ? c + n : c - n; return 1; }
+    return c < 0 ? 2 : 3;
+}
+
+}  // namespace lbm

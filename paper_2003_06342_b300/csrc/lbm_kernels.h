@@ -1,0 +1,62 @@
+// Kernel launchers shared between the kernel files and the C ABI layer, and
+// the FP64 block reduction used by the moment kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+// Sum two doubles over the block (warp shuffles, then one warp over the
+// per-warp sums) and store the pair at partial[2*blockIdx.x].  Every thread
+// of the block must call it.  The summation order is fixed, so results are
+// reproducible run to run.
+__device__ __forceinline__ void block_sum2(double a, double b, double *partial) {
+    __shared__ double sa[32], sb[32];
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(full, a, o);
+        b += __shfl_down_sync(full, b, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+    __syncthreads();
+    if (warp == 0) {
+        a = lane < nwarps ? sa[lane] : 0.0;
+        b = lane < nwarps ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(full, a, o);
+            b += __shfl_down_sync(full, b, o);
+        }
+        if (lane == 0) {
+            partial[2 * blockIdx.x] = a;
+            partial[2 * blockIdx.x + 1] = b;
+        }
+    }
+}
+
+// 2D (lbm2d.cu); S = float, __half or __nv_bfloat16 storage
+template <typename S>
+cudaError_t launch_step2d(const void *pin, void *pout, float *phi_prev, const float *q_in,
+                          float *q_out, const DevParams &P, cudaStream_t st);
+template <typename S>
+cudaError_t launch_macro2d(const void *pin, float *phi_tmp, const float *phi_prev,
+                           const float *q_in, float *o_phi, float *o_T, float *o_ux, float *o_uy,
+                           float *o_p, double *partial, double Cp, double Lh, const DevParams &P,
+                           cudaStream_t st);
+template <typename S>
+cudaError_t launch_init2d(const float *phi0, const float *T0, const float *ux0, const float *uy0,
+                          const float *p0, void *pout, float *phi_prev, float *q_out,
+                          const DevParams &P, cudaStream_t st);
+cudaError_t launch_streammap2d(int32_t *src, int8_t *kind, const DevParams &P, cudaStream_t st);
+
+// reductions (reduce.cu): sum nblocks (a, b) pairs into out[0..1]
+cudaError_t launch_final_sum2(const double *partial, int nblocks, double *out, cudaStream_t st);
+// float -> float copy with optional double conversion helpers
+cudaError_t launch_convert_f64_to_f32(const double *src, float *dst, size_t n, cudaStream_t st);
+cudaError_t launch_convert_f32_to_f64(const float *src, double *dst, size_t n, cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI: the in-tree library loads, exports every
+function include/lbm_pf.h declares, and validates grids, parameters and
+workspace sizes without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import workloads as W
+from paper_2003_06342_b300 import _binding as B
+from paper_2003_06342_b300.solver import make_grid, make_params
+
+HEADER_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(HEADER_DIR):
+        if fn.endswith(".h"):
+            src = open(os.path.join(HEADER_DIR, fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in sorted(names):
+        assert hasattr(B.lib, n), n
+    # and the binding declares every one of them
+    assert names <= set(B.SIGNATURES)
+
+
+def _ws(w, storage="fp32"):
+    g = make_grid(w.n, w.periodic)
+    p = make_params(w.params, storage)
+    out = ctypes.c_size_t()
+    lat = B.LBM_D2Q9 if w.dim == 2 else B.LBM_D3Q19_D3Q7
+    return B.lib.lbm_workspace_bytes(ctypes.byref(g), lat, ctypes.byref(p), ctypes.byref(out)), out.value, g, p, lat
+
+
+def test_workspace_bytes_scale_with_storage():
+    w = W.film_boiling_2d(64, 32)
+    r32, b32, *_ = _ws(w, "fp32")
+    r16, b16, *_ = _ws(w, "fp16")
+    assert r32 == 0 and r16 == 0
+    N = 64 * 32
+    assert b32 >= 2 * 27 * 4 * N + 3 * 4 * N
+    assert b16 >= 2 * 27 * 2 * N and b16 < b32
+    w3 = W.film_boiling_3d(16, 8, 12, modes=1, z0=5.0)
+    r3, b3, *_ = _ws(w3, "fp32")
+    assert r3 == 0 and b3 >= 2 * 45 * 4 * w3.cells
+
+
+@pytest.mark.parametrize("field,value", [("nu_l", 0.0), ("M_phi", -1.0), ("W", 0.0), ("rho_g", 0.0),
+                                         ("alpha_g", float("nan"))])
+def test_invalid_parameters_rejected(field, value):
+    w = W.film_boiling_2d(16, 16)
+    w.params[field] = value
+    r, *_ = _ws(w)
+    assert r == B.LBM_EINVAL
+
+
+def test_invalid_grids_rejected():
+    w = W.film_boiling_2d(16, 16)
+    w.periodic = (False, False)            # two wall axes
+    assert _ws(w)[0] == B.LBM_EINVAL
+    w = W.film_boiling_2d(16, 16)
+    w.n = (0, 16)
+    assert _ws(w)[0] == B.LBM_EINVAL
+
+
+def test_create_checks_workspace_without_gpu():
+    w = W.film_boiling_2d(16, 16)
+    r, nbytes, g, p, lat = _ws(w)
+    buf = (ctypes.c_uint8 * (nbytes + 512))()
+    base = (ctypes.addressof(buf) + 255) // 256 * 256          # stand-in pointer, never dereferenced
+    h = ctypes.c_void_p()
+    assert B.lib.lbm_create(ctypes.byref(g), lat, ctypes.byref(p), ctypes.c_void_p(base), nbytes - 1,
+                            None, ctypes.byref(h)) == B.LBM_ENOMEM
+    assert B.lib.lbm_create(ctypes.byref(g), lat, ctypes.byref(p), ctypes.c_void_p(base + 8), nbytes,
+                            None, ctypes.byref(h)) == B.LBM_EINVAL           # misaligned
+    assert B.lib.lbm_create(ctypes.byref(g), lat, ctypes.byref(p), ctypes.c_void_p(base), nbytes,
+                            None, ctypes.byref(h)) == B.LBM_OK
+    steps = ctypes.c_int64(-1)
+    assert B.lib.lbm_steps_done(h, ctypes.byref(steps)) == 0 and steps.value == 0
+    assert B.lib.lbm_step(h, -1) == B.LBM_EINVAL
+    B.lib.lbm_destroy(h)
+
+
+def test_strerror():
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert B.lib.lbm_strerror(code)
+    assert B.lib.lbm_strerror(-99) == b"unknown error"
