@@ -1,0 +1,419 @@
+"""Benchmark of the fused phase-field LB step on B300.
+
+One bench step = one time step of the whole hot path on the 2D D2Q9 film
+boiling workload of 2048 x 4096 cells (FP32 populations): the fused
+collide-and-stream kernel (phi moment, stencils, closures, moments,
+production rate, three BGK collisions, streaming with wall links), plus the
+FP64 global mass / enthalpy reduction every REDUCE_EVERY steps.  The metric
+is MLUPS (million lattice-cell updates per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an
+independent replica of the workload on its own GPU (the path has no data
+exchange in this build: replicas only) and value = all ranks' cell updates /
+the slowest rank's time.  --impl reference times the FP64 CPU oracle on the
+host cores instead, on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "MLUPS and fraction of HBM roofline per fused step, FP32 vs FP16-storage vs adjoint"
+REDUCE_EVERY = 100
+# algorithmic bytes per cell and step: every population read once and written
+# once, plus phi^{n-1} read+write and the lagged source read+write (4 x 4 B)
+BYTES_PER_CELL = {("2d", "fp32"): 27 * 4 * 2 + 16, ("2d", "fp16"): 27 * 2 * 2 + 16,
+                  ("2d", "bf16"): 27 * 2 * 2 + 16, ("3d", "fp32"): 45 * 4 * 2 + 16,
+                  ("3d", "fp16"): 45 * 2 * 2 + 16, ("3d", "bf16"): 45 * 2 * 2 + 16}
+KERNEL_SOURCES = ["paper_2003_06342_b300/csrc/lbm2d.cu", "paper_2003_06342_b300/csrc/lbm3d.cu",
+                  "paper_2003_06342_b300/csrc/lbm_common.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary for `name`, or
+    None when absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"{name}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                mhz.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_c2():
+    w = W.c2_film_boiling()
+    return w
+
+
+def safe_reduce(solver):
+    """Phase-field mass of the current state, NaN when it is not finite."""
+    from paper_2003_06342_b300._binding import LBMError
+    try:
+        return solver.reduce()[0]
+    except LBMError:
+        return float("nan")
+
+
+def run_device(args, world, rank, local):
+    import torch
+    from paper_2003_06342_b300 import Solver
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    stream = torch.cuda.Stream(device=dev)
+    w = workload_c2()
+    s = Solver(w.n, w.periodic, w.params, storage="fp32", device=dev, stream=stream)
+    s.init(w.phi0, w.T0, p0=w.p0)
+    red = torch.zeros(2, dtype=torch.float64, device=dev)
+
+    def hot(nsteps):
+        launches = 0
+        done = 0
+        while done < nsteps:
+            k = min(REDUCE_EVERY, nsteps - done)
+            s.step(k)
+            launches += s.last_launches()
+            done += k
+            if done % REDUCE_EVERY == 0:
+                s.reduce_async(red)
+                launches += 3
+        return launches
+
+    with torch.cuda.stream(stream):
+        hot(args.warmup)
+    torch.cuda.synchronize(dev)
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        launches = hot(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        barrier()
+    ms = e0.elapsed_time(e1)
+    mass, energy = red.tolist()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    peak, peak_kind = peaks()
+    result = {
+        "ms": ms, "wall_s": wall, "launches": launches, "cells": w.cells, "mass": mass,
+        "energy": energy, "clocks": clk.summary(), "peak": peak, "peak_kind": peak_kind,
+    }
+
+    # roofline of the dominant kernel: step launches alone, same stream
+    def step_kernel_ms(solver, n):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(solver.stream)
+        solver.step(n)
+        b.record(solver.stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / n
+
+    result["step_ms"] = step_kernel_ms(s, max(200, min(args.steps, 2000)))
+    result["finite"] = bool(np.isfinite(mass) and np.isfinite(energy))
+
+    # storage and 3D variants (same stream, fewer steps)
+    variants = {}
+    if not args.skip_variants and rank == 0:
+        for storage in ("fp16", "bf16"):
+            v = Solver(w.n, w.periodic, w.params, storage=storage, device=dev, stream=stream)
+            v.init(w.phi0, w.T0, p0=w.p0)
+            v.step(20)
+            ms_v = step_kernel_ms(v, 500)
+            m_v = safe_reduce(v)
+            bpc = BYTES_PER_CELL[("2d", storage)]
+            variants[f"2d_{storage}"] = {
+                "workload": w.name, "MLUPS": w.cells / ms_v / 1e3, "ms_per_step": ms_v,
+                "bytes_per_cell": bpc, "achieved_GBs": bpc * w.cells / ms_v / 1e6,
+                "frac": bpc * w.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v)),
+                "traffic": profiled_traffic(f"step2d_{storage}_2048x4096")}
+            del v
+        w3 = W.c3_film_boiling_3d()
+        for storage in ("fp32", "fp16"):
+            v = Solver(w3.n, w3.periodic, w3.params, storage=storage, device=dev, stream=stream)
+            v.init(w3.phi0, w3.T0, p0=w3.p0)
+            v.step(5)
+            ms_v = step_kernel_ms(v, 100)
+            m_v = safe_reduce(v)
+            bpc = BYTES_PER_CELL[("3d", storage)]
+            variants[f"3d_{storage}"] = {
+                "workload": w3.name, "MLUPS": w3.cells / ms_v / 1e3, "ms_per_step": ms_v,
+                "bytes_per_cell": bpc, "achieved_GBs": bpc * w3.cells / ms_v / 1e6,
+                "frac": bpc * w3.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v)),
+                "traffic": profiled_traffic(f"step3d_{storage}_256x256x512")}
+            del v
+        torch.cuda.empty_cache()
+    result["variants"] = variants
+
+    # end to end through the public API: host fields in, K steps with the
+    # reduction read back every REDUCE_EVERY steps, host fields out
+    if not args.skip_e2e:
+        e = Solver(w.n, w.periodic, w.params, storage="fp32", device=dev, stream=stream)
+        K = args.steps
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e.init_host(w.phi0, w.T0, p0=w.p0)
+        done, d2h = 0, 0
+        while done < K:
+            k = min(REDUCE_EVERY, K - done)
+            e.step(k)
+            done += k
+            safe_reduce(e)
+            d2h += 16
+        F = e.fields_host()
+        torch.cuda.synchronize(dev)
+        t_e2e = time.perf_counter() - t0
+        barrier()
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = 3 * w.cells * 4                      # phi, T, p staged as float32
+        d2h += 5 * w.cells * 4                     # phi, T, ux, uy, p as float32
+        result["e2e"] = {"value": w.cells * K * world / t_e2e / 1e6, "unit": "MLUPS",
+                         "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+                         "wall_s": t_e2e, "finite": bool(np.isfinite(F["phi"]).all())}
+        del e
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    result["workload"] = w
+    return result
+
+
+def cpu_baseline(sample_steps=1):
+    """The FP64 oracle, as it stands, on the host cores: sample_steps time
+    steps of the full workload after initialisation."""
+    import torch
+    from oracle import model as M
+    w = workload_c2()
+    P, G = M.Params.from_dict(w.params), M.Grid(w.n, w.periodic)
+    st = M.init_state(w.phi0, w.T0, P, G, p0=w.p0)
+    t0 = time.perf_counter()
+    for _ in range(sample_steps):
+        st = M.step(st, P, G)
+    dt = time.perf_counter() - t0
+    return {"value": w.cells * sample_steps / dt / 1e6, "unit": "MLUPS",
+            "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{sample_steps} FP64 oracle step(s) of the full {w.n[0]}x{w.n[1]} workload "
+                      f"after initialisation ({dt:.1f} s)"}
+
+
+def reference_arm(args, world, rank):
+    """--impl reference: the oracle on the host cores, each step a bounded
+    sample (a horizontal band of the workload that contains the film) sized
+    so the whole run stays within a few minutes."""
+    if rank != 0:
+        return
+    import torch
+    from oracle import model as M
+    w = workload_c2()
+    budget_s = 120.0
+    per_cell = 1.2e-6 * 8 / max(1, torch.get_num_threads())   # rough s per cell-step
+    steps_total = args.steps + args.warmup
+    rows = int(max(8, min(w.n[1], budget_s / (per_cell * w.n[0] * max(1, steps_total)))))
+    rows = min(rows, 256)
+    band = W.film_boiling_2d(w.n[0], rows, modes=8, seed=1, y0=min(64.0, rows / 3.0), paper=True,
+                             phi_wall=tuple(w.params["phi_wall"]))
+    P, G = M.Params.from_dict(band.params), M.Grid(band.n, band.periodic)
+    st = M.init_state(band.phi0, band.T0, P, G, p0=band.p0)
+    for _ in range(args.warmup):
+        st = M.step(st, P, G)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = M.step(st, P, G)
+    dt = time.perf_counter() - t0
+    value = band.cells * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / max(1, args.steps) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"film_boiling_2d_{w.n[0]}x{w.n[1]} (sample: {band.n[0]}x{band.n[1]} band)",
+                   "lattice": "D2Q9x3", "storage": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": torch.get_num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} steps of the bottom {rows} rows x {w.n[0]} columns"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--skip-variants", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+
+    r = run_device(args, world, rank, local)
+    if rank != 0:
+        return
+    w = r["workload"]
+    ms_step = r["ms"] / args.steps
+    value = w.cells * args.steps * world / r["ms"] / 1e3
+    bpc = BYTES_PER_CELL[("2d", "fp32")]
+    achieved = bpc * w.cells / r["step_ms"] / 1e6          # GB/s
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name + " (paper Table parameters)", "nx": w.n[0], "ny": w.n[1],
+                   "lattice": "D2Q9x3 (f, g, s)",
+                   "storage": "fp32", "density_ratio": w.params["rho_l"] / w.params["rho_g"],
+                   "reduce_every": REDUCE_EVERY,
+                   "l2": "inputs larger than L2 (1.8 GB of populations per step)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": r["peak"], "unit": "GB/s",
+                     "frac": achieved / r["peak"],
+                     "traffic": profiled_traffic("step2d_fp32_2048x4096"),
+                     "kernel": "step2d_kernel<float>", "bytes_per_cell": bpc,
+                     "step_ms": r["step_ms"], "peak_kind": r["peak_kind"]},
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+        "finite": r["finite"],
+        "variants": r["variants"],
+    }
+    if "e2e" in r:
+        line["e2e"] = r["e2e"]
+    if not args.skip_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

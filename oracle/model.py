@@ -40,6 +40,9 @@ the design notes with its reason):
     about 7 cells from the centre of a W = 4 interface) the counter term is
     scaled down instead of following the direction of rounding noise;
   * alpha(phi) is interpolated linearly (switch: harmonic);
+  * rho(phi), nu(phi) and alpha(phi) are evaluated on phi clipped to [0, 1]
+    (the model's range): at density ratio 100 an overshoot phi - 1 > 0.0101
+    would otherwise make rho(phi) <= 0;
   * phi ghost value on a wall = the wall's Dirichlet value;
   * initial populations = barred equilibria, theta_bar = theta_eq - S/2,
     with phi_prev = phi_0 and q_prev = q(phi_0, T_0).
@@ -192,13 +195,22 @@ def gradient_laplacian(phi, grid, P):
 # closures (Sec. 2)
 # ----------------------------------------------------------------------------
 
+def _unit(phi):
+    """phi restricted to the model's range 0 <= phi <= 1 (Sec. 2.1) for the
+    property closures; overshoot beyond it is numerical."""
+    return torch.clamp(phi, 0.0, 1.0)
+
+
 def density(phi, P):
-    """Eq. Density."""
+    """Eq. Density, on phi restricted to [0, 1]."""
+    phi = _unit(phi)
     return phi * P.rho_g + (1.0 - phi) * P.rho_l
 
 
 def viscosity(phi, P):
-    """Eq. Viscosity (harmonic mean) or Eq. Visco_lin (linear)."""
+    """Eq. Viscosity (harmonic mean) or Eq. Visco_lin (linear), on phi
+    restricted to [0, 1]."""
+    phi = _unit(phi)
     if P.visc_interp == "harmonic":
         return P.nu_l * P.nu_g / (phi * P.nu_l + (1.0 - phi) * P.nu_g)
     return (1.0 - phi) * P.nu_l + phi * P.nu_g
@@ -206,7 +218,8 @@ def viscosity(phi, P):
 
 def diffusivity(phi, P):
     """Thermal diffusivity alpha(phi): linear interpolation (reading), or
-    harmonic mean as a switch."""
+    harmonic mean as a switch, on phi restricted to [0, 1]."""
+    phi = _unit(phi)
     if P.alpha_interp == "harmonic":
         return P.alpha_l * P.alpha_g / (phi * P.alpha_l + (1.0 - phi) * P.alpha_g)
     return phi * P.alpha_g + (1.0 - phi) * P.alpha_l

@@ -120,6 +120,7 @@ void fill_devparams(lbm_handle *h) {
     d.T_sat = (float)p.T_sat;
     const double cs2_g = h->dim == 2 ? 1.0 / 3.0 : 0.25;
     d.tau_g = (float)(p.M_phi / cs2_g);
+    d.om_g = (float)(1.0 / (p.M_phi / cs2_g + 0.5));
     d.kappa = (float)(1.0 - p.rho_g / p.rho_l);
     d.eps2 = (float)(p.normal_eps * p.normal_eps);
     for (int a = 0; a < 3; ++a) { d.gravity[a] = (float)p.gravity[a]; d.body[a] = (float)p.body_force[a]; }
@@ -128,6 +129,7 @@ void fill_devparams(lbm_handle *h) {
     d.visc_interp = p.visc_interp;
     d.alpha_interp = p.alpha_interp;
     d.storage = p.storage;
+    d.s_ref = (float)p.store_ref[2];
     // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
     int k = 0;
     for (int set = 0; set < 3; ++set) {

@@ -23,7 +23,7 @@ constexpr int QF = 19, QG = 7;
 constexpr int G0 = QF, S0 = QF + QG;         // first plane of g and of s
 
 struct Macro3 {
-    float phi, g[3], lap, rho, gr[3], F[3], u[3], p, T;
+    float phi, g[3], lap, rho, gr[3], F[3], u[3], p, T, Td;   // Td = T - T_ref
 };
 
 // nb[i] = phi(x + e_i) over the D3Q19 directions
@@ -48,7 +48,7 @@ __device__ __forceinline__ void stencil3d(const float nb[QF], float g[3], float 
 
 __device__ __forceinline__ void closures3d(Macro3 &m, const DevParams &P) {
     const float phi = m.phi;
-    m.rho = phi * P.rho_g + (1.0f - phi) * P.rho_l;
+    m.rho = density(phi, P);
     const float mu = 4.0f * P.H * phi * (phi - 1.0f) * (phi - 0.5f) - P.K * m.lap;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -78,7 +78,8 @@ __device__ __forceinline__ void moments3d(Macro3 &m, const float f[QF], const fl
         ug += m.u[a] * m.g[a];
     }
     m.p = sf + 0.5f * (LF::cs2 * ugr + m.rho * LF::cs2 * q_prev * P.kappa);
-    m.T = ss - 0.5f * P.L_over_Cp * ((m.phi - phi_prev) + ug + m.phi * q_prev * P.kappa);
+    m.Td = ss - 0.5f * P.L_over_Cp * ((m.phi - phi_prev) + ug + m.phi * q_prev * P.kappa);
+    m.T = m.Td + P.s_ref;
 }
 
 __device__ __forceinline__ void normal3d(const float g[3], float eps2, float n[3]) {
@@ -119,7 +120,7 @@ __device__ __forceinline__ void fs_eq_src(int i, const Macro3 &m, float q, float
     fS = F + w * m.rho * LF::cs2 * q * P.kappa;
     feqb = w * (m.p + m.rho * LF::cs2 * poly) - 0.5f * fS;
     sS = -w * P.L_over_Cp * D;
-    seqb = m.T * G - 0.5f * sS;
+    seqb = m.Td * G + P.s_ref * (w * poly) - 0.5f * sS;   // deviation from w_i T_ref
 }
 
 // ------------------------------------------------------------------ step
@@ -224,7 +225,7 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
 #pragma unroll
             for (int i = 0; i < QF; ++i) f[i] = Codec<S>::load(pin + i * N + c, i, P);
 #pragma unroll
-            for (int i = 0; i < QF; ++i) s[i] = Codec<S>::load(pin + (S0 + i) * N + c, S0 + i, P);
+            for (int i = 0; i < QF; ++i) s[i] = Codec<S>::load_dev(pin + (S0 + i) * N + c, S0 + i, P);
             const float phip = phi_prev[c];
             float nb[QF];
 #pragma unroll
@@ -281,11 +282,11 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
                     const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
                     const int o = LF::opp(i);
                     Codec<S>::store(pout + o * N + c, fs, o, P);
-                    Codec<S>::store(pout + (S0 + o) * N + c, -sv + 2.0f * LF::w(i) * P.T_wall[side], S0 + o, P);
+                    Codec<S>::store_dev(pout + (S0 + o) * N + c, -sv + 2.0f * LF::w(i) * (P.T_wall[side] - P.s_ref), S0 + o, P);
                 } else {
                     const size_t d = ((size_t)dz * ny + dy) * nx + dx;
                     Codec<S>::store(pout + i * N + d, fs, i, P);
-                    Codec<S>::store(pout + (S0 + i) * N + d, sv, S0 + i, P);
+                    Codec<S>::store_dev(pout + (S0 + i) * N + d, sv, S0 + i, P);
                 }
             }
         }
@@ -339,7 +340,7 @@ macro3d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
 #pragma unroll
         for (int i = 0; i < QF; ++i) {
             f[i] = Codec<S>::load(pin + i * N + c, i, P);
-            s[i] = Codec<S>::load(pin + (S0 + i) * N + c, S0 + i, P);
+            s[i] = Codec<S>::load_dev(pin + (S0 + i) * N + c, S0 + i, P);
         }
         Macro3 m;
         m.phi = nb[0];
@@ -379,6 +380,7 @@ init3d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
     m.u[2] = uz0 ? uz0[c] : 0.0f;
     m.p = p0 ? p0[c] : 0.0f;
     m.T = T0[c];
+    m.Td = m.T - P.s_ref;
     const float q = production(m.phi, m.T, P);
     float n[3];
     normal3d(m.g, P.eps2, n);
@@ -395,7 +397,7 @@ init3d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
         float feqb, fS, seqb, sS;
         fs_eq_src(i, m, q, D, usq, P, feqb, fS, seqb, sS);
         Codec<S>::store(pout + i * N + c, feqb, i, P);
-        Codec<S>::store(pout + (S0 + i) * N + c, seqb, S0 + i, P);
+        Codec<S>::store_dev(pout + (S0 + i) * N + c, seqb, S0 + i, P);
     }
     phi_prev[c] = m.phi;
     q_out[c] = q;

@@ -92,11 +92,13 @@ struct DevParams {
     float prod_coef;                   // 4 / (A W^2)
     float theta_I, L_over_Cp, Cp_over_L, T_sat;
     float tau_g;                       // M_phi / cs^2 of the phase-field lattice
+    float om_g;                        // 1 / (tau_g + 1/2)
     float kappa;                       // 1 - rho_g/rho_l
     float eps2;                        // normal_eps^2
     float gravity[3], body[3];
     float phi_wall[2], T_wall[2];
     int source_on, visc_interp, alpha_interp, storage;
+    float s_ref;                       // temperature storage reference T_ref
     // storage codec per population plane k (f planes, then g, then s):
     // FP32: theta = d + enc_c[k];  16-bit: theta = enc_c[k] + x * dec_s[k],
     // x = (theta - enc_c[k]) * enc_s[k]
@@ -106,12 +108,21 @@ struct DevParams {
 // ---------------------------------------------------------------- storage
 template <typename S> struct Codec;
 
+// load / store convert between the stored value and the full population;
+// load_dev / store_dev work on the deviation theta_i - enc_c[k] directly (the
+// temperature set is advanced in deviation form, see the step kernels).
 template <> struct Codec<float> {
     static __device__ __forceinline__ float load(const float *p, int k, const DevParams &P) {
         return __ldg(p) + P.enc_c[k];
     }
     static __device__ __forceinline__ void store(float *p, float v, int k, const DevParams &P) {
         *p = v - P.enc_c[k];
+    }
+    static __device__ __forceinline__ float load_dev(const float *p, int, const DevParams &) {
+        return __ldg(p);
+    }
+    static __device__ __forceinline__ void store_dev(float *p, float d, int, const DevParams &) {
+        *p = d;
     }
 };
 
@@ -122,6 +133,12 @@ template <> struct Codec<__half> {
     static __device__ __forceinline__ void store(__half *p, float v, int k, const DevParams &P) {
         *p = __float2half_rn((v - P.enc_c[k]) * P.enc_s[k]);
     }
+    static __device__ __forceinline__ float load_dev(const __half *p, int k, const DevParams &P) {
+        return __half2float(__ldg(p)) * P.dec_s[k];
+    }
+    static __device__ __forceinline__ void store_dev(__half *p, float d, int k, const DevParams &P) {
+        *p = __float2half_rn(d * P.enc_s[k]);
+    }
 };
 
 template <> struct Codec<__nv_bfloat16> {
@@ -131,15 +148,33 @@ template <> struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v, int k, const DevParams &P) {
         *p = __float2bfloat16_rn((v - P.enc_c[k]) * P.enc_s[k]);
     }
+    static __device__ __forceinline__ float load_dev(const __nv_bfloat16 *p, int k, const DevParams &P) {
+        return __bfloat162float(__ldg(p)) * P.dec_s[k];
+    }
+    static __device__ __forceinline__ void store_dev(__nv_bfloat16 *p, float d, int k, const DevParams &P) {
+        *p = __float2bfloat16_rn(d * P.enc_s[k]);
+    }
 };
 
 // ---------------------------------------------------------------- closures
+// Property closures take phi restricted to the model's range [0, 1]
+// (Sec. 2.1): overshoot beyond it is numerical, and at large density ratios
+// an unrestricted rho(phi) of Eq. Density would reach zero.
+__device__ __forceinline__ float unit_phi(float phi) { return fminf(fmaxf(phi, 0.0f), 1.0f); }
+
+__device__ __forceinline__ float density(float phi, const DevParams &P) {
+    phi = unit_phi(phi);
+    return phi * P.rho_g + (1.0f - phi) * P.rho_l;
+}
+
 __device__ __forceinline__ float viscosity(float phi, const DevParams &P) {
+    phi = unit_phi(phi);
     return P.visc_interp == 0 ? P.nu_l * P.nu_g / (phi * P.nu_l + (1.0f - phi) * P.nu_g)
                               : (1.0f - phi) * P.nu_l + phi * P.nu_g;
 }
 
 __device__ __forceinline__ float diffusivity(float phi, const DevParams &P) {
+    phi = unit_phi(phi);
     return P.alpha_interp == 0 ? phi * P.alpha_g + (1.0f - phi) * P.alpha_l
                                : P.alpha_l * P.alpha_g / (phi * P.alpha_l + (1.0f - phi) * P.alpha_g);
 }
