@@ -135,10 +135,11 @@ __device__ __forceinline__ float phi_at(const S *__restrict__ pin, const float *
 
 // Fill window slot `slot` with phi of plane z (tile + halo ring).  When
 // owners_write is set, each thread whose column is inside the grid has
-// already stored its own cell of an in-range plane (own_ok, own_phi);
-// every other slot is computed here: phi of the wrapped cell, or the wall's
-// Dirichlet value beyond a wall.
-template <typename S>
+// already stored its own cell of an in-range plane (own_ok, own_phi); every
+// other slot is computed here: phi of the wrapped cell, or the wall's
+// Dirichlet value beyond a wall.  FXY: the tile's halo ring lies inside the
+// grid in x and y, so an in-range plane needs no wrap or wall test.
+template <typename S, bool FXY>
 __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool owners_write,
                                            bool own_ok, float own_phi, const S *__restrict__ pin,
                                            const float *__restrict__ q_in, int x0, int y0, int tid,
@@ -148,6 +149,19 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
     float *plane = sphi + slot * PLANE;
     const bool z_in = z >= 0 && z < nz;
     if (owners_write && own_ok) plane[(ty + 1) * SX + tx + 1] = own_phi;
+    if (FXY && z_in && owners_write) {
+        constexpr int RING = 2 * SX + 2 * TY;
+        if (tid < RING) {
+            int sx, sy;
+            if (tid < SX) { sx = tid; sy = 0; }
+            else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
+            else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
+            else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
+            const size_t cc = ((size_t)z * ny + (y0 + sy - 1)) * nx + (x0 + sx - 1);
+            plane[sy * SX + sx] = phi_at<S>(pin, q_in, cc, N, P);
+        }
+        return;
+    }
     for (int sidx = tid; sidx < PLANE; sidx += TX * TY) {
         const int sx = sidx % SX, sy = sidx / SX;
         int cx = x0 + sx - 1, cy = y0 + sy - 1, cz = z;
@@ -166,11 +180,177 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
     }
 }
 
-template <typename S>
-__global__ void __launch_bounds__(TX * TY, 1)
-step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
-              const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P) {
-    __shared__ float sphi[3 * PLANE];
+__device__ __forceinline__ float sgnv(int e, float v) { return e > 0 ? v : -v; }
+// e.(a, b, c) for e in {-1, 0, 1}^3 without multiplications
+__device__ __forceinline__ float edot3(int ex, int ey, int ez, float a, float b, float c) {
+    float r = 0.0f;
+    bool any = false;
+    if (ex != 0) { r = sgnv(ex, a); any = true; }
+    if (ey != 0) { r = any ? r + sgnv(ey, b) : sgnv(ey, b); any = true; }
+    if (ez != 0) { r = any ? r + sgnv(ez, c) : sgnv(ez, c); }
+    return r;
+}
+
+// positive half of the D3Q19 directions: each pair (i, opposite) once
+__device__ __forceinline__ constexpr int half19(int k) {
+    return k < 3 ? k + 1 : (k < 5 ? k + 4 : (k < 7 ? k + 6 : k + 8));   // 1,2,3,7,8,11,12,15,16
+}
+
+// Update of one cell of layer z: stencils from the three window planes,
+// moments, closures, production, the three collisions (theta* = (1 - om)
+// theta + om theta_eq + (1 - om/2) S, identical to Eq. LBE), then the push.
+// FAST: no link of this cell wraps or meets a wall.
+template <typename S, bool FAST>
+__device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
+                                               const float f[QF], const float s[QF],
+                                               const float g[QG], float qp,
+                                               S *__restrict__ pout, float *__restrict__ phi_prev,
+                                               float *__restrict__ q_out, const DevParams &P) {
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const size_t N = (size_t)P.N;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int centre = (ty + 1) * SX + tx + 1;
+    const float *pl[3] = {sphi + (z % 3) * PLANE + centre, sphi + ((z + 1) % 3) * PLANE + centre,
+                          sphi + ((z + 2) % 3) * PLANE + centre};   // planes z-1, z, z+1
+    Macro3 m;
+    const float ph = pl[1][0];
+    m.phi = ph;
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f, la = 0.0f, ld = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = half19(k);
+        const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
+        const float a = pl[1 + ez][ey * SX + ex], b = pl[1 - ez][-ey * SX - ex];
+        const float d = a - b, sm = a + b;
+        if (ex != 0) gx += sgnv(ex, d) * LF::w(i);
+        if (ey != 0) gy += sgnv(ey, d) * LF::w(i);
+        if (ez != 0) gz += sgnv(ez, d) * LF::w(i);
+        if (i <= 6) la += sm; else ld += sm;
+    }
+    m.g[0] = 3.0f * gx; m.g[1] = 3.0f * gy; m.g[2] = 3.0f * gz;
+    m.lap = 6.0f * ((1.0f / 18.0f) * (la - 6.0f * ph) + (1.0f / 36.0f) * (ld - 12.0f * ph));
+    closures3d(m, P);
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f, sf = f[0], ss = s[0];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = half19(k), o = LF::opp(i);
+        const float d = f[i] - f[o];
+        if (LF::ex(i) != 0) jx += sgnv(LF::ex(i), d);
+        if (LF::ey(i) != 0) jy += sgnv(LF::ey(i), d);
+        if (LF::ez(i) != 0) jz += sgnv(LF::ez(i), d);
+    }
+#pragma unroll
+    for (int i = 1; i < QF; ++i) { sf += f[i]; ss += s[i]; }
+    const float inv_rho = __frcp_rn(m.rho);
+    m.u[0] = (3.0f * jx + 0.5f * m.F[0]) * inv_rho;
+    m.u[1] = (3.0f * jy + 0.5f * m.F[1]) * inv_rho;
+    m.u[2] = (3.0f * jz + 0.5f * m.F[2]) * inv_rho;
+    const float rcs2 = m.rho * LF::cs2;
+    const float ugr = m.u[0] * m.gr[0] + m.u[1] * m.gr[1] + m.u[2] * m.gr[2];
+    const float ug = m.u[0] * m.g[0] + m.u[1] * m.g[1] + m.u[2] * m.g[2];
+    const float phip = phi_prev[c];
+    m.p = sf + 0.5f * (LF::cs2 * ugr + rcs2 * qp * P.kappa);
+    m.Td = ss - 0.5f * P.L_over_Cp * ((ph - phip) + ug + ph * qp * P.kappa);
+    m.T = m.Td + P.s_ref;
+    const float q = production(ph, m.T, P);
+    const float inv_d = __frcp_rn(sqrtf(fmaxf(m.g[0] * m.g[0] + m.g[1] * m.g[1] + m.g[2] * m.g[2], P.eps2)));
+    const float n0 = m.g[0] * inv_d, n1 = m.g[1] * inv_d, n2 = m.g[2] * inv_d;
+    const float om_g = P.om_g;
+    const float om_f = __frcp_rn(viscosity(ph, P) * LF::inv_cs2 + 0.5f);
+    const float om_s = __frcp_rn(diffusivity(ph, P) * LF::inv_cs2 + 0.5f);
+    const float D = (ph - phip) + ug + ph * q * P.kappa;
+    phi_prev[c] = ph;
+    q_out[c] = q;
+
+    const float usq = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
+    const float iface = P.four_over_W * ph * (1.0f - ph);
+    const float a_g = 1.0f - om_g, b_g = 1.0f - 0.5f * om_g;
+    const float a_f = 1.0f - om_f, b_f = 1.0f - 0.5f * om_f;
+    const float a_s = 1.0f - om_s, b_s = 1.0f - 0.5f * om_s;
+
+    // phase field on D3Q7 (cs^2 = 1/4): Gamma_i = w (1 + 4 cu + 8 cu^2 - 2 u^2)
+    const float usq2 = 2.0f * usq;
+#pragma unroll
+    for (int i = 0; i < QG; ++i) {
+        const int ex = LG::ex(i), ey = LG::ey(i), ez = LG::ez(i);
+        const float w = LG::w(i);
+        const float cu = edot3(ex, ey, ez, m.u[0], m.u[1], m.u[2]);
+        const float poly = cu * fmaf(8.0f, cu, 4.0f) - usq2;
+        const float G = fmaf(w, poly, w);
+        const float Sg = w * (i == 0 ? q : fmaf(iface, edot3(ex, ey, ez, n0, n1, n2), q));
+        const float gs = fmaf(a_g, g[i], fmaf(om_g, ph * G, b_g * Sg));
+        int dx = x + ex, dy = y + ey, dz = z + ez;
+        if (FAST) {
+            const long long off = ((long long)ez * ny + ey) * nx + ex;
+            Codec<S>::store(pout + (G0 + i) * N + c + off, gs, G0 + i, P);
+        } else {
+            const int kx = wrap_coord(dx, nx, P.periodic[0]);
+            const int ky = wrap_coord(dy, ny, P.periodic[1]);
+            const int kz = wrap_coord(dz, nz, P.periodic[2]);
+            if (kx >= 2 || ky >= 2 || kz >= 2) {
+                const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
+                const int o = LG::opp(i);
+                Codec<S>::store(pout + (G0 + o) * N + c, -gs + 2.0f * w * P.phi_wall[side], G0 + o, P);
+            } else {
+                const size_t d = ((size_t)dz * ny + dy) * nx + dx;
+                Codec<S>::store(pout + (G0 + i) * N + d, gs, G0 + i, P);
+            }
+        }
+    }
+
+    // flow and temperature on D3Q19 (cs^2 = 1/3)
+    const float usq15 = 1.5f * usq;
+    const float gA0 = LF::cs2 * m.gr[0], gA1 = LF::cs2 * m.gr[1], gA2 = LF::cs2 * m.gr[2];
+    const float uA = m.u[0] * gA0 + m.u[1] * gA1 + m.u[2] * gA2;
+    const float uB = m.u[0] * m.F[0] + m.u[1] * m.F[1] + m.u[2] * m.F[2];
+    const float pf = rcs2 * q * P.kappa;
+    const float bsw = b_s * (-P.L_over_Cp * D);
+    const float Tref = P.s_ref;
+#pragma unroll
+    for (int i = 0; i < QF; ++i) {
+        const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
+        const float w = LF::w(i);
+        const float cu = edot3(ex, ey, ez, m.u[0], m.u[1], m.u[2]);
+        const float poly = cu * fmaf(4.5f, cu, 3.0f) - usq15;
+        const float G = fmaf(w, poly, w);
+        const float Gw = w * poly;
+        const float feq = w * fmaf(rcs2, poly, m.p);
+        const float eA = (i == 0) ? 0.0f : edot3(ex, ey, ez, gA0, gA1, gA2);
+        const float eB = (i == 0) ? 0.0f : edot3(ex, ey, ez, m.F[0], m.F[1], m.F[2]);
+        const float fS = fmaf(Gw, eA - uA, fmaf(G, eB - uB, w * pf));
+        const float fs = fmaf(a_f, f[i], fmaf(om_f, feq, b_f * fS));
+        const float seq = fmaf(m.Td, G, Tref * Gw);
+        const float sv = fmaf(a_s, s[i], fmaf(om_s, seq, w * bsw));
+        int dx = x + ex, dy = y + ey, dz = z + ez;
+        if (FAST) {
+            const long long off = ((long long)ez * ny + ey) * nx + ex;
+            S *dst = pout + c + off;
+            Codec<S>::store(dst + i * N, fs, i, P);
+            Codec<S>::store_dev(dst + (S0 + i) * N, sv, S0 + i, P);
+        } else {
+            const int kx = wrap_coord(dx, nx, P.periodic[0]);
+            const int ky = wrap_coord(dy, ny, P.periodic[1]);
+            const int kz = wrap_coord(dz, nz, P.periodic[2]);
+            if (kx >= 2 || ky >= 2 || kz >= 2) {
+                const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
+                const int o = LF::opp(i);
+                Codec<S>::store(pout + o * N + c, fs, o, P);
+                Codec<S>::store_dev(pout + (S0 + o) * N + c, -sv + 2.0f * w * (P.T_wall[side] - P.s_ref), S0 + o, P);
+            } else {
+                const size_t d = ((size_t)dz * ny + dy) * nx + dx;
+                Codec<S>::store(pout + i * N + d, fs, i, P);
+                Codec<S>::store_dev(pout + (S0 + i) * N + d, sv, S0 + i, P);
+            }
+        }
+    }
+}
+
+template <typename S, bool FXY>
+__device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__restrict__ pout,
+                                              float *__restrict__ phi_prev,
+                                              const float *__restrict__ q_in,
+                                              float *__restrict__ q_out, const DevParams &P,
+                                              float *sphi) {
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const size_t N = (size_t)P.N;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -178,11 +358,11 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
     const int zbeg = blockIdx.z * ZB;
     const int zend = min(zbeg + ZB, nz);
     const int x = x0 + tx, y = y0 + ty;
-    const bool col = (x < nx) && (y < ny);
+    const bool col = FXY || ((x < nx) && (y < ny));
     const size_t cxy = col ? (size_t)y * nx + x : 0;
     const size_t plane_cells = (size_t)nx * ny;
 
-    float g[QG], gn[QG], qcur = 0.0f, qnext = 0.0f;
+    float g[QG], qcur = 0.0f;
     // prologue: plane zbeg (own cells kept in registers) and plane zbeg-1;
     // plane p lives in window slot (p + 1) % 3
     {
@@ -197,12 +377,12 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
             for (int i = 1; i < QG; ++i) ph += g[i];
             ph += 0.5f * qcur;
         }
-        fill_plane<S>(sphi, (zbeg + 1) % 3, zbeg, true, col, ph, pin, q_in, x0, y0, tid, tx, ty, P);
-        fill_plane<S>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
+        fill_plane<S, FXY>(sphi, (zbeg + 1) % 3, zbeg, true, col, ph, pin, q_in, x0, y0, tid, tx, ty, P);
+        fill_plane<S, false>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
     }
 
     for (int z = zbeg; z < zend; ++z) {
-        // plane z+1 into the window
+        float gn[QG], qnext = 0.0f;
         {
             float ph = 0.0f;
             const bool ok = col && (z + 1 < nz);
@@ -216,7 +396,7 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
                 for (int i = 1; i < QG; ++i) ph += gn[i];
                 ph += 0.5f * qnext;
             }
-            fill_plane<S>(sphi, (z + 2) % 3, z + 1, true, ok, ph, pin, q_in, x0, y0, tid, tx, ty, P);
+            fill_plane<S, FXY>(sphi, (z + 2) % 3, z + 1, true, ok, ph, pin, q_in, x0, y0, tid, tx, ty, P);
         }
         __syncthreads();
         if (col) {
@@ -226,76 +406,27 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
             for (int i = 0; i < QF; ++i) f[i] = Codec<S>::load(pin + i * N + c, i, P);
 #pragma unroll
             for (int i = 0; i < QF; ++i) s[i] = Codec<S>::load_dev(pin + (S0 + i) * N + c, S0 + i, P);
-            const float phip = phi_prev[c];
-            float nb[QF];
-#pragma unroll
-            for (int i = 0; i < QF; ++i) {
-                const int slot = (z + 1 + LF::ez(i)) % 3;
-                nb[i] = sphi[slot * PLANE + (ty + 1 + LF::ey(i)) * SX + tx + 1 + LF::ex(i)];
-            }
-            Macro3 m;
-            m.phi = nb[0];
-            stencil3d(nb, m.g, m.lap);
-            moments3d(m, f, s, phip, qcur, P);
-            const float q = production(m.phi, m.T, P);
-            float n[3];
-            normal3d(m.g, P.eps2, n);
-            const float usq = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
-            const float om_g = 1.0f / (P.tau_g + 0.5f);
-            const float om_f = 1.0f / (viscosity(m.phi, P) * LF::inv_cs2 + 0.5f);
-            const float om_s = 1.0f / (diffusivity(m.phi, P) * LF::inv_cs2 + 0.5f);
-            const float D = (m.phi - phip) + (m.u[0] * m.g[0] + m.u[1] * m.g[1] + m.u[2] * m.g[2])
-                          + m.phi * q * P.kappa;
-            phi_prev[c] = m.phi;
-            q_out[c] = q;
-            // g on D3Q7
-#pragma unroll
-            for (int i = 0; i < QG; ++i) {
-                float eqb, src;
-                g_eq_src(i, m, n, q, usq, P, eqb, src);
-                const float gs = g[i] - om_g * (g[i] - eqb) + src;
-                int dx = x + LG::ex(i), dy = y + LG::ey(i), dz = z + LG::ez(i);
-                const int kx = wrap_coord(dx, nx, P.periodic[0]);
-                const int ky = wrap_coord(dy, ny, P.periodic[1]);
-                const int kz = wrap_coord(dz, nz, P.periodic[2]);
-                if (kx >= 2 || ky >= 2 || kz >= 2) {
-                    const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
-                    const int o = LG::opp(i);
-                    Codec<S>::store(pout + (G0 + o) * N + c, -gs + 2.0f * LG::w(i) * P.phi_wall[side], G0 + o, P);
-                } else {
-                    const size_t d = ((size_t)dz * ny + dy) * nx + dx;
-                    Codec<S>::store(pout + (G0 + i) * N + d, gs, G0 + i, P);
-                }
-            }
-            // f and s on D3Q19
-#pragma unroll
-            for (int i = 0; i < QF; ++i) {
-                float feqb, fS, seqb, sS;
-                fs_eq_src(i, m, q, D, usq, P, feqb, fS, seqb, sS);
-                const float fs = f[i] - om_f * (f[i] - feqb) + fS;
-                const float sv = s[i] - om_s * (s[i] - seqb) + sS;
-                int dx = x + LF::ex(i), dy = y + LF::ey(i), dz = z + LF::ez(i);
-                const int kx = wrap_coord(dx, nx, P.periodic[0]);
-                const int ky = wrap_coord(dy, ny, P.periodic[1]);
-                const int kz = wrap_coord(dz, nz, P.periodic[2]);
-                if (kx >= 2 || ky >= 2 || kz >= 2) {
-                    const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
-                    const int o = LF::opp(i);
-                    Codec<S>::store(pout + o * N + c, fs, o, P);
-                    Codec<S>::store_dev(pout + (S0 + o) * N + c, -sv + 2.0f * LF::w(i) * (P.T_wall[side] - P.s_ref), S0 + o, P);
-                } else {
-                    const size_t d = ((size_t)dz * ny + dy) * nx + dx;
-                    Codec<S>::store(pout + i * N + d, fs, i, P);
-                    Codec<S>::store_dev(pout + (S0 + i) * N + d, sv, S0 + i, P);
-                }
-            }
+            if (FXY && z >= 1 && z + 1 < nz)
+                layer_update3d<S, true>(sphi, z, x, y, c, f, s, g, qcur, pout, phi_prev, q_out, P);
+            else
+                layer_update3d<S, false>(sphi, z, x, y, c, f, s, g, qcur, pout, phi_prev, q_out, P);
         }
-        // rotate the own-cell registers to the next layer
 #pragma unroll
         for (int i = 0; i < QG; ++i) g[i] = gn[i];
         qcur = qnext;
-        __syncthreads();   // plane (z-1)%3 is overwritten next iteration
+        __syncthreads();   // plane (z - 1) % 3 is overwritten next iteration
     }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(TX * TY, 2)
+step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
+              const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P) {
+    __shared__ float sphi[3 * PLANE];
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const bool fxy = x0 >= 1 && x0 + TX + 1 <= P.n[0] && y0 >= 1 && y0 + TY + 1 <= P.n[1];
+    if (fxy) step3d_column<S, true>(pin, pout, phi_prev, q_in, q_out, P, sphi);
+    else step3d_column<S, false>(pin, pout, phi_prev, q_in, q_out, P, sphi);
 }
 
 // ------------------------------------------------------------------ phi moment
