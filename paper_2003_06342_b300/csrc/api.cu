@@ -130,6 +130,7 @@ void fill_devparams(lbm_handle *h) {
     d.alpha_interp = p.alpha_interp;
     d.storage = p.storage;
     d.s_ref = (float)p.store_ref[2];
+    d.g_ref = (float)p.store_ref[1];
     // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
     int k = 0;
     for (int set = 0; set < 3; ++set) {

@@ -145,7 +145,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     float f[9], g[9], s[9], phip = 0.0f, qp = 0.0f;
     if (active) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = Codec<S>::load(pin + (9 + i) * N + c, 9 + i, P);
+        for (int i = 0; i < 9; ++i) g[i] = Codec<S>::load_dev(pin + (9 + i) * N + c, 9 + i, P);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = Codec<S>::load(pin + i * N + c, i, P);
 #pragma unroll
@@ -155,7 +155,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
         float ph = g[0];
 #pragma unroll
         for (int i = 1; i < 9; ++i) ph += g[i];
-        sphi[(ty + 1) * SX + tx + 1] = ph + 0.5f * qp;
+        sphi[(ty + 1) * SX + tx + 1] = ph + 0.5f * qp;      // phi - phi_ref
     }
     if (FAST) {
         // the 2*SX + 2*TY halo cells, one per thread
@@ -167,9 +167,9 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
             else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
             else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
             const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
-            float v = Codec<S>::load(pin + 9 * N + cc, 9, P);
+            float v = Codec<S>::load_dev(pin + 9 * N + cc, 9, P);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) v += Codec<S>::load(pin + (9 + i) * N + cc, 9 + i, P);
+            for (int i = 1; i < 9; ++i) v += Codec<S>::load_dev(pin + (9 + i) * N + cc, 9 + i, P);
             sphi[sy * SX + sx] = v + 0.5f * q_in[cc];
         }
     } else {
@@ -184,13 +184,13 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
             const int kx = wrap_coord(cx, nx, P.periodic[0]);
             const int ky = wrap_coord(cy, ny, P.periodic[1]);
             float v;
-            if (kx >= 2) v = P.phi_wall[kx - 2];
-            else if (ky >= 2) v = P.phi_wall[ky - 2];
+            if (kx >= 2) v = P.phi_wall[kx - 2] - P.g_ref;
+            else if (ky >= 2) v = P.phi_wall[ky - 2] - P.g_ref;
             else {
                 const size_t cc = (size_t)cy * nx + cx;
-                v = Codec<S>::load(pin + 9 * N + cc, 9, P);
+                v = Codec<S>::load_dev(pin + 9 * N + cc, 9, P);
 #pragma unroll
-                for (int i = 1; i < 9; ++i) v += Codec<S>::load(pin + (9 + i) * N + cc, 9 + i, P);
+                for (int i = 1; i < 9; ++i) v += Codec<S>::load_dev(pin + (9 + i) * N + cc, 9 + i, P);
                 v += 0.5f * q_in[cc];
             }
             sphi[sidx] = v;
@@ -201,8 +201,10 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
 
     // stencils, pair-folded: each (i, opposite) pair of Eqs. Grad and
     // Laplacian contributes w_i e_i (phi_i - phi_i') and 2 w_i (phi_i + phi_i' - 2 phi)
+    // the window holds phi - phi_ref; differences are unaffected by the shift
     const float *sp = sphi + (ty + 1) * SX + tx + 1;
-    const float ph = sp[0];
+    const float phd = sp[0];
+    const float ph = phd + P.g_ref;
     const float pE = sp[1], pW = sp[-1], pN = sp[SX], pS = sp[-SX];
     const float pNE = sp[SX + 1], pNW = sp[SX - 1], pSW = sp[-SX - 1], pSE = sp[-SX + 1];
     Macro2 m;
@@ -211,8 +213,8 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
         const float dA = pNE - pSW, dB = pSE - pNW;
         m.gx = 3.0f * ((1.0f / 9.0f) * (pE - pW) + (1.0f / 36.0f) * (dA + dB));
         m.gy = 3.0f * ((1.0f / 9.0f) * (pN - pS) + (1.0f / 36.0f) * (dA - dB));
-        m.lap = 6.0f * ((1.0f / 9.0f) * ((pE + pW) + (pN + pS) - 4.0f * ph)
-                      + (1.0f / 36.0f) * ((pNE + pSW) + (pNW + pSE) - 4.0f * ph));
+        m.lap = 6.0f * ((1.0f / 9.0f) * ((pE + pW) + (pN + pS) - 4.0f * phd)
+                      + (1.0f / 36.0f) * ((pNE + pSW) + (pNW + pSE) - 4.0f * phd));
     }
     closures2d(m, P);
     // moments (Eqs. Velocity, Pressure, Moment_Temp)
@@ -227,7 +229,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     const float rcs2 = m.rho * L::cs2;
     m.p = sf + 0.5f * (L::cs2 * (m.ux * m.grx + m.uy * m.gry) + rcs2 * qp * P.kappa);
     const float ug = m.ux * m.gx + m.uy * m.gy;
-    m.Td = ss - 0.5f * P.L_over_Cp * ((ph - phip) + ug + ph * qp * P.kappa);
+    m.Td = ss - 0.5f * P.L_over_Cp * ((phd - phip) + ug + ph * qp * P.kappa);
     m.T = m.Td + P.s_ref;
 
     const float q = production(ph, m.T, P);
@@ -236,9 +238,9 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     const float om_g = P.om_g;
     const float om_f = __frcp_rn(viscosity(ph, P) * L::inv_cs2 + 0.5f);
     const float om_s = __frcp_rn(diffusivity(ph, P) * L::inv_cs2 + 0.5f);
-    const float D = (ph - phip) + ug + ph * q * P.kappa;
+    const float D = (phd - phip) + ug + ph * q * P.kappa;
 
-    phi_prev[c] = ph;
+    phi_prev[c] = phd;          // stored as phi - phi_ref
     q_out[c] = q;
 
     // collision in the form theta* = (1 - om) theta + om theta_eq + (1 - om/2) S,
@@ -265,7 +267,8 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
         const float Gw = w * poly;
         // phase field: F^g + P^g = w (iface e.n + q)
         const float Sg = w * (ex == 0 && ey == 0 ? q : fmaf(iface, edot(ex, ey, nx_, ny_), q));
-        const float gs = fmaf(a_g, g[i], fmaf(om_g, ph * G, b_g * Sg));
+        // phase field in deviation form: g_eq - w phi_ref = (phi - phi_ref) G + phi_ref (G - w)
+        const float gs = fmaf(a_g, g[i], fmaf(om_g, fmaf(phd, G, P.g_ref * Gw), b_g * Sg));
         // flow: f_eq = w (p + rho cs2 poly), F^f + P^f
         const float feq = w * fmaf(rcs2, poly, m.p);
         const float fS = fmaf(Gw, edot(ex, ey, gAx, gAy) - uA, fmaf(G, edot(ex, ey, m.Fx, m.Fy) - uB, w * pf));
@@ -277,7 +280,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
             const long long off = (long long)ey * nx + ex;
             S *dst = pout + c + off;
             Codec<S>::store(dst + i * N, fs, i, P);
-            Codec<S>::store(dst + (9 + i) * N, gs, 9 + i, P);
+            Codec<S>::store_dev(dst + (9 + i) * N, gs, 9 + i, P);
             Codec<S>::store_dev(dst + (18 + i) * N, ssv, 18 + i, P);
         } else {
             int dx = x + ex, dy = y + ey;
@@ -288,12 +291,12 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
                 const int o = L::opp(i);
                 const float w2 = 2.0f * w;
                 Codec<S>::store(pout + o * N + c, fs, o, P);
-                Codec<S>::store(pout + (9 + o) * N + c, -gs + w2 * P.phi_wall[side], 9 + o, P);
+                Codec<S>::store_dev(pout + (9 + o) * N + c, -gs + w2 * (P.phi_wall[side] - P.g_ref), 9 + o, P);
                 Codec<S>::store_dev(pout + (18 + o) * N + c, -ssv + w2 * (P.T_wall[side] - P.s_ref), 18 + o, P);
             } else {
                 const size_t d = (size_t)dy * nx + dx;
                 Codec<S>::store(pout + i * N + d, fs, i, P);
-                Codec<S>::store(pout + (9 + i) * N + d, gs, 9 + i, P);
+                Codec<S>::store_dev(pout + (9 + i) * N + d, gs, 9 + i, P);
                 Codec<S>::store_dev(pout + (18 + i) * N + d, ssv, 18 + i, P);
             }
         }
@@ -364,7 +367,7 @@ macro2d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
         Macro2 m;
         m.phi = nb[0];
         stencil2d(nb, m.gx, m.gy, m.lap);
-        moments2d(m, f, s, phi_prev[c], q_in[c], P);
+        moments2d(m, f, s, phi_prev[c] + P.g_ref, q_in[c], P);
         if (o_phi) o_phi[c] = m.phi;
         if (o_T) o_T[c] = m.T;
         if (o_ux) o_ux[c] = m.ux;
@@ -407,10 +410,10 @@ init2d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
     for (int i = 0; i < 9; ++i) {
         const EqSrc e = eq_src2d(i, m, nx_, ny_, q, D, P);
         Codec<S>::store(pout + i * N + c, e.feq - 0.5f * e.fS, i, P);
-        Codec<S>::store(pout + (9 + i) * N + c, e.geq - 0.5f * e.gS, 9 + i, P);
+        Codec<S>::store_dev(pout + (9 + i) * N + c, e.geq - 0.5f * e.gS - L::w(i) * P.g_ref, 9 + i, P);
         Codec<S>::store_dev(pout + (18 + i) * N + c, e.seq - 0.5f * e.sS, 18 + i, P);
     }
-    phi_prev[c] = m.phi;
+    phi_prev[c] = m.phi - P.g_ref;
     q_out[c] = q;
 }
 

@@ -124,13 +124,20 @@ __device__ __forceinline__ void fs_eq_src(int i, const Macro3 &m, float q, float
 }
 
 // ------------------------------------------------------------------ step
+// phi - phi_ref at one cell (the step works on the phase field's deviation)
+template <typename S>
+__device__ __forceinline__ float phid_at(const S *__restrict__ pin, const float *__restrict__ q_in,
+                                         size_t cc, size_t N, const DevParams &P) {
+    float v = Codec<S>::load_dev(pin + G0 * N + cc, G0, P);
+#pragma unroll
+    for (int i = 1; i < QG; ++i) v += Codec<S>::load_dev(pin + (G0 + i) * N + cc, G0 + i, P);
+    return v + 0.5f * q_in[cc];
+}
+
 template <typename S>
 __device__ __forceinline__ float phi_at(const S *__restrict__ pin, const float *__restrict__ q_in,
                                         size_t cc, size_t N, const DevParams &P) {
-    float v = Codec<S>::load(pin + G0 * N + cc, G0, P);
-#pragma unroll
-    for (int i = 1; i < QG; ++i) v += Codec<S>::load(pin + (G0 + i) * N + cc, G0 + i, P);
-    return v + 0.5f * q_in[cc];
+    return phid_at<S>(pin, q_in, cc, N, P) + P.g_ref;
 }
 
 // Fill window slot `slot` with phi of plane z (tile + halo ring).  When
@@ -158,7 +165,7 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
             else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
             else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
             const size_t cc = ((size_t)z * ny + (y0 + sy - 1)) * nx + (x0 + sx - 1);
-            plane[sy * SX + sx] = phi_at<S>(pin, q_in, cc, N, P);
+            plane[sy * SX + sx] = phid_at<S>(pin, q_in, cc, N, P);
         }
         return;
     }
@@ -172,10 +179,10 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
         const int ky = wrap_coord(cy, ny, P.periodic[1]);
         const int kz = wrap_coord(cz, nz, P.periodic[2]);
         float v;
-        if (kx >= 2) v = P.phi_wall[kx - 2];
-        else if (ky >= 2) v = P.phi_wall[ky - 2];
-        else if (kz >= 2) v = P.phi_wall[kz - 2];
-        else v = phi_at<S>(pin, q_in, ((size_t)cz * ny + cy) * nx + cx, N, P);
+        if (kx >= 2) v = P.phi_wall[kx - 2] - P.g_ref;
+        else if (ky >= 2) v = P.phi_wall[ky - 2] - P.g_ref;
+        else if (kz >= 2) v = P.phi_wall[kz - 2] - P.g_ref;
+        else v = phid_at<S>(pin, q_in, ((size_t)cz * ny + cy) * nx + cx, N, P);
         plane[sidx] = v;
     }
 }
@@ -213,7 +220,8 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float *pl[3] = {sphi + (z % 3) * PLANE + centre, sphi + ((z + 1) % 3) * PLANE + centre,
                           sphi + ((z + 2) % 3) * PLANE + centre};   // planes z-1, z, z+1
     Macro3 m;
-    const float ph = pl[1][0];
+    const float phd = pl[1][0];              // the window holds phi - phi_ref
+    const float ph = phd + P.g_ref;
     m.phi = ph;
     float gx = 0.0f, gy = 0.0f, gz = 0.0f, la = 0.0f, ld = 0.0f;
 #pragma unroll
@@ -228,7 +236,7 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         if (i <= 6) la += sm; else ld += sm;
     }
     m.g[0] = 3.0f * gx; m.g[1] = 3.0f * gy; m.g[2] = 3.0f * gz;
-    m.lap = 6.0f * ((1.0f / 18.0f) * (la - 6.0f * ph) + (1.0f / 36.0f) * (ld - 12.0f * ph));
+    m.lap = 6.0f * ((1.0f / 18.0f) * (la - 6.0f * phd) + (1.0f / 36.0f) * (ld - 12.0f * phd));
     closures3d(m, P);
     float jx = 0.0f, jy = 0.0f, jz = 0.0f, sf = f[0], ss = s[0];
 #pragma unroll
@@ -250,7 +258,7 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float ug = m.u[0] * m.g[0] + m.u[1] * m.g[1] + m.u[2] * m.g[2];
     const float phip = phi_prev[c];
     m.p = sf + 0.5f * (LF::cs2 * ugr + rcs2 * qp * P.kappa);
-    m.Td = ss - 0.5f * P.L_over_Cp * ((ph - phip) + ug + ph * qp * P.kappa);
+    m.Td = ss - 0.5f * P.L_over_Cp * ((phd - phip) + ug + ph * qp * P.kappa);
     m.T = m.Td + P.s_ref;
     const float q = production(ph, m.T, P);
     const float inv_d = __frcp_rn(sqrtf(fmaxf(m.g[0] * m.g[0] + m.g[1] * m.g[1] + m.g[2] * m.g[2], P.eps2)));
@@ -258,8 +266,8 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float om_g = P.om_g;
     const float om_f = __frcp_rn(viscosity(ph, P) * LF::inv_cs2 + 0.5f);
     const float om_s = __frcp_rn(diffusivity(ph, P) * LF::inv_cs2 + 0.5f);
-    const float D = (ph - phip) + ug + ph * q * P.kappa;
-    phi_prev[c] = ph;
+    const float D = (phd - phip) + ug + ph * q * P.kappa;
+    phi_prev[c] = phd;           // stored as phi - phi_ref
     q_out[c] = q;
 
     const float usq = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
@@ -278,11 +286,11 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float poly = cu * fmaf(8.0f, cu, 4.0f) - usq2;
         const float G = fmaf(w, poly, w);
         const float Sg = w * (i == 0 ? q : fmaf(iface, edot3(ex, ey, ez, n0, n1, n2), q));
-        const float gs = fmaf(a_g, g[i], fmaf(om_g, ph * G, b_g * Sg));
+        const float gs = fmaf(a_g, g[i], fmaf(om_g, fmaf(phd, G, P.g_ref * (G - w)), b_g * Sg));
         int dx = x + ex, dy = y + ey, dz = z + ez;
         if (FAST) {
             const long long off = ((long long)ez * ny + ey) * nx + ex;
-            Codec<S>::store(pout + (G0 + i) * N + c + off, gs, G0 + i, P);
+            Codec<S>::store_dev(pout + (G0 + i) * N + c + off, gs, G0 + i, P);
         } else {
             const int kx = wrap_coord(dx, nx, P.periodic[0]);
             const int ky = wrap_coord(dy, ny, P.periodic[1]);
@@ -290,10 +298,10 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
             if (kx >= 2 || ky >= 2 || kz >= 2) {
                 const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
                 const int o = LG::opp(i);
-                Codec<S>::store(pout + (G0 + o) * N + c, -gs + 2.0f * w * P.phi_wall[side], G0 + o, P);
+                Codec<S>::store_dev(pout + (G0 + o) * N + c, -gs + 2.0f * w * (P.phi_wall[side] - P.g_ref), G0 + o, P);
             } else {
                 const size_t d = ((size_t)dz * ny + dy) * nx + dx;
-                Codec<S>::store(pout + (G0 + i) * N + d, gs, G0 + i, P);
+                Codec<S>::store_dev(pout + (G0 + i) * N + d, gs, G0 + i, P);
             }
         }
     }
@@ -370,7 +378,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
         if (col) {
             const size_t c = zbeg * plane_cells + cxy;
 #pragma unroll
-            for (int i = 0; i < QG; ++i) g[i] = Codec<S>::load(pin + (G0 + i) * N + c, G0 + i, P);
+            for (int i = 0; i < QG; ++i) g[i] = Codec<S>::load_dev(pin + (G0 + i) * N + c, G0 + i, P);
             qcur = q_in[c];
             ph = g[0];
 #pragma unroll
@@ -389,7 +397,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             if (ok) {
                 const size_t c = (size_t)(z + 1) * plane_cells + cxy;
 #pragma unroll
-                for (int i = 0; i < QG; ++i) gn[i] = Codec<S>::load(pin + (G0 + i) * N + c, G0 + i, P);
+                for (int i = 0; i < QG; ++i) gn[i] = Codec<S>::load_dev(pin + (G0 + i) * N + c, G0 + i, P);
                 qnext = q_in[c];
                 ph = gn[0];
 #pragma unroll
@@ -476,7 +484,7 @@ macro3d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
         Macro3 m;
         m.phi = nb[0];
         stencil3d(nb, m.g, m.lap);
-        moments3d(m, f, s, phi_prev[c], q_in[c], P);
+        moments3d(m, f, s, phi_prev[c] + P.g_ref, q_in[c], P);
         if (o_phi) o_phi[c] = m.phi;
         if (o_T) o_T[c] = m.T;
         if (o_ux) o_ux[c] = m.u[0];
@@ -521,7 +529,7 @@ init3d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
     for (int i = 0; i < QG; ++i) {
         float eqb, src;
         g_eq_src(i, m, n, q, usq, P, eqb, src);
-        Codec<S>::store(pout + (G0 + i) * N + c, eqb, G0 + i, P);
+        Codec<S>::store_dev(pout + (G0 + i) * N + c, eqb - LG::w(i) * P.g_ref, G0 + i, P);
     }
 #pragma unroll
     for (int i = 0; i < QF; ++i) {
@@ -530,7 +538,7 @@ init3d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
         Codec<S>::store(pout + i * N + c, feqb, i, P);
         Codec<S>::store_dev(pout + (S0 + i) * N + c, seqb, S0 + i, P);
     }
-    phi_prev[c] = m.phi;
+    phi_prev[c] = m.phi - P.g_ref;
     q_out[c] = q;
 }
 

@@ -99,6 +99,7 @@ struct DevParams {
     float phi_wall[2], T_wall[2];
     int source_on, visc_interp, alpha_interp, storage;
     float s_ref;                       // temperature storage reference T_ref
+    float g_ref;                       // phase-field storage reference phi_ref
     // storage codec per population plane k (f planes, then g, then s):
     // FP32: theta = d + enc_c[k];  16-bit: theta = enc_c[k] + x * dec_s[k],
     // x = (theta - enc_c[k]) * enc_s[k]
