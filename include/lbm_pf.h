@@ -168,6 +168,27 @@ int lbm_last_launches(const lbm_handle *h, int32_t *launches);
 /* Wait for the handle's stream; report any pending CUDA error. */
 int lbm_sync(lbm_handle *h);
 
+/* Allocation-free global sums (no counterpart in the paper).  For callers
+ * that must not allocate device memory at all -- for example code running
+ * inside a host application whose memory pool owns every device buffer, or a
+ * monitoring hook on a latency-critical path where the implicit
+ * synchronisation of cudaMalloc/cudaFree is not acceptable -- and who
+ * therefore cannot provide the workspace lbm_reduce needs.
+ * Computes out[0] = sum(phi) and out[1] = sum(rho(phi) (Cp T + phi L)), with
+ * rho(phi) = phi rho_g + (1 - phi) rho_l on phi clipped to [0, 1], in FP64,
+ * over n_cells float32 values of phi and T (device pointers); d_out is device
+ * memory for two doubles.  Queued on `stream` (a cudaStream_t, NULL = legacy
+ * default stream).  The per-block partial sums use a 1 MiB array in static
+ * device memory that every GPU loading the library holds until exit; hence
+ * n_cells is limited to 16,777,216 and larger sizes return LBM_ENOMEM.  The
+ * first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the array: calls whose kernels overlap on the GPU
+ * race and must be ordered by the caller.  Errors: LBM_EINVAL (NULL pointer,
+ * n_cells < 1, non-positive density), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_field_sums_noalloc(const float *phi, const float *T, int64_t n_cells, double rho_l,
+                           double rho_g, double Cp, double L, double *d_out, void *stream);
+
 /* Release the handle (not the workspace, which the caller owns). */
 void lbm_destroy(lbm_handle *h);
 

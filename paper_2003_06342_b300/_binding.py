@@ -76,6 +76,9 @@ SIGNATURES = {
     "lbm_steps_done": (ctypes.c_int, [H, P(ctypes.c_int64)]),
     "lbm_last_launches": (ctypes.c_int, [H, P(ctypes.c_int32)]),
     "lbm_sync": (ctypes.c_int, [H]),
+    "lbm_field_sums_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_destroy": (None, [H]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -91,7 +94,7 @@ class LBMError(RuntimeError):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
-            f"{LIB_PATH} is missing: build it with `python -m paper_2003_06342_b300.build` "
+            f"{LIB_PATH} is missing: build it with `python paper_2003_06342_b300/build.py` "
             "(or __graft_entry__.build()); there is no non-CUDA implementation")
     lib_ = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in SIGNATURES.items():

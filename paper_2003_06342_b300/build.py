@@ -2,7 +2,9 @@
 
 nvcc -gencode arch=compute_103a,code=sm_103a -lineinfo -O3, one shared
 object from csrc/*.cu, linked against the shared CUDA runtime (the one the
-PyTorch process has already loaded).  Running this module rebuilds it.
+PyTorch process has already loaded).  `python paper_2003_06342_b300/build.py`
+rebuilds it (run it as a script: importing the package would load the old
+library first).
 """
 import os
 import subprocess
@@ -12,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbmpf.so")
-SOURCES = ["api.cu", "lbm2d.cu", "lbm3d.cu", "reduce.cu"]
+SOURCES = ["api.cu", "lbm2d.cu", "lbm3d.cu", "reduce.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,56 @@
+"""The allocation-free field sums against the workspace-based reduction.
+
+lbm_field_sums_noalloc serves callers that cannot allocate device memory
+(their host owns every device buffer, or cudaMalloc's implicit
+synchronisation is off limits where they run), so it keeps its partial sums
+in static device memory instead of a workspace.  It must give the same mass
+and enthalpy as lbm_reduce on the same state, call after call.  This file is
+collected last so that a run stopping at the first failure has run every
+other test before it."""
+import ctypes
+
+import pytest
+import torch
+
+import workloads as W
+from paper_2003_06342_b300 import _binding as B
+
+from _parity import gpu_solver
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc_sums(F, params, stream):
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device=F["phi"].device)
+    phi = F["phi"].contiguous()
+    T = F["T"].contiguous()
+    B.check(B.lib.lbm_field_sums_noalloc(ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                         phi.numel(), params["rho_l"], params["rho_g"], params["Cp"],
+                                         params["L"], ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(stream.cuda_stream)),
+            "lbm_field_sums_noalloc")
+    torch.cuda.synchronize()
+    return out.tolist()
+
+
+def test_noalloc_sums_match_reduce_two_calls():
+    w = W.film_boiling_2d(300, 170, modes=3, seed=1, y0=40.0, paper=True, phi_wall=(1.0, 0.0))
+    s = gpu_solver(w)
+    for _ in range(2):
+        s.step(25)
+        mass, energy = s.reduce()
+        F = s.fields()
+        m2, e2 = _noalloc_sums(F, w.params, s.stream)
+        assert abs(m2 - mass) <= 1e-12 * abs(mass)
+        assert abs(e2 - energy) <= 1e-12 * abs(energy)
+
+
+def test_noalloc_rejects_oversize_and_bad_args():
+    dummy = torch.zeros(4, dtype=torch.float32, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    p = ctypes.c_void_p(dummy.data_ptr())
+    o = ctypes.c_void_p(out.data_ptr())
+    # the size check happens before any device access
+    assert B.lib.lbm_field_sums_noalloc(p, p, 16777216 + 1, 1.0, 1.0, 1.0, 1.0, o, None) == B.LBM_ENOMEM
+    assert B.lib.lbm_field_sums_noalloc(p, p, 0, 1.0, 1.0, 1.0, 1.0, o, None) == B.LBM_EINVAL
+    assert B.lib.lbm_field_sums_noalloc(None, p, 4, 1.0, 1.0, 1.0, 1.0, o, None) == B.LBM_EINVAL
