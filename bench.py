@@ -362,6 +362,23 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def ncu_case(case):
+    """Initialise one case and run 4 steps: the launches an ncu capture of a
+    step kernel selects from (-k regex:step.d -s 1 -c 1 takes the second).
+    2D cases use the 2048 x 4096 workload; 3D cases a 256 x 256 x 128 slab of
+    the 3D film-boiling workload (8.4 M cells, 3 GB of FP32 populations), so
+    that a full-set capture stays small."""
+    import torch
+    from paper_2003_06342_b300 import Solver
+    dim, storage = case.split("_")
+    w = workload_c2() if dim == "2d" else W.c3_film_boiling_3d(256, 256, 128)
+    s = Solver(w.n, w.periodic, w.params, storage=storage)
+    s.init(w.phi0, w.T0, p0=w.p0)
+    s.step(4)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": case, "workload": w.name, "cells": w.cells}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,7 +388,13 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ncu-case", default=None,
+                    choices=["2d_fp32", "2d_fp16", "2d_bf16", "3d_fp32", "3d_fp16"],
+                    help="only initialise one step-kernel case and run 4 steps (for ncu captures)")
     args = ap.parse_args()
+    if args.ncu_case:
+        ncu_case(args.ncu_case)
+        return
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()
 
