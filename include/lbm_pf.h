@@ -168,6 +168,36 @@ int lbm_last_launches(const lbm_handle *h, int32_t *launches);
 /* Wait for the handle's stream; report any pending CUDA error. */
 int lbm_sync(lbm_handle *h);
 
+/* ---- discrete adjoint (2D, FP32 storage) ----------------------------------
+ * Reverse-mode derivative of the step for gradients of a final-time loss
+ * with respect to the latent heat L, the mobility M_phi, the surface tension
+ * sigma and the initial temperature field (the step is Eq. LBE with the
+ * sources of Sec. 3; the loss is J = 1/2 sum (phi^N - phi_target)^2).
+ * States are device buffers in the lbm_get_state layout (27 population
+ * planes, phi^{n-1}, lagged source; float32); an adjoint state has the same
+ * layout and holds dJ/d(stored value).  Other lattices and storages return
+ * LBM_EUNSUPPORTED. */
+
+/* Bytes of one adjoint state and of the per-step scratch (9 planes). */
+int lbm_adjoint_bytes(const lbm_handle *h, size_t *adj_state_bytes, size_t *scratch_bytes);
+
+/* Seed: adj = dJ/dX^N for the state X^N; adds J to *d_J (device double). */
+int lbm_adjoint_terminal(lbm_handle *h, const void *state, const float *phi_target, void *adj,
+                         double *d_J);
+
+/* One step backwards: adj = (dX^{n+1}/dX^n)^T adj_next, with X^n = state;
+ * adds dJ/dL, dJ/dM_phi, dJ/dsigma of this step to d_dparams[0..2] (device
+ * doubles).  adj and adj_next must differ; scratch from lbm_adjoint_bytes. */
+int lbm_adjoint_step(lbm_handle *h, const void *state, const void *adj_next, void *adj,
+                     void *scratch, double *d_dparams);
+
+/* Through the initialisation (lbm_init): dT0 = dJ/dT_0 (device float32,
+ * nx*ny) from adj0 = dJ/dX^0, and the initialisation's share of dJ/dL and
+ * dJ/dsigma added to d_dparams[0] and [2].  init holds the same device
+ * float32 phi, T (and optional ux, uy) given to lbm_init. */
+int lbm_adjoint_init(lbm_handle *h, const lbm_fields *init, const void *adj0, float *dT0,
+                     double *d_dparams);
+
 /* Allocation-free global sums (no counterpart in the paper).  For callers
  * that must not allocate device memory at all -- for example code running
  * inside a host application whose memory pool owns every device buffer, or a

@@ -43,7 +43,7 @@ def gradients(phi0, T0, params, grid, nsteps, phi_target, p0=None):
     J = _forward(torch.as_tensor(phi0, dtype=F64), T0t, params, grid, nsteps,
                  torch.as_tensor(phi_target, dtype=F64), L, Mp, sg, p0)
     J.backward()
-    return float(J), dict(L=float(L.grad), M_phi=float(Mp.grad), sigma=float(sg.grad),
+    return J.item(), dict(L=float(L.grad), M_phi=float(Mp.grad), sigma=float(sg.grad),
                           T0=T0t.grad.detach().clone())
 
 

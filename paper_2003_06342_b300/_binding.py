@@ -79,6 +79,13 @@ SIGNATURES = {
     "lbm_field_sums_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_adjoint_bytes": (ctypes.c_int, [H, P(ctypes.c_size_t), P(ctypes.c_size_t)]),
+    "lbm_adjoint_terminal": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "lbm_adjoint_step": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_adjoint_init": (ctypes.c_int, [H, P(lbm_fields), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "lbm_destroy": (None, [H]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

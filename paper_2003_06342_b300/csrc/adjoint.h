@@ -1,0 +1,50 @@
+// Adjoint launchers (adjoint2d.cu) and the FP64 block-sum-and-add helper.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+// Sum three doubles over the block (warp shuffles, then one warp) and add the
+// block's sums to out[0..2] with one atomic each.  Every thread must call it.
+__device__ __forceinline__ void block_sum3_atomic(double a, double b, double c, double *out) {
+    __shared__ double sa[32], sb[32], sc[32];
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(full, a, o);
+        b += __shfl_down_sync(full, b, o);
+        c += __shfl_down_sync(full, c, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    if (lane == 0) { sa[warp] = a; sb[warp] = b; sc[warp] = c; }
+    __syncthreads();
+    if (warp == 0) {
+        a = lane < nwarps ? sa[lane] : 0.0;
+        b = lane < nwarps ? sb[lane] : 0.0;
+        c = lane < nwarps ? sc[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(full, a, o);
+            b += __shfl_down_sync(full, b, o);
+            c += __shfl_down_sync(full, c, o);
+        }
+        if (lane == 0) {
+            atomicAdd(out, a);
+            atomicAdd(out + 1, b);
+            atomicAdd(out + 2, c);
+        }
+    }
+}
+
+cudaError_t launch_adj_terminal2d(const float *st, const float *target, float *adj, double *J,
+                                  const DevParams &P, cudaStream_t stream);
+cudaError_t launch_adj_step2d(const float *st, const float *lam_next, float *lam, float *cst,
+                              double *dparams, const DevParams &P, cudaStream_t stream);
+cudaError_t launch_adj_init2d(const float *phi0, const float *T0, const float *ux0,
+                              const float *uy0, const float *lam, float *dT0, double *dparams,
+                              const DevParams &P, cudaStream_t stream);
+
+}  // namespace lbm

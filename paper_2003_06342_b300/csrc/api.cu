@@ -10,6 +10,7 @@
 #include "../../include/lbm_pf.h"
 #include "lbm_kernels.h"
 #include "lbm3d.h"
+#include "adjoint.h"
 
 using namespace lbm;
 
@@ -131,6 +132,8 @@ void fill_devparams(lbm_handle *h) {
     d.storage = p.storage;
     d.s_ref = (float)p.store_ref[2];
     d.g_ref = (float)p.store_ref[1];
+    d.inv_Cp = (float)(1.0 / p.Cp);
+    d.Cp_over_L2 = (float)(p.Cp / (p.L * p.L));
     // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
     int k = 0;
     for (int set = 0; set < 3; ++set) {
@@ -457,6 +460,49 @@ int lbm_sync(lbm_handle *h) {
     if (!h) return LBM_EINVAL;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
     return cuda_status(cudaGetLastError());
+}
+
+static int adjoint_supported(const lbm_handle *h) {
+    if (!h) return LBM_EINVAL;
+    if (h->dim != 2 || h->params.storage != LBM_STORE_FP32) return LBM_EUNSUPPORTED;
+    return LBM_OK;
+}
+
+int lbm_adjoint_bytes(const lbm_handle *h, size_t *adj_state_bytes, size_t *scratch_bytes) {
+    const int r = adjoint_supported(h);
+    if (r != LBM_OK) return r;
+    if (adj_state_bytes) *adj_state_bytes = (size_t)(h->Qtot + 2) * h->N * sizeof(float);
+    if (scratch_bytes) *scratch_bytes = (size_t)9 * h->N * sizeof(float);
+    return LBM_OK;
+}
+
+int lbm_adjoint_terminal(lbm_handle *h, const void *state, const float *phi_target, void *adj,
+                         double *d_J) {
+    const int r = adjoint_supported(h);
+    if (r != LBM_OK) return r;
+    if (!state || !phi_target || !adj || !d_J) return LBM_EINVAL;
+    return cuda_status(launch_adj_terminal2d((const float *)state, phi_target, (float *)adj, d_J,
+                                             h->dp, h->stream));
+}
+
+int lbm_adjoint_step(lbm_handle *h, const void *state, const void *adj_next, void *adj,
+                     void *scratch, double *d_dparams) {
+    const int r = adjoint_supported(h);
+    if (r != LBM_OK) return r;
+    if (!state || !adj_next || !adj || !scratch || !d_dparams || adj == adj_next) return LBM_EINVAL;
+    return cuda_status(launch_adj_step2d((const float *)state, (const float *)adj_next, (float *)adj,
+                                         (float *)scratch, d_dparams, h->dp, h->stream));
+}
+
+int lbm_adjoint_init(lbm_handle *h, const lbm_fields *init, const void *adj0, float *dT0,
+                     double *d_dparams) {
+    const int r = adjoint_supported(h);
+    if (r != LBM_OK) return r;
+    if (!init || !init->phi || !init->T || !adj0 || !dT0 || !d_dparams) return LBM_EINVAL;
+    if (!init->on_device || init->dtype != 0) return LBM_EINVAL;
+    return cuda_status(launch_adj_init2d((const float *)init->phi, (const float *)init->T,
+                                         (const float *)init->ux, (const float *)init->uy,
+                                         (const float *)adj0, dT0, d_dparams, h->dp, h->stream));
 }
 
 void lbm_destroy(lbm_handle *h) { delete h; }

@@ -100,6 +100,7 @@ struct DevParams {
     int source_on, visc_interp, alpha_interp, storage;
     float s_ref;                       // temperature storage reference T_ref
     float g_ref;                       // phase-field storage reference phi_ref
+    float inv_Cp, Cp_over_L2;          // 1/Cp and Cp/L^2 (adjoint of L)
     // storage codec per population plane k (f planes, then g, then s):
     // FP32: theta = d + enc_c[k];  16-bit: theta = enc_c[k] + x * dec_s[k],
     // x = (theta - enc_c[k]) * enc_s[k]

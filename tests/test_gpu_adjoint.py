@@ -1,0 +1,68 @@
+"""The CUDA discrete adjoint against the FP64 oracle's reverse-mode
+gradients (torch autograd through oracle.model.step), for dJ/dL, dJ/dM_phi,
+dJ/dsigma and the field dJ/dT_0; J = 1/2 sum (phi^N - phi_target)^2.
+Relative tolerance 1e-4 on the scalars (the bound stated for the adjoint) and
+on the T_0 gradient field (max-abs difference over max-abs value)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import adjoint as A
+from oracle import model as M
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+CASES = [
+    ("droplet_periodic", lambda: W.droplet_2d(24, 6.0, T_offset=0.04, T_noise=0.01, corr_len=4.0), 10, 4),
+    ("film_walls", lambda: W.film_boiling_2d(20, 18, rho_ratio=5.0, y0=7.0, amplitude=1.5,
+                                             phi_wall=(1.0, 0.0), theta_I=0.05), 8, 3),
+]
+
+
+@pytest.mark.parametrize("name,make,steps,K", CASES, ids=[c[0] for c in CASES])
+def test_gpu_adjoint_matches_oracle(name, make, steps, K):
+    from paper_2003_06342_b300.adjoint import gradients
+    w = make()
+    target = w.phi0.copy()
+    G = M.Grid(w.n, w.periodic)
+    J_ref, g_ref = A.gradients(w.phi0, w.T0, w.params, G, steps, target, p0=w.p0)
+    J, g = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, target, steps, K=K, p0=w.p0)
+    print(name, "J", J, J_ref, {k: (g[k], g_ref[k]) for k in ("L", "M_phi", "sigma")})
+    assert abs(J - J_ref) <= 1e-4 * abs(J_ref)
+    for k in ("L", "M_phi", "sigma"):
+        assert abs(g[k] - g_ref[k]) <= TOL * abs(g_ref[k]) + 1e-12, (k, g[k], g_ref[k])
+    dT = g["T0"].double().cpu().numpy()
+    dT_ref = g_ref["T0"].numpy()
+    err = np.abs(dT - dT_ref).max() / np.abs(dT_ref).max()
+    print(name, "T0 gradient rel err", err)
+    assert err <= TOL
+
+
+def test_checkpoint_interval_does_not_change_gradients():
+    from paper_2003_06342_b300.adjoint import gradients
+    w = W.droplet_2d(24, 6.0, T_offset=0.04, T_noise=0.01, corr_len=4.0)
+    a = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, w.phi0, 9, K=9)
+    b = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, w.phi0, 9, K=2)
+    # the per-field adjoint is deterministic; the FP64 parameter sums are
+    # accumulated with atomics, so only their last bits may differ
+    assert abs(a[0] - b[0]) <= 1e-12 * abs(a[0])
+    for k in ("L", "M_phi", "sigma"):
+        assert abs(a[1][k] - b[1][k]) <= 1e-12 * abs(a[1][k])
+    assert torch.equal(a[1]["T0"], b[1]["T0"])
+
+
+def test_autograd_function():
+    from paper_2003_06342_b300.adjoint import FinalPhiMisfit, gradients
+    w = W.droplet_2d(24, 6.0, T_offset=0.04, T_noise=0.01, corr_len=4.0)
+    T0 = torch.tensor(w.T0, dtype=torch.float32, device="cuda", requires_grad=True)
+    L = torch.tensor(w.params["L"], dtype=torch.float64, requires_grad=True)
+    Mp = torch.tensor(w.params["M_phi"], dtype=torch.float64, requires_grad=True)
+    sg = torch.tensor(w.params["sigma"], dtype=torch.float64, requires_grad=True)
+    J = FinalPhiMisfit.apply(T0, L, Mp, sg, w.n, w.periodic, w.params, w.phi0, w.phi0, 5, 2)
+    J.backward()
+    J2, g = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, w.phi0, 5, K=2)
+    assert abs(float(J) - J2) <= 1e-12 * abs(J2)
+    assert abs(float(L.grad) - g["L"]) <= 1e-12 * abs(g["L"])
+    assert torch.allclose(T0.grad, g["T0"])
