@@ -264,6 +264,8 @@ def run_device(args, world, rank, local):
                 "traffic": profiled_traffic(f"step3d_{storage}_256x256x512")}
             del v
         torch.cuda.empty_cache()
+        variants["adjoint_2d_fp32"] = adjoint_variant(dev, peak)
+        torch.cuda.empty_cache()
     result["variants"] = variants
 
     # end to end through the public API: host fields in, K steps with the
@@ -302,6 +304,66 @@ def run_device(args, world, rank, local):
         dist.destroy_process_group()
     result["workload"] = w
     return result
+
+
+# adjoint step: kernel A reads the state (29 planes), the next adjoint state
+# (29) and writes the adjoint state (29) and nine stencil contributions;
+# kernel B reads those contributions and updates 10 adjoint planes
+ADJ_BYTES_PER_CELL = 4 * (29 + 29 + 29 + 9) + 4 * (9 + 10 + 10)
+
+
+def adjoint_variant(dev, peak, steps=2000, K=100):
+    """Gradient of J = 1/2 sum (phi^N - phi_target)^2 for the 512 x 512
+    evaporating droplet: target from a run with L x 1.05, M_phi x 0.95,
+    sigma x 1.1 and T_0 of seed 4; gradient w.r.t. L, M_phi, sigma, T_0."""
+    import ctypes
+    import torch
+    from paper_2003_06342_b300 import Solver
+    from paper_2003_06342_b300 import _binding as Bd
+    from paper_2003_06342_b300.adjoint import gradients
+    w = W.c4_droplet()
+    wt = W.droplet_2d(512, 40.0, seed=4)
+    pt = dict(w.params)
+    pt.update(L=w.params["L"] * 1.05, M_phi=w.params["M_phi"] * 0.95, sigma=w.params["sigma"] * 1.1)
+    st = Solver(w.n, w.periodic, pt, device=dev)
+    st.init(wt.phi0, wt.T0).step(steps)
+    target = st.fields()["phi"].clone()
+    del st
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    J, g = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, target, steps, K=K, device=dev)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    # the adjoint-step kernels alone, on one state
+    s = Solver(w.n, w.periodic, w.params, device=dev)
+    s.init(w.phi0, w.T0)
+    state = s.get_state().clone()
+    nb, sb = ctypes.c_size_t(), ctypes.c_size_t()
+    Bd.check(Bd.lib.lbm_adjoint_bytes(s._h, ctypes.byref(nb), ctypes.byref(sb)), "lbm_adjoint_bytes")
+    a = torch.zeros(nb.value // 4, device=dev)
+    b = torch.zeros_like(a)
+    scr = torch.zeros(sb.value // 4, device=dev)
+    dp = torch.zeros(3, dtype=torch.float64, device=dev)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    reps = 200
+    e0.record(s.stream)
+    for _ in range(reps):
+        Bd.check(Bd.lib.lbm_adjoint_step(s._h, vp(state), vp(a), vp(b), vp(scr), vp(dp)), "lbm_adjoint_step")
+        a, b = b, a
+    e1.record(s.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": w.name + " (2000 steps, checkpoint every 100)",
+            "MLUPS": w.cells * steps / dt / 1e6, "seconds": dt,
+            "what": "forward with checkpoints + reverse with segment recomputation, per forward step",
+            "J": J, "dJ_dL": g["L"], "dJ_dM_phi": g["M_phi"], "dJ_dsigma": g["sigma"],
+            "dJ_dT0_norm": float(g["T0"].norm()),
+            "adjoint_step_ms": ms, "adjoint_step_bytes_per_cell": ADJ_BYTES_PER_CELL,
+            "adjoint_step_achieved_GBs": ADJ_BYTES_PER_CELL * w.cells / ms / 1e6,
+            "adjoint_step_frac": ADJ_BYTES_PER_CELL * w.cells / ms / 1e6 / peak}
 
 
 def cpu_baseline(sample_steps=1):
@@ -370,9 +432,11 @@ def ncu_case(case):
     that a full-set capture stays small."""
     import torch
     from paper_2003_06342_b300 import Solver
-    dim, storage = case.split("_")
+    dim, storage = case.split("_")[:2]
     w = workload_c2() if dim == "2d" else W.c3_film_boiling_3d(256, 256, 128)
     s = Solver(w.n, w.periodic, w.params, storage=storage)
+    if case.endswith("_tma"):
+        s.set_kernel("tma")
     s.init(w.phi0, w.T0, p0=w.p0)
     s.step(4)
     torch.cuda.synchronize()
@@ -389,7 +453,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ncu-case", default=None,
-                    choices=["2d_fp32", "2d_fp16", "2d_bf16", "3d_fp32", "3d_fp16"],
+                    choices=["2d_fp32", "2d_fp16", "2d_bf16", "3d_fp32", "3d_fp16",
+                             "2d_fp32_tma", "2d_fp16_tma"],
                     help="only initialise one step-kernel case and run 4 steps (for ncu captures)")
     args = ap.parse_args()
     if args.ncu_case:

@@ -41,7 +41,7 @@ extern "C" {
 #define LBM_ENOMEM       -2   /* workspace or caller buffer too small            */
 #define LBM_ECUDA        -3   /* a CUDA runtime call or kernel launch failed     */
 #define LBM_ENONFINITE   -4   /* a reduction found NaN or Inf in the fields      */
-#define LBM_ETIMEOUT     -5   /* reserved: no kernel of this library waits       */
+#define LBM_ETIMEOUT     -5   /* a bounded in-kernel wait expired (see lbm_sync) */
 #define LBM_EUNSUPPORTED -6   /* combination not built (e.g. lattice/storage)    */
 
 /* ---- lattices (Sec. 3, lattice definitions) ----------------------------- */
@@ -159,13 +159,32 @@ int lbm_set_state(lbm_handle *h, const void *src, size_t bytes, int32_t on_devic
  * opposite direction).  Both buffers are device memory of Q*N entries. */
 int lbm_stream_map(lbm_handle *h, int32_t set, int32_t *src_index, int8_t *kind);
 
+/* Kernel variants of the 2D step.  AUTO (default) is the tiled kernel; TMA
+ * selects the persistent TMA-staged kernel, available when the grid allows
+ * 16-byte-aligned tensor boxes (row and plane strides a multiple of 16 bytes,
+ * at least 66 x 18 cells).  Both compute the same update bit for bit.  3D
+ * always uses the tiled z-marching kernel. */
+#define LBM_KERNEL_AUTO   0
+#define LBM_KERNEL_TILED  1
+#define LBM_KERNEL_TMA    2
+
+/* Select the step kernel; LBM_EUNSUPPORTED if TMA staging is not possible
+ * for this grid, storage or device. */
+int lbm_set_kernel(lbm_handle *h, int32_t kernel);
+
+/* The kernel lbm_step launches (LBM_KERNEL_TILED or LBM_KERNEL_TMA; AUTO is
+ * reported as what it resolves to once a step has run). */
+int lbm_get_kernel(const lbm_handle *h, int32_t *kernel);
+
 /* Number of time steps since lbm_init / lbm_set_state. */
 int lbm_steps_done(const lbm_handle *h, int64_t *steps);
 
 /* Kernel launches queued by the last lbm_step call. */
 int lbm_last_launches(const lbm_handle *h, int32_t *launches);
 
-/* Wait for the handle's stream; report any pending CUDA error. */
+/* Wait for the handle's stream; report any pending CUDA error, or
+ * LBM_ETIMEOUT if a bounded wait inside a step kernel expired (the kernel then
+ * stopped early and the state is not valid). */
 int lbm_sync(lbm_handle *h);
 
 /* ---- discrete adjoint (2D, FP32 storage) ----------------------------------

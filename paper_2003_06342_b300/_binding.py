@@ -21,6 +21,10 @@ LBM_EUNSUPPORTED = -6
 LBM_D2Q9 = 0
 LBM_D3Q19_D3Q7 = 1
 
+LBM_KERNEL_AUTO = 0
+LBM_KERNEL_TILED = 1
+LBM_KERNEL_TMA = 2
+
 LBM_STORE_FP32 = 0
 LBM_STORE_FP16 = 1
 LBM_STORE_BF16 = 2
@@ -73,6 +77,8 @@ SIGNATURES = {
     "lbm_get_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]),
     "lbm_set_state": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]),
     "lbm_stream_map": (ctypes.c_int, [H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_set_kernel": (ctypes.c_int, [H, ctypes.c_int32]),
+    "lbm_get_kernel": (ctypes.c_int, [H, P(ctypes.c_int32)]),
     "lbm_steps_done": (ctypes.c_int, [H, P(ctypes.c_int64)]),
     "lbm_last_launches": (ctypes.c_int, [H, P(ctypes.c_int32)]),
     "lbm_sync": (ctypes.c_int, [H]),

@@ -11,6 +11,7 @@
 #include "lbm_kernels.h"
 #include "lbm3d.h"
 #include "adjoint.h"
+#include "lbm2d_tma.h"
 
 using namespace lbm;
 
@@ -33,6 +34,11 @@ struct lbm_handle {
     int cur;
     int64_t steps;
     int32_t last_launches;
+    int *err;                // device error word (bounded waits that expired)
+    int kernel_choice;       // LBM_KERNEL_*
+    int tma_state;           // 0 not set up, 1 ready, -1 not available
+    int tma_blocks;
+    lbm::TmaMaps2d maps;
 };
 
 namespace {
@@ -42,7 +48,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t pops, phi, q, scratch, partial, red, total;
+    size_t pops, phi, q, scratch, partial, red, err, total;
     int red_blocks;
 };
 
@@ -93,7 +99,8 @@ Layout layout(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
     L.red_blocks = (int)((N + 255) / 256);
     L.partial = align_up((size_t)L.red_blocks * 2 * sizeof(double));
     L.red = align_up(2 * sizeof(double));
-    L.total = 2 * L.pops + L.phi + 2 * L.q + L.scratch + L.partial + L.red;
+    L.err = align_up(sizeof(int));
+    L.total = 2 * L.pops + L.phi + 2 * L.q + L.scratch + L.partial + L.red + L.err;
     return L;
 }
 
@@ -154,9 +161,41 @@ void fill_devparams(lbm_handle *h) {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
 
 // ---- dispatch on storage type and dimension
+// Lazily prepare the TMA-staged 2D kernel (needs a device): eligibility,
+// tensor maps over this handle's buffers, shared-memory limit, grid size.
+void setup_tma(lbm_handle *h) {
+    h->tma_state = -1;
+    if (h->dim != 2 || !lbm::tma2d_eligible(h->dp, (int)h->elem)) return;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return;
+    const int per_sm = lbm::tma2d_blocks_per_sm((int)h->elem);
+    if (per_sm < 1) return;
+    if (lbm::make_tma_maps2d(&h->maps, h->dp, (int)h->elem, h->pops, h->q, h->phi_prev) != 0) return;
+    if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return;
+    h->tma_blocks = sms * per_sm;
+    h->tma_state = 1;
+}
+
 int do_step(lbm_handle *h) {
     const int nxt = h->cur ^ 1;
     cudaError_t e;
+    if (h->dim == 2 && h->kernel_choice == LBM_KERNEL_TMA) {
+        if (h->tma_state == 0) setup_tma(h);
+        if (h->tma_state == 1) {
+            const int tiles = ((h->grid.nx + 31) / 32) * ((h->grid.ny + 7) / 8);
+            const int nb = h->tma_blocks < tiles ? h->tma_blocks : tiles;
+            switch (h->params.storage) {
+            case LBM_STORE_FP32: e = launch_step2d_tma<float>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, nb, h->stream); break;
+            case LBM_STORE_FP16: e = launch_step2d_tma<__half>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, nb, h->stream); break;
+            default: e = launch_step2d_tma<__nv_bfloat16>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, nb, h->stream); break;
+            }
+            if (e != cudaSuccess) return LBM_ECUDA;
+            h->cur = nxt;
+            return LBM_OK;
+        }
+        if (h->kernel_choice == LBM_KERNEL_TMA) return LBM_EUNSUPPORTED;
+    }
     if (h->dim == 2) {
         switch (h->params.storage) {
         case LBM_STORE_FP32: e = launch_step2d<float>(h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->dp, h->stream); break;
@@ -293,7 +332,11 @@ int lbm_create(const lbm_grid *grid, int32_t lattice, const lbm_params *params, 
     h->scratch = (float *)p; p += L.scratch;
     h->partial = (double *)p; p += L.partial;
     h->red_out = (double *)p; p += L.red;
+    h->err = (int *)p; p += L.err;
     h->red_blocks = L.red_blocks;
+    h->kernel_choice = LBM_KERNEL_AUTO;
+    h->tma_state = 0;
+    h->tma_blocks = 0;
     h->cur = 0;
     h->steps = 0;
     h->last_launches = 0;
@@ -459,7 +502,33 @@ int lbm_last_launches(const lbm_handle *h, int32_t *launches) {
 int lbm_sync(lbm_handle *h) {
     if (!h) return LBM_EINVAL;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
-    return cuda_status(cudaGetLastError());
+    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+    if (h->tma_state == 1) {
+        int flag = 0;
+        if (cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ECUDA;
+        if (flag) {
+            cudaMemset(h->err, 0, sizeof(int));
+            return LBM_ETIMEOUT;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_set_kernel(lbm_handle *h, int32_t kernel) {
+    if (!h || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA) return LBM_EINVAL;
+    if (kernel == LBM_KERNEL_TMA) {
+        if (h->tma_state == 0) setup_tma(h);
+        if (h->tma_state != 1) return LBM_EUNSUPPORTED;
+    }
+    h->kernel_choice = kernel;
+    return LBM_OK;
+}
+
+int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
+    if (!h || !kernel) return LBM_EINVAL;
+    if (h->dim == 2 && h->kernel_choice == LBM_KERNEL_TMA && h->tma_state == 1) *kernel = LBM_KERNEL_TMA;
+    else *kernel = LBM_KERNEL_TILED;
+    return LBM_OK;
 }
 
 static int adjoint_supported(const lbm_handle *h) {

@@ -126,6 +126,10 @@ template <> struct Codec<float> {
     static __device__ __forceinline__ void store_dev(float *p, float d, int, const DevParams &) {
         *p = d;
     }
+    static __device__ __forceinline__ float dec(float raw, int k, const DevParams &P) {
+        return raw + P.enc_c[k];
+    }
+    static __device__ __forceinline__ float dec_dev(float raw, int, const DevParams &) { return raw; }
 };
 
 template <> struct Codec<__half> {
@@ -135,11 +139,19 @@ template <> struct Codec<__half> {
     static __device__ __forceinline__ void store(__half *p, float v, int k, const DevParams &P) {
         *p = __float2half_rn((v - P.enc_c[k]) * P.enc_s[k]);
     }
+    // __fmul_rn: the decoded value is rounded here, never folded into a
+    // later addition, so every kernel that decodes a value gets the same float
     static __device__ __forceinline__ float load_dev(const __half *p, int k, const DevParams &P) {
-        return __half2float(__ldg(p)) * P.dec_s[k];
+        return __fmul_rn(__half2float(__ldg(p)), P.dec_s[k]);
     }
     static __device__ __forceinline__ void store_dev(__half *p, float d, int k, const DevParams &P) {
         *p = __float2half_rn(d * P.enc_s[k]);
+    }
+    static __device__ __forceinline__ float dec(__half raw, int k, const DevParams &P) {
+        return fmaf(__half2float(raw), P.dec_s[k], P.enc_c[k]);
+    }
+    static __device__ __forceinline__ float dec_dev(__half raw, int k, const DevParams &P) {
+        return __fmul_rn(__half2float(raw), P.dec_s[k]);
     }
 };
 
@@ -151,10 +163,16 @@ template <> struct Codec<__nv_bfloat16> {
         *p = __float2bfloat16_rn((v - P.enc_c[k]) * P.enc_s[k]);
     }
     static __device__ __forceinline__ float load_dev(const __nv_bfloat16 *p, int k, const DevParams &P) {
-        return __bfloat162float(__ldg(p)) * P.dec_s[k];
+        return __fmul_rn(__bfloat162float(__ldg(p)), P.dec_s[k]);
     }
     static __device__ __forceinline__ void store_dev(__nv_bfloat16 *p, float d, int k, const DevParams &P) {
         *p = __float2bfloat16_rn(d * P.enc_s[k]);
+    }
+    static __device__ __forceinline__ float dec(__nv_bfloat16 raw, int k, const DevParams &P) {
+        return fmaf(__bfloat162float(raw), P.dec_s[k], P.enc_c[k]);
+    }
+    static __device__ __forceinline__ float dec_dev(__nv_bfloat16 raw, int k, const DevParams &P) {
+        return __fmul_rn(__bfloat162float(raw), P.dec_s[k]);
     }
 };
 

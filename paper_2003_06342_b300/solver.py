@@ -218,6 +218,17 @@ class Solver:
                                      ctypes.c_void_p(kind.data_ptr())), "lbm_stream_map")
         return src, kind
 
+    def set_kernel(self, kind):
+        """'auto', 'tiled' or 'tma' (2D step kernel variant)."""
+        code = {"auto": B.LBM_KERNEL_AUTO, "tiled": B.LBM_KERNEL_TILED, "tma": B.LBM_KERNEL_TMA}[kind]
+        B.check(B.lib.lbm_set_kernel(self._h, code), "lbm_set_kernel")
+        return self
+
+    def kernel(self):
+        v = ctypes.c_int32()
+        B.check(B.lib.lbm_get_kernel(self._h, ctypes.byref(v)), "lbm_get_kernel")
+        return {B.LBM_KERNEL_TILED: "tiled", B.LBM_KERNEL_TMA: "tma"}.get(v.value, "auto")
+
     def steps_done(self):
         v = ctypes.c_int64()
         B.check(B.lib.lbm_steps_done(self._h, ctypes.byref(v)), "lbm_steps_done")
