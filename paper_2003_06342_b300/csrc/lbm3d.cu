@@ -391,24 +391,14 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
 
     for (int z = zbeg; z < zend; ++z) {
         float gn[QG], qnext = 0.0f;
-        // this layer's f and s first, so their loads are in flight during the
-        // window fill and the barrier below
-        float f[QF], s[QF];
-        const size_t c = (size_t)z * plane_cells + cxy;
-        if (col) {
-#pragma unroll
-            for (int i = 0; i < QF; ++i) f[i] = Codec<S>::load(pin + i * N + c, i, P);
-#pragma unroll
-            for (int i = 0; i < QF; ++i) s[i] = Codec<S>::load_dev(pin + (S0 + i) * N + c, S0 + i, P);
-        }
         {
             float ph = 0.0f;
             const bool ok = col && (z + 1 < nz);
             if (ok) {
-                const size_t cn = (size_t)(z + 1) * plane_cells + cxy;
+                const size_t c = (size_t)(z + 1) * plane_cells + cxy;
 #pragma unroll
-                for (int i = 0; i < QG; ++i) gn[i] = Codec<S>::load_dev(pin + (G0 + i) * N + cn, G0 + i, P);
-                qnext = q_in[cn];
+                for (int i = 0; i < QG; ++i) gn[i] = Codec<S>::load_dev(pin + (G0 + i) * N + c, G0 + i, P);
+                qnext = q_in[c];
                 ph = gn[0];
 #pragma unroll
                 for (int i = 1; i < QG; ++i) ph += gn[i];
@@ -418,6 +408,12 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
         }
         __syncthreads();
         if (col) {
+            const size_t c = (size_t)z * plane_cells + cxy;
+            float f[QF], s[QF];
+#pragma unroll
+            for (int i = 0; i < QF; ++i) f[i] = Codec<S>::load(pin + i * N + c, i, P);
+#pragma unroll
+            for (int i = 0; i < QF; ++i) s[i] = Codec<S>::load_dev(pin + (S0 + i) * N + c, S0 + i, P);
             if (FXY && z >= 1 && z + 1 < nz)
                 layer_update3d<S, true>(sphi, z, x, y, c, f, s, g, qcur, pout, phi_prev, q_out, P);
             else
