@@ -39,8 +39,8 @@ REDUCE_EVERY = 100
 BYTES_PER_CELL = {("2d", "fp32"): 27 * 4 * 2 + 16, ("2d", "fp16"): 27 * 2 * 2 + 16,
                   ("2d", "bf16"): 27 * 2 * 2 + 16, ("3d", "fp32"): 45 * 4 * 2 + 16,
                   ("3d", "fp16"): 45 * 2 * 2 + 16, ("3d", "bf16"): 45 * 2 * 2 + 16}
-KERNEL_SOURCES = ["paper_2003_06342_b300/csrc/lbm2d.cu", "paper_2003_06342_b300/csrc/lbm3d.cu",
-                  "paper_2003_06342_b300/csrc/lbm_common.cuh"]
+KERNEL_SOURCES = ["paper_2003_06342_b300/csrc/lbm2d.cu", "paper_2003_06342_b300/csrc/lbm2d_cell.cuh",
+                  "paper_2003_06342_b300/csrc/lbm3d.cu", "paper_2003_06342_b300/csrc/lbm_common.cuh"]
 
 
 def kernel_hash():
@@ -146,6 +146,24 @@ def workload_c2():
     return w
 
 
+def max_over_ranks(value, world, device=None):
+    """The largest of every rank's `value` (the slowest rank's time); the
+    identity for a single process."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank, steps, world, slowest_ms):
+    """Cell updates of all ranks (independent replicas, weak scaling) per
+    microsecond of the slowest rank's time: million lattice updates / s."""
+    return cells_per_rank * steps * world / (slowest_ms * 1e3)
+
+
 def safe_reduce(solver):
     """Phase-field mass of the current state, NaN when it is not finite."""
     from paper_2003_06342_b300._binding import LBMError
@@ -205,13 +223,8 @@ def run_device(args, world, rank, local):
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
         barrier()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     mass, energy = red.tolist()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
 
     peak, peak_kind = peaks()
     result = {
@@ -288,11 +301,7 @@ def run_device(args, world, rank, local):
         torch.cuda.synchronize(dev)
         t_e2e = time.perf_counter() - t0
         barrier()
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(t_e2e, world, dev)
         h2d = 3 * w.cells * 4                      # phi, T, p staged as float32
         d2h += 5 * w.cells * 4                     # phi, T, ux, uy, p as float32
         result["e2e"] = {"value": w.cells * K * world / t_e2e / 1e6, "unit": "MLUPS",
@@ -432,6 +441,8 @@ def ncu_case(case):
     that a full-set capture stays small."""
     import torch
     from paper_2003_06342_b300 import Solver
+    if case == "2d_adjoint":
+        return ncu_case_adjoint()
     dim, storage = case.split("_")[:2]
     w = workload_c2() if dim == "2d" else W.c3_film_boiling_3d(256, 256, 128)
     s = Solver(w.n, w.periodic, w.params, storage=storage)
@@ -441,6 +452,31 @@ def ncu_case(case):
     s.step(4)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": case, "workload": w.name, "cells": w.cells}))
+
+
+def ncu_case_adjoint():
+    """Four adjoint steps (kernels A and B each) of a 2048 x 2048 evaporating
+    droplet: 4.2 M cells, 2.1 GB of adjoint traffic per step, larger than L2."""
+    import ctypes
+    import torch
+    from paper_2003_06342_b300 import Solver
+    from paper_2003_06342_b300 import _binding as Bd
+    w = W.c4_droplet(2048)
+    s = Solver(w.n, w.periodic, w.params)
+    s.init(w.phi0, w.T0)
+    state = s.get_state().clone()
+    nb, sb = ctypes.c_size_t(), ctypes.c_size_t()
+    Bd.check(Bd.lib.lbm_adjoint_bytes(s._h, ctypes.byref(nb), ctypes.byref(sb)), "lbm_adjoint_bytes")
+    a = torch.zeros(nb.value // 4, device=s.device)
+    b = torch.zeros_like(a)
+    scr = torch.zeros(sb.value // 4, device=s.device)
+    dp = torch.zeros(3, dtype=torch.float64, device=s.device)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    for _ in range(4):
+        Bd.check(Bd.lib.lbm_adjoint_step(s._h, vp(state), vp(a), vp(b), vp(scr), vp(dp)), "lbm_adjoint_step")
+        a, b = b, a
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "2d_adjoint", "workload": w.name, "cells": w.cells}))
 
 
 def main():
@@ -454,8 +490,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ncu-case", default=None,
                     choices=["2d_fp32", "2d_fp16", "2d_bf16", "3d_fp32", "3d_fp16",
-                             "2d_fp32_tma", "2d_fp16_tma"],
-                    help="only initialise one step-kernel case and run 4 steps (for ncu captures)")
+                             "2d_fp32_tma", "2d_fp16_tma", "2d_adjoint"],
+                    help="only initialise one kernel case and run 4 steps (for ncu captures)")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
@@ -472,7 +508,7 @@ def main():
         return
     w = r["workload"]
     ms_step = r["ms"] / args.steps
-    value = w.cells * args.steps * world / r["ms"] / 1e3
+    value = whole_job_mlups(w.cells, args.steps, world, r["ms"])
     bpc = BYTES_PER_CELL[("2d", "fp32")]
     achieved = bpc * w.cells / r["step_ms"] / 1e6          # GB/s
     line = {

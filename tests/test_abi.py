@@ -94,3 +94,36 @@ def test_strerror():
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert B.lib.lbm_strerror(code)
     assert B.lib.lbm_strerror(-99) == b"unknown error"
+
+
+def test_calls_reject_bad_arguments_before_device_work():
+    w = W.film_boiling_2d(16, 16)
+    r, nbytes, g, p, lat = _ws(w)
+    buf = (ctypes.c_uint8 * (nbytes + 512))()
+    base = (ctypes.addressof(buf) + 255) // 256 * 256
+    h = ctypes.c_void_p()
+    assert B.lib.lbm_create(ctypes.byref(g), lat, ctypes.byref(p), ctypes.c_void_p(base), nbytes,
+                            None, ctypes.byref(h)) == B.LBM_OK
+    f = B.lbm_fields()                       # phi and T missing
+    assert B.lib.lbm_init(h, ctypes.byref(f)) == B.LBM_EINVAL
+    assert B.lib.lbm_get_fields(h, None) == B.LBM_EINVAL
+    f.dtype = 7
+    assert B.lib.lbm_get_fields(h, ctypes.byref(f)) == B.LBM_EINVAL
+    assert B.lib.lbm_stream_map(h, 2, None, None) == B.LBM_EINVAL
+    assert B.lib.lbm_set_kernel(h, 9) == B.LBM_EINVAL
+    small = ctypes.c_size_t()
+    assert B.lib.lbm_state_bytes(h, ctypes.byref(small)) == B.LBM_OK
+    assert B.lib.lbm_get_state(h, ctypes.c_void_p(base), small.value - 1, 1) == B.LBM_ENOMEM
+    # the adjoint exists for 2D FP32 only
+    a, sc = ctypes.c_size_t(), ctypes.c_size_t()
+    assert B.lib.lbm_adjoint_bytes(h, ctypes.byref(a), ctypes.byref(sc)) == B.LBM_OK
+    assert a.value == 29 * 16 * 16 * 4 and sc.value == 9 * 16 * 16 * 4
+    B.lib.lbm_destroy(h)
+    p16 = make_params(w.params, "fp16")
+    h2 = ctypes.c_void_p()
+    r16 = ctypes.c_size_t()
+    B.lib.lbm_workspace_bytes(ctypes.byref(g), lat, ctypes.byref(p16), ctypes.byref(r16))
+    assert B.lib.lbm_create(ctypes.byref(g), lat, ctypes.byref(p16), ctypes.c_void_p(base), r16.value,
+                            None, ctypes.byref(h2)) == B.LBM_OK
+    assert B.lib.lbm_adjoint_bytes(h2, ctypes.byref(a), ctypes.byref(sc)) == B.LBM_EUNSUPPORTED
+    B.lib.lbm_destroy(h2)

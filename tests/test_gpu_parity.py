@@ -193,3 +193,19 @@ def test_tma_kernel_parity_with_oracle():
     assert s.kernel() == "tma"
     err = max_errors(gpu_fields(s), ref)
     assert all(v < TOL for v in err.values()), err
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN planted in the initial temperature reaches the fields and the
+    FP64 reduction reports it as LBM_ENONFINITE instead of a number."""
+    from paper_2003_06342_b300._binding import LBMError, LBM_ENONFINITE
+    w = _film(64, 32)
+    T0 = w.T0.copy()
+    T0[10, 20] = float("nan")
+    w.T0 = T0
+    s = gpu_solver(w)
+    s.step(3)
+    with pytest.raises(LBMError) as e:
+        s.reduce()
+    assert e.value.code == LBM_ENONFINITE
+    s.sync()                                  # the context stays usable
