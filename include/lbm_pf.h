@@ -159,11 +159,14 @@ int lbm_set_state(lbm_handle *h, const void *src, size_t bytes, int32_t on_devic
  * opposite direction).  Both buffers are device memory of Q*N entries. */
 int lbm_stream_map(lbm_handle *h, int32_t set, int32_t *src_index, int8_t *kind);
 
-/* Kernel variants of the 2D step.  AUTO (default) is the tiled kernel; TMA
- * selects the persistent TMA-staged kernel, available when the grid allows
- * 16-byte-aligned tensor boxes (row and plane strides a multiple of 16 bytes,
- * at least 66 x 18 cells).  Both compute the same update bit for bit.  3D
- * always uses the tiled z-marching kernel. */
+/* Kernel variants of the step.  AUTO (default) is the tiled kernel (plain
+ * loads).  TMA selects the variant that stages populations in shared memory
+ * with bulk tensor copies, available when the grid allows 16-byte-aligned
+ * tensor boxes: in 2D a persistent kernel (row and plane strides a multiple of
+ * 16 bytes, at least 66 x 18 cells), in 3D the z-marching kernel with each
+ * tile layer staged two layers ahead (n_x a multiple of 4 for FP32 or 8 for
+ * 16-bit storage, at least 32 x 8 cells per layer).  Tiled and TMA variants
+ * compute the same update bit for bit. */
 #define LBM_KERNEL_AUTO   0
 #define LBM_KERNEL_TILED  1
 #define LBM_KERNEL_TMA    2

@@ -34,11 +34,14 @@ def gradients(n, periodic, params, phi0, T0, phi_target, nsteps, K=100, p0=None,
     nstate = s.state_bytes()
     # forward with checkpoints every K steps
     seg_starts = list(range(0, nsteps, K))
-    checkpoints = []
-    for start in seg_starts:
-        checkpoints.append(s.get_state().clone())
+    # device buffers allocated once: one checkpoint per segment and the
+    # states of the segment being reversed
+    ckpts = torch.empty((len(seg_starts), nstate), dtype=torch.uint8, device=dev)
+    seg_states = torch.empty((min(K, max(nsteps, 1)), nstate), dtype=torch.uint8, device=dev)
+    for k, start in enumerate(seg_starts):
+        s.get_state(ckpts[k])
         s.step(min(K, nsteps - start))
-    final = s.get_state().clone()
+    final = s.get_state()
     lam = torch.zeros(adj_bytes.value // 4, dtype=torch.float32, device=dev)
     lam_next = torch.zeros_like(lam)
     scratch = torch.zeros(scr_bytes.value // 4, dtype=torch.float32, device=dev)
@@ -47,18 +50,17 @@ def gradients(n, periodic, params, phi0, T0, phi_target, nsteps, K=100, p0=None,
     vp = lambda t: ctypes.c_void_p(t.data_ptr())
     B.check(B.lib.lbm_adjoint_terminal(s._h, vp(final), vp(tgt), vp(lam_next), vp(J)),
             "lbm_adjoint_terminal")
-    for start, ckpt in zip(reversed(seg_starts), reversed(checkpoints)):
-        seg = min(K, nsteps - start)
-        s.set_state(ckpt)
-        states = [ckpt]
-        for _ in range(seg - 1):
+    for k in reversed(range(len(seg_starts))):
+        seg = min(K, nsteps - seg_starts[k])
+        s.set_state(ckpts[k])
+        seg_states[0].copy_(ckpts[k])
+        for j in range(1, seg):
             s.step(1)
-            states.append(s.get_state().clone())
-        for k in reversed(range(seg)):
-            B.check(B.lib.lbm_adjoint_step(s._h, vp(states[k]), vp(lam_next), vp(lam), vp(scratch),
-                                           vp(dparams)), "lbm_adjoint_step")
+            s.get_state(seg_states[j])
+        for j in reversed(range(seg)):
+            B.check(B.lib.lbm_adjoint_step(s._h, vp(seg_states[j]), vp(lam_next), vp(lam),
+                                           vp(scratch), vp(dparams)), "lbm_adjoint_step")
             lam, lam_next = lam_next, lam
-        del states
     dT0 = torch.zeros_like(T0_t)
     f = B.lbm_fields()
     f.phi, f.T = phi0_t.data_ptr(), T0_t.data_ptr()

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbmpf.so")
-SOURCES = ["api.cu", "lbm2d.cu", "lbm3d.cu", "reduce.cu", "noalloc.cu", "adjoint2d.cu", "lbm2d_tma.cu"]
+SOURCES = ["api.cu", "lbm2d.cu", "lbm3d.cu", "reduce.cu", "noalloc.cu", "adjoint2d.cu", "lbm2d_tma.cu",
+           "lbm3d_tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -75,7 +75,9 @@ adj_terminal2d_kernel(const float *__restrict__ st, const float *__restrict__ ta
 }
 
 // ------------------------------------------------------------------ step A
-__global__ void __launch_bounds__(256)
+// two blocks per SM: 128 registers, no spills (at one block the kernel is
+// latency bound with 8 warps per SM)
+__global__ void __launch_bounds__(256, 2)
 adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_next,
                     float *__restrict__ lam, float *__restrict__ cst, double *dparams,
                     const DevParams P) {

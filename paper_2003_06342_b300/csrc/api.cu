@@ -12,6 +12,7 @@
 #include "lbm3d.h"
 #include "adjoint.h"
 #include "lbm2d_tma.h"
+#include "lbm3d_tma.h"
 
 using namespace lbm;
 
@@ -39,6 +40,7 @@ struct lbm_handle {
     int tma_state;           // 0 not set up, 1 ready, -1 not available
     int tma_blocks;
     lbm::TmaMaps2d maps;
+    lbm::TmaMaps3d maps3;
 };
 
 namespace {
@@ -146,6 +148,9 @@ void fill_devparams(lbm_handle *h) {
     for (int set = 0; set < 3; ++set) {
         const int Q = set == 1 ? h->Qg : h->Qf;
         const double scale = p.store_scale[set] != 0.0 ? p.store_scale[set] : 1.0;
+        d.set_ref[set] = (float)p.store_ref[set];
+        d.set_sc[set] = p.storage == LBM_STORE_FP32 ? 1.0f : (float)scale;
+        d.set_isc[set] = p.storage == LBM_STORE_FP32 ? 1.0f : (float)(1.0 / scale);
         for (int i = 0; i < Q; ++i, ++k) {
             double w;   // exact lattice weights in double
             if (h->dim == 2) w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
@@ -161,17 +166,23 @@ void fill_devparams(lbm_handle *h) {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
 
 // ---- dispatch on storage type and dimension
-// Lazily prepare the TMA-staged 2D kernel (needs a device): eligibility,
-// tensor maps over this handle's buffers, shared-memory limit, grid size.
+// Lazily prepare the TMA-staged kernel of the handle's dimension (needs a
+// device): eligibility, tensor maps over this handle's buffers, shared-memory
+// limit, grid size.
 void setup_tma(lbm_handle *h) {
     h->tma_state = -1;
-    if (h->dim != 2 || !lbm::tma2d_eligible(h->dp, (int)h->elem)) return;
+    const int es = (int)h->elem;
+    if (h->dim == 2 ? !lbm::tma2d_eligible(h->dp, es) : !lbm::tma3d_eligible(h->dp, es)) return;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return;
-    const int per_sm = lbm::tma2d_blocks_per_sm((int)h->elem);
+    const int per_sm = h->dim == 2 ? lbm::tma2d_blocks_per_sm(es) : lbm::tma3d_blocks_per_sm(es);
     if (per_sm < 1) return;
-    if (lbm::make_tma_maps2d(&h->maps, h->dp, (int)h->elem, h->pops, h->q, h->phi_prev) != 0) return;
+    if (h->dim == 2) {
+        if (lbm::make_tma_maps2d(&h->maps, h->dp, es, h->pops, h->q, h->phi_prev) != 0) return;
+    } else {
+        if (lbm::make_tma_maps3d(&h->maps3, h->dp, es, h->pops, h->q, h->phi_prev) != 0) return;
+    }
     if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return;
     h->tma_blocks = sms * per_sm;
     h->tma_state = 1;
@@ -195,6 +206,18 @@ int do_step(lbm_handle *h) {
             return LBM_OK;
         }
         if (h->kernel_choice == LBM_KERNEL_TMA) return LBM_EUNSUPPORTED;
+    }
+    if (h->dim == 3 && h->kernel_choice == LBM_KERNEL_TMA) {
+        if (h->tma_state == 0) setup_tma(h);
+        if (h->tma_state != 1) return LBM_EUNSUPPORTED;
+        switch (h->params.storage) {
+        case LBM_STORE_FP32: e = launch_step3d_tma<float>(h->maps3, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
+        case LBM_STORE_FP16: e = launch_step3d_tma<__half>(h->maps3, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
+        default: e = launch_step3d_tma<__nv_bfloat16>(h->maps3, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
+        }
+        if (e != cudaSuccess) return LBM_ECUDA;
+        h->cur = nxt;
+        return LBM_OK;
     }
     if (h->dim == 2) {
         switch (h->params.storage) {
@@ -526,7 +549,7 @@ int lbm_set_kernel(lbm_handle *h, int32_t kernel) {
 
 int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
     if (!h || !kernel) return LBM_EINVAL;
-    if (h->dim == 2 && h->kernel_choice == LBM_KERNEL_TMA && h->tma_state == 1) *kernel = LBM_KERNEL_TMA;
+    if (h->kernel_choice == LBM_KERNEL_TMA && h->tma_state == 1) *kernel = LBM_KERNEL_TMA;
     else *kernel = LBM_KERNEL_TILED;
     return LBM_OK;
 }

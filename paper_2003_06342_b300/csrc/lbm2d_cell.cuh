@@ -35,9 +35,9 @@ __device__ __forceinline__ void closures2d(Macro2 &m, const DevParams &P) {
     m.rho = density(phi, P);
     m.grx = P.drho * m.gx;
     m.gry = P.drho * m.gy;
-    const float mu = 4.0f * P.H * phi * (phi - 1.0f) * (phi - 0.5f) - P.K * m.lap;
-    m.Fx = mu * m.gx + (m.rho - P.rho_l) * P.gravity[0] + P.body[0];
-    m.Fy = mu * m.gy + (m.rho - P.rho_l) * P.gravity[1] + P.body[1];
+    const float mu = fmaf(-P.K, m.lap, 4.0f * P.H * phi * (phi - 1.0f) * (phi - 0.5f));
+    m.Fx = fmaf(mu, m.gx, fmaf(m.rho - P.rho_l, P.gravity[0], P.body[0]));
+    m.Fy = fmaf(mu, m.gy, fmaf(m.rho - P.rho_l, P.gravity[1], P.body[1]));
 }
 
 // Moments of the post-streaming populations (Eqs. Velocity, Pressure,
@@ -94,26 +94,102 @@ __device__ __forceinline__ void normal2d(float gx, float gy, float eps2, float &
 }
 
 // ------------------------------------------------------------------ step
-// +-v or 0 for a lattice component e in {-1, 0, 1}, and e.(a, b) without
-// multiplications (e is a compile-time constant once the loops are unrolled)
-__device__ __forceinline__ float sgnv(int e, float v) { return e > 0 ? v : -v; }
-__device__ __forceinline__ float edot(int ex, int ey, float a, float b) {
-    return ex == 0 ? (ey == 0 ? 0.0f : sgnv(ey, b))
-                   : (ey == 0 ? sgnv(ex, a) : sgnv(ex, a) + sgnv(ey, b));
+// Sums over one D2Q9 set in the working representation v (see IsNarrow):
+// sum_i mu_i v_i = sum_i theta_i - ref and sum_i mu_i e_i v_i, with mu_i = 1
+// for FP32 and w_i / scale for the 16-bit formats.  Every kernel that forms
+// phi from the stored g uses set_sum2d, so a cell's phi is the same float
+// wherever it is computed.
+template <typename S>
+__device__ __forceinline__ float set_sum2d(const float v[9], float inv_sc) {
+    const float ax = (v[1] + v[3]) + (v[2] + v[4]);
+    const float dg = (v[5] + v[7]) + (v[6] + v[8]);
+    if (!IsNarrow<S>::value) return v[0] + (ax + dg);
+    return fmaf(4.0f / 9.0f, v[0], fmaf(1.0f / 9.0f, ax, (1.0f / 36.0f) * dg)) * inv_sc;
 }
 
+template <typename S>
+__device__ __forceinline__ void set_flux2d(const float v[9], float inv_sc, float &jx, float &jy) {
+    const float ax = v[1] - v[3], ay = v[2] - v[4];
+    const float d57 = v[5] - v[7], d86 = v[8] - v[6];        // e5 = (1,1), e8 = (1,-1)
+    if (!IsNarrow<S>::value) {
+        jx = ax + (d57 + d86);
+        jy = ay + (d57 - d86);
+    } else {
+        jx = fmaf(1.0f / 9.0f, ax, (1.0f / 36.0f) * (d57 + d86)) * inv_sc;
+        jy = fmaf(1.0f / 9.0f, ay, (1.0f / 36.0f) * (d57 - d86)) * inv_sc;
+    }
+}
+
+// Multiplier taking a per-weight post-collision increment to the working
+// representation: w_i for FP32 deviations, the set's scale for 16-bit values.
+template <typename S>
+__device__ __forceinline__ float rep_mul(int i, int set, const DevParams &P) {
+    return IsNarrow<S>::value ? P.set_sc[set] : L::w(i);
+}
+
+// Push of direction i's three post-collision values (working representation)
+// from cell c = (x, y).  FAST: the link neither wraps nor meets a wall.
+template <typename S, bool FAST>
+__device__ __forceinline__ void push2d(int i, float vf, float vg, float vs, int x, int y, size_t c,
+                                       S *__restrict__ pout, const DevParams &P) {
+    const int ex = L::ex(i), ey = L::ey(i);
+    const int nx = P.n[0], ny = P.n[1];
+    const size_t N = (size_t)P.N;
+    if (FAST) {
+        S *dst = pout + c + ((long long)ey * nx + ex);
+        dst[i * N] = narrow<S>(vf);
+        dst[(9 + i) * N] = narrow<S>(vg);
+        dst[(18 + i) * N] = narrow<S>(vs);
+        return;
+    }
+    int dx = x + ex, dy = y + ey;
+    const int kx = wrap_coord(dx, nx, P.periodic[0]);
+    const int ky = wrap_coord(dy, ny, P.periodic[1]);
+    if (kx >= 2 || ky >= 2) {
+        // half-way bounce-back (f) and anti-bounce-back (g, s): back into c,
+        // opposite direction; the Dirichlet term 2 w (value - ref) in the
+        // working representation
+        const int side = (kx >= 2 ? kx : ky) - 2;
+        const int o = L::opp(i);
+        pout[o * N + c] = narrow<S>(vf);
+        pout[(9 + o) * N + c] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 1, P), P.phi_wall[side] - P.g_ref, -vg));
+        pout[(18 + o) * N + c] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 2, P), P.T_wall[side] - P.s_ref, -vs));
+    } else {
+        const size_t d = (size_t)dy * nx + dx;
+        pout[i * N + d] = narrow<S>(vf);
+        pout[(9 + i) * N + d] = narrow<S>(vg);
+        pout[(18 + i) * N + d] = narrow<S>(vs);
+    }
+}
+
+// Per-cell coefficients of the three collisions.  With poly_i = Gamma_i/w_i - 1
+// = 3 e.u + P_e, P_e = 4.5 (e.u)^2 - 1.5 u^2 (even in e), the post-collision
+// value of direction i of each set, in the form
+//   theta*_i - w_i ref = (1 - om)(theta_i - w_i ref) + w_i [E(e_i) + O(e_i)]
+// (algebraically Eq. LBE with theta_eq_bar = theta_eq - S/2), splits into a
+// part E even in e_i and a part O odd in e_i, so a direction and its opposite
+// share every product:
+//   g: E = Ag + Bg P_e,                     O = e.Vg
+//   f: E = K0 + K1 P_e + 3 (e.u)(e.Hf),     O = e.Vf + P_e (e.Hf)
+//   s: E = As + Bs P_e,                     O = e.Ws
+struct Coef2 {
+    float a_g, a_f, a_s;
+    float Ag, Bg, Vgx, Vgy;
+    float K0, K1, Hx, Hy, Vfx, Vfy;
+    float As, Bs, Wx, Wy;
+};
+
 // Update of one cell from a window of phi - phi_ref (`sp` points at the
-// cell, rows `pitch` floats apart) and the cell's own populations: stencils,
-// closures, moments, production rate, the three collisions and the push into
-// pout.  FAST: no link of the cell wraps or meets a wall.
+// cell, rows `pitch` floats apart) and the cell's own populations in the
+// working representation: stencils, closures, moments, production rate, the
+// three collisions and the push into pout.  FAST: no link of the cell wraps or
+// meets a wall.
 template <typename S, bool FAST>
 __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const float f[9],
                                               const float g[9], const float s[9], float phip,
                                               float qp, int x, int y, size_t c,
                                               S *__restrict__ pout, float *__restrict__ phi_prev,
                                               float *__restrict__ q_out, const DevParams &P) {
-    const int nx = P.n[0], ny = P.n[1];
-    const size_t N = (size_t)P.N;
     // stencils, pair-folded: each (i, opposite) pair of Eqs. Grad and
     // Laplacian contributes w_i e_i (phi_i - phi_i') and 2 w_i (phi_i + phi_i' - 2 phi)
     // the window holds phi - phi_ref; differences are unaffected by the shift
@@ -125,96 +201,118 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     m.phi = ph;
     {
         const float dA = pNE - pSW, dB = pSE - pNW;
-        m.gx = 3.0f * ((1.0f / 9.0f) * (pE - pW) + (1.0f / 36.0f) * (dA + dB));
-        m.gy = 3.0f * ((1.0f / 9.0f) * (pN - pS) + (1.0f / 36.0f) * (dA - dB));
-        m.lap = 6.0f * ((1.0f / 9.0f) * ((pE + pW) + (pN + pS) - 4.0f * phd)
-                      + (1.0f / 36.0f) * ((pNE + pSW) + (pNW + pSE) - 4.0f * phd));
+        m.gx = 3.0f * fmaf(1.0f / 9.0f, pE - pW, (1.0f / 36.0f) * (dA + dB));
+        m.gy = 3.0f * fmaf(1.0f / 9.0f, pN - pS, (1.0f / 36.0f) * (dA - dB));
+        const float la = fmaf(-4.0f, phd, (pE + pW) + (pN + pS));
+        const float ld = fmaf(-4.0f, phd, (pNE + pSW) + (pNW + pSE));
+        m.lap = 6.0f * fmaf(1.0f / 9.0f, la, (1.0f / 36.0f) * ld);
     }
     closures2d(m, P);
     // moments (Eqs. Velocity, Pressure, Moment_Temp)
-    const float jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
-    const float jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-    float sf = f[0], ss = s[0];
-#pragma unroll
-    for (int i = 1; i < 9; ++i) { sf += f[i]; ss += s[i]; }
-    const float inv_rho = __frcp_rn(m.rho);
-    m.ux = (3.0f * jx + 0.5f * m.Fx) * inv_rho;
-    m.uy = (3.0f * jy + 0.5f * m.Fy) * inv_rho;
+    float jx, jy;
+    set_flux2d<S>(f, P.set_isc[0], jx, jy);
+    const float sf = set_sum2d<S>(f, P.set_isc[0]) + P.set_ref[0];
+    const float ss = set_sum2d<S>(s, P.set_isc[2]);                  // T - T_ref
+    const float inv_rho = rcp_approx(m.rho);
+    m.ux = fmaf(0.5f, m.Fx, 3.0f * jx) * inv_rho;
+    m.uy = fmaf(0.5f, m.Fy, 3.0f * jy) * inv_rho;
     const float rcs2 = m.rho * L::cs2;
-    m.p = sf + 0.5f * (L::cs2 * (m.ux * m.grx + m.uy * m.gry) + rcs2 * qp * P.kappa);
-    const float ug = m.ux * m.gx + m.uy * m.gy;
-    m.Td = ss - 0.5f * P.L_over_Cp * ((phd - phip) + ug + ph * qp * P.kappa);
+    const float ugr = fmaf(m.ux, m.grx, m.uy * m.gry);
+    m.p = fmaf(0.5f, fmaf(L::cs2, ugr, (rcs2 * qp) * P.kappa), sf);
+    const float ug = fmaf(m.ux, m.gx, m.uy * m.gy);
+    m.Td = fmaf(-0.5f * P.L_over_Cp, fmaf(ph * qp, P.kappa, (phd - phip) + ug), ss);
     m.T = m.Td + P.s_ref;
 
     const float q = production(ph, m.T, P);
-    const float inv_d = __frcp_rn(sqrtf(fmaxf(m.gx * m.gx + m.gy * m.gy, P.eps2)));
+    const float inv_d = rsqrt_approx(fmaxf(fmaf(m.gx, m.gx, m.gy * m.gy), P.eps2));
     const float nx_ = m.gx * inv_d, ny_ = m.gy * inv_d;
+    const float phu = unit_phi(ph);
+    float om_f;
+    if (P.visc_interp == 0) {
+        // 1 / (nu / cs2 + 1/2) with the harmonic nu = nu_l nu_g / den
+        const float den = fmaf(phu, P.nu_l - P.nu_g, P.nu_g);
+        om_f = den * rcp_approx(fmaf(0.5f, den, 3.0f * P.nu_l * P.nu_g));
+    } else {
+        om_f = rcp_approx(fmaf(L::inv_cs2, fmaf(phu, P.nu_g - P.nu_l, P.nu_l), 0.5f));
+    }
+    const float om_s = rcp_approx(fmaf(L::inv_cs2, diffusivity(ph, P), 0.5f));
     const float om_g = P.om_g;
-    const float om_f = __frcp_rn(viscosity(ph, P) * L::inv_cs2 + 0.5f);
-    const float om_s = __frcp_rn(diffusivity(ph, P) * L::inv_cs2 + 0.5f);
-    const float D = (phd - phip) + ug + ph * q * P.kappa;
+    const float D = fmaf(ph * q, P.kappa, (phd - phip) + ug);
 
     phi_prev[c] = phd;          // stored as phi - phi_ref
     q_out[c] = q;
 
-    // collision in the form theta* = (1 - om) theta + om theta_eq + (1 - om/2) S,
-    // algebraically identical to Eq. LBE with theta_eq_bar = theta_eq - S/2
-    const float usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy);
+    const float ux = m.ux, uy = m.uy;
+    const float b_g = fmaf(-0.5f, om_g, 1.0f), b_f = fmaf(-0.5f, om_f, 1.0f);
+    const float b_s = fmaf(-0.5f, om_s, 1.0f);
+    Coef2 k;
+    k.a_g = 1.0f - om_g; k.a_f = 1.0f - om_f; k.a_s = 1.0f - om_s;
+    // g: F^g + P^g = w (iface e.n + q); g_eq - w phi_ref = w (phd + phi poly)
     const float iface = P.four_over_W * ph * (1.0f - ph);
-    const float gAx = L::cs2 * m.grx, gAy = L::cs2 * m.gry;
-    const float uA = m.ux * gAx + m.uy * gAy;
-    const float uB = m.ux * m.Fx + m.uy * m.Fy;
-    const float pf = rcs2 * q * P.kappa;                 // P^f_i / w_i
-    const float a_g = 1.0f - om_g, b_g = 1.0f - 0.5f * om_g;
-    const float a_f = 1.0f - om_f, b_f = 1.0f - 0.5f * om_f;
-    const float a_s = 1.0f - om_s, b_s = 1.0f - 0.5f * om_s;
-    const float bsw = b_s * (-P.L_over_Cp * D);          // (1 - om_s/2) S^s_i / w_i
-    const float Tref = P.s_ref;
+    k.Ag = fmaf(om_g, phd, b_g * q);
+    k.Bg = om_g * ph;
+    const float bgi = b_g * iface;
+    k.Vgx = fmaf(3.0f * k.Bg, ux, bgi * nx_);
+    k.Vgy = fmaf(3.0f * k.Bg, uy, bgi * ny_);
+    // f: f_eq = w (p + rho cs2 poly); F^f + P^f = w [(e.F - u.F + pf) + poly (e.H - u.H)]
+    // with H = cs2 grad(rho) + F (Eq. Forcing with Gamma_i = w_i (1 + poly_i))
+    const float hx = fmaf(L::cs2, m.grx, m.Fx), hy = fmaf(L::cs2, m.gry, m.Fy);
+    const float hU = fmaf(ux, hx, uy * hy);
+    const float uB = fmaf(ux, m.Fx, uy * m.Fy);
+    // P^f_i / w_i = rho cs2 q kappa, here minus u.F
+    k.K0 = fmaf(om_f, m.p - P.set_ref[0], b_f * fmaf(rcs2 * q, P.kappa, -uB));
+    k.K1 = fmaf(om_f, rcs2, -b_f * hU);
+    k.Hx = b_f * hx; k.Hy = b_f * hy;
+    k.Vfx = fmaf(3.0f * k.K1, ux, b_f * m.Fx);
+    k.Vfy = fmaf(3.0f * k.K1, uy, b_f * m.Fy);
+    // s: s_eq - w T_ref = w (Td + T poly); S^s = -w (L/Cp) D
+    k.As = fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D);
+    k.Bs = om_s * m.T;
+    // __fmul_rn: W enters E +- W as a finished product, never fused into the sum
+    k.Wx = __fmul_rn(3.0f * k.Bs, ux); k.Wy = __fmul_rn(3.0f * k.Bs, uy);
 
+    // even parts P_e of poly: rest, x axis, y axis, diagonals (1,1) and (-1,1)
+    const float uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
+    const float usq = fmaf(ux, ux, uyy);
+    const float P0 = -1.5f * usq;
+    const float Pxa = fmaf(3.0f, uxx, -1.5f * uyy), Pya = fmaf(3.0f, uyy, -1.5f * uxx);
+    const float Pd0 = 3.0f * usq;
+
+    // rest
+    push2d<S, FAST>(0,
+        fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)),
+        fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)),
+        fmaf(k.a_s, s[0], rep_mul<S>(0, 2, P) * fmaf(k.Bs, P0, k.As)), x, y, c, pout, P);
+    // a direction i with e = (ex, ey) and its opposite o
+    auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eVf, float eW) {
+        const float Eg = fmaf(k.Bg, Pe, k.Ag);
+        const float Ef = fmaf(3.0f * cu, eH, fmaf(k.K1, Pe, k.K0));
+        const float Of = fmaf(Pe, eH, eVf);
+        const float Es = fmaf(k.Bs, Pe, k.As);
+        const float mf = rep_mul<S>(i, 0, P), mg = rep_mul<S>(i, 1, P), ms = rep_mul<S>(i, 2, P);
+        push2d<S, FAST>(i, fmaf(k.a_f, f[i], mf * (Ef + Of)), fmaf(k.a_g, g[i], mg * (Eg + eVg)),
+                        fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P);
+        push2d<S, FAST>(o, fmaf(k.a_f, f[o], mf * (Ef - Of)), fmaf(k.a_g, g[o], mg * (Eg - eVg)),
+                        fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P);
+    };
+    pair(1, 3, ux, Pxa, k.Vgx, k.Hx, k.Vfx, k.Wx);                               // (1, 0)
+    pair(2, 4, uy, Pya, k.Vgy, k.Hy, k.Vfy, k.Wy);                               // (0, 1)
+    // the diagonal components are sums of products: __fadd_rn / __fsub_rn keep
+    // the compiler from fusing one of the products into the sum
+    pair(5, 7, __fadd_rn(ux, uy), fmaf(9.0f, uxy, Pd0), __fadd_rn(k.Vgx, k.Vgy),
+         __fadd_rn(k.Hx, k.Hy), __fadd_rn(k.Vfx, k.Vfy), __fadd_rn(k.Wx, k.Wy));          // (1, 1)
+    pair(6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(k.Vgy, k.Vgx),
+         __fsub_rn(k.Hy, k.Hx), __fsub_rn(k.Vfy, k.Vfx), __fsub_rn(k.Wy, k.Wx));          // (-1, 1)
+}
+
+// phi - phi_ref of one cell from its nine stored g values and lagged source
+template <typename S>
+__device__ __forceinline__ float phid_cell2d(const S *__restrict__ pin, size_t cc, size_t N,
+                                             float qv, const DevParams &P) {
+    float v[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int ex = L::ex(i), ey = L::ey(i);
-        const float w = L::w(i);
-        const float cu = edot(ex, ey, m.ux, m.uy);
-        const float poly = cu * fmaf(4.5f, cu, 3.0f) - usq15;     // Gamma_i / w_i - 1
-        const float G = fmaf(w, poly, w);                          // Eq. FunctionGamma
-        const float Gw = w * poly;
-        // phase field: F^g + P^g = w (iface e.n + q)
-        const float Sg = w * (ex == 0 && ey == 0 ? q : fmaf(iface, edot(ex, ey, nx_, ny_), q));
-        // phase field in deviation form: g_eq - w phi_ref = (phi - phi_ref) G + phi_ref (G - w)
-        const float gs = fmaf(a_g, g[i], fmaf(om_g, fmaf(phd, G, P.g_ref * Gw), b_g * Sg));
-        // flow: f_eq = w (p + rho cs2 poly), F^f + P^f
-        const float feq = w * fmaf(rcs2, poly, m.p);
-        const float fS = fmaf(Gw, edot(ex, ey, gAx, gAy) - uA, fmaf(G, edot(ex, ey, m.Fx, m.Fy) - uB, w * pf));
-        const float fs = fmaf(a_f, f[i], fmaf(om_f, feq, b_f * fS));
-        // temperature, deviation form: s_eq - w T_ref = (T - T_ref) G + T_ref (G - w)
-        const float seq = fmaf(m.Td, G, Tref * Gw);
-        const float ssv = fmaf(a_s, s[i], fmaf(om_s, seq, w * bsw));
-        if (FAST) {
-            const long long off = (long long)ey * nx + ex;
-            S *dst = pout + c + off;
-            Codec<S>::store(dst + i * N, fs, i, P);
-            Codec<S>::store_dev(dst + (9 + i) * N, gs, 9 + i, P);
-            Codec<S>::store_dev(dst + (18 + i) * N, ssv, 18 + i, P);
-        } else {
-            int dx = x + ex, dy = y + ey;
-            const int kx = wrap_coord(dx, nx, P.periodic[0]);
-            const int ky = wrap_coord(dy, ny, P.periodic[1]);
-            if (kx >= 2 || ky >= 2) {
-                const int side = (kx >= 2 ? kx : ky) - 2;
-                const int o = L::opp(i);
-                const float w2 = 2.0f * w;
-                Codec<S>::store(pout + o * N + c, fs, o, P);
-                Codec<S>::store_dev(pout + (9 + o) * N + c, -gs + w2 * (P.phi_wall[side] - P.g_ref), 9 + o, P);
-                Codec<S>::store_dev(pout + (18 + o) * N + c, -ssv + w2 * (P.T_wall[side] - P.s_ref), 18 + o, P);
-            } else {
-                const size_t d = (size_t)dy * nx + dx;
-                Codec<S>::store(pout + i * N + d, fs, i, P);
-                Codec<S>::store_dev(pout + (9 + i) * N + d, gs, 9 + i, P);
-                Codec<S>::store_dev(pout + (18 + i) * N + d, ssv, 18 + i, P);
-            }
-        }
-    }
+    for (int i = 0; i < 9; ++i) v[i] = load_raw(pin + (9 + i) * N + cc);
+    return fmaf(0.5f, qv, set_sum2d<S>(v, P.set_isc[1]));
 }
 
 // The whole update of one tile.  FAST: the tile and its halo ring lie inside
@@ -235,17 +333,14 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     float f[9], g[9], s[9], phip = 0.0f, qp = 0.0f;
     if (active) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = Codec<S>::load_dev(pin + (9 + i) * N + c, 9 + i, P);
+        for (int i = 0; i < 9; ++i) g[i] = load_raw(pin + (9 + i) * N + c);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = Codec<S>::load(pin + i * N + c, i, P);
+        for (int i = 0; i < 9; ++i) f[i] = load_raw(pin + i * N + c);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s[i] = Codec<S>::load_dev(pin + (18 + i) * N + c, 18 + i, P);
+        for (int i = 0; i < 9; ++i) s[i] = load_raw(pin + (18 + i) * N + c);
         phip = phi_prev[c];
         qp = q_in[c];
-        float ph = g[0];
-#pragma unroll
-        for (int i = 1; i < 9; ++i) ph += g[i];
-        sphi[(ty + 1) * SX + tx + 1] = ph + 0.5f * qp;      // phi - phi_ref
+        sphi[(ty + 1) * SX + tx + 1] = fmaf(0.5f, qp, set_sum2d<S>(g, P.set_isc[1]));   // phi - phi_ref
     }
     if (FAST) {
         // the 2*SX + 2*TY halo cells, one per thread
@@ -257,10 +352,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
             else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
             else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
             const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
-            float v = Codec<S>::load_dev(pin + 9 * N + cc, 9, P);
-#pragma unroll
-            for (int i = 1; i < 9; ++i) v += Codec<S>::load_dev(pin + (9 + i) * N + cc, 9 + i, P);
-            sphi[sy * SX + sx] = v + 0.5f * q_in[cc];
+            sphi[sy * SX + sx] = phid_cell2d<S>(pin, cc, N, q_in[cc], P);
         }
     } else {
         // halo ring and ragged-tile slots: phi at the (wrapped) neighbour
@@ -278,10 +370,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
             else if (ky >= 2) v = P.phi_wall[ky - 2] - P.g_ref;
             else {
                 const size_t cc = (size_t)cy * nx + cx;
-                v = Codec<S>::load_dev(pin + 9 * N + cc, 9, P);
-#pragma unroll
-                for (int i = 1; i < 9; ++i) v += Codec<S>::load_dev(pin + (9 + i) * N + cc, 9 + i, P);
-                v += 0.5f * q_in[cc];
+                v = phid_cell2d<S>(pin, cc, N, q_in[cc], P);
             }
             sphi[sidx] = v;
         }

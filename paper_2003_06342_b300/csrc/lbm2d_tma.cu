@@ -30,6 +30,7 @@
 #include "lbm_kernels.h"
 #include "lbm2d_cell.cuh"
 #include "lbm2d_tma.h"
+#include "tma_util.cuh"
 
 namespace lbm {
 
@@ -58,53 +59,6 @@ template <typename S> struct TmaGeom {
     static constexpr unsigned TX_BYTES = GC_BYTES + 2 * GS_BYTES + QC_BYTES + 2 * QS_BYTES +
                                          2 * F_BYTES + PP_BYTES;
 };
-
-constexpr int WAIT_LIMIT = 1 << 22;      // try_wait rounds before giving up
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\t"
-                 "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
-                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < WAIT_LIMIT; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            uint64_t *bar) {
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3, %4}], [%5];"
-                 ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar) {
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3}], [%4];"
-                 ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-                 : "memory");
-}
 
 __device__ __forceinline__ bool tile_is_fast(int x0, int y0, const DevParams &P) {
     return x0 >= 1 && x0 + TX + 1 <= P.n[0] && y0 >= 1 && y0 + TY + 1 <= P.n[1];
@@ -203,10 +157,10 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
                 else { gb = GC; col = sx - 1; w = TX; qv = QC[sy * TX + sx - 1]; }
                 const int gi = sy * w + col;
                 const int plane = Gm::GH * w;
-                float v = Codec<S>::dec_dev(gb[gi], 9, P);
+                float v[9];
 #pragma unroll
-                for (int i = 1; i < 9; ++i) v += Codec<S>::dec_dev(gb[i * plane + gi], 9 + i, P);
-                sphi[sidx] = v + 0.5f * qv;
+                for (int i = 0; i < 9; ++i) v[i] = widen(gb[i * plane + gi]);
+                sphi[sidx] = fmaf(0.5f, qv, set_sum2d<S>(v, P.set_isc[1]));
             }
             __syncthreads();
             float f[9], g[9], s[9];
@@ -214,9 +168,9 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
             const int gown = (ty + 1) * TX + tx;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                f[i] = Codec<S>::dec(F[i * TY * TX + own], i, P);
-                g[i] = Codec<S>::dec_dev(GC[i * Gm::GH * TX + gown], 9 + i, P);
-                s[i] = Codec<S>::dec_dev(Sv[i * TY * TX + own], 18 + i, P);
+                f[i] = widen(F[i * TY * TX + own]);
+                g[i] = widen(GC[i * Gm::GH * TX + gown]);
+                s[i] = widen(Sv[i * TY * TX + own]);
             }
             const float phip = PP[own];
             const float qp = QC[(ty + 1) * TX + tx];
@@ -244,18 +198,6 @@ bool tma2d_eligible(const DevParams &P, int elem_bytes) {
     if ((nx * elem_bytes) % 16 != 0 || (nx * 4) % 16 != 0) return false;
     if ((P.N * elem_bytes) % 16 != 0) return false;
     return true;
-}
-
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
 }
 
 int make_tma_maps2d(TmaMaps2d *M, const DevParams &P, int elem_bytes, void *const pops[2],

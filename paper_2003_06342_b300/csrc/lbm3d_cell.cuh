@@ -1,0 +1,486 @@
+// Per-cell pieces of the 3D step (D3Q19 for f and s, D3Q7 for g), shared by
+// the z-marching kernel that loads with plain loads (lbm3d.cu) and the one
+// that stages each layer with bulk tensor copies (lbm3d_tma.cu).
+#pragma once
+
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+using LF = D3Q19L;   // f and s
+using LG = D3Q7L;    // g
+constexpr int TX = 32, TY = 8, SX = TX + 2, SY = TY + 2, PLANE = SX * SY;
+constexpr int ZB = 32;                       // z planes per block
+constexpr int QF = 19, QG = 7;
+constexpr int G0 = QF, S0 = QF + QG;         // first plane of g and of s
+
+struct Macro3 {
+    float phi, g[3], lap, rho, gr[3], F[3], u[3], p, T, Td;   // Td = T - T_ref
+};
+
+// nb[i] = phi(x + e_i) over the D3Q19 directions
+__device__ __forceinline__ void stencil3d(const float nb[QF], float g[3], float &lap) {
+    const float phi = nb[0];
+    g[0] = g[1] = g[2] = 0.0f;
+    lap = 0.0f;
+#pragma unroll
+    for (int i = 1; i < QF; ++i) {
+        const float plus = nb[i], minus = nb[LF::opp(i)];
+        const float dir = (plus - minus) * 0.5f;
+        const float sec = plus - 2.0f * phi + minus;
+        if (LF::ex(i) != 0) g[0] += (LF::w(i) * (float)LF::ex(i)) * dir;
+        if (LF::ey(i) != 0) g[1] += (LF::w(i) * (float)LF::ey(i)) * dir;
+        if (LF::ez(i) != 0) g[2] += (LF::w(i) * (float)LF::ez(i)) * dir;
+        lap += LF::w(i) * sec;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[a] *= LF::inv_cs2;
+    lap *= LF::inv_cs2;
+}
+
+__device__ __forceinline__ void closures3d(Macro3 &m, const DevParams &P) {
+    const float phi = m.phi;
+    m.rho = density(phi, P);
+    const float mu = fmaf(-P.K, m.lap, 4.0f * P.H * phi * (phi - 1.0f) * (phi - 0.5f));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        m.gr[a] = P.drho * m.g[a];
+        m.F[a] = fmaf(mu, m.g[a], fmaf(m.rho - P.rho_l, P.gravity[a], P.body[a]));
+    }
+}
+
+__device__ __forceinline__ void moments3d(Macro3 &m, const float f[QF], const float s[QF],
+                                          float phi_prev, float q_prev, const DevParams &P) {
+    closures3d(m, P);
+    float j[3] = {0.0f, 0.0f, 0.0f};
+    float sf = f[0], ss = s[0];
+#pragma unroll
+    for (int i = 1; i < QF; ++i) {
+        if (LF::ex(i) != 0) j[0] += (float)LF::ex(i) * f[i];
+        if (LF::ey(i) != 0) j[1] += (float)LF::ey(i) * f[i];
+        if (LF::ez(i) != 0) j[2] += (float)LF::ez(i) * f[i];
+        sf += f[i];
+        ss += s[i];
+    }
+    float ugr = 0.0f, ug = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        m.u[a] = (j[a] * LF::inv_cs2 + 0.5f * m.F[a]) / m.rho;
+        ugr += m.u[a] * m.gr[a];
+        ug += m.u[a] * m.g[a];
+    }
+    m.p = sf + 0.5f * (LF::cs2 * ugr + m.rho * LF::cs2 * q_prev * P.kappa);
+    m.Td = ss - 0.5f * P.L_over_Cp * ((m.phi - phi_prev) + ug + m.phi * q_prev * P.kappa);
+    m.T = m.Td + P.s_ref;
+}
+
+__device__ __forceinline__ void normal3d(const float g[3], float eps2, float n[3]) {
+    const float d = sqrtf(fmaxf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2], eps2));
+    n[0] = g[0] / d; n[1] = g[1] / d; n[2] = g[2] / d;
+}
+
+// Gamma_i (Eq. FunctionGamma) on lattice Lt with its own cs^2
+template <class Lt>
+__device__ __forceinline__ float gamma_i(int i, const float u[3], float usq) {
+    const float cu = (float)Lt::ex(i) * u[0] + (float)Lt::ey(i) * u[1] + (float)Lt::ez(i) * u[2];
+    return Lt::w(i) * (1.0f + cu * Lt::inv_cs2 + cu * cu * (0.5f * Lt::inv_cs2 * Lt::inv_cs2)
+                       - usq * (0.5f * Lt::inv_cs2));
+}
+
+// barred equilibrium and source of g (D3Q7)
+__device__ __forceinline__ void g_eq_src(int i, const Macro3 &m, const float n[3], float q, float usq,
+                                         const DevParams &P, float &eqb, float &src) {
+    const float G = gamma_i<LG>(i, m.u, usq);
+    const float en = (float)LG::ex(i) * n[0] + (float)LG::ey(i) * n[1] + (float)LG::ez(i) * n[2];
+    src = P.four_over_W * m.phi * (1.0f - m.phi) * LG::w(i) * en + LG::w(i) * q;
+    eqb = m.phi * G - 0.5f * src;
+}
+
+// barred equilibria and sources of f and s (D3Q19)
+__device__ __forceinline__ void fs_eq_src(int i, const Macro3 &m, float q, float D, float usq,
+                                          const DevParams &P, float &feqb, float &fS, float &seqb,
+                                          float &sS) {
+    const float w = LF::w(i);
+    const float e[3] = {(float)LF::ex(i), (float)LF::ey(i), (float)LF::ez(i)};
+    const float cu = e[0] * m.u[0] + e[1] * m.u[1] + e[2] * m.u[2];
+    const float poly = 3.0f * cu + 4.5f * cu * cu - 1.5f * usq;
+    const float G = w * (1.0f + poly);
+    const float Gw = G - w;
+    float F = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F += (e[a] - m.u[a]) * (Gw * m.gr[a] * LF::cs2 + G * m.F[a]);
+    fS = F + w * m.rho * LF::cs2 * q * P.kappa;
+    feqb = w * (m.p + m.rho * LF::cs2 * poly) - 0.5f * fS;
+    sS = -w * P.L_over_Cp * D;
+    seqb = m.Td * G + P.s_ref * (w * poly) - 0.5f * sS;   // deviation from w_i T_ref
+}
+
+// ------------------------------------------------------------------ step
+// The step works on the working representation of the stored values (the
+// raw number widened to float, see IsNarrow): FP32 deviations theta - w ref,
+// or 16-bit (theta / w - ref) * scale.  theta = w ref + mu v with mu = 1 or
+// w / scale.
+
+// sum_i mu_i v_i over D3Q7 (g) and D3Q19 (f, s) sets
+template <typename S>
+__device__ __forceinline__ float set_sum7(const float v[QG], float inv_sc) {
+    const float ax = ((v[1] + v[4]) + (v[2] + v[5])) + (v[3] + v[6]);
+    if (!IsNarrow<S>::value) return v[0] + ax;
+    return fmaf(0.25f, v[0], 0.125f * ax) * inv_sc;
+}
+
+template <typename S>
+__device__ __forceinline__ float set_sum19(const float v[QF], float inv_sc) {
+    const float ax = ((v[1] + v[4]) + (v[2] + v[5])) + (v[3] + v[6]);
+    const float dg = (((v[7] + v[10]) + (v[8] + v[9])) + ((v[11] + v[14]) + (v[12] + v[13])))
+                   + ((v[15] + v[18]) + (v[16] + v[17]));
+    if (!IsNarrow<S>::value) return v[0] + (ax + dg);
+    return fmaf(1.0f / 3.0f, v[0], fmaf(1.0f / 18.0f, ax, (1.0f / 36.0f) * dg)) * inv_sc;
+}
+
+__device__ __forceinline__ float sgnv(int e, float v) { return e > 0 ? v : -v; }
+// e.(a, b, c) for e in {-1, 0, 1}^3 without multiplications; __fadd_rn keeps
+// a product among a, b, c from being fused into the sum
+__device__ __forceinline__ float edot3(int ex, int ey, int ez, float a, float b, float c) {
+    float r = 0.0f;
+    bool any = false;
+    if (ex != 0) { r = sgnv(ex, a); any = true; }
+    if (ey != 0) { r = any ? __fadd_rn(r, sgnv(ey, b)) : sgnv(ey, b); any = true; }
+    if (ez != 0) { r = any ? __fadd_rn(r, sgnv(ez, c)) : sgnv(ez, c); }
+    return r;
+}
+
+// positive half of the D3Q19 directions: each pair (i, opposite) once
+__device__ __forceinline__ constexpr int half19(int k) {
+    return k < 3 ? k + 1 : (k < 5 ? k + 4 : (k < 7 ? k + 6 : k + 8));   // 1,2,3,7,8,11,12,15,16
+}
+
+// sum_i mu_i e_i v_i over a D3Q19 set
+template <typename S>
+__device__ __forceinline__ void set_flux19(const float v[QF], float inv_sc, float j[3]) {
+    float ja[3] = {0.0f, 0.0f, 0.0f}, jd[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = half19(k), o = LF::opp(i);
+        const float d = v[i] - v[o];
+        float *acc = i <= 6 ? ja : jd;
+        if (LF::ex(i) != 0) acc[0] += sgnv(LF::ex(i), d);
+        if (LF::ey(i) != 0) acc[1] += sgnv(LF::ey(i), d);
+        if (LF::ez(i) != 0) acc[2] += sgnv(LF::ez(i), d);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        j[a] = IsNarrow<S>::value ? fmaf(1.0f / 18.0f, ja[a], (1.0f / 36.0f) * jd[a]) * inv_sc
+                                  : ja[a] + jd[a];
+}
+
+// phi - phi_ref at one cell
+template <typename S>
+__device__ __forceinline__ float phid_at(const S *__restrict__ pin, const float *__restrict__ q_in,
+                                         size_t cc, size_t N, const DevParams &P) {
+    float v[QG];
+#pragma unroll
+    for (int i = 0; i < QG; ++i) v[i] = load_raw(pin + (G0 + i) * N + cc);
+    return fmaf(0.5f, q_in[cc], set_sum7<S>(v, P.set_isc[1]));
+}
+
+template <typename S>
+__device__ __forceinline__ float phi_at(const S *__restrict__ pin, const float *__restrict__ q_in,
+                                        size_t cc, size_t N, const DevParams &P) {
+    return phid_at<S>(pin, q_in, cc, N, P) + P.g_ref;
+}
+
+// Fill window slot `slot` with phi of plane z (tile + halo ring).  When
+// owners_write is set, each thread whose column is inside the grid has
+// already stored its own cell of an in-range plane (own_ok, own_phi); every
+// other slot is computed here: phi of the wrapped cell, or the wall's
+// Dirichlet value beyond a wall.  FXY: the tile's halo ring lies inside the
+// grid in x and y, so an in-range plane needs no wrap or wall test.
+template <typename S, bool FXY>
+__device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool owners_write,
+                                           bool own_ok, float own_phi, const S *__restrict__ pin,
+                                           const float *__restrict__ q_in, int x0, int y0, int tid,
+                                           int tx, int ty, const DevParams &P) {
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const size_t N = (size_t)P.N;
+    float *plane = sphi + slot * PLANE;
+    const bool z_in = z >= 0 && z < nz;
+    if (owners_write && own_ok) plane[(ty + 1) * SX + tx + 1] = own_phi;
+    if (FXY && z_in && owners_write) {
+        constexpr int RING = 2 * SX + 2 * TY;
+        if (tid < RING) {
+            int sx, sy;
+            if (tid < SX) { sx = tid; sy = 0; }
+            else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
+            else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
+            else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
+            const size_t cc = ((size_t)z * ny + (y0 + sy - 1)) * nx + (x0 + sx - 1);
+            plane[sy * SX + sx] = phid_at<S>(pin, q_in, cc, N, P);
+        }
+        return;
+    }
+    for (int sidx = tid; sidx < PLANE; sidx += TX * TY) {
+        const int sx = sidx % SX, sy = sidx / SX;
+        int cx = x0 + sx - 1, cy = y0 + sy - 1, cz = z;
+        const bool inner = sx >= 1 && sx <= TX && sy >= 1 && sy <= TY;
+        if (owners_write && z_in && inner && cx < nx && cy < ny) continue;   // owner wrote it
+        if (cx < -1 || cx > nx || cy < -1 || cy > ny || cz < -1 || cz > nz) { plane[sidx] = 0.0f; continue; }
+        const int kx = wrap_coord(cx, nx, P.periodic[0]);
+        const int ky = wrap_coord(cy, ny, P.periodic[1]);
+        const int kz = wrap_coord(cz, nz, P.periodic[2]);
+        float v;
+        if (kx >= 2) v = P.phi_wall[kx - 2] - P.g_ref;
+        else if (ky >= 2) v = P.phi_wall[ky - 2] - P.g_ref;
+        else if (kz >= 2) v = P.phi_wall[kz - 2] - P.g_ref;
+        else v = phid_at<S>(pin, q_in, ((size_t)cz * ny + cy) * nx + cx, N, P);
+        plane[sidx] = v;
+    }
+}
+
+// Multiplier taking a per-weight increment to the working representation:
+// the lattice weight for FP32 deviations, the set's scale for 16-bit values.
+template <typename S, class Lt>
+__device__ __forceinline__ float rep_mul3(int i, int set, const DevParams &P) {
+    return IsNarrow<S>::value ? P.set_sc[set] : Lt::w(i);
+}
+
+// Push of one post-collision value of plane `plane` (direction i of lattice
+// Lt, set `set`) from cell c = (x, y, z).  FAST: the link neither wraps nor
+// meets a wall.  Through a wall the value comes back to c in the opposite
+// direction: unchanged for f (bounce-back), -v + 2 w (value - ref) for g and
+// s (anti-bounce-back), in the working representation.
+template <typename S, class Lt, bool FAST>
+__device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int x, int y, int z,
+                                       size_t c, S *__restrict__ pout, const DevParams &P) {
+    const int ex = Lt::ex(i), ey = Lt::ey(i), ez = Lt::ez(i);
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const size_t N = (size_t)P.N;
+    if (FAST) {
+        const long long off = ((long long)ez * ny + ey) * nx + ex;
+        pout[(plane0 + i) * N + c + off] = narrow<S>(v);
+        return;
+    }
+    int dx = x + ex, dy = y + ey, dz = z + ez;
+    const int kx = wrap_coord(dx, nx, P.periodic[0]);
+    const int ky = wrap_coord(dy, ny, P.periodic[1]);
+    const int kz = wrap_coord(dz, nz, P.periodic[2]);
+    if (kx >= 2 || ky >= 2 || kz >= 2) {
+        const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
+        const int o = Lt::opp(i);
+        if (set != 0) {
+            const float wall = set == 1 ? P.phi_wall[side] - P.g_ref : P.T_wall[side] - P.s_ref;
+            v = fmaf(2.0f * rep_mul3<S, Lt>(i, set, P), wall, -v);
+        }
+        pout[(plane0 + o) * N + c] = narrow<S>(v);
+    } else {
+        pout[(plane0 + i) * N + ((size_t)dz * ny + dy) * nx + dx] = narrow<S>(v);
+    }
+}
+
+// Update of one cell of layer z: stencils from the three window planes,
+// moments, closures, production, the three collisions, then the push.  The
+// collisions use the even / odd split of the 2D step: with
+// poly_i = Gamma_i / w_i - 1 = e.u / cs2 + P_e (P_e even in e),
+//   theta*_i - w_i ref = (1 - om)(theta_i - w_i ref) + w_i [E(e_i) + O(e_i)]
+//   g (D3Q7, cs2 = 1/4): E = Ag + Bg P_e,                 O = e.Vg
+//   f (D3Q19):           E = K0 + K1 P_e + 3 (e.u)(e.Hf),  O = e.Vf + P_e (e.Hf)
+//   s (D3Q19):           E = As + Bs P_e,                 O = e.Ws
+// (algebraically Eq. LBE with theta_eq_bar = theta_eq - S/2 and the sources of
+// Eqs. Forcing, MicroProduction, SourceTerm_AllenCahn, Def_SourceTerms_Temp).
+// FAST: no link of this cell wraps or meets a wall.
+template <typename S, bool FAST>
+__device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
+                                               const float f[QF], const float s[QF],
+                                               const float g[QG], float qp, float phip,
+                                               S *__restrict__ pout, float *__restrict__ phi_prev,
+                                               float *__restrict__ q_out, const DevParams &P) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int centre = (ty + 1) * SX + tx + 1;
+    const float *pl[3] = {sphi + (z % 3) * PLANE + centre, sphi + ((z + 1) % 3) * PLANE + centre,
+                          sphi + ((z + 2) % 3) * PLANE + centre};   // planes z-1, z, z+1
+    Macro3 m;
+    const float phd = pl[1][0];              // the window holds phi - phi_ref
+    const float ph = phd + P.g_ref;
+    m.phi = ph;
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f, la = 0.0f, ld = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = half19(k);
+        const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
+        const float a = pl[1 + ez][ey * SX + ex], b = pl[1 - ez][-ey * SX - ex];
+        const float d = a - b, sm = a + b;
+        if (ex != 0) gx += sgnv(ex, d) * LF::w(i);
+        if (ey != 0) gy += sgnv(ey, d) * LF::w(i);
+        if (ez != 0) gz += sgnv(ez, d) * LF::w(i);
+        if (i <= 6) la += sm; else ld += sm;
+    }
+    m.g[0] = 3.0f * gx; m.g[1] = 3.0f * gy; m.g[2] = 3.0f * gz;
+    m.lap = 6.0f * fmaf(1.0f / 18.0f, fmaf(-6.0f, phd, la), (1.0f / 36.0f) * fmaf(-12.0f, phd, ld));
+    closures3d(m, P);
+    float j[3];
+    set_flux19<S>(f, P.set_isc[0], j);
+    const float sf = set_sum19<S>(f, P.set_isc[0]) + P.set_ref[0];
+    const float ss = set_sum19<S>(s, P.set_isc[2]);                  // T - T_ref
+    const float inv_rho = rcp_approx(m.rho);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) m.u[a] = fmaf(0.5f, m.F[a], 3.0f * j[a]) * inv_rho;
+    const float ux = m.u[0], uy = m.u[1], uz = m.u[2];
+    const float rcs2 = m.rho * LF::cs2;
+    const float ugr = fmaf(uz, m.gr[2], fmaf(uy, m.gr[1], ux * m.gr[0]));
+    const float ug = fmaf(uz, m.g[2], fmaf(uy, m.g[1], ux * m.g[0]));
+    m.p = fmaf(0.5f, fmaf(LF::cs2, ugr, (rcs2 * qp) * P.kappa), sf);
+    m.Td = fmaf(-0.5f * P.L_over_Cp, fmaf(ph * qp, P.kappa, (phd - phip) + ug), ss);
+    m.T = m.Td + P.s_ref;
+    const float q = production(ph, m.T, P);
+    const float inv_d = rsqrt_approx(fmaxf(fmaf(m.g[2], m.g[2], fmaf(m.g[1], m.g[1], m.g[0] * m.g[0])), P.eps2));
+    const float n0 = m.g[0] * inv_d, n1 = m.g[1] * inv_d, n2 = m.g[2] * inv_d;
+    const float phu = unit_phi(ph);
+    float om_f;
+    if (P.visc_interp == 0) {
+        const float den = fmaf(phu, P.nu_l - P.nu_g, P.nu_g);
+        om_f = den * rcp_approx(fmaf(0.5f, den, 3.0f * P.nu_l * P.nu_g));
+    } else {
+        om_f = rcp_approx(fmaf(LF::inv_cs2, fmaf(phu, P.nu_g - P.nu_l, P.nu_l), 0.5f));
+    }
+    const float om_s = rcp_approx(fmaf(LF::inv_cs2, diffusivity(ph, P), 0.5f));
+    const float om_g = P.om_g;
+    const float D = fmaf(ph * q, P.kappa, (phd - phip) + ug);
+    phi_prev[c] = phd;           // stored as phi - phi_ref
+    q_out[c] = q;
+
+    const float usq = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+    const float b_g = fmaf(-0.5f, om_g, 1.0f), b_f = fmaf(-0.5f, om_f, 1.0f);
+    const float b_s = fmaf(-0.5f, om_s, 1.0f);
+    const float a_g = 1.0f - om_g, a_f = 1.0f - om_f, a_s = 1.0f - om_s;
+
+    // phase field on D3Q7: poly = 4 e.u + 8 (e.u)^2 - 2 u^2
+    {
+        const float iface = P.four_over_W * ph * (1.0f - ph);
+        const float Ag = fmaf(om_g, phd, b_g * q), Bg = om_g * ph;
+        const float bgi = b_g * iface;
+        const float Vg[3] = {fmaf(4.0f * Bg, ux, bgi * n0), fmaf(4.0f * Bg, uy, bgi * n1),
+                             fmaf(4.0f * Bg, uz, bgi * n2)};
+        const float usq2 = 2.0f * usq;
+        push3d<S, LG, FAST>(0, G0, 1, fmaf(a_g, g[0], rep_mul3<S, LG>(0, 1, P) * fmaf(Bg, -usq2, Ag)),
+                            x, y, z, c, pout, P);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float ua = m.u[a];
+            const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
+            const float mg = rep_mul3<S, LG>(a + 1, 1, P);
+            push3d<S, LG, FAST>(a + 1, G0, 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P);
+            push3d<S, LG, FAST>(a + 4, G0, 1, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P);
+        }
+    }
+
+    // flow and temperature on D3Q19: poly = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2
+    const float usq15 = 1.5f * usq;
+    const float hx = fmaf(LF::cs2, m.gr[0], m.F[0]);
+    const float hy = fmaf(LF::cs2, m.gr[1], m.F[1]);
+    const float hz = fmaf(LF::cs2, m.gr[2], m.F[2]);
+    const float hU = fmaf(uz, hz, fmaf(uy, hy, ux * hx));
+    const float uB = fmaf(uz, m.F[2], fmaf(uy, m.F[1], ux * m.F[0]));
+    // P^f_i / w_i = rho cs2 q kappa, here minus u.F
+    const float K0 = fmaf(om_f, m.p - P.set_ref[0], b_f * fmaf(rcs2 * q, P.kappa, -uB));
+    const float K1 = fmaf(om_f, rcs2, -b_f * hU);
+    const float Hx = b_f * hx, Hy = b_f * hy, Hz = b_f * hz;
+    const float Vfx = fmaf(3.0f * K1, ux, b_f * m.F[0]);
+    const float Vfy = fmaf(3.0f * K1, uy, b_f * m.F[1]);
+    const float Vfz = fmaf(3.0f * K1, uz, b_f * m.F[2]);
+    const float As = fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D), Bs = om_s * m.T;
+    // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
+    const float Wx = __fmul_rn(3.0f * Bs, ux), Wy = __fmul_rn(3.0f * Bs, uy), Wz = __fmul_rn(3.0f * Bs, uz);
+    push3d<S, LF, FAST>(0, 0, 0, fmaf(a_f, f[0], rep_mul3<S, LF>(0, 0, P) * fmaf(K1, -usq15, K0)),
+                        x, y, z, c, pout, P);
+    push3d<S, LF, FAST>(0, S0, 2, fmaf(a_s, s[0], rep_mul3<S, LF>(0, 2, P) * fmaf(Bs, -usq15, As)),
+                        x, y, z, c, pout, P);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = half19(k), o = LF::opp(i);
+        const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
+        const float cu = edot3(ex, ey, ez, ux, uy, uz);
+        const float Pe = fmaf(4.5f * cu, cu, -usq15);
+        const float eH = edot3(ex, ey, ez, Hx, Hy, Hz);
+        const float Ef = fmaf(3.0f * cu, eH, fmaf(K1, Pe, K0));
+        const float Of = fmaf(Pe, eH, edot3(ex, ey, ez, Vfx, Vfy, Vfz));
+        const float Es = fmaf(Bs, Pe, As);
+        const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
+        const float mf = rep_mul3<S, LF>(i, 0, P), ms = rep_mul3<S, LF>(i, 2, P);
+        push3d<S, LF, FAST>(i, 0, 0, fmaf(a_f, f[i], mf * (Ef + Of)), x, y, z, c, pout, P);
+        push3d<S, LF, FAST>(o, 0, 0, fmaf(a_f, f[o], mf * (Ef - Of)), x, y, z, c, pout, P);
+        push3d<S, LF, FAST>(i, S0, 2, fmaf(a_s, s[i], ms * (Es + Os)), x, y, z, c, pout, P);
+        push3d<S, LF, FAST>(o, S0, 2, fmaf(a_s, s[o], ms * (Es - Os)), x, y, z, c, pout, P);
+    }
+}
+
+// One z-column of a 32x8 tile over layers [blockIdx.z * ZB, +ZB), every
+// value read with plain loads (see lbm3d.cu).
+template <typename S, bool FXY>
+__device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__restrict__ pout,
+                                              float *__restrict__ phi_prev,
+                                              const float *__restrict__ q_in,
+                                              float *__restrict__ q_out, const DevParams &P,
+                                              float *sphi) {
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const size_t N = (size_t)P.N;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int zbeg = blockIdx.z * ZB;
+    const int zend = min(zbeg + ZB, nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool col = FXY || ((x < nx) && (y < ny));
+    const size_t cxy = col ? (size_t)y * nx + x : 0;
+    const size_t plane_cells = (size_t)nx * ny;
+
+    float g[QG], qcur = 0.0f;
+    // prologue: plane zbeg (own cells kept in registers) and plane zbeg-1;
+    // plane p lives in window slot (p + 1) % 3
+    {
+        float ph = 0.0f;
+        if (col) {
+            const size_t c = zbeg * plane_cells + cxy;
+#pragma unroll
+            for (int i = 0; i < QG; ++i) g[i] = load_raw(pin + (G0 + i) * N + c);
+            qcur = q_in[c];
+            ph = fmaf(0.5f, qcur, set_sum7<S>(g, P.set_isc[1]));
+        }
+        fill_plane<S, FXY>(sphi, (zbeg + 1) % 3, zbeg, true, col, ph, pin, q_in, x0, y0, tid, tx, ty, P);
+        fill_plane<S, false>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
+    }
+
+    for (int z = zbeg; z < zend; ++z) {
+        float gn[QG], qnext = 0.0f;
+        {
+            float ph = 0.0f;
+            const bool ok = col && (z + 1 < nz);
+            if (ok) {
+                const size_t c = (size_t)(z + 1) * plane_cells + cxy;
+#pragma unroll
+                for (int i = 0; i < QG; ++i) gn[i] = load_raw(pin + (G0 + i) * N + c);
+                qnext = q_in[c];
+                ph = fmaf(0.5f, qnext, set_sum7<S>(gn, P.set_isc[1]));
+            }
+            fill_plane<S, FXY>(sphi, (z + 2) % 3, z + 1, true, ok, ph, pin, q_in, x0, y0, tid, tx, ty, P);
+        }
+        __syncthreads();
+        if (col) {
+            const size_t c = (size_t)z * plane_cells + cxy;
+            float f[QF], s[QF];
+#pragma unroll
+            for (int i = 0; i < QF; ++i) f[i] = load_raw(pin + i * N + c);
+#pragma unroll
+            for (int i = 0; i < QF; ++i) s[i] = load_raw(pin + (S0 + i) * N + c);
+            const float phip = phi_prev[c];
+            if (FXY && z >= 1 && z + 1 < nz)
+                layer_update3d<S, true>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P);
+            else
+                layer_update3d<S, false>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P);
+        }
+#pragma unroll
+        for (int i = 0; i < QG; ++i) g[i] = gn[i];
+        qcur = qnext;
+        __syncthreads();   // plane (z - 1) % 3 is overwritten next iteration
+    }
+}
+
+}  // namespace lbm

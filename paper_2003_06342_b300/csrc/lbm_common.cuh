@@ -105,6 +105,8 @@ struct DevParams {
     // FP32: theta = d + enc_c[k];  16-bit: theta = enc_c[k] + x * dec_s[k],
     // x = (theta - enc_c[k]) * enc_s[k]
     float enc_c[MAXQ_TOTAL], enc_s[MAXQ_TOTAL], dec_s[MAXQ_TOTAL];
+    // per set (f, g, s): storage reference, 16-bit scale and its inverse
+    float set_ref[3], set_sc[3], set_isc[3];
 };
 
 // ---------------------------------------------------------------- storage
@@ -176,7 +178,46 @@ template <> struct Codec<__nv_bfloat16> {
     }
 };
 
+// Working representation of a stored value (the fused 2D step): the raw
+// stored number widened to float.  FP32 stores the deviation theta - w ref of
+// its set; the 16-bit formats store (theta / w - ref) * scale, so the step
+// works on that normalised value directly and spends no multiplication on
+// decoding or encoding.
+template <typename S> struct IsNarrow { static constexpr bool value = true; };
+template <> struct IsNarrow<float> { static constexpr bool value = false; };
+
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(__half v) { return __half2float(v); }
+__device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename S> __device__ __forceinline__ S narrow(float v);
+template <> __device__ __forceinline__ float narrow<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half narrow<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 narrow<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <typename S> __device__ __forceinline__ float load_raw(const S *p) { return widen(__ldg(p)); }
+
+// Approximate reciprocal and reciprocal square root, one instruction each
+// (PTX rcp.approx.ftz.f32, rsqrt.approx.ftz.f32: about one ulp); used where
+// the argument is a density, a relaxation time or a squared norm, never
+// subnormal.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---------------------------------------------------------------- closures
+// Sums of two products are written with an explicit fmaf throughout the step
+// code: left to the compiler, a*b + c*d may be fused either way round
+// depending on the surrounding kernel, and the kernels that share a cell
+// update must produce the same bits.
+//
 // Property closures take phi restricted to the model's range [0, 1]
 // (Sec. 2.1): overshoot beyond it is numerical, and at large density ratios
 // an unrestricted rho(phi) of Eq. Density would reach zero.
@@ -184,7 +225,7 @@ __device__ __forceinline__ float unit_phi(float phi) { return fminf(fmaxf(phi, 0
 
 __device__ __forceinline__ float density(float phi, const DevParams &P) {
     phi = unit_phi(phi);
-    return phi * P.rho_g + (1.0f - phi) * P.rho_l;
+    return fmaf(phi, P.rho_g, (1.0f - phi) * P.rho_l);
 }
 
 __device__ __forceinline__ float viscosity(float phi, const DevParams &P) {
@@ -195,15 +236,16 @@ __device__ __forceinline__ float viscosity(float phi, const DevParams &P) {
 
 __device__ __forceinline__ float diffusivity(float phi, const DevParams &P) {
     phi = unit_phi(phi);
-    return P.alpha_interp == 0 ? phi * P.alpha_g + (1.0f - phi) * P.alpha_l
+    return P.alpha_interp == 0 ? fmaf(phi, P.alpha_g, (1.0f - phi) * P.alpha_l)
                                : P.alpha_l * P.alpha_g / (phi * P.alpha_l + (1.0f - phi) * P.alpha_g);
 }
 
 // mdot'''/rho_g of Eq. ProductionRate
 __device__ __forceinline__ float production(float phi, float T, const DevParams &P) {
     if (!P.source_on) return 0.0f;
-    const float theta = P.Cp_over_L * (T - P.T_sat);
-    return -(P.prod_coef * diffusivity(phi, P)) * (P.theta_I - theta) * phi * (1.0f - phi);
+    // theta_I - theta with theta = (Cp/L)(T - T_sat)
+    const float dth = fmaf(-P.Cp_over_L, T - P.T_sat, P.theta_I);
+    return -(P.prod_coef * diffusivity(phi, P)) * dth * phi * (1.0f - phi);
 }
 
 // Periodic wrap / wall test of one coordinate.  Returns 0 in range, 1 wrapped,

@@ -163,6 +163,12 @@ TMA_CASES = [
     ("droplet_periodic_fp32", lambda: W.droplet_2d(96, 20.0, T_offset=0.05), "fp32", 40),
     ("film_walls_fp16", lambda: _film(128, 96), "fp16", 40),
     ("film_walls_bf16", lambda: _film(128, 96), "bf16", 20),
+    # 3D: periodic x, y (edge tiles wrap), walls in z, several z blocks of 32
+    # layers, and a grid whose last tiles are ragged in x and y
+    ("film3d_fp32", lambda: W.film_boiling_3d(64, 24, 70, modes=2, z0=20.0, phi_wall=(1.0, 0.0)), "fp32", 12),
+    ("film3d_ragged", lambda: W.film_boiling_3d(44, 13, 37, modes=1, z0=12.0, phi_wall=(1.0, 0.0)), "fp32", 10),
+    ("film3d_fp16", lambda: W.film_boiling_3d(64, 24, 70, modes=2, z0=20.0, phi_wall=(1.0, 0.0)), "fp16", 12),
+    ("film3d_bf16", lambda: W.film_boiling_3d(64, 16, 40, modes=2, z0=12.0, phi_wall=(1.0, 0.0)), "bf16", 8),
 ]
 
 
@@ -190,6 +196,17 @@ def test_tma_kernel_parity_with_oracle():
     s = gpu_solver(w)
     s.set_kernel("tma")
     s.step(50)
+    assert s.kernel() == "tma"
+    err = max_errors(gpu_fields(s), ref)
+    assert all(v < TOL for v in err.values()), err
+
+
+def test_tma3d_kernel_parity_with_oracle():
+    w = W.film_boiling_3d(40, 16, 36, modes=1, z0=10.0, phi_wall=(1.0, 0.0))
+    ref = oracle_fields(w, 12)
+    s = gpu_solver(w)
+    s.set_kernel("tma")
+    s.step(12)
     assert s.kernel() == "tma"
     err = max_errors(gpu_fields(s), ref)
     assert all(v < TOL for v in err.values()), err
