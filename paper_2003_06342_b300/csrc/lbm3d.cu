@@ -22,9 +22,10 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P) {
     __shared__ float sphi[3 * PLANE];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const bool fxy = x0 >= 1 && x0 + TX + 1 <= P.n[0] && y0 >= 1 && y0 + TY + 1 <= P.n[1];
-    if (fxy) step3d_column<S, true>(pin, pout, phi_prev, q_in, q_out, P, sphi);
-    else step3d_column<S, false>(pin, pout, phi_prev, q_in, q_out, P, sphi);
+    const int cls = tile_class3d(x0, y0, P);
+    if (cls == XY_IN) step3d_column<S, XY_IN>(pin, pout, phi_prev, q_in, q_out, P, sphi);
+    else if (cls == XY_WRAP) step3d_column<S, XY_WRAP>(pin, pout, phi_prev, q_in, q_out, P, sphi);
+    else step3d_column<S, XY_GEN>(pin, pout, phi_prev, q_in, q_out, P, sphi);
 }
 
 // ------------------------------------------------------------------ phi moment

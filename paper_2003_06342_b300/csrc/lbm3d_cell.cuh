@@ -190,13 +190,29 @@ __device__ __forceinline__ float phi_at(const S *__restrict__ pin, const float *
     return phid_at<S>(pin, q_in, cc, N, P) + P.g_ref;
 }
 
+// Classes of a 32x8 column tile.  XY_IN: the tile and its halo ring lie
+// inside the grid in x and y.  XY_WRAP: the tile lies inside the grid and its
+// ring crosses only periodic x / y boundaries (so every x / y link of its
+// cells lands on a grid cell after the periodic wrap).  XY_GEN: anything
+// else (a ragged tile, or a wall next to the tile), handled generically.
+constexpr int XY_GEN = 0, XY_IN = 1, XY_WRAP = 2;
+
+__device__ __forceinline__ int tile_class3d(int x0, int y0, const DevParams &P) {
+    const int nx = P.n[0], ny = P.n[1];
+    if (x0 + TX > nx || y0 + TY > ny) return XY_GEN;
+    const bool xin = x0 >= 1 && x0 + TX + 1 <= nx, yin = y0 >= 1 && y0 + TY + 1 <= ny;
+    if (xin && yin) return XY_IN;
+    if ((xin || P.periodic[0]) && (yin || P.periodic[1])) return XY_WRAP;
+    return XY_GEN;
+}
+
 // Fill window slot `slot` with phi of plane z (tile + halo ring).  When
 // owners_write is set, each thread whose column is inside the grid has
 // already stored its own cell of an in-range plane (own_ok, own_phi); every
 // other slot is computed here: phi of the wrapped cell, or the wall's
-// Dirichlet value beyond a wall.  FXY: the tile's halo ring lies inside the
-// grid in x and y, so an in-range plane needs no wrap or wall test.
-template <typename S, bool FXY>
+// Dirichlet value beyond a wall.  XY (a tile class): for XY_IN / XY_WRAP an
+// in-range plane needs no wall test, one thread per ring cell.
+template <typename S, int XY>
 __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool owners_write,
                                            bool own_ok, float own_phi, const S *__restrict__ pin,
                                            const float *__restrict__ q_in, int x0, int y0, int tid,
@@ -206,7 +222,7 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
     float *plane = sphi + slot * PLANE;
     const bool z_in = z >= 0 && z < nz;
     if (owners_write && own_ok) plane[(ty + 1) * SX + tx + 1] = own_phi;
-    if (FXY && z_in && owners_write) {
+    if (XY != XY_GEN && z_in && owners_write) {
         constexpr int RING = 2 * SX + 2 * TY;
         if (tid < RING) {
             int sx, sy;
@@ -214,7 +230,12 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
             else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
             else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
             else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
-            const size_t cc = ((size_t)z * ny + (y0 + sy - 1)) * nx + (x0 + sx - 1);
+            int cx = x0 + sx - 1, cy = y0 + sy - 1;
+            if (XY == XY_WRAP) {
+                cx = cx < 0 ? cx + nx : (cx >= nx ? cx - nx : cx);
+                cy = cy < 0 ? cy + ny : (cy >= ny ? cy - ny : cy);
+            }
+            const size_t cc = ((size_t)z * ny + cy) * nx + cx;
             plane[sy * SX + sx] = phid_at<S>(pin, q_in, cc, N, P);
         }
         return;
@@ -245,18 +266,29 @@ __device__ __forceinline__ float rep_mul3(int i, int set, const DevParams &P) {
 }
 
 // Push of one post-collision value of plane `plane` (direction i of lattice
-// Lt, set `set`) from cell c = (x, y, z).  FAST: the link neither wraps nor
-// meets a wall.  Through a wall the value comes back to c in the opposite
-// direction: unchanged for f (bounce-back), -v + 2 w (value - ref) for g and
-// s (anti-bounce-back), in the working representation.
-template <typename S, class Lt, bool FAST>
+// Lt, set `set`) from cell c = (x, y, z).  MODE XY_IN: the link stays inside
+// the grid; XY_WRAP: it may cross a periodic x / y boundary but not a z edge
+// or a wall; XY_GEN: anything.  Through a wall the value comes back to c in
+// the opposite direction: unchanged for f (bounce-back), -v + 2 w (value -
+// ref) for g and s (anti-bounce-back), in the working representation.
+template <typename S, class Lt, int MODE>
 __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int x, int y, int z,
                                        size_t c, S *__restrict__ pout, const DevParams &P) {
     const int ex = Lt::ex(i), ey = Lt::ey(i), ez = Lt::ez(i);
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const size_t N = (size_t)P.N;
-    if (FAST) {
+    if (MODE == XY_IN) {
         const long long off = ((long long)ez * ny + ey) * nx + ex;
+        pout[(plane0 + i) * N + c + off] = narrow<S>(v);
+        return;
+    }
+    if (MODE == XY_WRAP) {
+        int oxy = 0;
+        if (ex > 0) oxy = x == nx - 1 ? 1 - nx : 1;
+        if (ex < 0) oxy = x == 0 ? nx - 1 : -1;
+        if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
+        if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
+        const long long off = (long long)ez * ny * nx + oxy;
         pout[(plane0 + i) * N + c + off] = narrow<S>(v);
         return;
     }
@@ -287,8 +319,8 @@ __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int 
 //   s (D3Q19):           E = As + Bs P_e,                 O = e.Ws
 // (algebraically Eq. LBE with theta_eq_bar = theta_eq - S/2 and the sources of
 // Eqs. Forcing, MicroProduction, SourceTerm_AllenCahn, Def_SourceTerms_Temp).
-// FAST: no link of this cell wraps or meets a wall.
-template <typename S, bool FAST>
+// MODE (see push3d): how the links of this cell are pushed.
+template <typename S, int MODE>
 __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
                                                const float f[QF], const float s[QF],
                                                const float g[QG], float qp, float phip,
@@ -361,15 +393,15 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Vg[3] = {fmaf(4.0f * Bg, ux, bgi * n0), fmaf(4.0f * Bg, uy, bgi * n1),
                              fmaf(4.0f * Bg, uz, bgi * n2)};
         const float usq2 = 2.0f * usq;
-        push3d<S, LG, FAST>(0, G0, 1, fmaf(a_g, g[0], rep_mul3<S, LG>(0, 1, P) * fmaf(Bg, -usq2, Ag)),
+        push3d<S, LG, MODE>(0, G0, 1, fmaf(a_g, g[0], rep_mul3<S, LG>(0, 1, P) * fmaf(Bg, -usq2, Ag)),
                             x, y, z, c, pout, P);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float ua = m.u[a];
             const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
             const float mg = rep_mul3<S, LG>(a + 1, 1, P);
-            push3d<S, LG, FAST>(a + 1, G0, 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P);
-            push3d<S, LG, FAST>(a + 4, G0, 1, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P);
+            push3d<S, LG, MODE>(a + 1, G0, 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P);
+            push3d<S, LG, MODE>(a + 4, G0, 1, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P);
         }
     }
 
@@ -390,9 +422,9 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float As = fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D), Bs = om_s * m.T;
     // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
     const float Wx = __fmul_rn(3.0f * Bs, ux), Wy = __fmul_rn(3.0f * Bs, uy), Wz = __fmul_rn(3.0f * Bs, uz);
-    push3d<S, LF, FAST>(0, 0, 0, fmaf(a_f, f[0], rep_mul3<S, LF>(0, 0, P) * fmaf(K1, -usq15, K0)),
+    push3d<S, LF, MODE>(0, 0, 0, fmaf(a_f, f[0], rep_mul3<S, LF>(0, 0, P) * fmaf(K1, -usq15, K0)),
                         x, y, z, c, pout, P);
-    push3d<S, LF, FAST>(0, S0, 2, fmaf(a_s, s[0], rep_mul3<S, LF>(0, 2, P) * fmaf(Bs, -usq15, As)),
+    push3d<S, LF, MODE>(0, S0, 2, fmaf(a_s, s[0], rep_mul3<S, LF>(0, 2, P) * fmaf(Bs, -usq15, As)),
                         x, y, z, c, pout, P);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -406,16 +438,16 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Es = fmaf(Bs, Pe, As);
         const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
         const float mf = rep_mul3<S, LF>(i, 0, P), ms = rep_mul3<S, LF>(i, 2, P);
-        push3d<S, LF, FAST>(i, 0, 0, fmaf(a_f, f[i], mf * (Ef + Of)), x, y, z, c, pout, P);
-        push3d<S, LF, FAST>(o, 0, 0, fmaf(a_f, f[o], mf * (Ef - Of)), x, y, z, c, pout, P);
-        push3d<S, LF, FAST>(i, S0, 2, fmaf(a_s, s[i], ms * (Es + Os)), x, y, z, c, pout, P);
-        push3d<S, LF, FAST>(o, S0, 2, fmaf(a_s, s[o], ms * (Es - Os)), x, y, z, c, pout, P);
+        push3d<S, LF, MODE>(i, 0, 0, fmaf(a_f, f[i], mf * (Ef + Of)), x, y, z, c, pout, P);
+        push3d<S, LF, MODE>(o, 0, 0, fmaf(a_f, f[o], mf * (Ef - Of)), x, y, z, c, pout, P);
+        push3d<S, LF, MODE>(i, S0, 2, fmaf(a_s, s[i], ms * (Es + Os)), x, y, z, c, pout, P);
+        push3d<S, LF, MODE>(o, S0, 2, fmaf(a_s, s[o], ms * (Es - Os)), x, y, z, c, pout, P);
     }
 }
 
 // One z-column of a 32x8 tile over layers [blockIdx.z * ZB, +ZB), every
 // value read with plain loads (see lbm3d.cu).
-template <typename S, bool FXY>
+template <typename S, int XY>
 __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__restrict__ pout,
                                               float *__restrict__ phi_prev,
                                               const float *__restrict__ q_in,
@@ -428,7 +460,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
     const int zbeg = blockIdx.z * ZB;
     const int zend = min(zbeg + ZB, nz);
     const int x = x0 + tx, y = y0 + ty;
-    const bool col = FXY || ((x < nx) && (y < ny));
+    const bool col = XY != XY_GEN || ((x < nx) && (y < ny));
     const size_t cxy = col ? (size_t)y * nx + x : 0;
     const size_t plane_cells = (size_t)nx * ny;
 
@@ -444,8 +476,8 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             qcur = q_in[c];
             ph = fmaf(0.5f, qcur, set_sum7<S>(g, P.set_isc[1]));
         }
-        fill_plane<S, FXY>(sphi, (zbeg + 1) % 3, zbeg, true, col, ph, pin, q_in, x0, y0, tid, tx, ty, P);
-        fill_plane<S, false>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
+        fill_plane<S, XY>(sphi, (zbeg + 1) % 3, zbeg, true, col, ph, pin, q_in, x0, y0, tid, tx, ty, P);
+        fill_plane<S, XY_GEN>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
     }
 
     for (int z = zbeg; z < zend; ++z) {
@@ -460,7 +492,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
                 qnext = q_in[c];
                 ph = fmaf(0.5f, qnext, set_sum7<S>(gn, P.set_isc[1]));
             }
-            fill_plane<S, FXY>(sphi, (z + 2) % 3, z + 1, true, ok, ph, pin, q_in, x0, y0, tid, tx, ty, P);
+            fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, ok, ph, pin, q_in, x0, y0, tid, tx, ty, P);
         }
         __syncthreads();
         if (col) {
@@ -471,10 +503,10 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
 #pragma unroll
             for (int i = 0; i < QF; ++i) s[i] = load_raw(pin + (S0 + i) * N + c);
             const float phip = phi_prev[c];
-            if (FXY && z >= 1 && z + 1 < nz)
-                layer_update3d<S, true>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P);
+            if (XY != XY_GEN && z >= 1 && z + 1 < nz)
+                layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P);
             else
-                layer_update3d<S, false>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P);
+                layer_update3d<S, XY_GEN>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P);
         }
 #pragma unroll
         for (int i = 0; i < QG; ++i) g[i] = gn[i];

@@ -1,23 +1,22 @@
 // 3D step with every tile layer staged by bulk tensor copies.
 //
 // Same update as step3d_kernel (lbm3d.cu): each block marches a 32x8 column
-// tile through ZB layers.  For each layer L of its range (and the layer above
-// the range), one thread issues five cp.async.bulk.tensor copies into a
-// shared-memory stage:
-//   f planes   32 x 8 x 1 x 19 from (x0, y0, L, 0)    4D map (x, y, z, plane)
-//   s planes   32 x 8 x 1 x 19 from (x0, y0, L, 26)
-//   g planes   32 x 8 x 1 x 7  from (x0, y0, L, 19)
-//   q^{n-1}    32 x 8 x 1      from (x0, y0, L)       3D maps (x, y, z)
-//   phi^{n-1}  32 x 8 x 1      from (x0, y0, L)
-// completing on that stage's mbarrier (each box row is one whole 128-byte line
-// of FP32, or 64 bytes of 16-bit values).  Two stages alternate: when layer z
-// is computed, the copies of layer z+1 have landed (the phi window needs them
-// first) and those of layer z+2 are issued as soon as layer z's stage is
-// free, so the next layer's loads overlap this layer's arithmetic without
-// holding the populations in registers.  The halo ring of the phi window is
-// formed with plain loads, which find those cells in L2 (the neighbouring
-// blocks stage them at about the same time).  A tile that does not fit the
-// grid whole takes the plain-load column of step3d_kernel.
+// tile through ZB layers.  One thread issues cp.async.bulk.tensor copies of
+// the tile's layers into shared-memory stages:
+//   f/s stage  f planes 32 x 8 x 1 x 19 from (x0, y0, L, 0)   4D map (x, y, z, plane)
+//              s planes 32 x 8 x 1 x 19 from (x0, y0, L, 26)
+//              phi^{n-1} 32 x 8 x 1    from (x0, y0, L)       3D map (x, y, z)
+//   g stage    g planes 32 x 8 x 1 x 7  from (x0, y0, L, 19)
+//              q^{n-1}  32 x 8 x 1     from (x0, y0, L)
+// each completing on its own mbarrier (a box row is one whole 128-byte line
+// of FP32, or 64 bytes of 16-bit values).  Two f/s stages and three g stages
+// rotate so that every copy is issued a whole layer before it is needed: while
+// layer z is computed (it needs f/s of z and g of z and z + 1, the latter for
+// the phi window), the copies of f/s(z + 1) and g(z + 2) are in flight.  The
+// populations therefore never wait in registers.  The halo ring of the phi
+// window is formed with plain loads, which find those cells in L2 (the
+// neighbouring blocks staged them a layer earlier).  A tile that does not fit
+// the grid whole takes the plain-load column of step3d_kernel.
 //
 // Waits on the mbarriers are bounded: on expiry the block records an error in
 // a device word, waits (bounded) for its copies in flight and returns; the
@@ -37,123 +36,164 @@ template <typename S> struct Tma3Geom {
     static constexpr int F_BYTES = QF * CELLS * ES;
     static constexpr int G_BYTES = QG * CELLS * ES;
     static constexpr int Q_BYTES = CELLS * 4;
+    // f/s stage: f, s and phi^{n-1} of one layer; g stage: g and q^{n-1}
     static constexpr int OFF_F = 0;
     static constexpr int OFF_S = OFF_F + al(F_BYTES);
-    static constexpr int OFF_G = OFF_S + al(F_BYTES);
+    static constexpr int OFF_PP = OFF_S + al(F_BYTES);
+    static constexpr int FS_STAGE = OFF_PP + al(Q_BYTES);
+    static constexpr int OFF_G = 0;
     static constexpr int OFF_Q = OFF_G + al(G_BYTES);
-    static constexpr int OFF_PP = OFF_Q + al(Q_BYTES);
-    static constexpr int STAGE = OFF_PP + al(Q_BYTES);
-    static constexpr unsigned TX_BYTES = 2 * F_BYTES + G_BYTES + 2 * Q_BYTES;
-    static constexpr int DYN = 2 * STAGE + 128;     // two stages + alignment slack
+    static constexpr int G_STAGE = OFF_Q + al(Q_BYTES);
+    static constexpr int NFS = 2, NG = 3;                  // stages of each kind
+    static constexpr int G_BASE = NFS * FS_STAGE;
+    static constexpr unsigned FS_TX = 2 * F_BYTES + Q_BYTES;
+    static constexpr unsigned G_TX = G_BYTES + Q_BYTES;
+    static constexpr int DYN = NFS * FS_STAGE + NG * G_STAGE + 128;   // + alignment slack
 };
 
 template <typename S>
-__device__ __forceinline__ void issue_layer(unsigned char *stage, uint64_t *bar, const TmaMaps3d &M,
-                                            int par, int x0, int y0, int z) {
+__device__ __forceinline__ void issue_fs(unsigned char *stage, uint64_t *bar, const TmaMaps3d &M,
+                                         int par, int x0, int y0, int z) {
     using Gm = Tma3Geom<S>;
     // order earlier generic-proxy reads of this stage before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, Gm::TX_BYTES);
+    mbar_expect_tx(bar, Gm::FS_TX);
     tma_load_4d(stage + Gm::OFF_F, &M.fs[par], x0, y0, z, 0, bar);
     tma_load_4d(stage + Gm::OFF_S, &M.fs[par], x0, y0, z, S0, bar);
-    tma_load_4d(stage + Gm::OFF_G, &M.g[par], x0, y0, z, G0, bar);
-    tma_load_3d(stage + Gm::OFF_Q, &M.q[par], x0, y0, z, bar);
     tma_load_3d(stage + Gm::OFF_PP, &M.pp, x0, y0, z, bar);
 }
 
-// phi - phi_ref of the thread's own cell from a stage (same arithmetic as
+template <typename S>
+__device__ __forceinline__ void issue_g(unsigned char *stage, uint64_t *bar, const TmaMaps3d &M,
+                                        int par, int x0, int y0, int z) {
+    using Gm = Tma3Geom<S>;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, Gm::G_TX);
+    tma_load_4d(stage + Gm::OFF_G, &M.g[par], x0, y0, z, G0, bar);
+    tma_load_3d(stage + Gm::OFF_Q, &M.q[par], x0, y0, z, bar);
+}
+
+// phi - phi_ref of the thread's own cell from a g stage (same arithmetic as
 // phid_at, so the halo ring of a neighbouring block sees the same float)
 template <typename S>
-__device__ __forceinline__ float staged_phid(const unsigned char *stage, int own, const DevParams &P) {
+__device__ __forceinline__ float staged_phid(const unsigned char *gstage, int own, const DevParams &P) {
     using Gm = Tma3Geom<S>;
-    const S *G = (const S *)(stage + Gm::OFF_G);
+    const S *G = (const S *)(gstage + Gm::OFF_G);
     float v[QG];
 #pragma unroll
     for (int i = 0; i < QG; ++i) v[i] = widen(G[i * Gm::CELLS + own]);
-    return fmaf(0.5f, ((const float *)(stage + Gm::OFF_Q))[own], set_sum7<S>(v, P.set_isc[1]));
+    return fmaf(0.5f, ((const float *)(gstage + Gm::OFF_Q))[own], set_sum7<S>(v, P.set_isc[1]));
 }
 
-template <typename S, bool FXY>
+// Stage bookkeeping: bit b of `par_*` = parity awaited next on barrier b,
+// bit b of `pend_*` = copies issued on barrier b and not yet seen complete.
+struct StageSet {
+    uint32_t par = 0u, pend = 0u;
+    __device__ __forceinline__ bool wait(uint64_t *bars, int b) {
+        const bool ok = mbar_wait_bounded(&bars[b], (par >> b) & 1u);
+        if (ok) { par ^= 1u << b; pend &= ~(1u << b); }
+        return ok;
+    }
+    __device__ __forceinline__ void drain(uint64_t *bars, int n) {
+        for (int b = 0; b < n; ++b)
+            if ((pend >> b) & 1u) mbar_wait_bounded(&bars[b], (par >> b) & 1u);
+    }
+};
+
+// Layer z uses f/s stage (z - zbeg) % 2 and g stage (z - zbeg) % 3.  In
+// iteration z the block needs the f/s stage of z and the g stages of z and
+// z + 1; the copies of f/s(z + 1) and g(z + 2) are in flight, and when layer
+// z is done its stages receive f/s(z + 2) and g(z + 3): every copy is issued
+// at least one whole layer before it is awaited.
+template <typename S, int XY>
 __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S *__restrict__ pin,
                                            S *__restrict__ pout, float *__restrict__ phi_prev,
                                            const float *__restrict__ q_in, float *__restrict__ q_out,
                                            int *err, const DevParams &P, unsigned char *smem,
-                                           uint64_t *bars, float *sphi) {
+                                           uint64_t *barF, uint64_t *barG, float *sphi) {
     using Gm = Tma3Geom<S>;
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int zbeg = blockIdx.z * ZB;
     const int zend = min(zbeg + ZB, nz);
-    const int zlast = min(zend, nz - 1);          // last layer staged
+    const int zlast = min(zend, nz - 1);          // last layer whose g is staged
     const int x = x0 + tx, y = y0 + ty;
     const size_t cxy = (size_t)y * nx + x;
     const size_t plane_cells = (size_t)nx * ny;
+    unsigned char *fs_base = smem;
+    unsigned char *g_base = smem + Gm::G_BASE;
 
-    // layer L lives in stage (L - zbeg) & 1; ph* = parity awaited next,
-    // pend* = copies issued and not yet seen complete
-    uint32_t ph0 = 0u, ph1 = 0u;
-    bool pend0 = true, pend1 = zbeg + 1 <= zlast;
+    StageSet F, G;
+    for (int k = 0; k < Gm::NFS; ++k)
+        if (zbeg + k < zend) F.pend |= 1u << k;
+    for (int k = 0; k < Gm::NG; ++k)
+        if (zbeg + k <= zlast) G.pend |= 1u << k;
     if (tid == 0) {
-        issue_layer<S>(smem, &bars[0], M, par, x0, y0, zbeg);
-        if (pend1) issue_layer<S>(smem + Gm::STAGE, &bars[1], M, par, x0, y0, zbeg + 1);
+        for (int k = 0; k < Gm::NG; ++k)
+            if ((G.pend >> k) & 1u) issue_g<S>(g_base + k * Gm::G_STAGE, &barG[k], M, par, x0, y0, zbeg + k);
+        for (int k = 0; k < Gm::NFS; ++k)
+            if ((F.pend >> k) & 1u) issue_fs<S>(fs_base + k * Gm::FS_STAGE, &barF[k], M, par, x0, y0, zbeg + k);
     }
-    auto wait_stage = [&](int st) -> bool {
-        const bool ok = mbar_wait_bounded(&bars[st], st ? ph1 : ph0);
-        if (ok) {
-            if (st) { ph1 ^= 1u; pend1 = false; } else { ph0 ^= 1u; pend0 = false; }
-        }
-        return ok;
-    };
 
-    // window: plane zbeg - 1 with plain loads, plane zbeg from stage 0
-    fill_plane<S, false>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
-    bool ok = wait_stage(0);
-    fill_plane<S, FXY>(sphi, (zbeg + 1) % 3, zbeg, true, true, staged_phid<S>(smem, tid, P), pin,
+    // window: plane zbeg - 1 with plain loads, plane zbeg from its g stage
+    fill_plane<S, XY_GEN>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
+    bool ok = G.wait(barG, 0);
+    fill_plane<S, XY>(sphi, (zbeg + 1) % 3, zbeg, true, true, staged_phid<S>(g_base, tid, P), pin,
                        q_in, x0, y0, tid, tx, ty, P);
 
+    int fb = 0, gb = 0;            // stages of layer z
     for (int z = zbeg; z < zend; ++z) {
-        const int st = (z - zbeg) & 1;
+        const int gn = gb == Gm::NG - 1 ? 0 : gb + 1;       // g stage of layer z + 1
         const bool has_next = z + 1 < nz;
         float phn = 0.0f;
         if (has_next) {
-            ok = wait_stage(st ^ 1) && ok;
-            phn = staged_phid<S>(smem + (st ^ 1) * Gm::STAGE, tid, P);
+            ok = G.wait(barG, gn) && ok;
+            phn = staged_phid<S>(g_base + gn * Gm::G_STAGE, tid, P);
         }
-        fill_plane<S, FXY>(sphi, (z + 2) % 3, z + 1, true, has_next, phn, pin, q_in, x0, y0, tid,
+        fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, has_next, phn, pin, q_in, x0, y0, tid,
                            tx, ty, P);
+        ok = F.wait(barF, fb) && ok;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
-            if (pend0) mbar_wait_bounded(&bars[0], ph0);     // copies that may still land
-            if (pend1) mbar_wait_bounded(&bars[1], ph1);
+            F.drain(barF, Gm::NFS);                  // copies that may still land
+            G.drain(barG, Gm::NG);
             return;
         }
         {
-            const unsigned char *b = smem + st * Gm::STAGE;
-            const S *F = (const S *)(b + Gm::OFF_F);
-            const S *Sv = (const S *)(b + Gm::OFF_S);
-            const S *G = (const S *)(b + Gm::OFF_G);
+            const unsigned char *b = fs_base + fb * Gm::FS_STAGE;
+            const unsigned char *bg = g_base + gb * Gm::G_STAGE;
+            const S *Fp = (const S *)(b + Gm::OFF_F);
+            const S *Sp = (const S *)(b + Gm::OFF_S);
+            const S *Gp = (const S *)(bg + Gm::OFF_G);
             float f[QF], s[QF], g[QG];
 #pragma unroll
             for (int i = 0; i < QF; ++i) {
-                f[i] = widen(F[i * Gm::CELLS + tid]);
-                s[i] = widen(Sv[i * Gm::CELLS + tid]);
+                f[i] = widen(Fp[i * Gm::CELLS + tid]);
+                s[i] = widen(Sp[i * Gm::CELLS + tid]);
             }
 #pragma unroll
-            for (int i = 0; i < QG; ++i) g[i] = widen(G[i * Gm::CELLS + tid]);
-            const float qp = ((const float *)(b + Gm::OFF_Q))[tid];
+            for (int i = 0; i < QG; ++i) g[i] = widen(Gp[i * Gm::CELLS + tid]);
+            const float qp = ((const float *)(bg + Gm::OFF_Q))[tid];
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const size_t c = (size_t)z * plane_cells + cxy;
-            if (FXY && z >= 1 && z + 1 < nz)
-                layer_update3d<S, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P);
+            if (XY != XY_GEN && z >= 1 && z + 1 < nz)
+                layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P);
             else
-                layer_update3d<S, false>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P);
+                layer_update3d<S, XY_GEN>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P);
         }
-        __syncthreads();      // stage st and window slot (z - 1) % 3 are free again
-        if (z + 2 <= zlast) {
-            if (tid == 0) issue_layer<S>(smem + st * Gm::STAGE, &bars[st], M, par, x0, y0, z + 2);
-            if (st) pend1 = true; else pend0 = true;
+        __syncthreads();      // the stages of layer z and window slot (z - 1) % 3 are free
+        if (z + Gm::NFS < zend) {
+            if (tid == 0)
+                issue_fs<S>(fs_base + fb * Gm::FS_STAGE, &barF[fb], M, par, x0, y0, z + Gm::NFS);
+            F.pend |= 1u << fb;
         }
+        if (z + Gm::NG <= zlast) {
+            if (tid == 0) issue_g<S>(g_base + gb * Gm::G_STAGE, &barG[gb], M, par, x0, y0, z + Gm::NG);
+            G.pend |= 1u << gb;
+        }
+        fb ^= 1;
+        gb = gn;
     }
 }
 
@@ -166,22 +206,26 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // bulk tensor copies want 128-byte aligned destinations
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t barF[Tma3Geom<S>::NFS], barG[Tma3Geom<S>::NG];
     __shared__ float sphi[3 * PLANE];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if (x0 + TX > P.n[0] || y0 + TY > P.n[1]) {          // ragged tile: plain loads
-        step3d_column<S, false>(pin, pout, phi_prev, q_in, q_out, P, sphi);
+        step3d_column<S, XY_GEN>(pin, pout, phi_prev, q_in, q_out, P, sphi);
         return;
     }
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int k = 0; k < Tma3Geom<S>::NFS; ++k) mbar_init(&barF[k], 1);
+        for (int k = 0; k < Tma3Geom<S>::NG; ++k) mbar_init(&barG[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const bool fxy = x0 >= 1 && x0 + TX + 1 <= P.n[0] && y0 >= 1 && y0 + TY + 1 <= P.n[1];
-    if (fxy) tma_column<S, true>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, bars, sphi);
-    else tma_column<S, false>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, bars, sphi);
+    const int cls = tile_class3d(x0, y0, P);
+    if (cls == XY_IN)
+        tma_column<S, XY_IN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi);
+    else if (cls == XY_WRAP)
+        tma_column<S, XY_WRAP>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi);
+    else
+        tma_column<S, XY_GEN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi);
 }
 
 // ------------------------------------------------------------------ host side
