@@ -282,8 +282,7 @@ def run_device(args, world, rank, local):
         for storage in ("fp32", "fp16"):
             for kern in ("tiled", "tma"):
                 v = Solver(w3.n, w3.periodic, w3.params, storage=storage, device=dev, stream=stream)
-                if kern == "tma":
-                    v.set_kernel("tma")
+                v.set_kernel(kern)
                 v.init(w3.phi0, w3.T0, p0=w3.p0)
                 v.step(5)
                 ms_v = step_kernel_ms(v, 100)
@@ -303,8 +302,7 @@ def run_device(args, world, rank, local):
         # the 512 x 512 x 768 FP16 film (201 M cells, 36 GB of populations)
         w5 = W.c5_film_boiling_3d_large()
         v = Solver(w5.n, w5.periodic, w5.params, storage="fp16", device=dev, stream=stream)
-        if best16[0] == "tma":
-            v.set_kernel("tma")
+        v.set_kernel(best16[0])
         v.init(w5.phi0, w5.T0, p0=w5.p0)
         del w5.phi0, w5.T0, w5.p0
         v.step(3)
@@ -486,8 +484,7 @@ def ncu_case(case):
     dim, storage = case.split("_")[:2]
     w = workload_c2() if dim == "2d" else W.c3_film_boiling_3d(256, 256, 128)
     s = Solver(w.n, w.periodic, w.params, storage=storage)
-    if case.endswith("_tma"):
-        s.set_kernel("tma")
+    s.set_kernel("tma" if case.endswith("_tma") else "tiled")
     s.init(w.phi0, w.T0, p0=w.p0)
     s.step(4)
     torch.cuda.synchronize()

@@ -159,14 +159,15 @@ int lbm_set_state(lbm_handle *h, const void *src, size_t bytes, int32_t on_devic
  * opposite direction).  Both buffers are device memory of Q*N entries. */
 int lbm_stream_map(lbm_handle *h, int32_t set, int32_t *src_index, int8_t *kind);
 
-/* Kernel variants of the step.  AUTO (default) is the tiled kernel (plain
- * loads).  TMA selects the variant that stages populations in shared memory
- * with bulk tensor copies, available when the grid allows 16-byte-aligned
- * tensor boxes: in 2D a persistent kernel (row and plane strides a multiple of
- * 16 bytes, at least 66 x 18 cells), in 3D the z-marching kernel with each
- * tile layer staged two layers ahead (n_x a multiple of 4 for FP32 or 8 for
- * 16-bit storage, at least 32 x 8 cells per layer).  Tiled and TMA variants
- * compute the same update bit for bit. */
+/* Kernel variants of the step.  TILED reads populations with plain loads.
+ * TMA stages them in shared memory with bulk tensor copies, available when the
+ * grid allows 16-byte-aligned tensor boxes: in 2D a persistent kernel (row and
+ * plane strides a multiple of 16 bytes, at least 66 x 18 cells), in 3D the
+ * z-marching kernel with each tile layer staged a layer ahead (n_x a multiple
+ * of 4 for FP32 or 8 for 16-bit storage, at least 32 x 8 cells per layer).
+ * AUTO (default) is the faster of the two on B300: TILED in 2D, TMA in 3D when
+ * available (else TILED).  Tiled and TMA variants compute the same update bit
+ * for bit. */
 #define LBM_KERNEL_AUTO   0
 #define LBM_KERNEL_TILED  1
 #define LBM_KERNEL_TMA    2
@@ -176,7 +177,7 @@ int lbm_stream_map(lbm_handle *h, int32_t set, int32_t *src_index, int8_t *kind)
 int lbm_set_kernel(lbm_handle *h, int32_t kernel);
 
 /* The kernel lbm_step launches (LBM_KERNEL_TILED or LBM_KERNEL_TMA; AUTO is
- * reported as what it resolves to once a step has run). */
+ * reported as what it resolves to). */
 int lbm_get_kernel(const lbm_handle *h, int32_t *kernel);
 
 /* Number of time steps since lbm_init / lbm_set_state. */

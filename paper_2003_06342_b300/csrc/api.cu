@@ -207,9 +207,12 @@ int do_step(lbm_handle *h) {
         }
         if (h->kernel_choice == LBM_KERNEL_TMA) return LBM_EUNSUPPORTED;
     }
-    if (h->dim == 3 && h->kernel_choice == LBM_KERNEL_TMA) {
+    // 3D: AUTO resolves to the TMA-staged kernel whenever it is available
+    if (h->dim == 3 && h->kernel_choice != LBM_KERNEL_TILED) {
         if (h->tma_state == 0) setup_tma(h);
-        if (h->tma_state != 1) return LBM_EUNSUPPORTED;
+    }
+    if (h->dim == 3 && h->kernel_choice == LBM_KERNEL_TMA && h->tma_state != 1) return LBM_EUNSUPPORTED;
+    if (h->dim == 3 && h->kernel_choice != LBM_KERNEL_TILED && h->tma_state == 1) {
         switch (h->params.storage) {
         case LBM_STORE_FP32: e = launch_step3d_tma<float>(h->maps3, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
         case LBM_STORE_FP16: e = launch_step3d_tma<__half>(h->maps3, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
@@ -549,7 +552,11 @@ int lbm_set_kernel(lbm_handle *h, int32_t kernel) {
 
 int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
     if (!h || !kernel) return LBM_EINVAL;
-    if (h->kernel_choice == LBM_KERNEL_TMA && h->tma_state == 1) *kernel = LBM_KERNEL_TMA;
+    if (h->dim == 3 && h->kernel_choice == LBM_KERNEL_AUTO && h->tma_state == 0)
+        setup_tma(const_cast<lbm_handle *>(h));
+    const bool tma = h->kernel_choice == LBM_KERNEL_TMA ||
+                     (h->dim == 3 && h->kernel_choice == LBM_KERNEL_AUTO);
+    if (tma && h->tma_state == 1) *kernel = LBM_KERNEL_TMA;
     else *kernel = LBM_KERNEL_TILED;
     return LBM_OK;
 }
