@@ -331,6 +331,24 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     const size_t c = active ? (size_t)y * nx + x : 0;
 
     float f[9], g[9], s[9], phip = 0.0f, qp = 0.0f;
+    // FAST: the ring cells' g and q are requested first, so their latency
+    // (an L2 hit: the neighbouring tiles load the same lines) overlaps the
+    // tile's own loads instead of following them
+    constexpr int RING = 2 * SX + 2 * TY;
+    float rv[9], rq = 0.0f;
+    int rslot = 0;
+    if (FAST && tid < RING) {
+        int sx, sy;
+        if (tid < SX) { sx = tid; sy = 0; }
+        else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
+        else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
+        else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
+        rslot = sy * SX + sx;
+        const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) rv[i] = load_raw(pin + (9 + i) * N + cc);
+        rq = q_in[cc];
+    }
     if (active) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = load_raw(pin + (9 + i) * N + c);
@@ -343,17 +361,9 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
         sphi[(ty + 1) * SX + tx + 1] = fmaf(0.5f, qp, set_sum2d<S>(g, P.set_isc[1]));   // phi - phi_ref
     }
     if (FAST) {
-        // the 2*SX + 2*TY halo cells, one per thread
-        constexpr int RING = 2 * SX + 2 * TY;
-        if (tid < RING) {
-            int sx, sy;
-            if (tid < SX) { sx = tid; sy = 0; }
-            else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
-            else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
-            else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
-            const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
-            sphi[sy * SX + sx] = phid_cell2d<S>(pin, cc, N, q_in[cc], P);
-        }
+        // the 2*SX + 2*TY halo cells, one per thread (same arithmetic as
+        // phid_cell2d)
+        if (tid < RING) sphi[rslot] = fmaf(0.5f, rq, set_sum2d<S>(rv, P.set_isc[1]));
     } else {
         // halo ring and ragged-tile slots: phi at the (wrapped) neighbour
         // cell, or the wall's Dirichlet value beyond a wall
