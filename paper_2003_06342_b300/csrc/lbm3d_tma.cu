@@ -100,6 +100,82 @@ struct StageSet {
     }
 };
 
+// Halo ring of the phi window, fetched a layer ahead with cp.async (4-byte
+// copies straight into shared memory, no registers held): ring cell r of the
+// tile (one per thread r < RING_CELLS) gets its 7 g values and q in words
+// buf[k * RING_CELLS + r].  A 16-bit value is fetched as the aligned 32-bit
+// word that holds it (the workspace is 256-byte aligned, so element e sits in
+// the word at 2 (e / 2) and in half e % 2 of it).
+constexpr int RING_CELLS = 2 * SX + 2 * TY;
+constexpr int RING_WORDS = 8 * RING_CELLS;
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// grid cell (column index + plane offset) of ring cell r for plane z
+template <int XY>
+__device__ __forceinline__ size_t ring_cell(int r, int z, int x0, int y0, const DevParams &P, int &slot) {
+    const int nx = P.n[0], ny = P.n[1];
+    int sx, sy;
+    if (r < SX) { sx = r; sy = 0; }
+    else if (r < 2 * SX) { sx = r - SX; sy = SY - 1; }
+    else if (r < 2 * SX + TY) { sx = 0; sy = 1 + r - 2 * SX; }
+    else { sx = SX - 1; sy = 1 + r - 2 * SX - TY; }
+    slot = sy * SX + sx;
+    int cx = x0 + sx - 1, cy = y0 + sy - 1;
+    if (XY == XY_WRAP) {
+        cx = cx < 0 ? cx + nx : (cx >= nx ? cx - nx : cx);
+        cy = cy < 0 ? cy + ny : (cy >= ny ? cy - ny : cy);
+    }
+    return ((size_t)z * ny + cy) * nx + cx;
+}
+
+template <typename S, int XY>
+__device__ __forceinline__ void ring_prefetch(uint32_t *buf, const S *__restrict__ pin,
+                                              const float *__restrict__ q_in, int z, int x0, int y0,
+                                              int tid, const DevParams &P) {
+    if (tid >= RING_CELLS) return;
+    int slot;
+    const size_t cc = ring_cell<XY>(tid, z, x0, y0, P, slot);
+    const size_t N = (size_t)P.N;
+#pragma unroll
+    for (int i = 0; i < QG; ++i) {
+        const size_t e = (G0 + i) * N + cc;
+        const S *src = pin + (IsNarrow<S>::value ? (e & ~(size_t)1) : e);
+        cp_async4(&buf[i * RING_CELLS + tid], src);
+    }
+    cp_async4(&buf[QG * RING_CELLS + tid], q_in + cc);
+    cp_async_commit();
+}
+
+// phi - phi_ref of ring cell tid from its fetched words (same arithmetic as phid_at)
+template <typename S, int XY>
+__device__ __forceinline__ void ring_store(float *plane, const uint32_t *buf, int z, int x0, int y0,
+                                           int tid, const DevParams &P) {
+    if (tid >= RING_CELLS) return;
+    int slot;
+    const size_t cc = ring_cell<XY>(tid, z, x0, y0, P, slot);
+    const size_t N = (size_t)P.N;
+    float v[QG];
+#pragma unroll
+    for (int i = 0; i < QG; ++i) {
+        const uint32_t w = buf[i * RING_CELLS + tid];
+        if (IsNarrow<S>::value) {
+            const size_t e = (G0 + i) * N + cc;
+            const unsigned short h = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
+            S val;
+            memcpy(&val, &h, 2);
+            v[i] = widen(val);
+        } else {
+            v[i] = __uint_as_float(w);
+        }
+    }
+    plane[slot] = fmaf(0.5f, __uint_as_float(buf[QG * RING_CELLS + tid]), set_sum7<S>(v, P.set_isc[1]));
+}
+
 // Layer z uses f/s stage (z - zbeg) % 2 and g stage (z - zbeg) % 3.  In
 // iteration z the block needs the f/s stage of z and the g stages of z and
 // z + 1; the copies of f/s(z + 1) and g(z + 2) are in flight, and when layer
@@ -110,8 +186,11 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
                                            S *__restrict__ pout, float *__restrict__ phi_prev,
                                            const float *__restrict__ q_in, float *__restrict__ q_out,
                                            int *err, const DevParams &P, unsigned char *smem,
-                                           uint64_t *barF, uint64_t *barG, float *sphi) {
+                                           uint64_t *barF, uint64_t *barG, float *sphi,
+                                           uint32_t *rbuf) {
     using Gm = Tma3Geom<S>;
+    // XY_IN / XY_WRAP tiles fetch their halo ring a layer ahead (cp.async)
+    constexpr bool PRE = XY != XY_GEN;
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -141,6 +220,8 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
     bool ok = G.wait(barG, 0);
     fill_plane<S, XY>(sphi, (zbeg + 1) % 3, zbeg, true, true, staged_phid<S>(g_base, tid, P), pin,
                        q_in, x0, y0, tid, tx, ty, P);
+    if (PRE && zbeg + 1 < nz)
+        ring_prefetch<S, XY>(rbuf + ((zbeg + 1) & 1) * RING_WORDS, pin, q_in, zbeg + 1, x0, y0, tid, P);
 
     int fb = 0, gb = 0;            // stages of layer z
     for (int z = zbeg; z < zend; ++z) {
@@ -151,15 +232,26 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             ok = G.wait(barG, gn) && ok;
             phn = staged_phid<S>(g_base + gn * Gm::G_STAGE, tid, P);
         }
-        fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, has_next, phn, pin, q_in, x0, y0, tid,
-                           tx, ty, P);
+        if (PRE && has_next) {
+            float *plane = sphi + ((z + 2) % 3) * PLANE;
+            plane[(ty + 1) * SX + tx + 1] = phn;
+            cp_async_wait_all();                     // this thread's ring words have landed
+            ring_store<S, XY>(plane, rbuf + ((z + 1) & 1) * RING_WORDS, z + 1, x0, y0, tid, P);
+        } else {
+            fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, has_next, phn, pin, q_in, x0, y0, tid,
+                               tx, ty, P);
+        }
         ok = F.wait(barF, fb) && ok;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
+            cp_async_wait_all();
             F.drain(barF, Gm::NFS);                  // copies that may still land
             G.drain(barG, Gm::NG);
             return;
         }
+        // the ring of plane z + 2 goes into the buffer plane z's ring used
+        if (PRE && z + 2 < nz && z + 1 < zend)
+            ring_prefetch<S, XY>(rbuf + (z & 1) * RING_WORDS, pin, q_in, z + 2, x0, y0, tid, P);
         {
             const unsigned char *b = fs_base + fb * Gm::FS_STAGE;
             const unsigned char *bg = g_base + gb * Gm::G_STAGE;
@@ -208,6 +300,7 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t barF[Tma3Geom<S>::NFS], barG[Tma3Geom<S>::NG];
     __shared__ float sphi[3 * PLANE];
+    __shared__ uint32_t rbuf[2 * RING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if (x0 + TX > P.n[0] || y0 + TY > P.n[1]) {          // ragged tile: plain loads
         step3d_column<S, XY_GEN>(pin, pout, phi_prev, q_in, q_out, P, sphi);
@@ -221,11 +314,11 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     __syncthreads();
     const int cls = tile_class3d(x0, y0, P);
     if (cls == XY_IN)
-        tma_column<S, XY_IN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi);
+        tma_column<S, XY_IN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf);
     else if (cls == XY_WRAP)
-        tma_column<S, XY_WRAP>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi);
+        tma_column<S, XY_WRAP>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf);
     else
-        tma_column<S, XY_GEN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi);
+        tma_column<S, XY_GEN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf);
 }
 
 // ------------------------------------------------------------------ host side
