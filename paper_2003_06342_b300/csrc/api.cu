@@ -194,12 +194,10 @@ int do_step(lbm_handle *h) {
     if (h->dim == 2 && h->kernel_choice == LBM_KERNEL_TMA) {
         if (h->tma_state == 0) setup_tma(h);
         if (h->tma_state == 1) {
-            const int tiles = ((h->grid.nx + 31) / 32) * ((h->grid.ny + 7) / 8);
-            const int nb = h->tma_blocks < tiles ? h->tma_blocks : tiles;
             switch (h->params.storage) {
-            case LBM_STORE_FP32: e = launch_step2d_tma<float>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, nb, h->stream); break;
-            case LBM_STORE_FP16: e = launch_step2d_tma<__half>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, nb, h->stream); break;
-            default: e = launch_step2d_tma<__nv_bfloat16>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, nb, h->stream); break;
+            case LBM_STORE_FP32: e = launch_step2d_tma<float>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
+            case LBM_STORE_FP16: e = launch_step2d_tma<__half>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
+            default: e = launch_step2d_tma<__nv_bfloat16>(h->maps, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
             }
             if (e != cudaSuccess) return LBM_ECUDA;
             h->cur = nxt;

@@ -1,28 +1,29 @@
-// 2D step, persistent and TMA-staged.
+// 2D step marching in y with every chunk staged by bulk tensor copies.
 //
-// Same update as step2d_kernel (lbm2d.cu), organised so that the loads of the
-// next tile overlap the arithmetic of the current one.  Each block walks the
-// 32x8 tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...  For a tile whose
-// one-cell halo lies inside the grid, one thread issues five bulk tensor
-// copies (cp.async.bulk.tensor) into a shared-memory stage:
-//   g planes  9 x 10 x 32 from (x0, y0 - 1)  (tile columns, both halo rows)
-//             9 x 10 x SW from (x0 - SW, y0 - 1) and (x0 + 32, y0 - 1)
-//             (the halo columns, in 16-byte boxes: SW = 4 floats or 8 halves)
-//   q         10 x 32 and two 10 x 4 side boxes, placed the same way
-//   f planes  9 x 8 x 32  from (x0, y0)
-//   s planes  9 x 8 x 32  from (x0, y0)
-//   phi^{n-1} 8 x 32      from (x0, y0)
-// (each row of a centre box is one whole 128-byte line of a 32-float row)
-// completing on that stage's mbarrier; two stages alternate, so the copies of
-// tile k+1 are in flight while tile k is computed.  The block then forms
-// phi^n - phi_ref on the tile and its halo from the staged g and q (no global
-// loads), and each thread runs the shared per-cell update and pushes its 27
-// post-collision values to global memory.  Tiles that touch the grid's edge
-// (periodic wrap or walls) take the generic path of the tiled kernel.
+// Same update as step2d_kernel (lbm2d.cu), organised like the 3D z-march
+// (lbm3d_tma.cu): each block owns a strip of 32 columns and walks YC chunks
+// of 8 rows through it.  One thread issues cp.async.bulk.tensor copies of a
+// chunk into shared-memory stages:
+//   f/s stage  f planes 32 x 8 x 9 from (x0, y0, 0)    3D map (x, y, plane)
+//              s planes 32 x 8 x 9 from (x0, y0, 18)
+//              phi^{n-1} 32 x 8    from (x0, y0)       2D map (x, y)
+//   g stage    g planes 32 x 8 x 9 from (x0, y0, 9)
+//              q^{n-1}  32 x 8     from (x0, y0)
+// completing on the stage's mbarrier.  Two f/s stages and three g stages
+// rotate so that every copy is issued a whole chunk before it is awaited
+// (chunk c needs f/s of c and g of c and c + 1, the latter for the row below
+// it).  The phi window of a chunk (10 rows x 34 columns) takes its top row
+// from the previous chunk's window, its own rows and the row below from the g
+// stages, and only the 18 cells of the left and right halo columns from
+// global memory, fetched a chunk ahead with cp.async.  So the populations
+// never wait in registers and the halo costs 18 instead of 84 cells a tile.
+// Strips whose halo leaves the grid in x, and chunks that touch the first or
+// last row of the grid, take the generic path of the tiled kernel (plain
+// loads, periodic wrap, wall links) on the same window buffer.
 //
-// Every wait on an mbarrier is bounded: on expiry the block records an error
-// code in a device word, waits (again bounded) for a copy it may still have in
-// flight, and returns; the host reports it as LBM_ETIMEOUT at the next sync.
+// Waits on the mbarriers are bounded: on expiry the block records an error in
+// a device word, waits (bounded) for its copies in flight and returns; the
+// host reports LBM_ETIMEOUT at the next sync.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -34,167 +35,279 @@
 
 namespace lbm {
 
-template <typename S> struct TmaGeom {
+constexpr int YC = 4;                       // chunks of TY rows per block
+constexpr int RING2 = 2 * (TY + 1);         // halo-column cells of window rows 1..9
+constexpr int RWORDS = 10 * RING2;          // 9 g words + q per cell
+
+template <typename S> struct March2Geom {
     static constexpr int ES = (int)sizeof(S);
-    static constexpr int SW = 16 / ES;                    // side boxes: 16 bytes wide
-    static constexpr int GH = TY + 2;                     // tile rows + the two halo rows
-    static constexpr int QSW = 4;                         // q is float32
+    static constexpr int CELLS = TX * TY;
     static constexpr int al(int b) { return (b + 127) / 128 * 128; }
-    static constexpr int GC_BYTES = 9 * GH * TX * ES;     // g, columns x0..x0+31
-    static constexpr int GS_BYTES = 9 * GH * SW * ES;     // g, SW columns left or right
-    static constexpr int QC_BYTES = GH * TX * 4;
-    static constexpr int QS_BYTES = GH * QSW * 4;
-    static constexpr int F_BYTES = 9 * TY * TX * ES;
-    static constexpr int PP_BYTES = TY * TX * 4;
-    static constexpr int OFF_GC = 0;
-    static constexpr int OFF_GL = OFF_GC + al(GC_BYTES);
-    static constexpr int OFF_GR = OFF_GL + al(GS_BYTES);
-    static constexpr int OFF_QC = OFF_GR + al(GS_BYTES);
-    static constexpr int OFF_QL = OFF_QC + al(QC_BYTES);
-    static constexpr int OFF_QR = OFF_QL + al(QS_BYTES);
-    static constexpr int OFF_F = OFF_QR + al(QS_BYTES);
-    static constexpr int OFF_S = OFF_F + al(F_BYTES);
-    static constexpr int OFF_PP = OFF_S + al(F_BYTES);
-    static constexpr int STAGE = OFF_PP + al(PP_BYTES);
-    static constexpr unsigned TX_BYTES = GC_BYTES + 2 * GS_BYTES + QC_BYTES + 2 * QS_BYTES +
-                                         2 * F_BYTES + PP_BYTES;
+    static constexpr int P_BYTES = 9 * CELLS * ES;        // one set of a chunk
+    static constexpr int Q_BYTES = CELLS * 4;
+    static constexpr int OFF_F = 0;
+    static constexpr int OFF_S = OFF_F + al(P_BYTES);
+    static constexpr int OFF_PP = OFF_S + al(P_BYTES);
+    static constexpr int FS_STAGE = OFF_PP + al(Q_BYTES);
+    static constexpr int OFF_G = 0;
+    static constexpr int OFF_Q = OFF_G + al(P_BYTES);
+    static constexpr int G_STAGE = OFF_Q + al(Q_BYTES);
+    static constexpr int NFS = 2, NG = 3;
+    static constexpr int G_BASE = NFS * FS_STAGE;
+    static constexpr unsigned FS_TX = 2 * P_BYTES + Q_BYTES;
+    static constexpr unsigned G_TX = P_BYTES + Q_BYTES;
+    static constexpr int DYN = NFS * FS_STAGE + NG * G_STAGE + 128;   // + alignment slack
 };
 
-__device__ __forceinline__ bool tile_is_fast(int x0, int y0, const DevParams &P) {
-    return x0 >= 1 && x0 + TX + 1 <= P.n[0] && y0 >= 1 && y0 + TY + 1 <= P.n[1];
-}
-
 template <typename S>
-__device__ __forceinline__ void issue_tile(unsigned char *stage, uint64_t *bar, const TmaMaps2d &M,
-                                           int par, int x0, int y0) {
-    using Gm = TmaGeom<S>;
-    // order earlier generic-proxy accesses of this stage before the async writes
+__device__ __forceinline__ void issue_fs2(unsigned char *stage, uint64_t *bar, const TmaMaps2d &M,
+                                          int par, int x0, int y0) {
+    using Gm = March2Geom<S>;
+    // order earlier generic-proxy reads of this stage before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, Gm::TX_BYTES);
-    // every box starts on a 16-byte boundary; the centre boxes cover whole
-    // 128-byte lines of the tile's own columns
-    tma_load_3d(stage + Gm::OFF_GC, &M.gc[par], x0, y0 - 1, 9, bar);
-    tma_load_3d(stage + Gm::OFF_GL, &M.gs[par], x0 - Gm::SW, y0 - 1, 9, bar);
-    tma_load_3d(stage + Gm::OFF_GR, &M.gs[par], x0 + TX, y0 - 1, 9, bar);
-    tma_load_2d(stage + Gm::OFF_QC, &M.qc[par], x0, y0 - 1, bar);
-    tma_load_2d(stage + Gm::OFF_QL, &M.qs[par], x0 - Gm::QSW, y0 - 1, bar);
-    tma_load_2d(stage + Gm::OFF_QR, &M.qs[par], x0 + TX, y0 - 1, bar);
-    tma_load_3d(stage + Gm::OFF_F, &M.fs[par], x0, y0, 0, bar);
-    tma_load_3d(stage + Gm::OFF_S, &M.fs[par], x0, y0, 18, bar);
+    mbar_expect_tx(bar, Gm::FS_TX);
+    tma_load_3d(stage + Gm::OFF_F, &M.pops[par], x0, y0, 0, bar);
+    tma_load_3d(stage + Gm::OFF_S, &M.pops[par], x0, y0, 18, bar);
     tma_load_2d(stage + Gm::OFF_PP, &M.pp, x0, y0, bar);
 }
 
 template <typename S>
-__global__ void __launch_bounds__(TX * TY, 2)
+__device__ __forceinline__ void issue_g2(unsigned char *stage, uint64_t *bar, const TmaMaps2d &M,
+                                         int par, int x0, int y0) {
+    using Gm = March2Geom<S>;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, Gm::G_TX);
+    tma_load_3d(stage + Gm::OFF_G, &M.pops[par], x0, y0, 9, bar);
+    tma_load_2d(stage + Gm::OFF_Q, &M.q[par], x0, y0, bar);
+}
+
+// phi - phi_ref of cell `k` of a staged chunk (same arithmetic as phid_cell2d)
+template <typename S>
+__device__ __forceinline__ float staged_phid2(const unsigned char *gstage, int k, const DevParams &P) {
+    using Gm = March2Geom<S>;
+    const S *G = (const S *)(gstage + Gm::OFF_G);
+    float v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = widen(G[i * Gm::CELLS + k]);
+    return fmaf(0.5f, ((const float *)(gstage + Gm::OFF_Q))[k], set_sum2d<S>(v, P.set_isc[1]));
+}
+
+struct StageBits {
+    uint32_t par = 0u, pend = 0u;     // parity awaited next / copies in flight, per barrier
+    __device__ __forceinline__ bool wait(uint64_t *bars, int b) {
+        const bool ok = mbar_wait_bounded(&bars[b], (par >> b) & 1u);
+        if (ok) { par ^= 1u << b; pend &= ~(1u << b); }
+        return ok;
+    }
+    __device__ __forceinline__ void drain(uint64_t *bars, int n) {
+        for (int b = 0; b < n; ++b)
+            if ((pend >> b) & 1u) mbar_wait_bounded(&bars[b], (par >> b) & 1u);
+    }
+};
+
+__device__ __forceinline__ void cp_async4_2d(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// halo-column cell r of a chunk starting at row y0 (rows y0 .. y0 + TY): its
+// grid cell and its window slot
+__device__ __forceinline__ size_t ring2_cell(int r, int x0, int y0, int nx, int &slot) {
+    const int side = r / (TY + 1), row = r % (TY + 1);
+    slot = (row + 1) * SX + (side ? SX - 1 : 0);
+    return (size_t)(y0 + row) * nx + (side ? x0 + TX : x0 - 1);
+}
+
+// fetch the halo columns of the chunk at row y0 into buf (one cell per thread
+// r < RING2; a 16-bit value as the aligned 32-bit word that holds it)
+template <typename S>
+__device__ __forceinline__ void ring2_prefetch(uint32_t *buf, const S *__restrict__ pin,
+                                               const float *__restrict__ q_in, int x0, int y0,
+                                               int tid, const DevParams &P) {
+    if (tid >= RING2) return;
+    int slot;
+    const size_t cc = ring2_cell(tid, x0, y0, P.n[0], slot);
+    const size_t N = (size_t)P.N;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const size_t e = (9 + i) * N + cc;
+        cp_async4_2d(&buf[i * RING2 + tid], pin + (IsNarrow<S>::value ? (e & ~(size_t)1) : e));
+    }
+    cp_async4_2d(&buf[9 * RING2 + tid], q_in + cc);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <typename S>
+__device__ __forceinline__ void ring2_store(float *win, const uint32_t *buf, int x0, int y0, int tid,
+                                            const DevParams &P) {
+    if (tid >= RING2) return;
+    int slot;
+    const size_t cc = ring2_cell(tid, x0, y0, P.n[0], slot);
+    const size_t N = (size_t)P.N;
+    float v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const uint32_t w = buf[i * RING2 + tid];
+        if (IsNarrow<S>::value) {
+            const size_t e = (9 + i) * N + cc;
+            const unsigned short h = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
+            S val;
+            memcpy(&val, &h, 2);
+            v[i] = widen(val);
+        } else {
+            v[i] = __uint_as_float(w);
+        }
+    }
+    win[slot] = fmaf(0.5f, __uint_as_float(buf[9 * RING2 + tid]), set_sum2d<S>(v, P.set_isc[1]));
+}
+
+template <typename S>
+__global__ void __launch_bounds__(TX * TY, 3)
 step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ pin,
                   S *__restrict__ pout, float *__restrict__ phi_prev,
                   const float *__restrict__ q_in, float *__restrict__ q_out, int par, int *err,
                   const DevParams P) {
-    using Gm = TmaGeom<S>;
+    using Gm = March2Geom<S>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // bulk tensor copies want 128-byte aligned destinations
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    __shared__ __align__(8) uint64_t bars[2];
-    __shared__ float sphi[SY * SX];
-    const int nx = P.n[0];
+    __shared__ __align__(8) uint64_t barF[Gm::NFS], barG[Gm::NG];
+    __shared__ float win[2][SY * SX];
+    __shared__ uint32_t rbuf[2][RWORDS];
+    const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int tiles_x = (nx + TX - 1) / TX;
-    const int ntiles = tiles_x * ((P.n[1] + TY - 1) / TY);
+    const int x0 = blockIdx.x * TX;
+    const int ybeg = blockIdx.y * (TY * YC);
+    const int nc = min(YC, (ny - ybeg + TY - 1) / TY);
+    const bool xin = x0 >= 1 && x0 + TX + 1 <= nx;
 
+    if (!xin) {     // strip at (or beyond) the x edges: generic tiles, plain loads
+        for (int c = 0; c < nc; ++c) {
+            step2d_tile<S, false>(pin, pout, phi_prev, q_in, q_out, P, win[0], x0, ybeg + c * TY);
+            __syncthreads();
+        }
+        return;
+    }
+    auto fast = [&](int c) {     // chunk c needs no wrap or wall (rows y0 - 1 .. y0 + TY inside)
+        const int y0 = ybeg + c * TY;
+        return y0 >= 1 && y0 + TY + 1 <= ny;
+    };
+    unsigned char *fs_base = smem;
+    unsigned char *g_base = smem + Gm::G_BASE;
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int k = 0; k < Gm::NFS; ++k) mbar_init(&barF[k], 1);
+        for (int k = 0; k < Gm::NG; ++k) mbar_init(&barG[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-
-    uint32_t phase0 = 0, phase1 = 0;
-    int stage = 0;
-    int t = blockIdx.x;
-    if (t < ntiles && tid == 0) {
-        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
-        if (tile_is_fast(x0, y0, P)) issue_tile<S>(smem, &bars[0], maps, par, x0, y0);
+    // every chunk of the strip is staged (rows past the grid read as zero)
+    StageBits F, G;
+    for (int k = 0; k < Gm::NFS; ++k)
+        if (k < nc) F.pend |= 1u << k;
+    for (int k = 0; k < Gm::NG; ++k)
+        if (k < nc) G.pend |= 1u << k;
+    if (tid == 0) {
+        for (int k = 0; k < Gm::NG; ++k)
+            if (k < nc) issue_g2<S>(g_base + k * Gm::G_STAGE, &barG[k], maps, par, x0, ybeg + k * TY);
+        for (int k = 0; k < Gm::NFS; ++k)
+            if (k < nc) issue_fs2<S>(fs_base + k * Gm::FS_STAGE, &barF[k], maps, par, x0, ybeg + k * TY);
     }
-    for (; t < ntiles; t += gridDim.x) {
-        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
-        const int tn = t + gridDim.x;
-        bool next_issued = false;
-        if (tn < ntiles) {
-            const int xn = (tn % tiles_x) * TX, yn = (tn / tiles_x) * TY;
-            next_issued = tile_is_fast(xn, yn, P);
-            if (next_issued && tid == 0)
-                issue_tile<S>(smem + (stage ^ 1) * Gm::STAGE, &bars[stage ^ 1], maps, par, xn, yn);
+    bool ok = G.wait(barG, 0);
+
+    int fb = 0, gb = 0;                     // stages of chunk c
+    for (int c = 0; c < nc; ++c) {
+        const int y0 = ybeg + c * TY;
+        const int gn = gb == Gm::NG - 1 ? 0 : gb + 1;
+        const bool fc = fast(c);
+        float *W = win[c & 1];
+        if (c + 1 < nc) ok = G.wait(barG, gn) && ok;
+        ok = F.wait(barF, fb) && ok;
+        if (fc) {
+            // top row: the previous chunk's row TY (its window row 8), or loaded
+            if (tid < SX) {
+                if (c > 0) {
+                    W[tid] = win[(c - 1) & 1][TY * SX + tid];
+                } else {
+                    const size_t cc = (size_t)(y0 - 1) * nx + (x0 + tid - 1);
+                    W[tid] = phid_cell2d<S>(pin, cc, N, q_in[cc], P);
+                }
+            }
+            // own rows from this chunk's g stage
+            W[(ty + 1) * SX + tx + 1] = staged_phid2<S>(g_base + gb * Gm::G_STAGE, tid, P);
+            // the row below: row 0 of the next chunk's stage, or loaded
+            if (tid < TX) {
+                float v;
+                if (c + 1 < nc) {
+                    v = staged_phid2<S>(g_base + gn * Gm::G_STAGE, tid, P);
+                } else {
+                    const size_t cc = (size_t)(y0 + TY) * nx + (x0 + tid);
+                    v = phid_cell2d<S>(pin, cc, N, q_in[cc], P);
+                }
+                W[(TY + 1) * SX + tid + 1] = v;
+            }
+            // halo columns of rows 1 .. TY + 1
+            if (c > 0) {
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                ring2_store<S>(W, rbuf[c & 1], x0, y0, tid, P);
+            } else if (tid < RING2) {
+                int slot;
+                const size_t cc = ring2_cell(tid, x0, y0, nx, slot);
+                W[slot] = phid_cell2d<S>(pin, cc, N, q_in[cc], P);
+            }
         }
-        if (tile_is_fast(x0, y0, P)) {
-            const uint32_t ph = stage ? phase1 : phase0;
-            const bool ok = mbar_wait_bounded(&bars[stage], ph);
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicExch(err, 1);
-                if (next_issued)     // a copy of the next tile may still be landing here
-                    mbar_wait_bounded(&bars[stage ^ 1], stage ? phase0 : phase1);
-                return;
-            }
-            if (stage) phase1 ^= 1u; else phase0 ^= 1u;
-            const unsigned char *base = smem + stage * Gm::STAGE;
-            const S *GC = (const S *)(base + Gm::OFF_GC);
-            const S *GL = (const S *)(base + Gm::OFF_GL);
-            const S *GR = (const S *)(base + Gm::OFF_GR);
-            const float *QC = (const float *)(base + Gm::OFF_QC);
-            const float *QL = (const float *)(base + Gm::OFF_QL);
-            const float *QR = (const float *)(base + Gm::OFF_QR);
-            const S *F = (const S *)(base + Gm::OFF_F);
-            const S *Sv = (const S *)(base + Gm::OFF_S);
-            const float *PP = (const float *)(base + Gm::OFF_PP);
-            // phi^n - phi_ref on the tile and its halo, from the staged boxes
-            for (int sidx = tid; sidx < SX * SY; sidx += TX * TY) {
-                const int sx = sidx % SX, sy = sidx / SX;
-                const S *gb;
-                int col, w;
-                float qv;
-                if (sx == 0) { gb = GL; col = Gm::SW - 1; w = Gm::SW; qv = QL[sy * Gm::QSW + Gm::QSW - 1]; }
-                else if (sx == SX - 1) { gb = GR; col = 0; w = Gm::SW; qv = QR[sy * Gm::QSW]; }
-                else { gb = GC; col = sx - 1; w = TX; qv = QC[sy * TX + sx - 1]; }
-                const int gi = sy * w + col;
-                const int plane = Gm::GH * w;
-                float v[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) v[i] = widen(gb[i * plane + gi]);
-                sphi[sidx] = fmaf(0.5f, qv, set_sum2d<S>(v, P.set_isc[1]));
-            }
-            __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            F.drain(barF, Gm::NFS);                 // copies that may still land
+            G.drain(barG, Gm::NG);
+            return;
+        }
+        // the next chunk's halo columns, a chunk ahead
+        if (c + 1 < nc && fast(c + 1))
+            ring2_prefetch<S>(rbuf[(c + 1) & 1], pin, q_in, x0, y0 + TY, tid, P);
+        if (fc) {
+            const unsigned char *b = fs_base + fb * Gm::FS_STAGE;
+            const unsigned char *bg = g_base + gb * Gm::G_STAGE;
+            const S *Fp = (const S *)(b + Gm::OFF_F);
+            const S *Sp = (const S *)(b + Gm::OFF_S);
+            const S *Gp = (const S *)(bg + Gm::OFF_G);
             float f[9], g[9], s[9];
-            const int own = ty * TX + tx;
-            const int gown = (ty + 1) * TX + tx;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                f[i] = widen(F[i * TY * TX + own]);
-                g[i] = widen(GC[i * Gm::GH * TX + gown]);
-                s[i] = widen(Sv[i * TY * TX + own]);
+                f[i] = widen(Fp[i * Gm::CELLS + tid]);
+                g[i] = widen(Gp[i * Gm::CELLS + tid]);
+                s[i] = widen(Sp[i * Gm::CELLS + tid]);
             }
-            const float phip = PP[own];
-            const float qp = QC[(ty + 1) * TX + tx];
+            const float qp = ((const float *)(bg + Gm::OFF_Q))[tid];
+            const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const int x = x0 + tx, y = y0 + ty;
-            const size_t c = (size_t)y * nx + x;
-            cell_update2d<S, true>(sphi + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y, c,
-                                   pout, phi_prev, q_out, P);
+            cell_update2d<S, true>(W + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y,
+                                   (size_t)y * nx + x, pout, phi_prev, q_out, P);
         } else {
-            step2d_tile<S, false>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0);
+            // first or last rows of the grid (or a ragged chunk): generic tile
+            // on the same window buffer, so the next chunk can take its top row
+            step2d_tile<S, false>(pin, pout, phi_prev, q_in, q_out, P, W, x0, y0);
         }
-        __syncthreads();      // stage buffers and the phi window are free again
-        stage ^= 1;
+        __syncthreads();      // the stages of chunk c and window c - 1 are free again
+        if (c + Gm::NFS < nc) {
+            if (tid == 0)
+                issue_fs2<S>(fs_base + fb * Gm::FS_STAGE, &barF[fb], maps, par, x0, ybeg + (c + Gm::NFS) * TY);
+            F.pend |= 1u << fb;
+        }
+        if (c + Gm::NG < nc) {
+            if (tid == 0)
+                issue_g2<S>(g_base + gb * Gm::G_STAGE, &barG[gb], maps, par, x0, ybeg + (c + Gm::NG) * TY);
+            G.pend |= 1u << gb;
+        }
+        fb ^= 1;
+        gb = gn;
     }
-    (void)N;
 }
 
 // ------------------------------------------------------------------ host side
-static cuuint32_t dtype_for(int es) {
-    return es == 4 ? (cuuint32_t)CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : (cuuint32_t)CU_TENSOR_MAP_DATA_TYPE_UINT16;
-}
-
 bool tma2d_eligible(const DevParams &P, int elem_bytes) {
     const long long nx = P.n[0], ny = P.n[1];
-    if (nx < 2 * TX + 2 || ny < 2 * TY + 2) return false;
+    if (nx < TX || ny < TY) return false;
     if ((nx * elem_bytes) % 16 != 0 || (nx * 4) % 16 != 0) return false;
     if ((P.N * elem_bytes) % 16 != 0) return false;
     return true;
@@ -206,75 +319,68 @@ int make_tma_maps2d(TmaMaps2d *M, const DevParams &P, int elem_bytes, void *cons
     if (!enc) return -1;
     const cuuint64_t nx = (cuuint64_t)P.n[0], ny = (cuuint64_t)P.n[1], N = (cuuint64_t)P.N;
     const cuuint64_t es = (cuuint64_t)elem_bytes;
-    const cuuint32_t sw = (cuuint32_t)(16 / elem_bytes);
     const cuuint32_t one[3] = {1, 1, 1};
-    const CUtensorMapDataType dt = (CUtensorMapDataType)dtype_for(elem_bytes);
-    auto map3 = [&](CUtensorMap *m, void *base, cuuint32_t bx, cuuint32_t by) {
+    const CUtensorMapDataType dt = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    auto map3 = [&](CUtensorMap *m, void *base) {
         const cuuint64_t dims[3] = {nx, ny, 27};
         const cuuint64_t str[2] = {nx * es, N * es};
-        const cuuint32_t box[3] = {bx, by, 9};
+        const cuuint32_t box[3] = {TX, TY, 9};
         return enc(m, dt, 3, base, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
-    auto map2 = [&](CUtensorMap *m, void *base, cuuint32_t bx, cuuint32_t by) {
+    auto map2 = [&](CUtensorMap *m, void *base) {
         const cuuint64_t dims[2] = {nx, ny};
         const cuuint64_t str[1] = {nx * 4};
-        const cuuint32_t box[2] = {bx, by};
+        const cuuint32_t box[2] = {TX, TY};
         return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, str, box, one,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     for (int b = 0; b < 2; ++b) {
-        if (!map3(&M->gc[b], pops[b], TX, TY + 2)) return -2;
-        if (!map3(&M->gs[b], pops[b], sw, TY + 2)) return -3;
-        if (!map3(&M->fs[b], pops[b], TX, TY)) return -4;
-        if (!map2(&M->qc[b], q[b], TX, TY + 2)) return -5;
-        if (!map2(&M->qs[b], q[b], 4, TY + 2)) return -6;
+        if (!map3(&M->pops[b], pops[b])) return -2;
+        if (!map2(&M->q[b], q[b])) return -3;
     }
-    if (!map2(&M->pp, phi_prev, TX, TY)) return -7;
+    if (!map2(&M->pp, phi_prev)) return -4;
     return 0;
+}
+
+template <typename S>
+static int blocks_per_sm_for2() {
+    int n = 0;
+    const int dyn = March2Geom<S>::DYN;
+    if (cudaFuncSetAttribute(step2d_tma_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
+        cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step2d_tma_kernel<S>, TX * TY, dyn) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+int tma2d_blocks_per_sm(int elem_bytes) {
+    if (elem_bytes == 4) return blocks_per_sm_for2<float>();
+    const int a = blocks_per_sm_for2<__half>(), b = blocks_per_sm_for2<__nv_bfloat16>();
+    return a < b ? a : b;
 }
 
 template <typename S>
 cudaError_t launch_step2d_tma(const TmaMaps2d &M, int par, const void *pin, void *pout,
                               float *phi_prev, const float *q_in, float *q_out, int *err,
-                              const DevParams &P, int nblocks, cudaStream_t st) {
-    using Gm = TmaGeom<S>;
-    const int dyn = 2 * Gm::STAGE + 128;  // attribute set by tma2d_blocks_per_sm
+                              const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
-    step2d_tma_kernel<S><<<nblocks, block, dyn, st>>>(M, (const S *)pin, (S *)pout, phi_prev, q_in,
-                                                       q_out, par, err, P);
+    dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY * YC - 1) / (TY * YC));
+    step2d_tma_kernel<S><<<grid, block, March2Geom<S>::DYN, st>>>(M, (const S *)pin, (S *)pout,
+                                                                  phi_prev, q_in, q_out, par, err, P);
     return cudaGetLastError();
 }
 
-int tma2d_blocks_per_sm(int elem_bytes) {
-    int n = 0;
-    cudaError_t e;
-    if (elem_bytes == 4) {
-        const int dyn = 2 * TmaGeom<float>::STAGE + 128;
-        e = cudaFuncSetAttribute(step2d_tma_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step2d_tma_kernel<float>, TX * TY, dyn);
-    } else {
-        const int dyn = 2 * TmaGeom<__half>::STAGE + 128;
-        e = cudaFuncSetAttribute(step2d_tma_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(step2d_tma_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step2d_tma_kernel<__half>, TX * TY, dyn);
-    }
-    return e == cudaSuccess ? n : 0;
-}
-
-template cudaError_t launch_step2d_tma<float>(const TmaMaps2d &, int, const void *, void *, float *,
-                                              const float *, float *, int *, const DevParams &, int,
-                                              cudaStream_t);
-template cudaError_t launch_step2d_tma<__half>(const TmaMaps2d &, int, const void *, void *, float *,
-                                               const float *, float *, int *, const DevParams &, int,
-                                               cudaStream_t);
-template cudaError_t launch_step2d_tma<__nv_bfloat16>(const TmaMaps2d &, int, const void *, void *,
-                                                      float *, const float *, float *, int *,
-                                                      const DevParams &, int, cudaStream_t);
+#define LBM_INST2DTMA(S)                                                                        \
+    template cudaError_t launch_step2d_tma<S>(const TmaMaps2d &, int, const void *, void *,     \
+                                              float *, const float *, float *, int *,           \
+                                              const DevParams &, cudaStream_t);
+LBM_INST2DTMA(float)
+LBM_INST2DTMA(__half)
+LBM_INST2DTMA(__nv_bfloat16)
 
 }  // namespace lbm

@@ -1,4 +1,4 @@
-// TMA-staged persistent 2D step (lbm2d_tma.cu): tensor maps and launchers.
+// TMA-staged 2D step marching in y (lbm2d_tma.cu): tensor maps and launchers.
 #pragma once
 
 #include <cuda.h>
@@ -7,14 +7,15 @@
 
 namespace lbm {
 
-// Tensor maps of the two population buffers (g centre and side boxes, f/s
-// box), the two lagged-source buffers (centre and side boxes) and phi^{n-1};
-// index = which buffer is read.
+// Tensor maps of the two population buffers as (x, y, plane) with a 32 x 8 x 9
+// box (one set of a 32x8 chunk), of the two lagged-source buffers and of
+// phi^{n-1} (32 x 8 boxes); index = which buffer is read.
 struct TmaMaps2d {
-    CUtensorMap gc[2], gs[2], fs[2], qc[2], qs[2], pp;
+    CUtensorMap pops[2], q[2], pp;
 };
 
-// Grid and storage allow 16-byte-aligned boxes (row and plane strides).
+// Row and plane strides are multiples of 16 bytes and the grid holds at
+// least one whole 32 x 8 chunk.
 bool tma2d_eligible(const DevParams &P, int elem_bytes);
 // Encode the maps; 0 on success.
 int make_tma_maps2d(TmaMaps2d *M, const DevParams &P, int elem_bytes, void *const pops[2],
@@ -25,6 +26,6 @@ int tma2d_blocks_per_sm(int elem_bytes);
 template <typename S>
 cudaError_t launch_step2d_tma(const TmaMaps2d &M, int par, const void *pin, void *pout,
                               float *phi_prev, const float *q_in, float *q_out, int *err,
-                              const DevParams &P, int nblocks, cudaStream_t st);
+                              const DevParams &P, cudaStream_t st);
 
 }  // namespace lbm
