@@ -40,18 +40,6 @@ __device__ __forceinline__ float phid_cell(const float *__restrict__ st, size_t 
     return v + 0.5f * st[28 * N + c];
 }
 
-// phi - phi_ref at x + e_j, or the wall ghost (then `ghost` is set)
-__device__ __forceinline__ float phid_nb(const float *__restrict__ st, int x, int y, int j,
-                                         size_t N, const DevParams &P, bool &ghost) {
-    int cx = x + L::ex(j), cy = y + L::ey(j);
-    const int kx = wrap_coord(cx, P.n[0], P.periodic[0]);
-    const int ky = wrap_coord(cy, P.n[1], P.periodic[1]);
-    ghost = false;
-    if (kx >= 2) { ghost = true; return P.phi_wall[kx - 2] - P.g_ref; }
-    if (ky >= 2) { ghost = true; return P.phi_wall[ky - 2] - P.g_ref; }
-    return phid_cell(st, (size_t)cy * P.n[0] + cx, N, P);
-}
-
 __device__ __forceinline__ float edot2(int ex, int ey, float a, float b) {
     return (float)ex * a + (float)ey * b;
 }
@@ -83,15 +71,36 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
                     const DevParams P) {
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
-    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    // one 32x8 tile per block; phi - phi_ref of the tile and its one-cell ring
+    // in shared memory (each window value formed once, not once per neighbour)
+    constexpr int WX = 34, WY = 10;
+    __shared__ float sphi[WX * WY];
+    const int tiles_x = (nx + 31) / 32;
+    const int x0 = (int)(blockIdx.x % tiles_x) * 32, y0 = (int)(blockIdx.x / tiles_x) * 8;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < nx && y < ny;
+    const size_t c = active ? (size_t)y * nx + x : 0;
+    for (int sidx = threadIdx.x; sidx < WX * WY; sidx += blockDim.x) {
+        int cx = x0 + sidx % WX - 1, cy = y0 + sidx / WX - 1;
+        if (cx > nx || cy > ny) { sphi[sidx] = 0.0f; continue; }     // beyond a ragged tile
+        const int kx = wrap_coord(cx, nx, P.periodic[0]);
+        const int ky = wrap_coord(cy, ny, P.periodic[1]);
+        sphi[sidx] = kx >= 2 ? P.phi_wall[kx - 2] - P.g_ref
+                   : (ky >= 2 ? P.phi_wall[ky - 2] - P.g_ref : phid_cell(st, (size_t)cy * nx + cx, N, P));
+    }
+    __syncthreads();
     double dL = 0.0, dM = 0.0, dS = 0.0;
-    if (c < N) {
-        const int x = (int)(c % nx), y = (int)(c / nx);
+    if (active) {
         // ---------------- forward recomputation
         float nb[9];
         bool ghost[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) nb[j] = phid_nb(st, x, y, j, N, P, ghost[j]);
+        for (int j = 0; j < 9; ++j) {
+            nb[j] = sphi[(ty + 1 + L::ey(j)) * WX + tx + 1 + L::ex(j)];
+            int cx = x + L::ex(j), cy = y + L::ey(j);
+            ghost[j] = wrap_coord(cx, nx, P.periodic[0]) >= 2 || wrap_coord(cy, ny, P.periodic[1]) >= 2;
+        }
         float f[9], g[9], s[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -479,8 +488,9 @@ cudaError_t launch_adj_terminal2d(const float *st, const float *target, float *a
 
 cudaError_t launch_adj_step2d(const float *st, const float *lam_next, float *lam, float *cst,
                               double *dparams, const DevParams &P, cudaStream_t stream) {
+    const int tiles = ((P.n[0] + 31) / 32) * ((P.n[1] + 7) / 8);
     const int nb = (int)((P.N + 255) / 256);
-    adj_step2d_a_kernel<<<nb, 256, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
+    adj_step2d_a_kernel<<<tiles, 256, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
     adj_step2d_b_kernel<<<nb, 256, 0, stream>>>(cst, lam, P);
     return cudaGetLastError();
 }
