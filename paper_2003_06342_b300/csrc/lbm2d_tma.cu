@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TX * TY, 3)
 step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ pin,
                   S *__restrict__ pout, float *__restrict__ phi_prev,
                   const float *__restrict__ q_in, float *__restrict__ q_out, int par, int *err,
-                  const DevParams P) {
+                  const DevParams P, const __grid_constant__ Planes2d<S> PL) {
     using Gm = March2Geom<S>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // bulk tensor copies want 128-byte aligned destinations
@@ -183,7 +183,7 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
 
     if (!xin) {     // strip at (or beyond) the x edges: generic tiles, plain loads
         for (int c = 0; c < nc; ++c) {
-            step2d_tile<S, false>(pin, pout, phi_prev, q_in, q_out, P, win[0], x0, ybeg + c * TY);
+            step2d_tile<S, false>(pin, pout, phi_prev, q_in, q_out, P, win[0], x0, ybeg + c * TY, PL);
             __syncthreads();
         }
         return;
@@ -282,11 +282,11 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const int x = x0 + tx, y = y0 + ty;
             cell_update2d<S, true>(W + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y,
-                                   (size_t)y * nx + x, pout, phi_prev, q_out, P);
+                                   (size_t)y * nx + x, pout, phi_prev, q_out, P, PL);
         } else {
             // first or last rows of the grid (or a ragged chunk): generic tile
             // on the same window buffer, so the next chunk can take its top row
-            step2d_tile<S, false>(pin, pout, phi_prev, q_in, q_out, P, W, x0, y0);
+            step2d_tile<S, false>(pin, pout, phi_prev, q_in, q_out, P, W, x0, y0, PL);
         }
         __syncthreads();      // the stages of chunk c and window c - 1 are free again
         if (c + Gm::NFS < nc) {
@@ -371,7 +371,8 @@ cudaError_t launch_step2d_tma(const TmaMaps2d &M, int par, const void *pin, void
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY * YC - 1) / (TY * YC));
     step2d_tma_kernel<S><<<grid, block, March2Geom<S>::DYN, st>>>(M, (const S *)pin, (S *)pout,
-                                                                  phi_prev, q_in, q_out, par, err, P);
+                                                                  phi_prev, q_in, q_out, par, err, P,
+                                                                  planes2d<S>(pin, pout, P));
     return cudaGetLastError();
 }
 

@@ -258,6 +258,24 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
     }
 }
 
+// Base pointers of the 45 population planes of the buffer read and of the
+// buffer written, passed to the kernels as a parameter, so that a load or a
+// fast-path store addresses its plane as base + cell.
+template <typename S> struct Planes3d {
+    const S *in[QF + QG + QF];
+    S *out[QF + QG + QF];
+};
+
+template <typename S>
+inline Planes3d<S> planes3d(const void *pin, void *pout, const DevParams &P) {
+    Planes3d<S> PL;
+    for (int k = 0; k < QF + QG + QF; ++k) {
+        PL.in[k] = (const S *)pin + (size_t)k * (size_t)P.N;
+        PL.out[k] = (S *)pout + (size_t)k * (size_t)P.N;
+    }
+    return PL;
+}
+
 // Multiplier taking a per-weight increment to the working representation:
 // the lattice weight for FP32 deviations, the set's scale for 16-bit values.
 template <typename S, class Lt>
@@ -271,15 +289,20 @@ __device__ __forceinline__ float rep_mul3(int i, int set, const DevParams &P) {
 // or a wall; XY_GEN: anything.  Through a wall the value comes back to c in
 // the opposite direction: unchanged for f (bounce-back), -v + 2 w (value -
 // ref) for g and s (anti-bounce-back), in the working representation.
-template <typename S, class Lt, int MODE>
+// PLP: fast-path stores address their plane through PL (faster in every
+// variant except the TMA-staged FP32 kernel, where pout + plane * N measured
+// 1.7% faster).
+template <typename S, class Lt, int MODE, bool PLP>
 __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int x, int y, int z,
-                                       size_t c, S *__restrict__ pout, const DevParams &P) {
+                                       size_t c, S *__restrict__ pout, const DevParams &P,
+                                       const Planes3d<S> &PL) {
     const int ex = Lt::ex(i), ey = Lt::ey(i), ez = Lt::ez(i);
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const size_t N = (size_t)P.N;
     if (MODE == XY_IN) {
         const long long off = ((long long)ez * ny + ey) * nx + ex;
-        pout[(plane0 + i) * N + c + off] = narrow<S>(v);
+        if (PLP) PL.out[plane0 + i][(long long)c + off] = narrow<S>(v);
+        else pout[(plane0 + i) * N + c + off] = narrow<S>(v);
         return;
     }
     if (MODE == XY_WRAP) {
@@ -289,7 +312,8 @@ __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int 
         if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
         if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
         const long long off = (long long)ez * ny * nx + oxy;
-        pout[(plane0 + i) * N + c + off] = narrow<S>(v);
+        if (PLP) PL.out[plane0 + i][(long long)c + off] = narrow<S>(v);
+        else pout[(plane0 + i) * N + c + off] = narrow<S>(v);
         return;
     }
     int dx = x + ex, dy = y + ey, dz = z + ez;
@@ -320,12 +344,13 @@ __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int 
 // (algebraically Eq. LBE with theta_eq_bar = theta_eq - S/2 and the sources of
 // Eqs. Forcing, MicroProduction, SourceTerm_AllenCahn, Def_SourceTerms_Temp).
 // MODE (see push3d): how the links of this cell are pushed.
-template <typename S, int MODE>
+template <typename S, int MODE, bool PLP = true>
 __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
                                                const float f[QF], const float s[QF],
                                                const float g[QG], float qp, float phip,
                                                S *__restrict__ pout, float *__restrict__ phi_prev,
-                                               float *__restrict__ q_out, const DevParams &P) {
+                                               float *__restrict__ q_out, const DevParams &P,
+                                               const Planes3d<S> &PL) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int centre = (ty + 1) * SX + tx + 1;
     const float *pl[3] = {sphi + (z % 3) * PLANE + centre, sphi + ((z + 1) % 3) * PLANE + centre,
@@ -393,15 +418,15 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Vg[3] = {fmaf(4.0f * Bg, ux, bgi * n0), fmaf(4.0f * Bg, uy, bgi * n1),
                              fmaf(4.0f * Bg, uz, bgi * n2)};
         const float usq2 = 2.0f * usq;
-        push3d<S, LG, MODE>(0, G0, 1, fmaf(a_g, g[0], rep_mul3<S, LG>(0, 1, P) * fmaf(Bg, -usq2, Ag)),
-                            x, y, z, c, pout, P);
+        push3d<S, LG, MODE, PLP>(0, G0, 1, fmaf(a_g, g[0], rep_mul3<S, LG>(0, 1, P) * fmaf(Bg, -usq2, Ag)),
+                            x, y, z, c, pout, P, PL);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float ua = m.u[a];
             const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
             const float mg = rep_mul3<S, LG>(a + 1, 1, P);
-            push3d<S, LG, MODE>(a + 1, G0, 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P);
-            push3d<S, LG, MODE>(a + 4, G0, 1, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P);
+            push3d<S, LG, MODE, PLP>(a + 1, G0, 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
+            push3d<S, LG, MODE, PLP>(a + 4, G0, 1, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
         }
     }
 
@@ -422,10 +447,10 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float As = fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D), Bs = om_s * m.T;
     // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
     const float Wx = __fmul_rn(3.0f * Bs, ux), Wy = __fmul_rn(3.0f * Bs, uy), Wz = __fmul_rn(3.0f * Bs, uz);
-    push3d<S, LF, MODE>(0, 0, 0, fmaf(a_f, f[0], rep_mul3<S, LF>(0, 0, P) * fmaf(K1, -usq15, K0)),
-                        x, y, z, c, pout, P);
-    push3d<S, LF, MODE>(0, S0, 2, fmaf(a_s, s[0], rep_mul3<S, LF>(0, 2, P) * fmaf(Bs, -usq15, As)),
-                        x, y, z, c, pout, P);
+    push3d<S, LF, MODE, PLP>(0, 0, 0, fmaf(a_f, f[0], rep_mul3<S, LF>(0, 0, P) * fmaf(K1, -usq15, K0)),
+                        x, y, z, c, pout, P, PL);
+    push3d<S, LF, MODE, PLP>(0, S0, 2, fmaf(a_s, s[0], rep_mul3<S, LF>(0, 2, P) * fmaf(Bs, -usq15, As)),
+                        x, y, z, c, pout, P, PL);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = half19(k), o = LF::opp(i);
@@ -438,10 +463,10 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Es = fmaf(Bs, Pe, As);
         const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
         const float mf = rep_mul3<S, LF>(i, 0, P), ms = rep_mul3<S, LF>(i, 2, P);
-        push3d<S, LF, MODE>(i, 0, 0, fmaf(a_f, f[i], mf * (Ef + Of)), x, y, z, c, pout, P);
-        push3d<S, LF, MODE>(o, 0, 0, fmaf(a_f, f[o], mf * (Ef - Of)), x, y, z, c, pout, P);
-        push3d<S, LF, MODE>(i, S0, 2, fmaf(a_s, s[i], ms * (Es + Os)), x, y, z, c, pout, P);
-        push3d<S, LF, MODE>(o, S0, 2, fmaf(a_s, s[o], ms * (Es - Os)), x, y, z, c, pout, P);
+        push3d<S, LF, MODE, PLP>(i, 0, 0, fmaf(a_f, f[i], mf * (Ef + Of)), x, y, z, c, pout, P, PL);
+        push3d<S, LF, MODE, PLP>(o, 0, 0, fmaf(a_f, f[o], mf * (Ef - Of)), x, y, z, c, pout, P, PL);
+        push3d<S, LF, MODE, PLP>(i, S0, 2, fmaf(a_s, s[i], ms * (Es + Os)), x, y, z, c, pout, P, PL);
+        push3d<S, LF, MODE, PLP>(o, S0, 2, fmaf(a_s, s[o], ms * (Es - Os)), x, y, z, c, pout, P, PL);
     }
 }
 
@@ -452,9 +477,8 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
                                               float *__restrict__ phi_prev,
                                               const float *__restrict__ q_in,
                                               float *__restrict__ q_out, const DevParams &P,
-                                              float *sphi) {
+                                              float *sphi, const Planes3d<S> &PL) {
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-    const size_t N = (size_t)P.N;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int zbeg = blockIdx.z * ZB;
@@ -472,7 +496,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
         if (col) {
             const size_t c = zbeg * plane_cells + cxy;
 #pragma unroll
-            for (int i = 0; i < QG; ++i) g[i] = load_raw(pin + (G0 + i) * N + c);
+            for (int i = 0; i < QG; ++i) g[i] = load_raw(PL.in[G0 + i] + c);
             qcur = q_in[c];
             ph = fmaf(0.5f, qcur, set_sum7<S>(g, P.set_isc[1]));
         }
@@ -488,7 +512,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             if (ok) {
                 const size_t c = (size_t)(z + 1) * plane_cells + cxy;
 #pragma unroll
-                for (int i = 0; i < QG; ++i) gn[i] = load_raw(pin + (G0 + i) * N + c);
+                for (int i = 0; i < QG; ++i) gn[i] = load_raw(PL.in[G0 + i] + c);
                 qnext = q_in[c];
                 ph = fmaf(0.5f, qnext, set_sum7<S>(gn, P.set_isc[1]));
             }
@@ -499,14 +523,14 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             const size_t c = (size_t)z * plane_cells + cxy;
             float f[QF], s[QF];
 #pragma unroll
-            for (int i = 0; i < QF; ++i) f[i] = load_raw(pin + i * N + c);
+            for (int i = 0; i < QF; ++i) f[i] = load_raw(PL.in[i] + c);
 #pragma unroll
-            for (int i = 0; i < QF; ++i) s[i] = load_raw(pin + (S0 + i) * N + c);
+            for (int i = 0; i < QF; ++i) s[i] = load_raw(PL.in[S0 + i] + c);
             const float phip = phi_prev[c];
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P);
+                layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P);
+                layer_update3d<S, XY_GEN>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
         }
 #pragma unroll
         for (int i = 0; i < QG; ++i) g[i] = gn[i];

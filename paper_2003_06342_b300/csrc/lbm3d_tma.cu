@@ -187,7 +187,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
                                            const float *__restrict__ q_in, float *__restrict__ q_out,
                                            int *err, const DevParams &P, unsigned char *smem,
                                            uint64_t *barF, uint64_t *barG, float *sphi,
-                                           uint32_t *rbuf) {
+                                           uint32_t *rbuf, const Planes3d<S> &PL) {
     using Gm = Tma3Geom<S>;
     // XY_IN / XY_WRAP tiles fetch their halo ring a layer ahead (cp.async)
     constexpr bool PRE = XY != XY_GEN;
@@ -270,9 +270,11 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const size_t c = (size_t)z * plane_cells + cxy;
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P);
+                layer_update3d<S, XY, IsNarrow<S>::value>(sphi, z, x, y, c, f, s, g, qp, phip, pout,
+                                                          phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P);
+                layer_update3d<S, XY_GEN, IsNarrow<S>::value>(sphi, z, x, y, c, f, s, g, qp, phip, pout,
+                                                              phi_prev, q_out, P, PL);
         }
         __syncthreads();      // the stages of layer z and window slot (z - 1) % 3 are free
         if (z + Gm::NFS < zend) {
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(TX * TY, 2)
 step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ pin,
                   S *__restrict__ pout, float *__restrict__ phi_prev,
                   const float *__restrict__ q_in, float *__restrict__ q_out, int par, int *err,
-                  const DevParams P) {
+                  const DevParams P, const __grid_constant__ Planes3d<S> PL) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // bulk tensor copies want 128-byte aligned destinations
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -303,7 +305,7 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     __shared__ uint32_t rbuf[2 * RING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if (x0 + TX > P.n[0] || y0 + TY > P.n[1]) {          // ragged tile: plain loads
-        step3d_column<S, XY_GEN>(pin, pout, phi_prev, q_in, q_out, P, sphi);
+        step3d_column<S, XY_GEN>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
         return;
     }
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -314,11 +316,11 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     __syncthreads();
     const int cls = tile_class3d(x0, y0, P);
     if (cls == XY_IN)
-        tma_column<S, XY_IN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf);
+        tma_column<S, XY_IN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
     else if (cls == XY_WRAP)
-        tma_column<S, XY_WRAP>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf);
+        tma_column<S, XY_WRAP>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
     else
-        tma_column<S, XY_GEN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf);
+        tma_column<S, XY_GEN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
 }
 
 // ------------------------------------------------------------------ host side
@@ -388,7 +390,8 @@ cudaError_t launch_step3d_tma(const TmaMaps3d &M, int par, const void *pin, void
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, (P.n[2] + ZB - 1) / ZB);
     step3d_tma_kernel<S><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, (const S *)pin, (S *)pout, phi_prev,
-                                                                q_in, q_out, par, err, P);
+                                                                q_in, q_out, par, err, P,
+                                                                planes3d<S>(pin, pout, P));
     return cudaGetLastError();
 }
 
