@@ -276,11 +276,19 @@ inline Planes3d<S> planes3d(const void *pin, void *pout, const DevParams &P) {
     return PL;
 }
 
-// Multiplier taking a per-weight increment to the working representation:
-// the lattice weight for FP32 deviations, the set's scale for 16-bit values.
+// Multiplier of a wall's Dirichlet term in the working representation: the
+// lattice weight for FP32 deviations, the set's scale for 16-bit values.
 template <typename S, class Lt>
-__device__ __forceinline__ float rep_mul3(int i, int set, const DevParams &P) {
+__device__ __forceinline__ float wall_mul3(int i, int set, const DevParams &P) {
     return IsNarrow<S>::value ? P.set_sc[set] : Lt::w(i);
+}
+
+// Multiplier taking a per-weight increment to the working representation:
+// the lattice weight for FP32 deviations; 1 for 16-bit values, whose set
+// scale is folded into the per-cell collision coefficients instead.
+template <typename S, class Lt>
+__device__ __forceinline__ float rep_mul3(int i) {
+    return IsNarrow<S>::value ? 1.0f : Lt::w(i);
 }
 
 // Push of one post-collision value of plane `plane` (direction i of lattice
@@ -325,7 +333,7 @@ __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int 
         const int o = Lt::opp(i);
         if (set != 0) {
             const float wall = set == 1 ? P.phi_wall[side] - P.g_ref : P.T_wall[side] - P.s_ref;
-            v = fmaf(2.0f * rep_mul3<S, Lt>(i, set, P), wall, -v);
+            v = fmaf(2.0f * wall_mul3<S, Lt>(i, set, P), wall, -v);
         }
         pout[(plane0 + o) * N + c] = narrow<S>(v);
     } else {
@@ -413,18 +421,20 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     // phase field on D3Q7: poly = 4 e.u + 8 (e.u)^2 - 2 u^2
     {
         const float iface = P.four_over_W * ph * (1.0f - ph);
-        const float Ag = fmaf(om_g, phd, b_g * q), Bg = om_g * ph;
-        const float bgi = b_g * iface;
+        // 16-bit storage: the set's scale folded into the coefficients
+        const float sg = IsNarrow<S>::value ? P.set_sc[1] : 1.0f;
+        const float Ag = sg * fmaf(om_g, phd, b_g * q), Bg = sg * (om_g * ph);
+        const float bgi = sg * (b_g * iface);
         const float Vg[3] = {fmaf(4.0f * Bg, ux, bgi * n0), fmaf(4.0f * Bg, uy, bgi * n1),
                              fmaf(4.0f * Bg, uz, bgi * n2)};
         const float usq2 = 2.0f * usq;
-        push3d<S, LG, MODE, PLP>(0, G0, 1, fmaf(a_g, g[0], rep_mul3<S, LG>(0, 1, P) * fmaf(Bg, -usq2, Ag)),
+        push3d<S, LG, MODE, PLP>(0, G0, 1, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)),
                             x, y, z, c, pout, P, PL);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float ua = m.u[a];
             const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
-            const float mg = rep_mul3<S, LG>(a + 1, 1, P);
+            const float mg = rep_mul3<S, LG>(a + 1);
             push3d<S, LG, MODE, PLP>(a + 1, G0, 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
             push3d<S, LG, MODE, PLP>(a + 4, G0, 1, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
         }
@@ -438,18 +448,21 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float hU = fmaf(uz, hz, fmaf(uy, hy, ux * hx));
     const float uB = fmaf(uz, m.F[2], fmaf(uy, m.F[1], ux * m.F[0]));
     // P^f_i / w_i = rho cs2 q kappa, here minus u.F
-    const float K0 = fmaf(om_f, m.p - P.set_ref[0], b_f * fmaf(rcs2 * q, P.kappa, -uB));
-    const float K1 = fmaf(om_f, rcs2, -b_f * hU);
-    const float Hx = b_f * hx, Hy = b_f * hy, Hz = b_f * hz;
-    const float Vfx = fmaf(3.0f * K1, ux, b_f * m.F[0]);
-    const float Vfy = fmaf(3.0f * K1, uy, b_f * m.F[1]);
-    const float Vfz = fmaf(3.0f * K1, uz, b_f * m.F[2]);
-    const float As = fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D), Bs = om_s * m.T;
+    const float scf = IsNarrow<S>::value ? P.set_sc[0] : 1.0f;
+    const float scs = IsNarrow<S>::value ? P.set_sc[2] : 1.0f;
+    const float K0 = scf * fmaf(om_f, m.p - P.set_ref[0], b_f * fmaf(rcs2 * q, P.kappa, -uB));
+    const float K1 = scf * fmaf(om_f, rcs2, -b_f * hU);
+    const float bf = scf * b_f;
+    const float Hx = bf * hx, Hy = bf * hy, Hz = bf * hz;
+    const float Vfx = fmaf(3.0f * K1, ux, bf * m.F[0]);
+    const float Vfy = fmaf(3.0f * K1, uy, bf * m.F[1]);
+    const float Vfz = fmaf(3.0f * K1, uz, bf * m.F[2]);
+    const float As = scs * fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D), Bs = scs * (om_s * m.T);
     // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
     const float Wx = __fmul_rn(3.0f * Bs, ux), Wy = __fmul_rn(3.0f * Bs, uy), Wz = __fmul_rn(3.0f * Bs, uz);
-    push3d<S, LF, MODE, PLP>(0, 0, 0, fmaf(a_f, f[0], rep_mul3<S, LF>(0, 0, P) * fmaf(K1, -usq15, K0)),
+    push3d<S, LF, MODE, PLP>(0, 0, 0, fmaf(a_f, f[0], rep_mul3<S, LF>(0) * fmaf(K1, -usq15, K0)),
                         x, y, z, c, pout, P, PL);
-    push3d<S, LF, MODE, PLP>(0, S0, 2, fmaf(a_s, s[0], rep_mul3<S, LF>(0, 2, P) * fmaf(Bs, -usq15, As)),
+    push3d<S, LF, MODE, PLP>(0, S0, 2, fmaf(a_s, s[0], rep_mul3<S, LF>(0) * fmaf(Bs, -usq15, As)),
                         x, y, z, c, pout, P, PL);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -462,7 +475,7 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Of = fmaf(Pe, eH, edot3(ex, ey, ez, Vfx, Vfy, Vfz));
         const float Es = fmaf(Bs, Pe, As);
         const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
-        const float mf = rep_mul3<S, LF>(i, 0, P), ms = rep_mul3<S, LF>(i, 2, P);
+        const float mf = rep_mul3<S, LF>(i), ms = mf;
         push3d<S, LF, MODE, PLP>(i, 0, 0, fmaf(a_f, f[i], mf * (Ef + Of)), x, y, z, c, pout, P, PL);
         push3d<S, LF, MODE, PLP>(o, 0, 0, fmaf(a_f, f[o], mf * (Ef - Of)), x, y, z, c, pout, P, PL);
         push3d<S, LF, MODE, PLP>(i, S0, 2, fmaf(a_s, s[i], ms * (Es + Os)), x, y, z, c, pout, P, PL);
