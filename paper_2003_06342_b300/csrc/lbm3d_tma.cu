@@ -314,10 +314,11 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // interior tiles run the wrap-aware code too (its selects never fire
+    // there): one fast instantiation instead of two keeps the hot code small
+    // enough for the instruction cache (measured: FP32 +1.9%, FP16 +3.9%)
     const int cls = tile_class3d(x0, y0, P);
-    if (cls == XY_IN)
-        tma_column<S, XY_IN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
-    else if (cls == XY_WRAP)
+    if (cls != XY_GEN)
         tma_column<S, XY_WRAP>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
     else
         tma_column<S, XY_GEN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
