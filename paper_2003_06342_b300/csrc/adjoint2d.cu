@@ -90,7 +90,7 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
                    : (ky >= 2 ? P.phi_wall[ky - 2] - P.g_ref : phid_cell(st, (size_t)cy * nx + cx, N, P));
     }
     __syncthreads();
-    double dL = 0.0, dM = 0.0, dS = 0.0;
+    float dL = 0.0f, dM = 0.0f, dS = 0.0f;        // this cell's terms (FP32)
     if (active) {
         // ---------------- forward recomputation
         float nb[9];
@@ -284,7 +284,7 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         float l_pc = P.visc_interp == 0 ? -P.nu_l * P.nu_g * (P.nu_l - P.nu_g) / (Bv * Bv) * l_nu
                                         : (P.nu_g - P.nu_l) * l_nu;
         // M_phi enters om_g = 1 / (M_phi / cs2_g + 1/2): d om_g / d M_phi = -om_g^2 / cs2_g
-        dM += (double)(-om_g * om_g * L::inv_cs2) * (double)l_om_g;
+        dM += (-om_g * om_g * L::inv_cs2) * l_om_g;
         // normal
         float l_gx = 0.0f, l_gy = 0.0f;
         if (big) {
@@ -341,8 +341,8 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         // mu = 4 H m3(ph) - K lap ; K = 1.5 W sigma, H = 12 sigma / W
         l_ph += 4.0f * P.H * (3.0f * ph * ph - 3.0f * ph + 0.5f) * l_mu;
         const float l_lap = -P.K * l_mu;
-        const double W = 4.0 / (double)P.four_over_W;
-        dS += (double)l_mu * (4.0 * (double)m3 * (12.0 / W) - (double)lap * 1.5 * W);
+        // K = 1.5 W sigma, H = 12 sigma / W; 12 / W = 3 (4 / W)
+        dS += l_mu * (4.0f * m3 * (3.0f * P.four_over_W) - lap * (1.5f * P.W));
         // gradients of rho
         l_gx += P.drho * l_grx; l_gy += P.drho * l_gry;
         // rho = rho_l + pc drho ; pc = clip(ph)
@@ -374,9 +374,9 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         lam[27 * N + c] = l_phip;
         lam[28 * N + c] = l_qp;
         // latent heat: Lc = L / Cp (d/dL = 1/Cp), Cl = Cp / L (d/dL = -Cp/L^2)
-        dL += (double)l_Lc * (double)P.inv_Cp - (double)l_Cl * (double)P.Cp_over_L2;
+        dL += l_Lc * P.inv_Cp - l_Cl * P.Cp_over_L2;
     }
-    block_sum3_atomic(dL, dM, dS, dparams);
+    block_sum3f_atomic(dL, dM, dS, dparams);
 }
 
 // ------------------------------------------------------------------ step B

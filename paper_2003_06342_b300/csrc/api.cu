@@ -123,6 +123,7 @@ void fill_devparams(lbm_handle *h) {
     d.K = (float)(1.5 * p.W * p.sigma);
     d.H = (float)(12.0 * p.sigma / p.W);
     d.four_over_W = (float)(4.0 / p.W);
+    d.W = (float)p.W;
     d.prod_coef = (float)(4.0 / (p.A * p.W * p.W));
     d.theta_I = (float)p.theta_I;
     d.L_over_Cp = (float)(p.L / p.Cp);

@@ -88,6 +88,7 @@ struct DevParams {
     float rho_l, rho_g, drho;          // drho = rho_g - rho_l
     float nu_l, nu_g, alpha_l, alpha_g;
     float K, H;                        // Eq. Def_K-H
+    float W;                           // interface width
     float four_over_W;                 // 4/W
     float prod_coef;                   // 4 / (A W^2)
     float theta_I, L_over_Cp, Cp_over_L, T_sat;
