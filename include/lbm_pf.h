@@ -180,6 +180,12 @@ int lbm_set_kernel(lbm_handle *h, int32_t kernel);
  * reported as what it resolves to). */
 int lbm_get_kernel(const lbm_handle *h, int32_t *kernel);
 
+/* n time steps, saving the state after each: after step k (k = 0..n-1) the
+ * state (lbm_get_state layout) is copied to buf + k*stride, device memory.
+ * Used to recompute a checkpointed segment for the adjoint in one call.
+ * stride >= lbm_state_bytes; LBM_ENOMEM for a short stride. */
+int lbm_step_record(lbm_handle *h, int32_t n, void *buf, size_t stride);
+
 /* Number of time steps since lbm_init / lbm_set_state. */
 int lbm_steps_done(const lbm_handle *h, int64_t *steps);
 
@@ -213,6 +219,15 @@ int lbm_adjoint_terminal(lbm_handle *h, const void *state, const float *phi_targ
  * doubles).  adj and adj_next must differ; scratch from lbm_adjoint_bytes. */
 int lbm_adjoint_step(lbm_handle *h, const void *state, const void *adj_next, void *adj,
                      void *scratch, double *d_dparams);
+
+/* A segment of the reverse sweep in one call: for j = count-1 down to 0,
+ * one lbm_adjoint_step with state = states + j*stride (device), the two
+ * adjoint buffers swapping roles after every step.  On return the adjoint of
+ * the segment's first state is in adj_next when count is even and in adj
+ * when count is odd.  stride >= lbm_state_bytes (a multiple of 4);
+ * LBM_EINVAL for count < 0 or a bad pointer, LBM_ENOMEM for a short stride. */
+int lbm_adjoint_steps(lbm_handle *h, const void *states, size_t stride, int32_t count,
+                      void *adj_next, void *adj, void *scratch, double *d_dparams);
 
 /* Through the initialisation (lbm_init): dT0 = dJ/dT_0 (device float32,
  * nx*ny) from adj0 = dJ/dX^0, and the initialisation's share of dJ/dL and

@@ -90,8 +90,12 @@ SIGNATURES = {
                                             ctypes.c_void_p]),
     "lbm_adjoint_step": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_adjoint_steps": (ctypes.c_int, [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     "lbm_adjoint_init": (ctypes.c_int, [H, P(lbm_fields), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
+    "lbm_step_record": (ctypes.c_int, [H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t]),
     "lbm_destroy": (None, [H]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

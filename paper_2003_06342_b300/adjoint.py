@@ -50,16 +50,19 @@ def gradients(n, periodic, params, phi0, T0, phi_target, nsteps, K=100, p0=None,
     vp = lambda t: ctypes.c_void_p(t.data_ptr())
     B.check(B.lib.lbm_adjoint_terminal(s._h, vp(final), vp(tgt), vp(lam_next), vp(J)),
             "lbm_adjoint_terminal")
+    stride = seg_states.stride(0)
     for k in reversed(range(len(seg_starts))):
         seg = min(K, nsteps - seg_starts[k])
+        # recompute the segment from its checkpoint, keeping every state
         s.set_state(ckpts[k])
         seg_states[0].copy_(ckpts[k])
-        for j in range(1, seg):
-            s.step(1)
-            s.get_state(seg_states[j])
-        for j in reversed(range(seg)):
-            B.check(B.lib.lbm_adjoint_step(s._h, vp(seg_states[j]), vp(lam_next), vp(lam),
-                                           vp(scratch), vp(dparams)), "lbm_adjoint_step")
+        if seg > 1:
+            B.check(B.lib.lbm_step_record(s._h, seg - 1, vp(seg_states[1]), stride), "lbm_step_record")
+        # and walk it backwards in one call; the result sits in lam_next after
+        # an even number of steps, in lam after an odd one
+        B.check(B.lib.lbm_adjoint_steps(s._h, vp(seg_states), stride, seg, vp(lam_next), vp(lam),
+                                        vp(scratch), vp(dparams)), "lbm_adjoint_steps")
+        if seg % 2:
             lam, lam_next = lam_next, lam
     dT0 = torch.zeros_like(T0_t)
     f = B.lbm_fields()

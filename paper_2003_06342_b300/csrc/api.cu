@@ -403,6 +403,25 @@ int lbm_step(lbm_handle *h, int32_t n) {
     return LBM_OK;
 }
 
+static int copy_state(lbm_handle *h, void *buf, size_t bytes, int32_t on_device, bool save);
+
+int lbm_step_record(lbm_handle *h, int32_t n, void *buf, size_t stride) {
+    if (!h || n < 0 || (!buf && n > 0)) return LBM_EINVAL;
+    size_t need;
+    lbm_state_bytes(h, &need);
+    if (stride < need) return LBM_ENOMEM;
+    h->last_launches = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        int r = do_step(h);
+        if (r != LBM_OK) return r;
+        ++h->steps;
+        ++h->last_launches;
+        r = copy_state(h, (char *)buf + (size_t)k * stride, stride, 1, true);
+        if (r != LBM_OK) return r;
+    }
+    return LBM_OK;
+}
+
 int lbm_get_fields(lbm_handle *h, lbm_fields *out) {
     if (!h || !out) return LBM_EINVAL;
     if (out->dtype != 0 && out->dtype != 1) return LBM_EINVAL;
@@ -590,6 +609,27 @@ int lbm_adjoint_step(lbm_handle *h, const void *state, const void *adj_next, voi
     if (!state || !adj_next || !adj || !scratch || !d_dparams || adj == adj_next) return LBM_EINVAL;
     return cuda_status(launch_adj_step2d((const float *)state, (const float *)adj_next, (float *)adj,
                                          (float *)scratch, d_dparams, h->dp, h->stream));
+}
+
+int lbm_adjoint_steps(lbm_handle *h, const void *states, size_t stride, int32_t count,
+                      void *adj_next, void *adj, void *scratch, double *d_dparams) {
+    const int r = adjoint_supported(h);
+    if (r != LBM_OK) return r;
+    if (count < 0 || !states || !adj_next || !adj || !scratch || !d_dparams || adj == adj_next)
+        return LBM_EINVAL;
+    size_t need;
+    lbm_state_bytes(h, &need);
+    if (stride < need || stride % 4 != 0) return LBM_ENOMEM;
+    const char *base = (const char *)states;
+    void *a = adj_next, *b = adj;
+    for (int32_t j = count - 1; j >= 0; --j) {
+        const cudaError_t e = launch_adj_step2d((const float *)(base + (size_t)j * stride),
+                                                (const float *)a, (float *)b, (float *)scratch,
+                                                d_dparams, h->dp, h->stream);
+        if (e != cudaSuccess) return LBM_ECUDA;
+        void *t = a; a = b; b = t;
+    }
+    return LBM_OK;
 }
 
 int lbm_adjoint_init(lbm_handle *h, const lbm_fields *init, const void *adj0, float *dT0,

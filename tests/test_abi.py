@@ -114,6 +114,13 @@ def test_calls_reject_bad_arguments_before_device_work():
     small = ctypes.c_size_t()
     assert B.lib.lbm_state_bytes(h, ctypes.byref(small)) == B.LBM_OK
     assert B.lib.lbm_get_state(h, ctypes.c_void_p(base), small.value - 1, 1) == B.LBM_ENOMEM
+    # segment calls: a stride shorter than one state, a negative count
+    assert B.lib.lbm_step_record(h, 2, ctypes.c_void_p(base), small.value - 4) == B.LBM_ENOMEM
+    assert B.lib.lbm_step_record(h, -1, ctypes.c_void_p(base), small.value) == B.LBM_EINVAL
+    vb = ctypes.c_void_p(base)
+    assert B.lib.lbm_adjoint_steps(h, vb, small.value, -1, vb, ctypes.c_void_p(base + 4), vb, vb) == B.LBM_EINVAL
+    assert B.lib.lbm_adjoint_steps(h, vb, small.value - 4, 1, vb, ctypes.c_void_p(base + 4), vb,
+                                   vb) == B.LBM_ENOMEM
     # the adjoint exists for 2D FP32 only
     a, sc = ctypes.c_size_t(), ctypes.c_size_t()
     assert B.lib.lbm_adjoint_bytes(h, ctypes.byref(a), ctypes.byref(sc)) == B.LBM_OK

@@ -89,3 +89,42 @@ def test_gpu_adjoint_matches_central_differences():
     ad = float((g["T0"].double().cpu().numpy() * d).sum())
     print("T0 direction", ad, fd)
     assert abs(ad - fd) <= TOL * abs(fd)
+
+
+def test_segment_calls_match_single_steps():
+    """lbm_step_record keeps exactly the states that stepping and reading the
+    state one step at a time gives, and lbm_adjoint_steps over a segment
+    equals the same number of lbm_adjoint_step calls."""
+    import ctypes
+    from paper_2003_06342_b300 import Solver
+    from paper_2003_06342_b300 import _binding as Bd
+    w = W.droplet_2d(40, 9.0, T_offset=0.04, T_noise=0.01, corr_len=4.0)
+    n = 5
+    a = Solver(w.n, w.periodic, w.params).init(w.phi0, w.T0)
+    b = Solver(w.n, w.periodic, w.params).init(w.phi0, w.T0)
+    nb = a.state_bytes()
+    rec = torch.zeros((n, nb), dtype=torch.uint8, device="cuda")
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    Bd.check(Bd.lib.lbm_step_record(a._h, n, vp(rec), rec.stride(0)), "lbm_step_record")
+    for k in range(n):
+        b.step(1)
+        assert torch.equal(rec[k], b.get_state())
+    assert a.steps_done() == n
+    # reverse over the recorded states both ways
+    ab, sb = ctypes.c_size_t(), ctypes.c_size_t()
+    Bd.check(Bd.lib.lbm_adjoint_bytes(a._h, ctypes.byref(ab), ctypes.byref(sb)), "bytes")
+    seed = torch.randn(ab.value // 4, device="cuda")
+    scr = torch.zeros(sb.value // 4, device="cuda")
+    l1, l2 = seed.clone(), torch.zeros_like(seed)
+    d1 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for k in reversed(range(n)):
+        Bd.check(Bd.lib.lbm_adjoint_step(a._h, vp(rec[k]), vp(l1), vp(l2), vp(scr), vp(d1)), "step")
+        l1, l2 = l2, l1
+    m1, m2 = seed.clone(), torch.zeros_like(seed)
+    d2 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    Bd.check(Bd.lib.lbm_adjoint_steps(a._h, vp(rec), rec.stride(0), n, vp(m1), vp(m2), vp(scr), vp(d2)),
+             "steps")
+    res = m2 if n % 2 else m1
+    torch.cuda.synchronize()
+    assert torch.equal(res, l1)
+    assert torch.allclose(d1, d2, rtol=1e-12, atol=0.0)
