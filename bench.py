@@ -10,8 +10,8 @@ is MLUPS (million lattice-cell updates per second).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an
-independent replica of the workload on its own GPU (the path has no data
-exchange in this build: replicas only) and value = all ranks' cell updates /
+independent replica of the workload on its own GPU (one lattice per GPU, no
+data exchange: replicas only) and value = all ranks' cell updates /
 the slowest rank's time.  --impl reference times the FP64 CPU oracle on the
 host cores instead, on a bounded sample of the same workload.
 """

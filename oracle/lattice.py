@@ -9,8 +9,8 @@ e7,8=(+-1,1,0), e9,10=(+-1,-1,0), e11,12=(+-1,0,1), e13,14=(+-1,0,-1),
 e15,16=(0,+-1,1), e17,18=(0,+-1,-1); w0=1/3, w1..6=1/18, w7..18=1/36; cs^2=1/3.
 
 The paper lists only e1=(1,0,0), e2=(0,1,0) and e6=(0,0,-1) of the axis
-vectors; the order e3=(0,0,1), e4=(-1,0,0), e5=(0,-1,0) is this build's reading
-(it mirrors the D2Q9 pattern).  The order only fixes the summation order.
+vectors; the order e3=(0,0,1), e4=(-1,0,0), e5=(0,-1,0) is a reading taken
+here (it mirrors the D2Q9 pattern).  The order only fixes the summation order.
 """
 from dataclasses import dataclass
 from fractions import Fraction
