@@ -1,0 +1,64 @@
+"""Pins of the phase-field-alone oracle (oracle.cac, Sec. 3.2 with an imposed
+velocity, Sec. 4.1): exact mass conservation on a periodic box, the tanh
+profile of Eq. Kernel-Function as a stationary solution at rest, and
+translation by a uniform velocity at the right speed and in the right
+direction (a sign error in Gamma's e.u term moves the slab the other way)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cac as C
+from oracle import model as M
+
+
+def _slab(nx=64, ny=8, a=16.0, b=48.0, width=6.0):
+    x = np.arange(nx, dtype=np.float64)
+    prof = 0.5 * (np.tanh(2.0 * (x - a) / width) - np.tanh(2.0 * (x - b) / width))
+    return np.tile(prof, (ny, 1))
+
+
+def _setup(nx=64, ny=8):
+    P = M.Params.from_dict(W.cac_params())
+    G = M.Grid((nx, ny), (True, True))
+    return P, G
+
+
+def test_mass_conserved_to_round_off():
+    P, G = _setup()
+    w = W.vortex_disk(n=41)
+    P = M.Params.from_dict(w.params)
+    G = M.Grid(w.n, w.periodic)
+    u = [uu * 5.0 for uu in w.extra["u"]]         # a faster swirl, same shape
+    g = C.init_state(w.phi0, u, P, G)
+    m0 = float(C.phase_field(g).sum())
+    g = C.run(g, u, P, G, 60)
+    assert abs(float(C.phase_field(g).sum()) - m0) <= 1e-12 * m0
+
+
+def test_tanh_profile_is_stationary_at_rest():
+    P, G = _setup()
+    phi0 = _slab(width=P.W)
+    zero = (np.zeros_like(phi0), np.zeros_like(phi0))
+    g = C.run(C.init_state(phi0, zero, P, G), zero, P, G, 300)
+    assert np.abs(C.phase_field(g).numpy() - phi0).max() < 2e-3
+
+
+@pytest.mark.parametrize("ux,uy,shift", [(0.1, 0.0, (0, 16)), (0.0, -0.1, (-16, 0))])
+def test_uniform_velocity_translates(ux, uy, shift):
+    nx, ny = (64, 8) if uy == 0.0 else (8, 64)
+    P, G = _setup(nx, ny)
+    phi0 = _slab() if uy == 0.0 else _slab().T.copy()
+    u = (np.full_like(phi0, ux), np.full_like(phi0, uy))
+    g = C.run(C.init_state(phi0, u, P, G), u, P, G, 160)
+    phi = C.phase_field(g).numpy()
+    moved = np.roll(phi0, shift, axis=(0, 1))
+    back = np.roll(phi0, (-shift[0], -shift[1]), axis=(0, 1))
+    assert np.abs(phi - moved).max() < 5e-3
+    assert np.abs(phi - back).max() > 0.5
+
+
+def test_velocity_factor_reverses():
+    assert C.velocity_factor(0, 8.0) == 1.0
+    assert abs(C.velocity_factor(4, 8.0)) < 1e-15
+    assert C.velocity_factor(8, 8.0) == -1.0
+    assert C.velocity_factor(123, 0.0) == 1.0

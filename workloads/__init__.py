@@ -270,3 +270,65 @@ def c5_film_boiling_3d_large(top_phi=0.0):
                         phi_wall=(1.0, float(top_phi)))
     w.steps = 2000
     return w
+
+
+# ----------------------------------------------------------------------------
+# phase field alone in an imposed velocity field (Sec. 4.1 CAC validations)
+# ----------------------------------------------------------------------------
+
+def cac_params(M_phi=2.0e-3, W=6.0, **over):
+    """Lattice-unit parameters of the CAC validations: dx = 5e-3, dt = 1e-4,
+    so M_phi = 5e-4 dt / dx^2 = 2e-3 and W = 6 dx = 6 cells; no phase change
+    and no body force (the flow populations are not stepped)."""
+    return base_params(M_phi=M_phi, W=W, source_on=0, gravity=(0.0, 0.0, 0.0),
+                       rho_l=1.0, rho_g=1.0, model=1, **over)
+
+
+def _disk(n, xc, yc, R, width):
+    y, x = np.meshgrid(np.arange(n[1], dtype=np.float64), np.arange(n[0], dtype=np.float64),
+                       indexing="ij")
+    d = np.sqrt((x - xc) ** 2 + (y - yc) ** 2)
+    return 0.5 * (1.0 + np.tanh((R - d) / width)), x, y
+
+
+def zalesak_disk(n=201, u0=0.7853975, dx=5.0e-3, dt=1.0e-4):
+    """Sec. 4.1: a disk of radius R = 80 at the centre of an n x n periodic
+    box, phi = [1 + tanh((R - d) / (sqrt(2) W0))] / 2 with W0 = 2, slotted
+    (phi = 0) for x_c - R/6 <= x <= x_c + R/6, y_c - 1.1 R <= y <= y_c, in the
+    rigid rotation u_x = u0 (2y - 1), u_y = u0 (1 - 2x) (x, y in [0, 1]) that
+    turns it once in T_f = 4 (4 / dt steps)."""
+    c = (n - 1) / 2.0
+    R = 80.0 * (n - 1) / 200.0
+    phi, x, y = _disk((n, n), c, c, R, np.sqrt(2.0) * 2.0)
+    slot = (x >= c - R / 6.0) & (x <= c + R / 6.0) & (y >= c - 1.1 * R) & (y <= c)
+    phi[slot] = 0.0
+    L = (n - 1) * dx                                  # box length in physical units
+    xs, ys = x * dx / L, y * dx / L                   # in [0, 1]
+    scale = dt / dx                                   # physical -> lattice velocity
+    ux = u0 * (2.0 * ys - 1.0) * scale
+    uy = u0 * (1.0 - 2.0 * xs) * scale
+    w = Workload(name=f"zalesak_{n}x{n}", n=(n, n), periodic=(True, True),
+                 params=cac_params(), phi0=phi, T0=np.ones_like(phi),
+                 steps=int(round(4.0 / dt)))
+    w.extra.update(u=(ux, uy), period=0.0)
+    return w
+
+
+def vortex_disk(n=201, u0=0.7853975, dx=5.0e-3, dt=1.0e-4, reverse=True):
+    """Sec. 4.1: a disk of radius 40 centred at (100, 60) (for n = 201) in the
+    vortex u_x = -u0 cos(pi (x - 1/2)) sin(pi (y - 1/2)),
+    u_y = u0 sin(pi (x - 1/2)) cos(pi (y - 1/2)); with `reverse` the field is
+    multiplied by cos(pi t / (2 T_f)), T_f = 4, so the disk returns at 2 T_f."""
+    s = (n - 1) / 200.0
+    phi, x, y = _disk((n, n), 100.0 * s, 60.0 * s, 40.0 * s, np.sqrt(2.0) * 2.0)
+    L = (n - 1) * dx
+    xs, ys = x * dx / L, y * dx / L
+    scale = dt / dx
+    ux = -u0 * np.cos(np.pi * (xs - 0.5)) * np.sin(np.pi * (ys - 0.5)) * scale
+    uy = u0 * np.sin(np.pi * (xs - 0.5)) * np.cos(np.pi * (ys - 0.5)) * scale
+    Tf = int(round(4.0 / dt))
+    w = Workload(name=f"vortex_{n}x{n}", n=(n, n), periodic=(True, True),
+                 params=cac_params(), phi0=phi, T0=np.ones_like(phi),
+                 steps=2 * Tf if reverse else Tf)
+    w.extra.update(u=(ux, uy), period=float(2 * Tf) if reverse else 0.0)
+    return w
