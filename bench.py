@@ -38,7 +38,9 @@ REDUCE_EVERY = 100
 # once, plus phi^{n-1} read+write and the lagged source read+write (4 x 4 B)
 BYTES_PER_CELL = {("2d", "fp32"): 27 * 4 * 2 + 16, ("2d", "fp16"): 27 * 2 * 2 + 16,
                   ("2d", "bf16"): 27 * 2 * 2 + 16, ("3d", "fp32"): 45 * 4 * 2 + 16,
-                  ("3d", "fp16"): 45 * 2 * 2 + 16, ("3d", "bf16"): 45 * 2 * 2 + 16}
+                  ("3d", "fp16"): 45 * 2 * 2 + 16, ("3d", "bf16"): 45 * 2 * 2 + 16,
+                  # phase field alone: the 9 g planes each way and the imposed (ux, uy)
+                  ("cac2d", "fp32"): 9 * 4 * 2 + 8, ("cac2d", "fp16"): 9 * 2 * 2 + 8}
 CSRC = "paper_2003_06342_b300/csrc/"
 # sources that make up each profiled kernel; a committed ncu summary is used
 # only while the hash of its kernel's sources is unchanged
@@ -47,6 +49,7 @@ KERNEL_SOURCES = {
     "step3d": ["lbm3d.cu", "lbm3d_cell.cuh", "lbm_common.cuh"],
     "step3d_tma": ["lbm3d_tma.cu", "lbm3d_cell.cuh", "lbm_common.cuh", "tma_util.cuh"],
     "adjoint2d": ["adjoint2d.cu", "adjoint.h", "lbm_common.cuh"],
+    "cac2d": ["cac2d.cu", "lbm2d_cell.cuh", "lbm_common.cuh"],
 }
 
 
@@ -315,6 +318,22 @@ def run_device(args, world, rank, local):
             "frac": bpc * w5.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v))}
         del v
         torch.cuda.empty_cache()
+        # phase field alone in the reversing vortex (Sec. 4.1), 4096 x 4096
+        wv = W.vortex_disk(n=4096)
+        for storage in ("fp32", "fp16"):
+            v = Solver(wv.n, wv.periodic, wv.params, storage=storage, device=dev, stream=stream)
+            v.set_velocity(wv.extra["u"], wv.extra["period"]).init(wv.phi0, wv.T0)
+            v.step(5)
+            ms_v = step_kernel_ms(v, 200)
+            m_v = safe_reduce(v)
+            bpc = BYTES_PER_CELL[("cac2d", storage)]
+            variants[f"phase_field_2d_{storage}"] = {
+                "workload": wv.name + " (imposed reversing vortex)", "MLUPS": wv.cells / ms_v / 1e3,
+                "ms_per_step": ms_v, "bytes_per_cell": bpc, "achieved_GBs": bpc * wv.cells / ms_v / 1e6,
+                "frac": bpc * wv.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v))}
+            del v
+        del wv
+        torch.cuda.empty_cache()
         variants["adjoint_2d_fp32"] = adjoint_variant(dev, peak)
         torch.cuda.empty_cache()
     result["variants"] = variants
@@ -481,6 +500,14 @@ def ncu_case(case):
     from paper_2003_06342_b300 import Solver
     if case == "2d_adjoint":
         return ncu_case_adjoint()
+    if case == "2d_phase_field":
+        wv = W.vortex_disk(n=4096)
+        s = Solver(wv.n, wv.periodic, wv.params)
+        s.set_velocity(wv.extra["u"], wv.extra["period"]).init(wv.phi0, wv.T0)
+        s.step(4)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": case, "workload": wv.name, "cells": wv.cells}))
+        return
     dim, storage = case.split("_")[:2]
     w = workload_c2() if dim == "2d" else W.c3_film_boiling_3d(256, 256, 128)
     s = Solver(w.n, w.periodic, w.params, storage=storage)
@@ -528,7 +555,7 @@ def main():
     ap.add_argument("--ncu-case", default=None,
                     choices=["2d_fp32", "2d_fp16", "2d_bf16", "3d_fp32", "3d_fp16",
                              "2d_fp32_tma", "2d_fp16_tma", "3d_fp32_tma", "3d_fp16_tma",
-                             "2d_adjoint"],
+                             "2d_adjoint", "2d_phase_field"],
                     help="only initialise one kernel case and run 4 steps (for ncu captures)")
     args = ap.parse_args()
     if args.ncu_case:

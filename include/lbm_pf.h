@@ -87,7 +87,17 @@ typedef struct {
     int32_t visc_interp;          /* 0: harmonic Eq. Viscosity, 1: linear Eq. Visco_lin */
     int32_t alpha_interp;         /* 0: linear in phi, 1: harmonic               */
     int32_t storage;              /* LBM_STORE_*                                 */
+    int32_t model;                /* LBM_MODEL_*                                 */
 } lbm_params;
+
+/* Models.  COUPLED: the three coupled schemes of Sec. 3 (the default).
+ * PHASE_FIELD: the phase-field scheme alone (Sec. 3.2, no phase change) in a
+ * velocity field imposed with lbm_set_velocity -- the setting of the CAC
+ * validations of Sec. 4.1; the flow and temperature populations are not
+ * stepped, lbm_get_fields returns phi (u, p and T are not meaningful) and
+ * source_on must be 0.  2D only. */
+#define LBM_MODEL_COUPLED      0
+#define LBM_MODEL_PHASE_FIELD  1
 
 /* Macroscopic fields.  Any pointer may be NULL (that field is skipped on
  * output; on input NULL means zero, except phi and T, which are required).
@@ -235,6 +245,14 @@ int lbm_adjoint_steps(lbm_handle *h, const void *states, size_t stride, int32_t 
  * float32 phi, T (and optional ux, uy) given to lbm_init. */
 int lbm_adjoint_init(lbm_handle *h, const lbm_fields *init, const void *adj0, float *dT0,
                      double *d_dparams);
+
+/* LBM_MODEL_PHASE_FIELD: the imposed velocity u(x) (ux, uy of `u`, same
+ * layout and pointer rules as lbm_init) and its time factor: the velocity at
+ * step n is u(x) cos(pi n / period) when period > 0 (the reversing vortex of
+ * Sec. 4.1 uses period = 2 T_f), u(x) otherwise.  Call before lbm_init, which
+ * then builds the populations with that velocity.  LBM_EUNSUPPORTED for the
+ * coupled model. */
+int lbm_set_velocity(lbm_handle *h, const lbm_fields *u, double period);
 
 /* Allocation-free global sums (no counterpart in the paper).  For callers
  * that must not allocate device memory at all -- for example code running

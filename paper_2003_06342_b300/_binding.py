@@ -29,6 +29,9 @@ LBM_STORE_FP32 = 0
 LBM_STORE_FP16 = 1
 LBM_STORE_BF16 = 2
 
+LBM_MODEL_COUPLED = 0
+LBM_MODEL_PHASE_FIELD = 1
+
 
 class lbm_grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
@@ -50,6 +53,7 @@ class lbm_params(ctypes.Structure):
         ("store_ref", ctypes.c_double * 3), ("store_scale", ctypes.c_double * 3),
         ("source_on", ctypes.c_int32), ("visc_interp", ctypes.c_int32),
         ("alpha_interp", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("model", ctypes.c_int32),
     ]
 
 
@@ -96,6 +100,7 @@ SIGNATURES = {
     "lbm_adjoint_init": (ctypes.c_int, [H, P(lbm_fields), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     "lbm_step_record": (ctypes.c_int, [H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t]),
+    "lbm_set_velocity": (ctypes.c_int, [H, P(lbm_fields), ctypes.c_double]),
     "lbm_destroy": (None, [H]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

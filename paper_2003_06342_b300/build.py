@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbmpf.so")
 SOURCES = ["api.cu", "lbm2d.cu", "lbm3d.cu", "reduce.cu", "noalloc.cu", "adjoint2d.cu", "lbm2d_tma.cu",
-           "lbm3d_tma.cu"]
+           "lbm3d_tma.cu", "cac2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

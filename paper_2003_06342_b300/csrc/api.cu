@@ -41,6 +41,9 @@ struct lbm_handle {
     int tma_blocks;
     lbm::TmaMaps2d maps;
     lbm::TmaMaps3d maps3;
+    float *vel;              // LBM_MODEL_PHASE_FIELD: imposed velocity, dim planes
+    double vel_period;       // time factor cos(pi n / period) when > 0
+    int vel_set;
 };
 
 namespace {
@@ -50,7 +53,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t pops, phi, q, scratch, partial, red, err, total;
+    size_t pops, phi, q, scratch, partial, red, err, vel, total;
     int red_blocks;
 };
 
@@ -78,6 +81,11 @@ int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
           p->sigma >= 0 && p->normal_eps > 0))
         return LBM_EINVAL;
     if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16) return LBM_EINVAL;
+    if (p->model != LBM_MODEL_COUPLED && p->model != LBM_MODEL_PHASE_FIELD) return LBM_EINVAL;
+    if (p->model == LBM_MODEL_PHASE_FIELD) {
+        if (p->source_on) return LBM_EINVAL;          // no phase change in this model
+        if (dim != 2) return LBM_EUNSUPPORTED;
+    }
     const double vals[] = {p->rho_l, p->rho_g, p->nu_l, p->nu_g, p->alpha_l, p->alpha_g, p->sigma,
                            p->W, p->M_phi, p->A, p->theta_I, p->L, p->Cp, p->T_sat,
                            p->gravity[0], p->gravity[1], p->gravity[2], p->body_force[0],
@@ -102,7 +110,8 @@ Layout layout(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
     L.partial = align_up((size_t)L.red_blocks * 2 * sizeof(double));
     L.red = align_up(2 * sizeof(double));
     L.err = align_up(sizeof(int));
-    L.total = 2 * L.pops + L.phi + 2 * L.q + L.scratch + L.partial + L.red + L.err;
+    L.vel = p->model == LBM_MODEL_PHASE_FIELD ? align_up((size_t)dim * N * sizeof(float)) : 0;
+    L.total = 2 * L.pops + L.phi + 2 * L.q + L.scratch + L.partial + L.red + L.err + L.vel;
     return L;
 }
 
@@ -192,6 +201,18 @@ void setup_tma(lbm_handle *h) {
 int do_step(lbm_handle *h) {
     const int nxt = h->cur ^ 1;
     cudaError_t e;
+    if (h->params.model == LBM_MODEL_PHASE_FIELD) {
+        const double n = (double)h->steps;
+        const float factor = h->vel_period > 0.0 ? (float)std::cos(M_PI * n / h->vel_period) : 1.0f;
+        switch (h->params.storage) {
+        case LBM_STORE_FP32: e = launch_cac2d<float>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
+        case LBM_STORE_FP16: e = launch_cac2d<__half>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
+        default: e = launch_cac2d<__nv_bfloat16>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
+        }
+        if (e != cudaSuccess) return LBM_ECUDA;
+        h->cur = nxt;
+        return LBM_OK;
+    }
     if (h->dim == 2 && h->kernel_choice == LBM_KERNEL_TMA) {
         if (h->tma_state == 0) setup_tma(h);
         if (h->tma_state == 1) {
@@ -358,6 +379,9 @@ int lbm_create(const lbm_grid *grid, int32_t lattice, const lbm_params *params, 
     h->partial = (double *)p; p += L.partial;
     h->red_out = (double *)p; p += L.red;
     h->err = (int *)p; p += L.err;
+    h->vel = L.vel ? (float *)p : nullptr; p += L.vel;
+    h->vel_period = 0.0;
+    h->vel_set = 0;
     h->red_blocks = L.red_blocks;
     h->kernel_choice = LBM_KERNEL_AUTO;
     h->tma_state = 0;
@@ -386,6 +410,11 @@ int lbm_init(lbm_handle *h, const lbm_fields *in) {
     if ((r = stage_in(h, in->uy, in->on_device, in->dtype, 3, &u0[1])) != LBM_OK) return r;
     if (h->dim == 3 && (r = stage_in(h, in->uz, in->on_device, in->dtype, 4, &u0[2])) != LBM_OK) return r;
     if ((r = stage_in(h, in->p, in->on_device, in->dtype, 5, &p0)) != LBM_OK) return r;
+    if (h->params.model == LBM_MODEL_PHASE_FIELD) {
+        // the populations start from the imposed velocity (factor 1 at n = 0)
+        u0[0] = h->vel_set ? h->vel : nullptr;
+        u0[1] = h->vel_set ? h->vel + h->N : nullptr;
+    }
     h->cur = 0;
     h->steps = 0;
     return do_init(h, phi0, T0, u0, p0);
@@ -581,7 +610,9 @@ int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
 
 static int adjoint_supported(const lbm_handle *h) {
     if (!h) return LBM_EINVAL;
-    if (h->dim != 2 || h->params.storage != LBM_STORE_FP32) return LBM_EUNSUPPORTED;
+    if (h->dim != 2 || h->params.storage != LBM_STORE_FP32 ||
+        h->params.model != LBM_MODEL_COUPLED)
+        return LBM_EUNSUPPORTED;
     return LBM_OK;
 }
 
@@ -609,6 +640,24 @@ int lbm_adjoint_step(lbm_handle *h, const void *state, const void *adj_next, voi
     if (!state || !adj_next || !adj || !scratch || !d_dparams || adj == adj_next) return LBM_EINVAL;
     return cuda_status(launch_adj_step2d((const float *)state, (const float *)adj_next, (float *)adj,
                                          (float *)scratch, d_dparams, h->dp, h->stream));
+}
+
+int lbm_set_velocity(lbm_handle *h, const lbm_fields *u, double period) {
+    if (!h || !u || !u->ux || (h->dim >= 2 && !u->uy)) return LBM_EINVAL;
+    if (h->params.model != LBM_MODEL_PHASE_FIELD) return LBM_EUNSUPPORTED;
+    if (!std::isfinite(period) || period < 0.0) return LBM_EINVAL;
+    const void *src[2] = {u->ux, u->uy};
+    for (int a = 0; a < h->dim; ++a) {
+        const float *dev;
+        const int r = stage_in(h, src[a], u->on_device, u->dtype, a, &dev);
+        if (r != LBM_OK) return r;
+        if (cudaMemcpyAsync(h->vel + (size_t)a * h->N, dev, h->N * sizeof(float),
+                            cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+            return LBM_ECUDA;
+    }
+    h->vel_period = period;
+    h->vel_set = 1;
+    return LBM_OK;
 }
 
 int lbm_adjoint_steps(lbm_handle *h, const void *states, size_t stride, int32_t count,

@@ -38,6 +38,12 @@ __device__ __forceinline__ void block_sum2(double a, double b, double *partial) 
     }
 }
 
+// 2D phase field alone in an imposed velocity u(x) * factor (cac2d.cu);
+// vel holds ux then uy, N floats each
+template <typename S>
+cudaError_t launch_cac2d(const void *pin, void *pout, const float *vel, float factor,
+                         const DevParams &P, cudaStream_t st);
+
 // 2D (lbm2d.cu); S = float, __half or __nv_bfloat16 storage
 template <typename S>
 cudaError_t launch_step2d(const void *pin, void *pout, float *phi_prev, const float *q_in,

@@ -33,6 +33,7 @@ def make_params(d, storage="fp32", store_ref=None, store_scale=None):
     p.visc_interp = int(d.get("visc_interp", 0))
     p.alpha_interp = int(d.get("alpha_interp", 0))
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.model = int(d.get("model", 0))
     return p
 
 
@@ -150,6 +151,20 @@ class Solver:
         f.p = p.ctypes.data if p is not None else None
         f.on_device, f.dtype = 0, 1
         B.check(B.lib.lbm_init(self._h, ctypes.byref(f)), "lbm_init")
+        return self
+
+    def set_velocity(self, u, period=0.0):
+        """Phase-field model: the imposed velocity (list of per-axis arrays)
+        and its time factor cos(pi n / period) (period 0: constant)."""
+        arrs = [np.ascontiguousarray(ua, dtype=np.float64) for ua in u]
+        f = B.lbm_fields()
+        f.phi = f.T = None
+        f.ux = arrs[0].ctypes.data
+        f.uy = arrs[1].ctypes.data if len(arrs) > 1 else None
+        f.uz = arrs[2].ctypes.data if len(arrs) > 2 else None
+        f.p = None
+        f.on_device, f.dtype = 0, 1
+        B.check(B.lib.lbm_set_velocity(self._h, ctypes.byref(f), float(period)), "lbm_set_velocity")
         return self
 
     def step(self, n=1):

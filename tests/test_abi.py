@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 import workloads as W
@@ -134,3 +136,38 @@ def test_calls_reject_bad_arguments_before_device_work():
                             None, ctypes.byref(h2)) == B.LBM_OK
     assert B.lib.lbm_adjoint_bytes(h2, ctypes.byref(a), ctypes.byref(sc)) == B.LBM_EUNSUPPORTED
     B.lib.lbm_destroy(h2)
+
+
+def test_phase_field_model_validation():
+    w = W.vortex_disk(n=33)
+    g = B.lbm_grid()
+    g.nx, g.ny, g.nz = 33, 33, 1
+    g.periodic[:] = [1, 1, 1]
+    size = ctypes.c_size_t()
+    p = make_params(w.params)
+    assert B.lib.lbm_workspace_bytes(ctypes.byref(g), B.LBM_D2Q9, ctypes.byref(p), ctypes.byref(size)) == B.LBM_OK
+    pc = make_params(dict(w.params, model=0))
+    size_c = ctypes.c_size_t()
+    B.lib.lbm_workspace_bytes(ctypes.byref(g), B.LBM_D2Q9, ctypes.byref(pc), ctypes.byref(size_c))
+    assert size.value > size_c.value                       # room for the imposed velocity
+    for bad in (dict(w.params, model=2), dict(w.params, source_on=1)):
+        pb = make_params(bad)
+        assert B.lib.lbm_workspace_bytes(ctypes.byref(g), B.LBM_D2Q9, ctypes.byref(pb),
+                                         ctypes.byref(size_c)) == B.LBM_EINVAL
+    g3 = B.lbm_grid()
+    g3.nx, g3.ny, g3.nz = 8, 8, 8
+    g3.periodic[:] = [1, 1, 1]
+    assert B.lib.lbm_workspace_bytes(ctypes.byref(g3), B.LBM_D3Q19_D3Q7, ctypes.byref(p),
+                                     ctypes.byref(size_c)) == B.LBM_EUNSUPPORTED
+    # lbm_set_velocity belongs to the phase-field model only
+    buf = (ctypes.c_uint8 * (size.value + 512))()
+    base = (ctypes.addressof(buf) + 255) // 256 * 256
+    h = ctypes.c_void_p()
+    assert B.lib.lbm_create(ctypes.byref(g), B.LBM_D2Q9, ctypes.byref(pc), ctypes.c_void_p(base),
+                            size.value, None, ctypes.byref(h)) == B.LBM_OK
+    f = B.lbm_fields()
+    ux = np.zeros(33 * 33)
+    f.ux = f.uy = ux.ctypes.data
+    f.on_device, f.dtype = 0, 1
+    assert B.lib.lbm_set_velocity(h, ctypes.byref(f), 0.0) == B.LBM_EUNSUPPORTED
+    B.lib.lbm_destroy(h)
