@@ -111,8 +111,9 @@ typedef struct {
 
 /* Device workspace needed by lbm_create for this grid, lattice and storage:
  * two population buffers (read/write per step), phi^{n-1}, two lagged-source
- * buffers, moment and reduction scratch.  Returns LBM_EINVAL on an invalid
- * grid or parameter set. */
+ * buffers, moment and reduction scratch, and for LBM_MODEL_PHASE_FIELD the
+ * imposed velocity.  Returns LBM_EINVAL on an invalid grid or parameter set,
+ * LBM_EUNSUPPORTED for a model not built for the lattice. */
 int lbm_workspace_bytes(const lbm_grid *grid, int32_t lattice, const lbm_params *params,
                         size_t *bytes);
 
@@ -171,10 +172,10 @@ int lbm_stream_map(lbm_handle *h, int32_t set, int32_t *src_index, int8_t *kind)
 
 /* Kernel variants of the step.  TILED reads populations with plain loads.
  * TMA stages them in shared memory with bulk tensor copies, available when the
- * grid allows 16-byte-aligned tensor boxes: in 2D a persistent kernel (row and
- * plane strides a multiple of 16 bytes, at least 66 x 18 cells), in 3D the
- * z-marching kernel with each tile layer staged a layer ahead (n_x a multiple
- * of 4 for FP32 or 8 for 16-bit storage, at least 32 x 8 cells per layer).
+ * grid allows 16-byte-aligned tensor boxes (n_x a multiple of 4 for FP32 or 8
+ * for 16-bit storage, at least 32 x 8 cells per plane): in 2D a kernel that
+ * marches 32-column strips in chunks of 8 rows, in 3D the z-marching kernel,
+ * each staging the next chunk or layer while the current one is computed.
  * AUTO (default) is the faster of the two on B300: TILED in 2D, TMA in 3D when
  * available (else TILED).  Tiled and TMA variants compute the same update bit
  * for bit. */
