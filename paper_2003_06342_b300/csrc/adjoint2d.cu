@@ -132,7 +132,9 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         const float jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
         float sf = f[0], ss = s[0];
         for (int i = 1; i < 9; ++i) { sf += f[i]; ss += s[i]; }
-        const float ir = 1.0f / rho;
+        // reciprocals and 1/|grad phi| by the one-instruction approximations
+        // the forward step uses (rcp.approx / rsqrt.approx)
+        const float ir = rcp_approx(rho);
         const float ux = (3.0f * jx + 0.5f * Fx) * ir;
         const float uy = (3.0f * jy + 0.5f * Fy) * ir;
         const float cs2 = L::cs2;
@@ -151,13 +153,14 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         const float q = P.source_on ? -(P.prod_coef * alpha) * Th * P2 : 0.0f;
         const float sq = gx * gx + gy * gy;
         const bool big = sq > P.eps2;
-        const float dnrm = big ? sqrtf(sq) : sqrtf(P.eps2);
-        const float n0 = gx / dnrm, n1 = gy / dnrm;
+        const float idn = rsqrt_approx(big ? sq : P.eps2);      // 1 / max(|grad phi|, eps)
+        const float n0 = gx * idn, n1 = gy * idn;
         const float om_g = P.om_g;
         const float Bv = pc * P.nu_l + (1.0f - pc) * P.nu_g;
-        const float nu = P.visc_interp == 0 ? P.nu_l * P.nu_g / Bv : (1.0f - pc) * P.nu_l + pc * P.nu_g;
-        const float om_f = 1.0f / (3.0f * nu + 0.5f);
-        const float om_s = 1.0f / (3.0f * alpha + 0.5f);
+        const float iBv = rcp_approx(Bv);
+        const float nu = P.visc_interp == 0 ? P.nu_l * P.nu_g * iBv : (1.0f - pc) * P.nu_l + pc * P.nu_g;
+        const float om_f = rcp_approx(3.0f * nu + 0.5f);
+        const float om_s = rcp_approx(3.0f * alpha + 0.5f);
         const float D = (phd - phip) + ug + ph * q * P.kappa;
         const float usq15 = 1.5f * (ux * ux + uy * uy);
         const float iface = P.four_over_W * P2;
@@ -281,7 +284,7 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         // relaxation rates
         float l_alpha = -3.0f * om_s * om_s * l_om_s;
         const float l_nu = -3.0f * om_f * om_f * l_om_f;
-        float l_pc = P.visc_interp == 0 ? -P.nu_l * P.nu_g * (P.nu_l - P.nu_g) / (Bv * Bv) * l_nu
+        float l_pc = P.visc_interp == 0 ? -P.nu_l * P.nu_g * (P.nu_l - P.nu_g) * (iBv * iBv) * l_nu
                                         : (P.nu_g - P.nu_l) * l_nu;
         // M_phi enters om_g = 1 / (M_phi / cs2_g + 1/2): d om_g / d M_phi = -om_g^2 / cs2_g
         dM += (-om_g * om_g * L::inv_cs2) * l_om_g;
@@ -289,11 +292,11 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         float l_gx = 0.0f, l_gy = 0.0f;
         if (big) {
             const float ndot = n0 * l_n0 + n1 * l_n1;
-            l_gx += (l_n0 - n0 * ndot) / dnrm;
-            l_gy += (l_n1 - n1 * ndot) / dnrm;
+            l_gx += (l_n0 - n0 * ndot) * idn;
+            l_gy += (l_n1 - n1 * ndot) * idn;
         } else {
-            l_gx += l_n0 / dnrm;
-            l_gy += l_n1 / dnrm;
+            l_gx += l_n0 * idn;
+            l_gy += l_n1 * idn;
         }
         // production rate
         float l_T = 0.0f, l_Cl = 0.0f;
