@@ -43,6 +43,7 @@ extern "C" {
 #define LBM_ENONFINITE   -4   /* a reduction found NaN or Inf in the fields      */
 #define LBM_ETIMEOUT     -5   /* a bounded in-kernel wait expired (see lbm_sync) */
 #define LBM_EUNSUPPORTED -6   /* combination not built (e.g. lattice/storage)    */
+#define LBM_EBOUNDS      -7   /* an index check failed (bounds-checking build)  */
 
 /* ---- lattices (Sec. 3, lattice definitions) ----------------------------- */
 #define LBM_D2Q9        0     /* 2D: D2Q9 for f, g and s                         */
@@ -205,7 +206,11 @@ int lbm_last_launches(const lbm_handle *h, int32_t *launches);
 
 /* Wait for the handle's stream; report any pending CUDA error, or
  * LBM_ETIMEOUT if a bounded wait inside a step kernel expired (the kernel then
- * stopped early and the state is not valid). */
+ * stopped early and the state is not valid), or -- in the bounds-checking
+ * build of the library (liblbmpf_debug.so, every computed population and
+ * field index checked against its buffer, a failing access skipped) --
+ * LBM_EBOUNDS if a check failed since lbm_init / lbm_set_state.  The status
+ * is cleared when reported. */
 int lbm_sync(lbm_handle *h);
 
 /* ---- discrete adjoint (2D, FP32 storage) ----------------------------------

@@ -2,13 +2,16 @@
 
 Every function of the C ABI is exposed under its own name on `lib`.  Loading
 fails loudly when the in-tree library has not been built: there is no
-fallback implementation.
+fallback implementation.  With LBM_PF_DEBUG=1 in the environment the
+bounds-checking build (liblbmpf_debug.so: every computed index checked against
+its buffer, failures reported by lbm_sync as LBM_EBOUNDS) is loaded instead.
 """
 import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "liblbmpf.so")
+DEBUG = os.environ.get("LBM_PF_DEBUG", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "_lib", "liblbmpf_debug.so" if DEBUG else "liblbmpf.so")
 
 LBM_OK = 0
 LBM_EINVAL = -1
@@ -17,6 +20,7 @@ LBM_ECUDA = -3
 LBM_ENONFINITE = -4
 LBM_ETIMEOUT = -5
 LBM_EUNSUPPORTED = -6
+LBM_EBOUNDS = -7
 
 LBM_D2Q9 = 0
 LBM_D3Q19_D3Q7 = 1

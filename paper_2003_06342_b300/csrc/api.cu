@@ -41,6 +41,7 @@ struct lbm_handle {
     int tma_blocks;
     lbm::TmaMaps2d maps;
     lbm::TmaMaps3d maps3;
+    int err_ready;           // the status word has been cleared on the device
     float *vel;              // LBM_MODEL_PHASE_FIELD: imposed velocity, dim planes
     double vel_period;       // time factor cos(pi n / period) when > 0
     int vel_set;
@@ -152,6 +153,9 @@ void fill_devparams(lbm_handle *h) {
     d.s_ref = (float)p.store_ref[2];
     d.g_ref = (float)p.store_ref[1];
     d.inv_Cp = (float)(1.0 / p.Cp);
+#ifdef LBM_CHECK_BOUNDS
+    d.dbg = h->err;
+#endif
     d.Cp_over_L2 = (float)(p.Cp / (p.L * p.L));
     // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
     int k = 0;
@@ -336,6 +340,7 @@ const char *lbm_strerror(int code) {
     case LBM_ECUDA: return "CUDA error";
     case LBM_ENONFINITE: return "non-finite value in the fields";
     case LBM_ETIMEOUT: return "timeout";
+    case LBM_EBOUNDS: return "an index check of the bounds-checking build failed";
     case LBM_EUNSUPPORTED: return "unsupported combination";
     default: return "unknown error";
     }
@@ -382,6 +387,7 @@ int lbm_create(const lbm_grid *grid, int32_t lattice, const lbm_params *params, 
     h->vel = L.vel ? (float *)p : nullptr; p += L.vel;
     h->vel_period = 0.0;
     h->vel_set = 0;
+    h->err_ready = 0;
     h->red_blocks = L.red_blocks;
     h->kernel_choice = LBM_KERNEL_AUTO;
     h->tma_state = 0;
@@ -417,6 +423,8 @@ int lbm_init(lbm_handle *h, const lbm_fields *in) {
     }
     h->cur = 0;
     h->steps = 0;
+    if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return LBM_ECUDA;
+    h->err_ready = 1;
     return do_init(h, phi0, T0, u0, p0);
 }
 
@@ -548,8 +556,11 @@ int lbm_get_state(lbm_handle *h, void *dst, size_t bytes, int32_t on_device) {
 int lbm_set_state(lbm_handle *h, const void *src, size_t bytes, int32_t on_device) {
     if (!h) return LBM_EINVAL;
     const int r = copy_state(h, const_cast<void *>(src), bytes, on_device, false);
-    if (r == LBM_OK) h->steps = 0;
-    return r;
+    if (r != LBM_OK) return r;
+    h->steps = 0;
+    if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return LBM_ECUDA;
+    h->err_ready = 1;
+    return LBM_OK;
 }
 
 int lbm_stream_map(lbm_handle *h, int32_t set, int32_t *src_index, int8_t *kind) {
@@ -576,13 +587,14 @@ int lbm_sync(lbm_handle *h) {
     if (!h) return LBM_EINVAL;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
     if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
-    if (h->tma_state == 1) {
-        int flag = 0;
-        if (cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ECUDA;
-        if (flag) {
-            cudaMemset(h->err, 0, sizeof(int));
-            return LBM_ETIMEOUT;
-        }
+    if (!h->err_ready) return LBM_OK;          // no kernel has run yet
+    // the status word: bit 1 a bounded wait expired, bit 2 an index check of
+    // the bounds-checking build failed
+    int flag = 0;
+    if (cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ECUDA;
+    if (flag) {
+        cudaMemset(h->err, 0, sizeof(int));
+        return (flag & 2) ? LBM_EBOUNDS : LBM_ETIMEOUT;
     }
     return LBM_OK;
 }

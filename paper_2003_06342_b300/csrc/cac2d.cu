@@ -27,7 +27,8 @@ __device__ __forceinline__ void cac_push2d(int i, float v, int x, int y, size_t 
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     if (FAST) {
-        PL.out[9 + i][(long long)c + ((long long)ey * nx + ex)] = narrow<S>(v);
+        const long long d = (long long)c + ((long long)ey * nx + ex);
+        if (in_bounds(d, (long long)N, P)) PL.out[9 + i][d] = narrow<S>(v);
         return;
     }
     int dx = x + ex, dy = y + ey;
@@ -37,9 +38,11 @@ __device__ __forceinline__ void cac_push2d(int i, float v, int x, int y, size_t 
         const int side = (kx >= 2 ? kx : ky) - 2;
         const int o = L::opp(i);
         const float m2 = 2.0f * (IsNarrow<S>::value ? P.set_sc[1] : L::w(i));
-        pout[(9 + o) * N + c] = narrow<S>(fmaf(m2, P.phi_wall[side] - P.g_ref, -v));
+        if (in_bounds((long long)c, (long long)N, P))
+            pout[(9 + o) * N + c] = narrow<S>(fmaf(m2, P.phi_wall[side] - P.g_ref, -v));
     } else {
-        pout[(9 + i) * N + (size_t)dy * nx + dx] = narrow<S>(v);
+        const size_t d = (size_t)dy * nx + dx;
+        if (in_bounds((long long)d, (long long)N, P)) pout[(9 + i) * N + d] = narrow<S>(v);
     }
 }
 
@@ -69,6 +72,7 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
         const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
 #pragma unroll
         for (int i = 0; i < 9; ++i) rv[i] = load_raw(pin + (9 + i) * N + cc);
+        (void)in_bounds((long long)cc, (long long)N, P);
     }
     float g[9];
     if (active) {

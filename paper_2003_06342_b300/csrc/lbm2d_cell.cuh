@@ -157,9 +157,11 @@ __device__ __forceinline__ void push2d(int i, float vf, float vg, float vs, int 
     const size_t N = (size_t)P.N;
     if (FAST) {
         const long long d = (long long)c + ((long long)ey * nx + ex);
-        PL.out[i][d] = narrow<S>(vf);
-        PL.out[9 + i][d] = narrow<S>(vg);
-        PL.out[18 + i][d] = narrow<S>(vs);
+        if (in_bounds(d, (long long)N, P)) {
+            PL.out[i][d] = narrow<S>(vf);
+            PL.out[9 + i][d] = narrow<S>(vg);
+            PL.out[18 + i][d] = narrow<S>(vs);
+        }
         return;
     }
     int dx = x + ex, dy = y + ey;
@@ -171,11 +173,13 @@ __device__ __forceinline__ void push2d(int i, float vf, float vg, float vs, int 
         // working representation
         const int side = (kx >= 2 ? kx : ky) - 2;
         const int o = L::opp(i);
+        if (!in_bounds((long long)c, (long long)N, P)) return;
         pout[o * N + c] = narrow<S>(vf);
         pout[(9 + o) * N + c] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 1, P), P.phi_wall[side] - P.g_ref, -vg));
         pout[(18 + o) * N + c] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 2, P), P.T_wall[side] - P.s_ref, -vs));
     } else {
         const size_t d = (size_t)dy * nx + dx;
+        if (!in_bounds((long long)d, (long long)N, P)) return;
         pout[i * N + d] = narrow<S>(vf);
         pout[(9 + i) * N + d] = narrow<S>(vg);
         pout[(18 + i) * N + d] = narrow<S>(vs);
@@ -260,8 +264,10 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     const float om_g = P.om_g;
     const float D = fmaf(ph * q, P.kappa, (phd - phip) + ug);
 
-    phi_prev[c] = phd;          // stored as phi - phi_ref
-    q_out[c] = q;
+    if (in_bounds((long long)c, P.N, P)) {
+        phi_prev[c] = phd;      // stored as phi - phi_ref
+        q_out[c] = q;
+    }
 
     const float ux = m.ux, uy = m.uy;
     const float b_g = fmaf(-0.5f, om_g, 1.0f), b_f = fmaf(-0.5f, om_f, 1.0f);
@@ -333,6 +339,7 @@ __device__ __forceinline__ float phid_cell2d(const S *__restrict__ pin, size_t c
     float v[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) v[i] = load_raw(pin + (9 + i) * N + cc);
+    (void)in_bounds((long long)cc, (long long)N, P);
     return fmaf(0.5f, qv, set_sum2d<S>(v, P.set_isc[1]));
 }
 
@@ -352,6 +359,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     const size_t c = active ? (size_t)y * nx + x : 0;
 
     float f[9], g[9], s[9], phip = 0.0f, qp = 0.0f;
+    (void)in_bounds(active ? (long long)c : 0, P.N, P);
     // FAST: the ring cells' g and q are requested first, so their latency
     // (an L2 hit: the neighbouring tiles load the same lines) overlaps the
     // tile's own loads instead of following them
@@ -366,9 +374,10 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
         else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
         rslot = sy * SX + sx;
         const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
+        const bool ok = in_bounds((long long)cc, (long long)N, P);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) rv[i] = load_raw(pin + (9 + i) * N + cc);
-        rq = q_in[cc];
+        for (int i = 0; i < 9; ++i) rv[i] = ok ? load_raw(pin + (9 + i) * N + cc) : 0.0f;
+        rq = ok ? q_in[cc] : 0.0f;
     }
     if (active) {
 #pragma unroll

@@ -127,6 +127,7 @@ __device__ __forceinline__ void ring2_prefetch(uint32_t *buf, const S *__restric
     int slot;
     const size_t cc = ring2_cell(tid, x0, y0, P.n[0], slot);
     const size_t N = (size_t)P.N;
+    if (!in_bounds((long long)cc, (long long)N, P)) return;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const size_t e = (9 + i) * N + cc;
@@ -256,7 +257,7 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
             }
         }
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(err, 1);
+            if (tid == 0) atomicOr(err, 1);
             asm volatile("cp.async.wait_all;" ::: "memory");
             F.drain(barF, Gm::NFS);                 // copies that may still land
             G.drain(barG, Gm::NG);

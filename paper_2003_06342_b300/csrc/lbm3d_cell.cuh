@@ -181,6 +181,7 @@ __device__ __forceinline__ float phid_at(const S *__restrict__ pin, const float 
     float v[QG];
 #pragma unroll
     for (int i = 0; i < QG; ++i) v[i] = load_raw(pin + (G0 + i) * N + cc);
+    (void)in_bounds((long long)cc, (long long)N, P);
     return fmaf(0.5f, q_in[cc], set_sum7<S>(v, P.set_isc[1]));
 }
 
@@ -309,6 +310,7 @@ __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int 
     const size_t N = (size_t)P.N;
     if (MODE == XY_IN) {
         const long long off = ((long long)ez * ny + ey) * nx + ex;
+        if (!in_bounds((long long)c + off, (long long)N, P)) return;
         if (PLP) PL.out[plane0 + i][(long long)c + off] = narrow<S>(v);
         else pout[(plane0 + i) * N + c + off] = narrow<S>(v);
         return;
@@ -320,6 +322,7 @@ __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int 
         if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
         if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
         const long long off = (long long)ez * ny * nx + oxy;
+        if (!in_bounds((long long)c + off, (long long)N, P)) return;
         if (PLP) PL.out[plane0 + i][(long long)c + off] = narrow<S>(v);
         else pout[(plane0 + i) * N + c + off] = narrow<S>(v);
         return;
@@ -335,9 +338,10 @@ __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int 
             const float wall = set == 1 ? P.phi_wall[side] - P.g_ref : P.T_wall[side] - P.s_ref;
             v = fmaf(2.0f * wall_mul3<S, Lt>(i, set, P), wall, -v);
         }
-        pout[(plane0 + o) * N + c] = narrow<S>(v);
+        if (in_bounds((long long)c, (long long)N, P)) pout[(plane0 + o) * N + c] = narrow<S>(v);
     } else {
-        pout[(plane0 + i) * N + ((size_t)dz * ny + dy) * nx + dx] = narrow<S>(v);
+        const size_t d = ((size_t)dz * ny + dy) * nx + dx;
+        if (in_bounds((long long)d, (long long)N, P)) pout[(plane0 + i) * N + d] = narrow<S>(v);
     }
 }
 
@@ -410,8 +414,10 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float om_s = rcp_approx(fmaf(LF::inv_cs2, diffusivity(ph, P), 0.5f));
     const float om_g = P.om_g;
     const float D = fmaf(ph * q, P.kappa, (phd - phip) + ug);
-    phi_prev[c] = phd;           // stored as phi - phi_ref
-    q_out[c] = q;
+    if (in_bounds((long long)c, P.N, P)) {
+        phi_prev[c] = phd;       // stored as phi - phi_ref
+        q_out[c] = q;
+    }
 
     const float usq = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
     const float b_g = fmaf(-0.5f, om_g, 1.0f), b_f = fmaf(-0.5f, om_f, 1.0f);

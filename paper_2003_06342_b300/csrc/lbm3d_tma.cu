@@ -141,6 +141,7 @@ __device__ __forceinline__ void ring_prefetch(uint32_t *buf, const S *__restrict
     int slot;
     const size_t cc = ring_cell<XY>(tid, z, x0, y0, P, slot);
     const size_t N = (size_t)P.N;
+    if (!in_bounds((long long)cc, (long long)N, P)) return;
 #pragma unroll
     for (int i = 0; i < QG; ++i) {
         const size_t e = (G0 + i) * N + cc;
@@ -243,7 +244,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
         }
         ok = F.wait(barF, fb) && ok;
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(err, 1);
+            if (tid == 0) atomicOr(err, 1);
             cp_async_wait_all();
             F.drain(barF, Gm::NFS);                  // copies that may still land
             G.drain(barG, Gm::NG);

@@ -108,7 +108,27 @@ struct DevParams {
     float enc_c[MAXQ_TOTAL], enc_s[MAXQ_TOTAL], dec_s[MAXQ_TOTAL];
     // per set (f, g, s): storage reference, 16-bit scale and its inverse
     float set_ref[3], set_sc[3], set_isc[3];
+#ifdef LBM_CHECK_BOUNDS
+    int *dbg;                          // device status word of the bounds checks
+#endif
 };
+
+// Index check of the bounds-checking build (compiled with LBM_CHECK_BOUNDS):
+// an index outside [0, lim) sets bit 2 of the handle's status word and the
+// caller skips the access; lbm_sync reports it as LBM_EBOUNDS.  The normal
+// build compiles every check away and its kernel parameters keep no status
+// pointer (a larger parameter block measurably slowed the 16-bit 2D kernels).  Callers never return early on a failed
+// check, so no thread leaves a block barrier behind.
+__device__ __forceinline__ bool in_bounds(long long idx, long long lim, const DevParams &P) {
+#ifdef LBM_CHECK_BOUNDS
+    if (idx < 0 || idx >= lim) {
+        if (P.dbg) atomicOr(P.dbg, 2);
+        return false;
+    }
+#endif
+    (void)idx; (void)lim; (void)P;
+    return true;
+}
 
 // ---------------------------------------------------------------- storage
 template <typename S> struct Codec;

@@ -35,6 +35,16 @@ def test_every_declared_symbol_is_exported():
     assert names <= set(B.SIGNATURES)
 
 
+def test_bounds_checking_build_exports_the_same_abi():
+    """liblbmpf_debug.so (LBM_CHECK_BOUNDS) is a drop-in replacement."""
+    path = os.path.join(os.path.dirname(B.LIB_PATH), "liblbmpf_debug.so")
+    dbg = ctypes.CDLL(path)
+    for n in sorted(declared_functions()):
+        assert hasattr(dbg, n), n
+    dbg.lbm_strerror.restype = ctypes.c_char_p
+    assert dbg.lbm_strerror(B.LBM_EBOUNDS) == B.lib.lbm_strerror(B.LBM_EBOUNDS)
+
+
 def _ws(w, storage="fp32"):
     g = make_grid(w.n, w.periodic)
     p = make_params(w.params, storage)
@@ -93,7 +103,7 @@ def test_create_checks_workspace_without_gpu():
 
 
 def test_strerror():
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert B.lib.lbm_strerror(code)
     assert B.lib.lbm_strerror(-99) == b"unknown error"
 
