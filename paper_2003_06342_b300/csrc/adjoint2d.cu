@@ -30,14 +30,27 @@ namespace lbm {
 using L = D2Q9L;
 
 // ------------------------------------------------------------------ helpers
+// Element of flat plane k of cell c in a state or adjoint-state buffer: the
+// population layout of off_f / off_g (f_i = plane i, g_i = 9 + i, s_i =
+// 18 + i), then phi^{n-1} (plane 27) and the lagged source (plane 28).
+__device__ __forceinline__ size_t st_idx(int k, size_t c, size_t N) {
+    return k < 9 ? off_f(k, c, N) : k < 18 ? off_g(9, k - 9, c, N) : k < 27 ? off_s(k - 18, c, N)
+                                                                              : (size_t)k * N + c;
+}
+
+// the (f_i, s_i) pair of cell c as one 8-byte load
+__device__ __forceinline__ float2 pair_at(const float *__restrict__ buf, int i, size_t c, size_t N) {
+    return __ldg(reinterpret_cast<const float2 *>(buf) + ((size_t)i * N + c));
+}
+
 __device__ __forceinline__ float phid_cell(const float *__restrict__ st, size_t c, size_t N,
                                            const DevParams &P) {
     // phi - phi_ref of a cell from the stored state (g planes 9..17 hold
     // deviations, the lagged source is plane 28)
-    float v = st[9 * N + c];
+    float v = st[st_idx(9, c, N)];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) v += st[(9 + i) * N + c];
-    return v + 0.5f * st[28 * N + c];
+    for (int i = 1; i < 9; ++i) v += st[st_idx(9 + i, c, N)];
+    return v + 0.5f * st[st_idx(28, c, N)];
 }
 
 __device__ __forceinline__ float edot2(int ex, int ey, float a, float b) {
@@ -54,9 +67,9 @@ adj_terminal2d_kernel(const float *__restrict__ st, const float *__restrict__ ta
     double part = 0.0;
     if (c < N) {
         const float r = phid_cell(st, c, N, P) + P.g_ref - target[c];
-        for (int k = 0; k < 29; ++k) adj[k * N + c] = 0.0f;
-        for (int i = 0; i < 9; ++i) adj[(9 + i) * N + c] = r;
-        adj[28 * N + c] = 0.5f * r;
+        for (int k = 0; k < 29; ++k) adj[st_idx(k, c, N)] = 0.0f;
+        for (int i = 0; i < 9; ++i) adj[st_idx(9 + i, c, N)] = r;
+        adj[st_idx(28, c, N)] = 0.5f * r;
         part = 0.5 * (double)r * (double)r;
     }
     block_sum3_atomic(part, 0.0, 0.0, J);
@@ -104,12 +117,13 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         float f[9], g[9], s[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            f[i] = st[i * N + c] + P.enc_c[i];
-            g[i] = st[(9 + i) * N + c];
-            s[i] = st[(18 + i) * N + c];
+            const float2 fs = pair_at(st, i, c, N);
+            f[i] = fs.x + P.enc_c[i];
+            g[i] = st[st_idx(9 + i, c, N)];
+            s[i] = fs.y;
         }
-        const float phip = st[27 * N + c];
-        const float qp = st[28 * N + c];
+        const float phip = st[st_idx(27, c, N)];
+        const float qp = st[st_idx(28, c, N)];
         const float phd = nb[0];
         const float ph = phd + P.g_ref;
         const float nE = nb[1], nN = nb[2], nW = nb[3], nS = nb[4];
@@ -181,18 +195,20 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
             const int ky = wrap_coord(dy, ny, P.periodic[1]);
             if (kx >= 2 || ky >= 2) {
                 const int o = L::opp(i);
-                lf[i] = lam_next[o * N + c];
-                lg[i] = -lam_next[(9 + o) * N + c];
-                ls[i] = -lam_next[(18 + o) * N + c];
+                const float2 fs = pair_at(lam_next, o, c, N);
+                lf[i] = fs.x;
+                lg[i] = -lam_next[st_idx(9 + o, c, N)];
+                ls[i] = -fs.y;
             } else {
                 const size_t d = (size_t)dy * nx + dx;
-                lf[i] = lam_next[i * N + d];
-                lg[i] = lam_next[(9 + i) * N + d];
-                ls[i] = lam_next[(18 + i) * N + d];
+                const float2 fs = pair_at(lam_next, i, d, N);
+                lf[i] = fs.x;
+                lg[i] = lam_next[st_idx(9 + i, d, N)];
+                ls[i] = fs.y;
             }
         }
-        const float l_phip_new = lam_next[27 * N + c];
-        const float l_q_new = lam_next[28 * N + c];
+        const float l_phip_new = lam_next[st_idx(27, c, N)];
+        const float l_q_new = lam_next[st_idx(28, c, N)];
 
         // ---------------- reverse sweep
         float l_f[9], l_g[9], l_s[9];
@@ -370,12 +386,11 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         for (int i = 0; i < 9; ++i) {
             l_f[i] += l_p + (float)L::ex(i) * l_jx + (float)L::ey(i) * l_jy;
             l_s[i] += l_Td;
-            lam[i * N + c] = l_f[i];
-            lam[(9 + i) * N + c] = l_g[i];
-            lam[(18 + i) * N + c] = l_s[i];
+            reinterpret_cast<float2 *>(lam)[(size_t)i * N + c] = make_float2(l_f[i], l_s[i]);
+            lam[st_idx(9 + i, c, N)] = l_g[i];
         }
-        lam[27 * N + c] = l_phip;
-        lam[28 * N + c] = l_qp;
+        lam[st_idx(27, c, N)] = l_phip;
+        lam[st_idx(28, c, N)] = l_qp;
         // latent heat: Lc = L / Cp (d/dL = 1/Cp), Cl = Cp / L (d/dL = -Cp/L^2)
         dL += l_Lc * P.inv_Cp - l_Cl * P.Cp_over_L2;
     }
@@ -400,8 +415,8 @@ adj_step2d_b_kernel(const float *__restrict__ cst, float *__restrict__ lam, cons
         lphi += cst[j * N + (size_t)sy * nx + sx];
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) lam[(9 + i) * N + c] += lphi;
-    lam[28 * N + c] += 0.5f * lphi;
+    for (int i = 0; i < 9; ++i) lam[st_idx(9 + i, c, N)] += lphi;
+    lam[st_idx(28, c, N)] += 0.5f * lphi;
 }
 
 // ------------------------------------------------------------------ init
@@ -448,14 +463,14 @@ adj_init2d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
         const float D = (ux * gx + uy * gy) + ph * q * P.kappa;
         const float rcs2 = rho * L::cs2;
         const float usq15 = 1.5f * (ux * ux + uy * uy);
-        float l_q = lam[28 * N + c], l_Td = 0.0f, l_Lc = 0.0f, l_Fx = 0.0f, l_Fy = 0.0f;
+        float l_q = lam[st_idx(28, c, N)], l_Td = 0.0f, l_Lc = 0.0f, l_Fx = 0.0f, l_Fy = 0.0f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float w = L::w(i);
             const float cu = edot2(L::ex(i), L::ey(i), ux, uy);
             const float poly = cu * (3.0f + 4.5f * cu) - usq15;
             const float G = w + w * poly;
-            const float lf = lam[i * N + c], lg = lam[(9 + i) * N + c], ls = lam[(18 + i) * N + c];
+            const float lf = lam[st_idx(i, c, N)], lg = lam[st_idx(9 + i, c, N)], ls = lam[st_idx(18 + i, c, N)];
             // f_i = feq - fS/2, fS contains G (e - u).F + w rcs2 q kappa
             l_Fx += -0.5f * G * ((float)L::ex(i) - ux) * lf;
             l_Fy += -0.5f * G * ((float)L::ey(i) - uy) * lf;

@@ -39,10 +39,10 @@ __device__ __forceinline__ void cac_push2d(int i, float v, int x, int y, size_t 
         const int o = L::opp(i);
         const float m2 = 2.0f * (IsNarrow<S>::value ? P.set_sc[1] : L::w(i));
         if (in_bounds((long long)c, (long long)N, P))
-            pout[(9 + o) * N + c] = narrow<S>(fmaf(m2, P.phi_wall[side] - P.g_ref, -v));
+            pout[off_g(9, o, c, N)] = narrow<S>(fmaf(m2, P.phi_wall[side] - P.g_ref, -v));
     } else {
         const size_t d = (size_t)dy * nx + dx;
-        if (in_bounds((long long)d, (long long)N, P)) pout[(9 + i) * N + d] = narrow<S>(v);
+        if (in_bounds((long long)d, (long long)N, P)) pout[off_g(9, i, d, N)] = narrow<S>(v);
     }
 }
 
@@ -71,13 +71,13 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
         rslot = sy * SX + sx;
         const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) rv[i] = load_raw(pin + (9 + i) * N + cc);
+        for (int i = 0; i < 9; ++i) rv[i] = load_raw(PL.in[9 + i] + cc);
         (void)in_bounds((long long)cc, (long long)N, P);
     }
     float g[9];
     if (active) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = load_raw(FAST ? PL.in[9 + i] + c : pin + (9 + i) * N + c);
+        for (int i = 0; i < 9; ++i) g[i] = load_raw(PL.in[9 + i] + c);
         sphi[(ty + 1) * SX + tx + 1] = set_sum2d<S>(g, isc);          // phi - phi_ref
     }
     if (FAST) {
@@ -98,7 +98,7 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
                 float w9[9];
                 const size_t cc = (size_t)cy * nx + cx;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) w9[i] = load_raw(pin + (9 + i) * N + cc);
+                for (int i = 0; i < 9; ++i) w9[i] = load_raw(pin + off_g(9, i, cc, N));
                 v = set_sum2d<S>(w9, isc);
             }
             sphi[sidx] = v;

@@ -1,8 +1,8 @@
 // 2D D2Q9 kernels: the fused time step, the initialisation, the moments
 // (fields and reductions) and the streaming-map test hook.
 //
-// State between steps (per cell, structure of arrays, plane k = set*9 + i with
-// set 0 = f, 1 = g, 2 = s): the post-streaming populations of time n,
+// State between steps (structure of arrays: the (f_i, s_i) pair planes, then
+// the g planes, see off_f / off_g): the post-streaming populations of time n,
 // phi^{n-1} and the lagged source q^{n-1} = mdot'''/rho_g of the previous
 // collision.  One step is one launch of step2d_kernel:
 //   1. every 32x8 tile computes phi^n = sum_i gbar_i + q^{n-1}/2 (Eq.
@@ -49,9 +49,9 @@ __global__ void phi2d_kernel(const S *__restrict__ pin, const float *__restrict_
                              float *__restrict__ phi_out, const DevParams P) {
     const size_t N = (size_t)P.N;
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
-        float v = Codec<S>::load(pin + 9 * N + c, 9, P);
+        float v = Codec<S>::load(pin + off_g(9, 0, c, N), 9, P);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) v += Codec<S>::load(pin + (9 + i) * N + c, 9 + i, P);
+        for (int i = 1; i < 9; ++i) v += Codec<S>::load(pin + off_g(9, i, c, N), 9 + i, P);
         phi_out[c] = v + 0.5f * q_in[c];
     }
 }
@@ -90,8 +90,8 @@ macro2d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
         gather_nb2d(phi_f, x, y, nb, P);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            f[i] = Codec<S>::load(pin + i * N + c, i, P);
-            s[i] = Codec<S>::load_dev(pin + (18 + i) * N + c, 18 + i, P);
+            f[i] = Codec<S>::load(pin + off_f(i, c, N), i, P);
+            s[i] = Codec<S>::load_dev(pin + off_s(i, c, N), 18 + i, P);
         }
         Macro2 m;
         m.phi = nb[0];
@@ -138,9 +138,9 @@ init2d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const EqSrc e = eq_src2d(i, m, nx_, ny_, q, D, P);
-        Codec<S>::store(pout + i * N + c, e.feq - 0.5f * e.fS, i, P);
-        Codec<S>::store_dev(pout + (9 + i) * N + c, e.geq - 0.5f * e.gS - L::w(i) * P.g_ref, 9 + i, P);
-        Codec<S>::store_dev(pout + (18 + i) * N + c, e.seq - 0.5f * e.sS, 18 + i, P);
+        Codec<S>::store(pout + off_f(i, c, N), e.feq - 0.5f * e.fS, i, P);
+        Codec<S>::store_dev(pout + off_g(9, i, c, N), e.geq - 0.5f * e.gS - L::w(i) * P.g_ref, 9 + i, P);
+        Codec<S>::store_dev(pout + off_s(i, c, N), e.seq - 0.5f * e.sS, 18 + i, P);
     }
     phi_prev[c] = m.phi - P.g_ref;
     q_out[c] = q;

@@ -93,21 +93,25 @@ __device__ __forceinline__ void normal2d(float gx, float gy, float eps2, float &
     ny_ = gy / d;
 }
 
-// Base pointers of the 27 population planes of the buffer read and of the
-// buffer written, passed to the kernels as a parameter: a fast-path load or
-// store then addresses its plane as base + cell, with no per-plane offset
-// arithmetic (measured: 2.8% faster 2D FP32 step).
+// Base pointers of the population planes of the buffer read and of the
+// buffer written, passed to the kernels as a parameter: entries 0..8 are the
+// (f_i, s_i) pair planes, 9..17 the g planes.  A fast-path load or store then
+// addresses its plane as base + cell, with no per-plane offset arithmetic
+// (measured: 2.8% faster 2D FP32 step).
 template <typename S> struct Planes2d {
-    const S *in[27];
-    S *out[27];
+    const S *in[18];
+    S *out[18];
 };
 
 template <typename S>
 inline Planes2d<S> planes2d(const void *pin, void *pout, const DevParams &P) {
     Planes2d<S> PL;
-    for (int k = 0; k < 27; ++k) {
-        PL.in[k] = (const S *)pin + (size_t)k * (size_t)P.N;
-        PL.out[k] = (S *)pout + (size_t)k * (size_t)P.N;
+    const size_t N = (size_t)P.N;
+    for (int i = 0; i < 9; ++i) {
+        PL.in[i] = (const S *)pin + off_f(i, 0, N);
+        PL.out[i] = (S *)pout + off_f(i, 0, N);
+        PL.in[9 + i] = (const S *)pin + off_g(9, i, 0, N);
+        PL.out[9 + i] = (S *)pout + off_g(9, i, 0, N);
     }
     return PL;
 }
@@ -158,9 +162,8 @@ __device__ __forceinline__ void push2d(int i, float vf, float vg, float vs, int 
     if (FAST) {
         const long long d = (long long)c + ((long long)ey * nx + ex);
         if (in_bounds(d, (long long)N, P)) {
-            PL.out[i][d] = narrow<S>(vf);
+            store_pair<S>(PL.out[i], d, vf, vs);
             PL.out[9 + i][d] = narrow<S>(vg);
-            PL.out[18 + i][d] = narrow<S>(vs);
         }
         return;
     }
@@ -174,15 +177,14 @@ __device__ __forceinline__ void push2d(int i, float vf, float vg, float vs, int 
         const int side = (kx >= 2 ? kx : ky) - 2;
         const int o = L::opp(i);
         if (!in_bounds((long long)c, (long long)N, P)) return;
-        pout[o * N + c] = narrow<S>(vf);
-        pout[(9 + o) * N + c] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 1, P), P.phi_wall[side] - P.g_ref, -vg));
-        pout[(18 + o) * N + c] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 2, P), P.T_wall[side] - P.s_ref, -vs));
+        store_pair<S>(pout + off_f(o, 0, N), (long long)c, vf,
+                      fmaf(2.0f * rep_mul<S>(i, 2, P), P.T_wall[side] - P.s_ref, -vs));
+        pout[off_g(9, o, c, N)] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 1, P), P.phi_wall[side] - P.g_ref, -vg));
     } else {
         const size_t d = (size_t)dy * nx + dx;
         if (!in_bounds((long long)d, (long long)N, P)) return;
-        pout[i * N + d] = narrow<S>(vf);
-        pout[(9 + i) * N + d] = narrow<S>(vg);
-        pout[(18 + i) * N + d] = narrow<S>(vs);
+        store_pair<S>(pout + off_f(i, 0, N), (long long)d, vf, vs);
+        pout[off_g(9, i, d, N)] = narrow<S>(vg);
     }
 }
 
@@ -338,7 +340,7 @@ __device__ __forceinline__ float phid_cell2d(const S *__restrict__ pin, size_t c
                                              float qv, const DevParams &P) {
     float v[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) v[i] = load_raw(pin + (9 + i) * N + cc);
+    for (int i = 0; i < 9; ++i) v[i] = load_raw(pin + off_g(9, i, cc, N));
     (void)in_bounds((long long)cc, (long long)N, P);
     return fmaf(0.5f, qv, set_sum2d<S>(v, P.set_isc[1]));
 }
@@ -376,16 +378,14 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
         const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
         const bool ok = in_bounds((long long)cc, (long long)N, P);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) rv[i] = ok ? load_raw(pin + (9 + i) * N + cc) : 0.0f;
+        for (int i = 0; i < 9; ++i) rv[i] = ok ? load_raw(PL.in[9 + i] + cc) : 0.0f;
         rq = ok ? q_in[cc] : 0.0f;
     }
     if (active) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = load_raw(FAST ? PL.in[9 + i] + c : pin + (9 + i) * N + c);
+        for (int i = 0; i < 9; ++i) g[i] = load_raw(PL.in[9 + i] + c);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = load_raw(FAST ? PL.in[i] + c : pin + i * N + c);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) s[i] = load_raw(FAST ? PL.in[18 + i] + c : pin + (18 + i) * N + c);
+        for (int i = 0; i < 9; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
         phip = phi_prev[c];
         qp = q_in[c];
         sphi[(ty + 1) * SX + tx + 1] = fmaf(0.5f, qp, set_sum2d<S>(g, P.set_isc[1]));   // phi - phi_ref

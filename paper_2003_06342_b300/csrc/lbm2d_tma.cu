@@ -4,10 +4,10 @@
 // (lbm3d_tma.cu): each block owns a strip of 32 columns and walks YC chunks
 // of 8 rows through it.  One thread issues cp.async.bulk.tensor copies of a
 // chunk into shared-memory stages:
-//   f/s stage  f planes 32 x 8 x 9 from (x0, y0, 0)    3D map (x, y, plane)
-//              s planes 32 x 8 x 9 from (x0, y0, 18)
+//   f/s stage  (f_i, s_i) pair planes 32 x 8 x 9 from (x0, y0, 0)
+//                                                   3D map (x, y, pair plane)
 //              phi^{n-1} 32 x 8    from (x0, y0)       2D map (x, y)
-//   g stage    g planes 32 x 8 x 9 from (x0, y0, 9)
+//   g stage    g planes 32 x 8 x 9 from (x0, y0, 0)    3D map (x, y, g plane)
 //              q^{n-1}  32 x 8     from (x0, y0)
 // completing on the stage's mbarrier.  Two f/s stages and three g stages
 // rotate so that every copy is issued a whole chunk before it is awaited
@@ -45,9 +45,8 @@ template <typename S> struct March2Geom {
     static constexpr int al(int b) { return (b + 127) / 128 * 128; }
     static constexpr int P_BYTES = 9 * CELLS * ES;        // one set of a chunk
     static constexpr int Q_BYTES = CELLS * 4;
-    static constexpr int OFF_F = 0;
-    static constexpr int OFF_S = OFF_F + al(P_BYTES);
-    static constexpr int OFF_PP = OFF_S + al(P_BYTES);
+    static constexpr int OFF_FS = 0;                       // pairs (f_i, s_i)
+    static constexpr int OFF_PP = OFF_FS + al(2 * P_BYTES);
     static constexpr int FS_STAGE = OFF_PP + al(Q_BYTES);
     static constexpr int OFF_G = 0;
     static constexpr int OFF_Q = OFF_G + al(P_BYTES);
@@ -66,8 +65,7 @@ __device__ __forceinline__ void issue_fs2(unsigned char *stage, uint64_t *bar, c
     // order earlier generic-proxy reads of this stage before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, Gm::FS_TX);
-    tma_load_3d(stage + Gm::OFF_F, &M.pops[par], x0, y0, 0, bar);
-    tma_load_3d(stage + Gm::OFF_S, &M.pops[par], x0, y0, 18, bar);
+    tma_load_3d(stage + Gm::OFF_FS, &M.fs[par], x0, y0, 0, bar);
     tma_load_2d(stage + Gm::OFF_PP, &M.pp, x0, y0, bar);
 }
 
@@ -77,7 +75,7 @@ __device__ __forceinline__ void issue_g2(unsigned char *stage, uint64_t *bar, co
     using Gm = March2Geom<S>;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, Gm::G_TX);
-    tma_load_3d(stage + Gm::OFF_G, &M.pops[par], x0, y0, 9, bar);
+    tma_load_3d(stage + Gm::OFF_G, &M.g[par], x0, y0, 0, bar);
     tma_load_2d(stage + Gm::OFF_Q, &M.q[par], x0, y0, bar);
 }
 
@@ -130,7 +128,7 @@ __device__ __forceinline__ void ring2_prefetch(uint32_t *buf, const S *__restric
     if (!in_bounds((long long)cc, (long long)N, P)) return;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const size_t e = (9 + i) * N + cc;
+        const size_t e = off_g(9, i, cc, N);
         cp_async4_2d(&buf[i * RING2 + tid], pin + (IsNarrow<S>::value ? (e & ~(size_t)1) : e));
     }
     cp_async4_2d(&buf[9 * RING2 + tid], q_in + cc);
@@ -149,7 +147,7 @@ __device__ __forceinline__ void ring2_store(float *win, const uint32_t *buf, int
     for (int i = 0; i < 9; ++i) {
         const uint32_t w = buf[i * RING2 + tid];
         if (IsNarrow<S>::value) {
-            const size_t e = (9 + i) * N + cc;
+            const size_t e = off_g(9, i, cc, N);
             const unsigned short h = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
             S val;
             memcpy(&val, &h, 2);
@@ -269,15 +267,13 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
         if (fc) {
             const unsigned char *b = fs_base + fb * Gm::FS_STAGE;
             const unsigned char *bg = g_base + gb * Gm::G_STAGE;
-            const S *Fp = (const S *)(b + Gm::OFF_F);
-            const S *Sp = (const S *)(b + Gm::OFF_S);
+            const auto *FSp = (const typename PairOf<S>::T *)(b + Gm::OFF_FS);
             const S *Gp = (const S *)(bg + Gm::OFF_G);
             float f[9], g[9], s[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                f[i] = widen(Fp[i * Gm::CELLS + tid]);
+                unpack_pair(FSp[i * Gm::CELLS + tid], f[i], s[i]);
                 g[i] = widen(Gp[i * Gm::CELLS + tid]);
-                s[i] = widen(Sp[i * Gm::CELLS + tid]);
             }
             const float qp = ((const float *)(bg + Gm::OFF_Q))[tid];
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
@@ -321,13 +317,17 @@ int make_tma_maps2d(TmaMaps2d *M, const DevParams &P, int elem_bytes, void *cons
     const cuuint64_t nx = (cuuint64_t)P.n[0], ny = (cuuint64_t)P.n[1], N = (cuuint64_t)P.N;
     const cuuint64_t es = (cuuint64_t)elem_bytes;
     const cuuint32_t one[3] = {1, 1, 1};
+    // a single value, and a (f_i, s_i) pair copied as one element of twice the size
     const CUtensorMapDataType dt = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    auto map3 = [&](CUtensorMap *m, void *base) {
-        const cuuint64_t dims[3] = {nx, ny, 27};
-        const cuuint64_t str[2] = {nx * es, N * es};
+    const CUtensorMapDataType dt2 = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+    // 9 planes of `e` bytes per element, rows nx elements apart, planes pstride bytes apart
+    auto map3 = [&](CUtensorMap *m, void *base, CUtensorMapDataType t, cuuint64_t e, cuuint64_t pstride) {
+        const cuuint64_t dims[3] = {nx, ny, 9};
+        const cuuint64_t str[2] = {nx * e, pstride};
         const cuuint32_t box[3] = {TX, TY, 9};
-        return enc(m, dt, 3, base, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        return enc(m, t, 3, base, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
@@ -340,7 +340,8 @@ int make_tma_maps2d(TmaMaps2d *M, const DevParams &P, int elem_bytes, void *cons
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     for (int b = 0; b < 2; ++b) {
-        if (!map3(&M->pops[b], pops[b])) return -2;
+        if (!map3(&M->fs[b], pops[b], dt2, 2 * es, 2 * N * es)) return -2;
+        if (!map3(&M->g[b], (char *)pops[b] + off_g(9, 0, 0, N) * es, dt, es, N * es)) return -2;
         if (!map2(&M->q[b], q[b])) return -3;
     }
     if (!map2(&M->pp, phi_prev)) return -4;

@@ -8,10 +8,11 @@
 namespace lbm {
 
 // Tensor maps of the two population buffers as (x, y, plane) with a 32 x 8 x 9
-// box (one set of a 32x8 chunk), of the two lagged-source buffers and of
-// phi^{n-1} (32 x 8 boxes); index = which buffer is read.
+// box: `fs` over the (f_i, s_i) pair planes (one element = one pair), `g` over
+// the g planes; of the two lagged-source buffers and of phi^{n-1} (32 x 8
+// boxes); index = which buffer is read.
 struct TmaMaps2d {
-    CUtensorMap pops[2], q[2], pp;
+    CUtensorMap fs[2], g[2], q[2], pp;
 };
 
 // Row and plane strides are multiples of 16 bytes and the grid holds at

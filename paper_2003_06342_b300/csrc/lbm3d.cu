@@ -70,8 +70,8 @@ macro3d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
         gather_nb3d(phi_f, x, y, z, nb, P);
 #pragma unroll
         for (int i = 0; i < QF; ++i) {
-            f[i] = Codec<S>::load(pin + i * N + c, i, P);
-            s[i] = Codec<S>::load_dev(pin + (S0 + i) * N + c, S0 + i, P);
+            f[i] = Codec<S>::load(pin + off_f(i, c, N), i, P);
+            s[i] = Codec<S>::load_dev(pin + off_s(i, c, N), S0 + i, P);
         }
         Macro3 m;
         m.phi = nb[0];
@@ -121,14 +121,14 @@ init3d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
     for (int i = 0; i < QG; ++i) {
         float eqb, src;
         g_eq_src(i, m, n, q, usq, P, eqb, src);
-        Codec<S>::store_dev(pout + (G0 + i) * N + c, eqb - LG::w(i) * P.g_ref, G0 + i, P);
+        Codec<S>::store_dev(pout + off_g(QF, i, c, N), eqb - LG::w(i) * P.g_ref, G0 + i, P);
     }
 #pragma unroll
     for (int i = 0; i < QF; ++i) {
         float feqb, fS, seqb, sS;
         fs_eq_src(i, m, q, D, usq, P, feqb, fS, seqb, sS);
-        Codec<S>::store(pout + i * N + c, feqb, i, P);
-        Codec<S>::store_dev(pout + (S0 + i) * N + c, seqb, S0 + i, P);
+        Codec<S>::store(pout + off_f(i, c, N), feqb, i, P);
+        Codec<S>::store_dev(pout + off_s(i, c, N), seqb, S0 + i, P);
     }
     phi_prev[c] = m.phi - P.g_ref;
     q_out[c] = q;

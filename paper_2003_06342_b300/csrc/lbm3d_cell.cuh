@@ -12,7 +12,7 @@ using LG = D3Q7L;    // g
 constexpr int TX = 32, TY = 8, SX = TX + 2, SY = TY + 2, PLANE = SX * SY;
 constexpr int ZB = 32;                       // z planes per block
 constexpr int QF = 19, QG = 7;
-constexpr int G0 = QF, S0 = QF + QG;         // first plane of g and of s
+constexpr int G0 = QF, S0 = QF + QG;         // flat plane number of g_0 and of s_0
 
 struct Macro3 {
     float phi, g[3], lap, rho, gr[3], F[3], u[3], p, T, Td;   // Td = T - T_ref
@@ -180,7 +180,7 @@ __device__ __forceinline__ float phid_at(const S *__restrict__ pin, const float 
                                          size_t cc, size_t N, const DevParams &P) {
     float v[QG];
 #pragma unroll
-    for (int i = 0; i < QG; ++i) v[i] = load_raw(pin + (G0 + i) * N + cc);
+    for (int i = 0; i < QG; ++i) v[i] = load_raw(pin + off_g(QF, i, cc, N));
     (void)in_bounds((long long)cc, (long long)N, P);
     return fmaf(0.5f, q_in[cc], set_sum7<S>(v, P.set_isc[1]));
 }
@@ -259,20 +259,26 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
     }
 }
 
-// Base pointers of the 45 population planes of the buffer read and of the
+// Base pointers of the population planes of the buffer read and of the
 // buffer written, passed to the kernels as a parameter, so that a load or a
-// fast-path store addresses its plane as base + cell.
+// fast-path store addresses its plane as base + cell: entries 0..18 are the
+// (f_i, s_i) pair planes, G0 + i the g planes.
 template <typename S> struct Planes3d {
-    const S *in[QF + QG + QF];
-    S *out[QF + QG + QF];
+    const S *in[QF + QG];
+    S *out[QF + QG];
 };
 
 template <typename S>
 inline Planes3d<S> planes3d(const void *pin, void *pout, const DevParams &P) {
     Planes3d<S> PL;
-    for (int k = 0; k < QF + QG + QF; ++k) {
-        PL.in[k] = (const S *)pin + (size_t)k * (size_t)P.N;
-        PL.out[k] = (S *)pout + (size_t)k * (size_t)P.N;
+    const size_t N = (size_t)P.N;
+    for (int i = 0; i < QF; ++i) {
+        PL.in[i] = (const S *)pin + off_f(i, 0, N);
+        PL.out[i] = (S *)pout + off_f(i, 0, N);
+    }
+    for (int i = 0; i < QG; ++i) {
+        PL.in[G0 + i] = (const S *)pin + off_g(QF, i, 0, N);
+        PL.out[G0 + i] = (S *)pout + off_g(QF, i, 0, N);
     }
     return PL;
 }
@@ -292,39 +298,36 @@ __device__ __forceinline__ float rep_mul3(int i) {
     return IsNarrow<S>::value ? 1.0f : Lt::w(i);
 }
 
-// Push of one post-collision value of plane `plane` (direction i of lattice
-// Lt, set `set`) from cell c = (x, y, z).  MODE XY_IN: the link stays inside
-// the grid; XY_WRAP: it may cross a periodic x / y boundary but not a z edge
-// or a wall; XY_GEN: anything.  Through a wall the value comes back to c in
-// the opposite direction: unchanged for f (bounce-back), -v + 2 w (value -
-// ref) for g and s (anti-bounce-back), in the working representation.
-// PLP: fast-path stores address their plane through PL (faster in every
-// variant except the TMA-staged FP32 kernel, where pout + plane * N measured
-// 1.7% faster).
-template <typename S, class Lt, int MODE, bool PLP>
-__device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int x, int y, int z,
-                                       size_t c, S *__restrict__ pout, const DevParams &P,
-                                       const Planes3d<S> &PL) {
-    const int ex = Lt::ex(i), ey = Lt::ey(i), ez = Lt::ez(i);
+// Push from cell c = (x, y, z).  MODE XY_IN: the link stays inside the grid;
+// XY_WRAP: it may cross a periodic x / y boundary but not a z edge or a wall;
+// XY_GEN: anything.  Through a wall a value comes back to c in the opposite
+// direction: unchanged for f (bounce-back), -v + 2 w (value - ref) for g and
+// s (anti-bounce-back), in the working representation.  PLP: fast-path
+// stores address their plane through PL (faster in every variant except the
+// TMA-staged FP32 kernel, where pout + plane offset measured 1.7% faster).
+
+// Push of direction i's g value (D3Q7).
+template <typename S, int MODE, bool PLP>
+__device__ __forceinline__ void push3d_g(int i, float v, int x, int y, int z, size_t c,
+                                         S *__restrict__ pout, const DevParams &P,
+                                         const Planes3d<S> &PL) {
+    const int ex = LG::ex(i), ey = LG::ey(i), ez = LG::ez(i);
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const size_t N = (size_t)P.N;
-    if (MODE == XY_IN) {
-        const long long off = ((long long)ez * ny + ey) * nx + ex;
+    if (MODE == XY_IN || MODE == XY_WRAP) {
+        long long off;
+        if (MODE == XY_IN) off = ((long long)ez * ny + ey) * nx + ex;
+        else {
+            int oxy = 0;
+            if (ex > 0) oxy = x == nx - 1 ? 1 - nx : 1;
+            if (ex < 0) oxy = x == 0 ? nx - 1 : -1;
+            if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
+            if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
+            off = (long long)ez * ny * nx + oxy;
+        }
         if (!in_bounds((long long)c + off, (long long)N, P)) return;
-        if (PLP) PL.out[plane0 + i][(long long)c + off] = narrow<S>(v);
-        else pout[(plane0 + i) * N + c + off] = narrow<S>(v);
-        return;
-    }
-    if (MODE == XY_WRAP) {
-        int oxy = 0;
-        if (ex > 0) oxy = x == nx - 1 ? 1 - nx : 1;
-        if (ex < 0) oxy = x == 0 ? nx - 1 : -1;
-        if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
-        if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
-        const long long off = (long long)ez * ny * nx + oxy;
-        if (!in_bounds((long long)c + off, (long long)N, P)) return;
-        if (PLP) PL.out[plane0 + i][(long long)c + off] = narrow<S>(v);
-        else pout[(plane0 + i) * N + c + off] = narrow<S>(v);
+        if (PLP) PL.out[G0 + i][(long long)c + off] = narrow<S>(v);
+        else pout[off_g(QF, i, c, N) + off] = narrow<S>(v);
         return;
     }
     int dx = x + ex, dy = y + ey, dz = z + ez;
@@ -333,15 +336,50 @@ __device__ __forceinline__ void push3d(int i, int plane0, int set, float v, int 
     const int kz = wrap_coord(dz, nz, P.periodic[2]);
     if (kx >= 2 || ky >= 2 || kz >= 2) {
         const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
-        const int o = Lt::opp(i);
-        if (set != 0) {
-            const float wall = set == 1 ? P.phi_wall[side] - P.g_ref : P.T_wall[side] - P.s_ref;
-            v = fmaf(2.0f * wall_mul3<S, Lt>(i, set, P), wall, -v);
-        }
-        if (in_bounds((long long)c, (long long)N, P)) pout[(plane0 + o) * N + c] = narrow<S>(v);
+        v = fmaf(2.0f * wall_mul3<S, LG>(i, 1, P), P.phi_wall[side] - P.g_ref, -v);
+        if (in_bounds((long long)c, (long long)N, P)) pout[off_g(QF, LG::opp(i), c, N)] = narrow<S>(v);
     } else {
         const size_t d = ((size_t)dz * ny + dy) * nx + dx;
-        if (in_bounds((long long)d, (long long)N, P)) pout[(plane0 + i) * N + d] = narrow<S>(v);
+        if (in_bounds((long long)d, (long long)N, P)) pout[off_g(QF, i, d, N)] = narrow<S>(v);
+    }
+}
+
+// Push of direction i's f and s values (D3Q19) as one (f_i, s_i) pair.
+template <typename S, int MODE, bool PLP>
+__device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int y, int z, size_t c,
+                                          S *__restrict__ pout, const DevParams &P,
+                                          const Planes3d<S> &PL) {
+    const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const size_t N = (size_t)P.N;
+    if (MODE == XY_IN || MODE == XY_WRAP) {
+        long long off;
+        if (MODE == XY_IN) off = ((long long)ez * ny + ey) * nx + ex;
+        else {
+            int oxy = 0;
+            if (ex > 0) oxy = x == nx - 1 ? 1 - nx : 1;
+            if (ex < 0) oxy = x == 0 ? nx - 1 : -1;
+            if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
+            if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
+            off = (long long)ez * ny * nx + oxy;
+        }
+        if (!in_bounds((long long)c + off, (long long)N, P)) return;
+        if (PLP) store_pair<S>(PL.out[i], (long long)c + off, vf, vs);
+        else store_pair<S>(pout + off_f(i, 0, N), (long long)c + off, vf, vs);
+        return;
+    }
+    int dx = x + ex, dy = y + ey, dz = z + ez;
+    const int kx = wrap_coord(dx, nx, P.periodic[0]);
+    const int ky = wrap_coord(dy, ny, P.periodic[1]);
+    const int kz = wrap_coord(dz, nz, P.periodic[2]);
+    if (kx >= 2 || ky >= 2 || kz >= 2) {
+        const int side = (kx >= 2 ? kx : (ky >= 2 ? ky : kz)) - 2;
+        vs = fmaf(2.0f * wall_mul3<S, LF>(i, 2, P), P.T_wall[side] - P.s_ref, -vs);
+        if (in_bounds((long long)c, (long long)N, P))
+            store_pair<S>(pout + off_f(LF::opp(i), 0, N), (long long)c, vf, vs);
+    } else {
+        const size_t d = ((size_t)dz * ny + dy) * nx + dx;
+        if (in_bounds((long long)d, (long long)N, P)) store_pair<S>(pout + off_f(i, 0, N), (long long)d, vf, vs);
     }
 }
 
@@ -434,15 +472,15 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Vg[3] = {fmaf(4.0f * Bg, ux, bgi * n0), fmaf(4.0f * Bg, uy, bgi * n1),
                              fmaf(4.0f * Bg, uz, bgi * n2)};
         const float usq2 = 2.0f * usq;
-        push3d<S, LG, MODE, PLP>(0, G0, 1, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)),
+        push3d_g<S, MODE, PLP>(0, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)),
                             x, y, z, c, pout, P, PL);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float ua = m.u[a];
             const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
             const float mg = rep_mul3<S, LG>(a + 1);
-            push3d<S, LG, MODE, PLP>(a + 1, G0, 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
-            push3d<S, LG, MODE, PLP>(a + 4, G0, 1, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
+            push3d_g<S, MODE, PLP>(a + 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
+            push3d_g<S, MODE, PLP>(a + 4, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
         }
     }
 
@@ -466,10 +504,9 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float As = scs * fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D), Bs = scs * (om_s * m.T);
     // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
     const float Wx = __fmul_rn(3.0f * Bs, ux), Wy = __fmul_rn(3.0f * Bs, uy), Wz = __fmul_rn(3.0f * Bs, uz);
-    push3d<S, LF, MODE, PLP>(0, 0, 0, fmaf(a_f, f[0], rep_mul3<S, LF>(0) * fmaf(K1, -usq15, K0)),
-                        x, y, z, c, pout, P, PL);
-    push3d<S, LF, MODE, PLP>(0, S0, 2, fmaf(a_s, s[0], rep_mul3<S, LF>(0) * fmaf(Bs, -usq15, As)),
-                        x, y, z, c, pout, P, PL);
+    push3d_fs<S, MODE, PLP>(0, fmaf(a_f, f[0], rep_mul3<S, LF>(0) * fmaf(K1, -usq15, K0)),
+                            fmaf(a_s, s[0], rep_mul3<S, LF>(0) * fmaf(Bs, -usq15, As)), x, y, z, c,
+                            pout, P, PL);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = half19(k), o = LF::opp(i);
@@ -482,10 +519,10 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Es = fmaf(Bs, Pe, As);
         const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
         const float mf = rep_mul3<S, LF>(i), ms = mf;
-        push3d<S, LF, MODE, PLP>(i, 0, 0, fmaf(a_f, f[i], mf * (Ef + Of)), x, y, z, c, pout, P, PL);
-        push3d<S, LF, MODE, PLP>(o, 0, 0, fmaf(a_f, f[o], mf * (Ef - Of)), x, y, z, c, pout, P, PL);
-        push3d<S, LF, MODE, PLP>(i, S0, 2, fmaf(a_s, s[i], ms * (Es + Os)), x, y, z, c, pout, P, PL);
-        push3d<S, LF, MODE, PLP>(o, S0, 2, fmaf(a_s, s[o], ms * (Es - Os)), x, y, z, c, pout, P, PL);
+        push3d_fs<S, MODE, PLP>(i, fmaf(a_f, f[i], mf * (Ef + Of)), fmaf(a_s, s[i], ms * (Es + Os)),
+                                x, y, z, c, pout, P, PL);
+        push3d_fs<S, MODE, PLP>(o, fmaf(a_f, f[o], mf * (Ef - Of)), fmaf(a_s, s[o], ms * (Es - Os)),
+                                x, y, z, c, pout, P, PL);
     }
 }
 
@@ -542,9 +579,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             const size_t c = (size_t)z * plane_cells + cxy;
             float f[QF], s[QF];
 #pragma unroll
-            for (int i = 0; i < QF; ++i) f[i] = load_raw(PL.in[i] + c);
-#pragma unroll
-            for (int i = 0; i < QF; ++i) s[i] = load_raw(PL.in[S0 + i] + c);
+            for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
             const float phip = phi_prev[c];
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
                 layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);

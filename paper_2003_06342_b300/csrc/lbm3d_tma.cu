@@ -3,13 +3,13 @@
 // Same update as step3d_kernel (lbm3d.cu): each block marches a 32x8 column
 // tile through ZB layers.  One thread issues cp.async.bulk.tensor copies of
 // the tile's layers into shared-memory stages:
-//   f/s stage  f planes 32 x 8 x 1 x 19 from (x0, y0, L, 0)   4D map (x, y, z, plane)
-//              s planes 32 x 8 x 1 x 19 from (x0, y0, L, 26)
+//   f/s stage  (f_i, s_i) pair planes 32 x 8 x 1 x 19 from (x0, y0, L, 0)
+//                                          4D map (x, y, z, pair plane)
 //              phi^{n-1} 32 x 8 x 1    from (x0, y0, L)       3D map (x, y, z)
-//   g stage    g planes 32 x 8 x 1 x 7  from (x0, y0, L, 19)
+//   g stage    g planes 32 x 8 x 1 x 7  from (x0, y0, L, 0)   4D map (x, y, z, g plane)
 //              q^{n-1}  32 x 8 x 1     from (x0, y0, L)
-// each completing on its own mbarrier (a box row is one whole 128-byte line
-// of FP32, or 64 bytes of 16-bit values).  Two f/s stages and three g stages
+// each completing on its own mbarrier (a box row of pairs is two whole
+// 128-byte lines of FP32, or one of 16-bit values).  Two f/s stages and three g stages
 // rotate so that every copy is issued a whole layer before it is needed: while
 // layer z is computed (it needs f/s of z and g of z and z + 1, the latter for
 // the phi window), the copies of f/s(z + 1) and g(z + 2) are in flight.  The
@@ -37,9 +37,8 @@ template <typename S> struct Tma3Geom {
     static constexpr int G_BYTES = QG * CELLS * ES;
     static constexpr int Q_BYTES = CELLS * 4;
     // f/s stage: f, s and phi^{n-1} of one layer; g stage: g and q^{n-1}
-    static constexpr int OFF_F = 0;
-    static constexpr int OFF_S = OFF_F + al(F_BYTES);
-    static constexpr int OFF_PP = OFF_S + al(F_BYTES);
+    static constexpr int OFF_FS = 0;                       // pairs (f_i, s_i)
+    static constexpr int OFF_PP = OFF_FS + al(2 * F_BYTES);
     static constexpr int FS_STAGE = OFF_PP + al(Q_BYTES);
     static constexpr int OFF_G = 0;
     static constexpr int OFF_Q = OFF_G + al(G_BYTES);
@@ -58,8 +57,7 @@ __device__ __forceinline__ void issue_fs(unsigned char *stage, uint64_t *bar, co
     // order earlier generic-proxy reads of this stage before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, Gm::FS_TX);
-    tma_load_4d(stage + Gm::OFF_F, &M.fs[par], x0, y0, z, 0, bar);
-    tma_load_4d(stage + Gm::OFF_S, &M.fs[par], x0, y0, z, S0, bar);
+    tma_load_4d(stage + Gm::OFF_FS, &M.fs[par], x0, y0, z, 0, bar);
     tma_load_3d(stage + Gm::OFF_PP, &M.pp, x0, y0, z, bar);
 }
 
@@ -69,7 +67,7 @@ __device__ __forceinline__ void issue_g(unsigned char *stage, uint64_t *bar, con
     using Gm = Tma3Geom<S>;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, Gm::G_TX);
-    tma_load_4d(stage + Gm::OFF_G, &M.g[par], x0, y0, z, G0, bar);
+    tma_load_4d(stage + Gm::OFF_G, &M.g[par], x0, y0, z, 0, bar);
     tma_load_3d(stage + Gm::OFF_Q, &M.q[par], x0, y0, z, bar);
 }
 
@@ -144,7 +142,7 @@ __device__ __forceinline__ void ring_prefetch(uint32_t *buf, const S *__restrict
     if (!in_bounds((long long)cc, (long long)N, P)) return;
 #pragma unroll
     for (int i = 0; i < QG; ++i) {
-        const size_t e = (G0 + i) * N + cc;
+        const size_t e = off_g(QF, i, cc, N);
         const S *src = pin + (IsNarrow<S>::value ? (e & ~(size_t)1) : e);
         cp_async4(&buf[i * RING_CELLS + tid], src);
     }
@@ -165,7 +163,7 @@ __device__ __forceinline__ void ring_store(float *plane, const uint32_t *buf, in
     for (int i = 0; i < QG; ++i) {
         const uint32_t w = buf[i * RING_CELLS + tid];
         if (IsNarrow<S>::value) {
-            const size_t e = (G0 + i) * N + cc;
+            const size_t e = off_g(QF, i, cc, N);
             const unsigned short h = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
             S val;
             memcpy(&val, &h, 2);
@@ -256,15 +254,11 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
         {
             const unsigned char *b = fs_base + fb * Gm::FS_STAGE;
             const unsigned char *bg = g_base + gb * Gm::G_STAGE;
-            const S *Fp = (const S *)(b + Gm::OFF_F);
-            const S *Sp = (const S *)(b + Gm::OFF_S);
+            const auto *FSp = (const typename PairOf<S>::T *)(b + Gm::OFF_FS);
             const S *Gp = (const S *)(bg + Gm::OFF_G);
             float f[QF], s[QF], g[QG];
 #pragma unroll
-            for (int i = 0; i < QF; ++i) {
-                f[i] = widen(Fp[i * Gm::CELLS + tid]);
-                s[i] = widen(Sp[i * Gm::CELLS + tid]);
-            }
+            for (int i = 0; i < QF; ++i) unpack_pair(FSp[i * Gm::CELLS + tid], f[i], s[i]);
 #pragma unroll
             for (int i = 0; i < QG; ++i) g[i] = widen(Gp[i * Gm::CELLS + tid]);
             const float qp = ((const float *)(bg + Gm::OFF_Q))[tid];
@@ -340,13 +334,18 @@ int make_tma_maps3d(TmaMaps3d *M, const DevParams &P, int elem_bytes, void *cons
     const cuuint64_t nx = (cuuint64_t)P.n[0], ny = (cuuint64_t)P.n[1], nz = (cuuint64_t)P.n[2];
     const cuuint64_t N = (cuuint64_t)P.N, es = (cuuint64_t)elem_bytes;
     const cuuint32_t one[4] = {1, 1, 1, 1};
+    // a single value, and a (f_i, s_i) pair copied as one element of twice the size
     const CUtensorMapDataType dt = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    auto map4 = [&](CUtensorMap *m, void *base, cuuint32_t planes) {
-        const cuuint64_t dims[4] = {nx, ny, nz, (cuuint64_t)(QF + QG + QF)};
-        const cuuint64_t str[3] = {nx * es, nx * ny * es, N * es};
+    const CUtensorMapDataType dt2 = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+    // `planes` planes of `e`-byte elements, population planes pstride bytes apart
+    auto map4 = [&](CUtensorMap *m, void *base, CUtensorMapDataType t, cuuint64_t e, cuuint32_t planes,
+                    cuuint64_t pstride) {
+        const cuuint64_t dims[4] = {nx, ny, nz, (cuuint64_t)planes};
+        const cuuint64_t str[3] = {nx * e, nx * ny * e, pstride};
         const cuuint32_t box[4] = {TX, TY, 1, planes};
-        return enc(m, dt, 4, base, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        return enc(m, t, 4, base, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
@@ -359,8 +358,8 @@ int make_tma_maps3d(TmaMaps3d *M, const DevParams &P, int elem_bytes, void *cons
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     for (int b = 0; b < 2; ++b) {
-        if (!map4(&M->fs[b], pops[b], QF)) return -2;
-        if (!map4(&M->g[b], pops[b], QG)) return -3;
+        if (!map4(&M->fs[b], pops[b], dt2, 2 * es, QF, 2 * N * es)) return -2;
+        if (!map4(&M->g[b], (char *)pops[b] + off_g(QF, 0, 0, N) * es, dt, es, QG, N * es)) return -3;
         if (!map3(&M->q[b], q[b])) return -4;
     }
     if (!map3(&M->pp, phi_prev)) return -5;

@@ -7,10 +7,11 @@
 
 namespace lbm {
 
-// Tensor maps of the two population buffers as (x, y, z, plane) with a box of
-// 32 x 8 x 1 x 19 (the f or the s set of one tile layer) and 32 x 8 x 1 x 7
-// (the g set), of the two lagged-source buffers and of phi^{n-1} (32 x 8 x 1
-// boxes); index = which buffer is read.
+// Tensor maps of the two population buffers as (x, y, z, plane): `fs` over
+// the (f_i, s_i) pair planes (one element = one pair) with a 32 x 8 x 1 x 19
+// box (the f and s sets of one tile layer), `g` over the g planes with a
+// 32 x 8 x 1 x 7 box; of the two lagged-source buffers and of phi^{n-1}
+// (32 x 8 x 1 boxes); index = which buffer is read.
 struct TmaMaps3d {
     CUtensorMap fs[2], g[2], q[2], pp;
 };

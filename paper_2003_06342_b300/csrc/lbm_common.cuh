@@ -117,8 +117,9 @@ struct DevParams {
 // an index outside [0, lim) sets bit 2 of the handle's status word and the
 // caller skips the access; lbm_sync reports it as LBM_EBOUNDS.  The normal
 // build compiles every check away and its kernel parameters keep no status
-// pointer (a larger parameter block measurably slowed the 16-bit 2D kernels).  Callers never return early on a failed
-// check, so no thread leaves a block barrier behind.
+// pointer (a larger parameter block measurably slowed the 16-bit 2D
+// kernels).  Callers never return early on a failed check, so no thread
+// leaves a block barrier behind.
 __device__ __forceinline__ bool in_bounds(long long idx, long long lim, const DevParams &P) {
 #ifdef LBM_CHECK_BOUNDS
     if (idx < 0 || idx >= lim) {
@@ -128,6 +129,58 @@ __device__ __forceinline__ bool in_bounds(long long idx, long long lim, const De
 #endif
     (void)idx; (void)lim; (void)P;
     return true;
+}
+
+// ---------------------------------------------------------------- layout
+// Memory layout of a population buffer (and of the saved and the adjoint
+// state).  f and s share their lattice (D2Q9 in 2D, D3Q19 in 3D) and the
+// values of direction i of both sets travel to the same cell, so they are
+// stored as a pair: pair plane i holds (f_i, s_i) of cell c at elements
+// 2 (i N + c) and 2 (i N + c) + 1.  The Qg phase-field planes follow the Qf
+// pair planes: g_i of cell c at (2 Qf + i) N + c.  A thread moves the f and s
+// values of a direction with one 8-byte (FP32) or 4-byte (16-bit) access.
+// The flat plane number k that indexes the per-plane codec tables is
+// unchanged by the layout: f_i = i, g_i = Qf + i, s_i = Qf + Qg + i.
+__host__ __device__ __forceinline__ size_t off_f(int i, size_t c, size_t N) {
+    return 2 * ((size_t)i * N + c);
+}
+__host__ __device__ __forceinline__ size_t off_s(int i, size_t c, size_t N) {
+    return 2 * ((size_t)i * N + c) + 1;
+}
+__host__ __device__ __forceinline__ size_t off_g(int Qf, int i, size_t c, size_t N) {
+    return (size_t)(2 * Qf + i) * N + c;
+}
+
+template <typename S> struct PairOf;
+template <> struct PairOf<float> { using T = float2; };
+template <> struct PairOf<__half> { using T = __half2; };
+template <> struct PairOf<__nv_bfloat16> { using T = __nv_bfloat162; };
+
+__device__ __forceinline__ void unpack_pair(float2 v, float &a, float &b) { a = v.x; b = v.y; }
+__device__ __forceinline__ void unpack_pair(__half2 v, float &a, float &b) {
+    a = __low2float(v); b = __high2float(v);
+}
+__device__ __forceinline__ void unpack_pair(__nv_bfloat162 v, float &a, float &b) {
+    a = __low2float(v); b = __high2float(v);
+}
+template <typename S> __device__ __forceinline__ typename PairOf<S>::T pack_pair(float a, float b);
+template <> __device__ __forceinline__ float2 pack_pair<float>(float a, float b) { return make_float2(a, b); }
+template <> __device__ __forceinline__ __half2 pack_pair<__half>(float a, float b) {
+    return __floats2half2_rn(a, b);
+}
+template <> __device__ __forceinline__ __nv_bfloat162 pack_pair<__nv_bfloat16>(float a, float b) {
+    return __floats2bfloat162_rn(a, b);
+}
+
+// The (f_i, s_i) pair of cell c from / to pair plane `plane` (its first
+// element), as raw stored values widened to float / narrowed from float.
+template <typename S>
+__device__ __forceinline__ void load_pair(const S *plane, long long c, float &f, float &s) {
+    unpack_pair(__ldg(reinterpret_cast<const typename PairOf<S>::T *>(plane) + c), f, s);
+}
+template <typename S>
+__device__ __forceinline__ void store_pair(S *plane, long long c, float f, float s) {
+    reinterpret_cast<typename PairOf<S>::T *>(plane)[c] = pack_pair<S>(f, s);
 }
 
 // ---------------------------------------------------------------- storage
