@@ -40,7 +40,7 @@ extern "C" {
 #define LBM_EINVAL       -1   /* bad argument: size, pointer, parameter range   */
 #define LBM_ENOMEM       -2   /* workspace or caller buffer too small            */
 #define LBM_ECUDA        -3   /* a CUDA runtime call or kernel launch failed     */
-#define LBM_ENONFINITE   -4   /* a reduction found NaN or Inf in the fields      */
+#define LBM_ENONFINITE   -4   /* NaN or Inf in the fields (reduction, state check) */
 #define LBM_ETIMEOUT     -5   /* a bounded in-kernel wait expired (see lbm_sync) */
 #define LBM_EUNSUPPORTED -6   /* combination not built (e.g. lattice/storage)    */
 #define LBM_EBOUNDS      -7   /* an index check failed (bounds-checking build)  */
@@ -155,8 +155,11 @@ int lbm_reduce(lbm_handle *h, double *phi_mass, double *energy);
 /* Same reduction, asynchronous: two doubles written to device memory d_out. */
 int lbm_reduce_async(lbm_handle *h, double *d_out);
 
-/* Checkpoint / resume: the state is the populations, phi^{n-1} and the lagged
- * source (bytes from lbm_state_bytes).  on_device selects the buffer's side.
+/* Checkpoint / resume: the state is the populations in their storage format
+ * -- the Qf (f_i, s_i) pair planes (2N values each, f_i of cell x at
+ * 2(iN + x), s_i at 2(iN + x) + 1), then the Qg g planes -- followed by
+ * phi^{n-1} and the lagged source as float32 (bytes from lbm_state_bytes).
+ * on_device selects the buffer's side.
  * Restoring a saved state and stepping reproduces the uninterrupted run bit
  * for bit. */
 int lbm_state_bytes(const lbm_handle *h, size_t *bytes);
@@ -204,13 +207,24 @@ int lbm_steps_done(const lbm_handle *h, int64_t *steps);
 /* Kernel launches queued by the last lbm_step call. */
 int lbm_last_launches(const lbm_handle *h, int32_t *launches);
 
+/* Periodic state check: when every > 0, every `every`-th step of lbm_step /
+ * lbm_step_record is followed by one extra launch that reads the state, forms
+ * phi = sum_i gbar_i + q/2 (Eq. Moment_Phi) of every cell and flags the state
+ * when phi leaves [1/2 - phi_excess, 1/2 + phi_excess] or a stored
+ * population, phi or the lagged source is not finite; lbm_sync then returns
+ * LBM_ENONFINITE.  The launch reads every population once (about half the
+ * traffic of a step).  every = 0 (the default) turns the check off.  Errors: LBM_EINVAL for every < 0 or,
+ * with every > 0, phi_excess not a positive finite number. */
+int lbm_set_health_check(lbm_handle *h, int32_t every, float phi_excess);
+
 /* Wait for the handle's stream; report any pending CUDA error, or
  * LBM_ETIMEOUT if a bounded wait inside a step kernel expired (the kernel then
  * stopped early and the state is not valid), or -- in the bounds-checking
  * build of the library (liblbmpf_debug.so, every computed population and
  * field index checked against its buffer, a failing access skipped) --
- * LBM_EBOUNDS if a check failed since lbm_init / lbm_set_state.  The status
- * is cleared when reported. */
+ * LBM_EBOUNDS if a check failed since lbm_init / lbm_set_state, or
+ * LBM_ENONFINITE if the periodic state check (lbm_set_health_check) flagged
+ * the state.  The status is cleared when reported. */
 int lbm_sync(lbm_handle *h);
 
 /* ---- discrete adjoint (2D, FP32 storage) ----------------------------------
@@ -218,9 +232,10 @@ int lbm_sync(lbm_handle *h);
  * with respect to the latent heat L, the mobility M_phi, the surface tension
  * sigma and the initial temperature field (the step is Eq. LBE with the
  * sources of Sec. 3; the loss is J = 1/2 sum (phi^N - phi_target)^2).
- * States are device buffers in the lbm_get_state layout (27 population
- * planes, phi^{n-1}, lagged source; float32); an adjoint state has the same
- * layout and holds dJ/d(stored value).  Other lattices and storages return
+ * States are device buffers in the lbm_get_state layout (float32: the nine
+ * (f_i, s_i) pair planes, 2N values each with f_i at 2(iN + x) and s_i at
+ * 2(iN + x) + 1, the nine g planes, phi^{n-1}, lagged source); an adjoint
+ * state has the same layout and holds dJ/d(stored value).  Other lattices and storages return
  * LBM_EUNSUPPORTED. */
 
 /* Bytes of one adjoint state and of the per-step scratch (9 planes). */

@@ -45,6 +45,8 @@ struct lbm_handle {
     float *vel;              // LBM_MODEL_PHASE_FIELD: imposed velocity, dim planes
     double vel_period;       // time factor cos(pi n / period) when > 0
     int vel_set;
+    int32_t health_every;    // lbm_set_health_check: steps between checks (0 = off)
+    float health_excess;     // allowed |phi - 1/2|
 };
 
 namespace {
@@ -387,6 +389,8 @@ int lbm_create(const lbm_grid *grid, int32_t lattice, const lbm_params *params, 
     h->vel = L.vel ? (float *)p : nullptr; p += L.vel;
     h->vel_period = 0.0;
     h->vel_set = 0;
+    h->health_every = 0;
+    h->health_excess = 0.0f;
     h->err_ready = 0;
     h->red_blocks = L.red_blocks;
     h->kernel_choice = LBM_KERNEL_AUTO;
@@ -428,15 +432,39 @@ int lbm_init(lbm_handle *h, const lbm_fields *in) {
     return do_init(h, phi0, T0, u0, p0);
 }
 
+// the periodic state check after a step, when one is due
+static int maybe_health(lbm_handle *h) {
+    if (h->health_every <= 0 || h->steps % h->health_every != 0) return LBM_OK;
+    cudaError_t e;
+    switch (h->params.storage) {
+    case LBM_STORE_FP32: e = launch_health<float>(h->pops[h->cur], h->q[h->cur], h->health_excess, h->err, h->dp, h->dim, h->stream); break;
+    case LBM_STORE_FP16: e = launch_health<__half>(h->pops[h->cur], h->q[h->cur], h->health_excess, h->err, h->dp, h->dim, h->stream); break;
+    default: e = launch_health<__nv_bfloat16>(h->pops[h->cur], h->q[h->cur], h->health_excess, h->err, h->dp, h->dim, h->stream); break;
+    }
+    if (e != cudaSuccess) return LBM_ECUDA;
+    ++h->last_launches;
+    return LBM_OK;
+}
+
 int lbm_step(lbm_handle *h, int32_t n) {
     if (!h || n < 0) return LBM_EINVAL;
     h->last_launches = 0;
     for (int32_t k = 0; k < n; ++k) {
-        const int r = do_step(h);
+        int r = do_step(h);
         if (r != LBM_OK) return r;
         ++h->steps;
         ++h->last_launches;
+        r = maybe_health(h);
+        if (r != LBM_OK) return r;
     }
+    return LBM_OK;
+}
+
+int lbm_set_health_check(lbm_handle *h, int32_t every, float phi_excess) {
+    if (!h || every < 0) return LBM_EINVAL;
+    if (every > 0 && !(phi_excess > 0.0f && std::isfinite(phi_excess))) return LBM_EINVAL;
+    h->health_every = every;
+    h->health_excess = phi_excess;
     return LBM_OK;
 }
 
@@ -453,6 +481,8 @@ int lbm_step_record(lbm_handle *h, int32_t n, void *buf, size_t stride) {
         if (r != LBM_OK) return r;
         ++h->steps;
         ++h->last_launches;
+        r = maybe_health(h);
+        if (r != LBM_OK) return r;
         r = copy_state(h, (char *)buf + (size_t)k * stride, stride, 1, true);
         if (r != LBM_OK) return r;
     }
@@ -589,12 +619,14 @@ int lbm_sync(lbm_handle *h) {
     if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
     if (!h->err_ready) return LBM_OK;          // no kernel has run yet
     // the status word: bit 1 a bounded wait expired, bit 2 an index check of
-    // the bounds-checking build failed
+    // the bounds-checking build failed, bit 4 the periodic state check failed
     int flag = 0;
     if (cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ECUDA;
     if (flag) {
         cudaMemset(h->err, 0, sizeof(int));
-        return (flag & 2) ? LBM_EBOUNDS : LBM_ETIMEOUT;
+        if (flag & 2) return LBM_EBOUNDS;
+        if (flag & 1) return LBM_ETIMEOUT;
+        return LBM_ENONFINITE;
     }
     return LBM_OK;
 }

@@ -302,12 +302,11 @@ __device__ __forceinline__ float rep_mul3(int i) {
 // XY_WRAP: it may cross a periodic x / y boundary but not a z edge or a wall;
 // XY_GEN: anything.  Through a wall a value comes back to c in the opposite
 // direction: unchanged for f (bounce-back), -v + 2 w (value - ref) for g and
-// s (anti-bounce-back), in the working representation.  PLP: fast-path
-// stores address their plane through PL (faster in every variant except the
-// TMA-staged FP32 kernel, where pout + plane offset measured 1.7% faster).
+// s (anti-bounce-back), in the working representation.  Fast-path stores
+// address their plane through PL (base + cell).
 
 // Push of direction i's g value (D3Q7).
-template <typename S, int MODE, bool PLP>
+template <typename S, int MODE>
 __device__ __forceinline__ void push3d_g(int i, float v, int x, int y, int z, size_t c,
                                          S *__restrict__ pout, const DevParams &P,
                                          const Planes3d<S> &PL) {
@@ -326,8 +325,7 @@ __device__ __forceinline__ void push3d_g(int i, float v, int x, int y, int z, si
             off = (long long)ez * ny * nx + oxy;
         }
         if (!in_bounds((long long)c + off, (long long)N, P)) return;
-        if (PLP) PL.out[G0 + i][(long long)c + off] = narrow<S>(v);
-        else pout[off_g(QF, i, c, N) + off] = narrow<S>(v);
+        PL.out[G0 + i][(long long)c + off] = narrow<S>(v);
         return;
     }
     int dx = x + ex, dy = y + ey, dz = z + ez;
@@ -345,7 +343,7 @@ __device__ __forceinline__ void push3d_g(int i, float v, int x, int y, int z, si
 }
 
 // Push of direction i's f and s values (D3Q19) as one (f_i, s_i) pair.
-template <typename S, int MODE, bool PLP>
+template <typename S, int MODE>
 __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int y, int z, size_t c,
                                           S *__restrict__ pout, const DevParams &P,
                                           const Planes3d<S> &PL) {
@@ -364,8 +362,7 @@ __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int 
             off = (long long)ez * ny * nx + oxy;
         }
         if (!in_bounds((long long)c + off, (long long)N, P)) return;
-        if (PLP) store_pair<S>(PL.out[i], (long long)c + off, vf, vs);
-        else store_pair<S>(pout + off_f(i, 0, N), (long long)c + off, vf, vs);
+        store_pair<S>(PL.out[i], (long long)c + off, vf, vs);
         return;
     }
     int dx = x + ex, dy = y + ey, dz = z + ez;
@@ -394,7 +391,7 @@ __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int 
 // (algebraically Eq. LBE with theta_eq_bar = theta_eq - S/2 and the sources of
 // Eqs. Forcing, MicroProduction, SourceTerm_AllenCahn, Def_SourceTerms_Temp).
 // MODE (see push3d): how the links of this cell are pushed.
-template <typename S, int MODE, bool PLP = true>
+template <typename S, int MODE>
 __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
                                                const float f[QF], const float s[QF],
                                                const float g[QG], float qp, float phip,
@@ -472,15 +469,15 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Vg[3] = {fmaf(4.0f * Bg, ux, bgi * n0), fmaf(4.0f * Bg, uy, bgi * n1),
                              fmaf(4.0f * Bg, uz, bgi * n2)};
         const float usq2 = 2.0f * usq;
-        push3d_g<S, MODE, PLP>(0, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)),
+        push3d_g<S, MODE>(0, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)),
                             x, y, z, c, pout, P, PL);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float ua = m.u[a];
             const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
             const float mg = rep_mul3<S, LG>(a + 1);
-            push3d_g<S, MODE, PLP>(a + 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
-            push3d_g<S, MODE, PLP>(a + 4, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
+            push3d_g<S, MODE>(a + 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
+            push3d_g<S, MODE>(a + 4, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
         }
     }
 
@@ -504,7 +501,7 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float As = scs * fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D), Bs = scs * (om_s * m.T);
     // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
     const float Wx = __fmul_rn(3.0f * Bs, ux), Wy = __fmul_rn(3.0f * Bs, uy), Wz = __fmul_rn(3.0f * Bs, uz);
-    push3d_fs<S, MODE, PLP>(0, fmaf(a_f, f[0], rep_mul3<S, LF>(0) * fmaf(K1, -usq15, K0)),
+    push3d_fs<S, MODE>(0, fmaf(a_f, f[0], rep_mul3<S, LF>(0) * fmaf(K1, -usq15, K0)),
                             fmaf(a_s, s[0], rep_mul3<S, LF>(0) * fmaf(Bs, -usq15, As)), x, y, z, c,
                             pout, P, PL);
 #pragma unroll
@@ -519,9 +516,9 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Es = fmaf(Bs, Pe, As);
         const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
         const float mf = rep_mul3<S, LF>(i), ms = mf;
-        push3d_fs<S, MODE, PLP>(i, fmaf(a_f, f[i], mf * (Ef + Of)), fmaf(a_s, s[i], ms * (Es + Os)),
+        push3d_fs<S, MODE>(i, fmaf(a_f, f[i], mf * (Ef + Of)), fmaf(a_s, s[i], ms * (Es + Os)),
                                 x, y, z, c, pout, P, PL);
-        push3d_fs<S, MODE, PLP>(o, fmaf(a_f, f[o], mf * (Ef - Of)), fmaf(a_s, s[o], ms * (Es - Os)),
+        push3d_fs<S, MODE>(o, fmaf(a_f, f[o], mf * (Ef - Of)), fmaf(a_s, s[o], ms * (Es - Os)),
                                 x, y, z, c, pout, P, PL);
     }
 }

@@ -265,11 +265,9 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const size_t c = (size_t)z * plane_cells + cxy;
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY, IsNarrow<S>::value>(sphi, z, x, y, c, f, s, g, qp, phip, pout,
-                                                          phi_prev, q_out, P, PL);
+                layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN, IsNarrow<S>::value>(sphi, z, x, y, c, f, s, g, qp, phip, pout,
-                                                              phi_prev, q_out, P, PL);
+                layer_update3d<S, XY_GEN>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
         }
         __syncthreads();      // the stages of layer z and window slot (z - 1) % 3 are free
         if (z + Gm::NFS < zend) {

@@ -44,6 +44,12 @@ template <typename S>
 cudaError_t launch_cac2d(const void *pin, void *pout, const float *vel, float factor,
                          const DevParams &P, cudaStream_t st);
 
+// periodic state check (health.cu): bit 4 of *err when phi leaves
+// [1/2 - excess, 1/2 + excess] or phi / the lagged source is not finite
+template <typename S>
+cudaError_t launch_health(const void *pops, const float *q, float excess, int *err, const DevParams &P,
+                          int dim, cudaStream_t st);
+
 // 2D (lbm2d.cu); S = float, __half or __nv_bfloat16 storage
 template <typename S>
 cudaError_t launch_step2d(const void *pin, void *pout, float *phi_prev, const float *q_in,

@@ -167,6 +167,12 @@ class Solver:
         B.check(B.lib.lbm_set_velocity(self._h, ctypes.byref(f), float(period)), "lbm_set_velocity")
         return self
 
+    def set_health_check(self, every, phi_excess=0.6):
+        """Check phi and the lagged source every `every` steps on the device
+        (0: off); a failed check makes sync() raise LBMError(LBM_ENONFINITE)."""
+        B.check(B.lib.lbm_set_health_check(self._h, int(every), float(phi_excess)), "lbm_set_health_check")
+        return self
+
     def step(self, n=1):
         B.check(B.lib.lbm_step(self._h, int(n)), "lbm_step")
         return self

@@ -123,6 +123,13 @@ def test_calls_reject_bad_arguments_before_device_work():
     assert B.lib.lbm_get_fields(h, ctypes.byref(f)) == B.LBM_EINVAL
     assert B.lib.lbm_stream_map(h, 2, None, None) == B.LBM_EINVAL
     assert B.lib.lbm_set_kernel(h, 9) == B.LBM_EINVAL
+    # periodic state check: a negative period, a non-positive or non-finite bound
+    assert B.lib.lbm_set_health_check(None, 10, 0.6) == B.LBM_EINVAL
+    assert B.lib.lbm_set_health_check(h, -1, 0.6) == B.LBM_EINVAL
+    assert B.lib.lbm_set_health_check(h, 10, 0.0) == B.LBM_EINVAL
+    assert B.lib.lbm_set_health_check(h, 10, float("nan")) == B.LBM_EINVAL
+    assert B.lib.lbm_set_health_check(h, 10, 0.6) == B.LBM_OK
+    assert B.lib.lbm_set_health_check(h, 0, 0.0) == B.LBM_OK         # off
     small = ctypes.c_size_t()
     assert B.lib.lbm_state_bytes(h, ctypes.byref(small)) == B.LBM_OK
     assert B.lib.lbm_get_state(h, ctypes.c_void_p(base), small.value - 1, 1) == B.LBM_ENOMEM
