@@ -91,6 +91,8 @@ class Params:
     g_form: str = "source"            # "source": Eq. LBE_PhaseField_Eq;
                                       # "cac_eq": Eq. LBE_PhaseField_Eq_Alternative
     normal_eps: float = 1e-3          # n = grad phi / max(|grad phi|, normal_eps)
+    collision: str = "bgk"            # "bgk": Eq. LBE; "trt": two relaxation rates
+    trt_magic: tuple = (0.25, 0.25, 0.25)   # Lambda of the f, g, s sets (TRT only)
 
     @classmethod
     def from_dict(cls, d):
@@ -101,6 +103,10 @@ class Params:
             keys["alpha_interp"] = "harmonic" if keys["alpha_interp"] else "linear"
         if "source_on" in keys:
             keys["source_on"] = bool(keys["source_on"])
+        if "collision" in keys and not isinstance(keys["collision"], str):
+            keys["collision"] = "trt" if keys["collision"] else "bgk"
+        if "trt_magic" in keys:
+            keys["trt_magic"] = tuple(float(v) for v in keys["trt_magic"])
         for k in ("gravity", "body_force", "phi_wall", "T_wall"):
             if k in keys:
                 keys[k] = tuple(float(v) for v in keys[k])
@@ -374,26 +380,62 @@ def _relax(pop, eq_bar, S, tau):
     return pop - (pop - eq_bar) / (tau + 0.5) + S
 
 
+def _relax_trt(pops, eq_bar, S, tau, magic, lat, transport_odd):
+    """Two-relaxation-time collision of one set (the "next" TRT row; not in
+    the paper, which uses Eq. LBE).  With the symmetric and antisymmetric
+    parts a+_i = (a_i + a_opp(i))/2, a-_i = (a_i - a_opp(i))/2 of the
+    populations, of the barred equilibria and of the sources,
+        theta*_i = theta_i - w+ (theta+_i - eq_bar+_i) - w- (theta-_i - eq_bar-_i) + S_i,
+    which for w+ = w- = 1/(tau + 1/2) is Eq. LBE.  The part that carries the
+    set's transport coefficient keeps the BGK rate 1/(tau + 1/2) (the
+    symmetric part for the flow, whose viscosity is a second-order moment;
+    the antisymmetric part for the phase field and the temperature, whose
+    diffusive fluxes are first-order moments); the other rate follows from
+    the magic parameter Lambda = (1/w+ - 1/2)(1/w- - 1/2)."""
+    tau_other = magic / tau
+    tau_p, tau_m = (tau_other, tau) if transport_odd else (tau, tau_other)
+    om_p, om_m = 1.0 / (tau_p + 0.5), 1.0 / (tau_m + 0.5)
+    out = []
+    opp = lat.opposite
+    for i in range(lat.Q):
+        o = opp[i]
+        d_p = 0.5 * ((pops[i] - eq_bar[i]) + (pops[o] - eq_bar[o]))
+        d_m = 0.5 * ((pops[i] - eq_bar[i]) - (pops[o] - eq_bar[o]))
+        out.append(pops[i] - om_p * d_p - om_m * d_m + S[i])
+    return out
+
+
 def collide(st, M, q, P, grid):
     """Post-collision populations of the three sets at time n."""
     Lf, Lg, _ = lattices_for(grid.dim)
     E = equilibria_and_sources(M["phi"], st["phi_prev"], M["u"], M["p"], M["T"], q, M, P, grid)
     g_eq, g_F, g_P, tau_g, n = E["g"]
-    g_out = []
+    g_bar, g_src = [], []
     for i in range(Lg.Q):
         if P.g_form == "source":
             S = g_F[i] + g_P[i]
-            g_out.append(_relax(st["g"][i], g_eq[i] - 0.5 * S, S, tau_g))
+            g_bar.append(g_eq[i] - 0.5 * S)
+            g_src.append(S)
         else:
             # Eq. Geq_AC-1: phi Gamma_i + M_phi (4/W) phi (1-phi) w_i c_i.n / cs^2
             interface = (4.0 / P.W) * M["phi"] * (1.0 - M["phi"])
             en = sum(float(Lg.e[i][a]) * n[a] for a in range(grid.dim))
             eq_cac = g_eq[i] + P.M_phi * interface * Lg.wf(i) * en / float(Lg.cs2)
-            g_out.append(_relax(st["g"][i], eq_cac - 0.5 * g_P[i], g_P[i], tau_g))
+            g_bar.append(eq_cac - 0.5 * g_P[i])
+            g_src.append(g_P[i])
     f_eq, f_S, tau_f = E["f"]
-    f_out = [_relax(st["f"][i], f_eq[i] - 0.5 * f_S[i], f_S[i], tau_f) for i in range(Lf.Q)]
+    f_bar = [f_eq[i] - 0.5 * f_S[i] for i in range(Lf.Q)]
     s_eq, s_S, tau_s = E["s"]
-    s_out = [_relax(st["s"][i], s_eq[i] - 0.5 * s_S[i], s_S[i], tau_s) for i in range(Lf.Q)]
+    s_bar = [s_eq[i] - 0.5 * s_S[i] for i in range(Lf.Q)]
+    if P.collision == "trt":
+        mf, mg, ms = P.trt_magic
+        f_out = _relax_trt(st["f"], f_bar, f_S, tau_f, mf, Lf, transport_odd=False)
+        g_out = _relax_trt(st["g"], g_bar, g_src, tau_g, mg, Lg, transport_odd=True)
+        s_out = _relax_trt(st["s"], s_bar, s_S, tau_s, ms, Lf, transport_odd=True)
+    else:
+        f_out = [_relax(st["f"][i], f_bar[i], f_S[i], tau_f) for i in range(Lf.Q)]
+        g_out = [_relax(st["g"][i], g_bar[i], g_src[i], tau_g) for i in range(Lg.Q)]
+        s_out = [_relax(st["s"][i], s_bar[i], s_S[i], tau_s) for i in range(Lf.Q)]
     return torch.stack(f_out), torch.stack(g_out), torch.stack(s_out)
 
 
