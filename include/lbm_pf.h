@@ -89,7 +89,24 @@ typedef struct {
     int32_t alpha_interp;         /* 0: linear in phi, 1: harmonic               */
     int32_t storage;              /* LBM_STORE_*                                 */
     int32_t model;                /* LBM_MODEL_*                                 */
+    int32_t collision;            /* LBM_COLLISION_*                             */
+    int32_t reserved;             /* set to 0                                    */
+    double trt_magic[3];          /* TRT magic parameter of the f, g, s sets     */
 } lbm_params;
+
+/* Collision operators.  BGK: Eq. LBE (the paper's scheme, the default).
+ * TRT: two relaxation rates per set, w+ for the symmetric and w- for the
+ * antisymmetric part of (population - barred equilibrium) and of the source
+ * (not in the paper; the two-relaxation-time extension its outlook names).
+ * The part that carries the set's transport coefficient keeps the BGK rate
+ * 1/(tau + 1/2) (the symmetric part for f: viscosity; the antisymmetric part
+ * for g and s: mobility and diffusivity); the other rate follows from the
+ * magic parameter Lambda = (1/w+ - 1/2)(1/w- - 1/2) > 0 of that set
+ * (Lambda = 3/16 puts the half-way bounce-back wall exactly at the middle of
+ * the link for Poiseuille flow).  TRT is implemented for LBM_MODEL_COUPLED
+ * in 2D and 3D; the adjoint covers BGK only. */
+#define LBM_COLLISION_BGK 0
+#define LBM_COLLISION_TRT 1
 
 /* Models.  COUPLED: the three coupled schemes of Sec. 3 (the default).
  * PHASE_FIELD: the phase-field scheme alone (Sec. 3.2, no phase change) in a

@@ -41,8 +41,8 @@ def _run(cmd, what, verbose):
         raise RuntimeError(f"nvcc failed building {what}")
 
 
-def _compile(out, defines, verbose, ptxas_info):
-    """One object per source, compiled in parallel, then one shared link."""
+def _jobs(out, defines, ptxas_info):
+    """(compile commands, objects) of one library: one object per source."""
     tag = os.path.splitext(os.path.basename(out))[0]
     objdir = os.path.join(HERE, "_build", tag)
     os.makedirs(objdir, exist_ok=True)
@@ -51,21 +51,23 @@ def _compile(out, defines, verbose, ptxas_info):
         flags.insert(0, "-Xptxas=-v")
     objs = [os.path.join(objdir, os.path.splitext(s)[0] + ".o") for s in SOURCES]
     jobs = [([nvcc(), *flags, "-c", os.path.join(CSRC, s), "-o", o], s) for s, o in zip(SOURCES, objs)]
-    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
-        for f in [ex.submit(_run, cmd, what, verbose) for cmd, what in jobs]:
-            f.result()
-    _run([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64",
-          "-o", out, *objs], os.path.basename(out), verbose)
-    return out
+    return jobs, objs
 
 
 def build(verbose=False, ptxas_info=False, debug=True):
     """Build the release library (and, unless debug=False, the bounds-checking
-    one); returns the release library's path."""
+    one): every object compiled in parallel, then one shared link per
+    library.  Returns the release library's path."""
     os.makedirs(LIBDIR, exist_ok=True)
-    _compile(LIB, [], verbose, ptxas_info)
-    if debug:
-        _compile(LIB_DEBUG, ["-DLBM_CHECK_BOUNDS"], verbose, False)
+    libs = [(LIB, [], ptxas_info)] + ([(LIB_DEBUG, ["-DLBM_CHECK_BOUNDS"], False)] if debug else [])
+    plan = [(out,) + _jobs(out, defines, pi) for out, defines, pi in libs]
+    jobs = [j for _, js, _ in plan for j in js]
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        for f in [ex.submit(_run, cmd, what, verbose) for cmd, what in jobs]:
+            f.result()
+    for out, _, objs in plan:
+        _run([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64",
+              "-o", out, *objs], os.path.basename(out), verbose)
     return LIB
 
 

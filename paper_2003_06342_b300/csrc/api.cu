@@ -89,6 +89,12 @@ int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
         if (p->source_on) return LBM_EINVAL;          // no phase change in this model
         if (dim != 2) return LBM_EUNSUPPORTED;
     }
+    if (p->collision != LBM_COLLISION_BGK && p->collision != LBM_COLLISION_TRT) return LBM_EINVAL;
+    if (p->collision == LBM_COLLISION_TRT) {
+        for (int s = 0; s < 3; ++s)
+            if (!(p->trt_magic[s] > 0.0 && std::isfinite(p->trt_magic[s]))) return LBM_EINVAL;
+        if (p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
+    }
     const double vals[] = {p->rho_l, p->rho_g, p->nu_l, p->nu_g, p->alpha_l, p->alpha_g, p->sigma,
                            p->W, p->M_phi, p->A, p->theta_I, p->L, p->Cp, p->T_sat,
                            p->gravity[0], p->gravity[1], p->gravity[2], p->body_force[0],
@@ -159,6 +165,8 @@ void fill_devparams(lbm_handle *h) {
     d.dbg = h->err;
 #endif
     d.Cp_over_L2 = (float)(p.Cp / (p.L * p.L));
+    d.trt = p.collision == LBM_COLLISION_TRT ? 1 : 0;
+    for (int s = 0; s < 3; ++s) d.trt_magic[s] = (float)p.trt_magic[s];
     // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
     int k = 0;
     for (int set = 0; set < 3; ++set) {
@@ -429,6 +437,11 @@ int lbm_init(lbm_handle *h, const lbm_fields *in) {
     h->steps = 0;
     if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return LBM_ECUDA;
     h->err_ready = 1;
+    // the phase-field-only kernel leaves the lagged source alone (it is zero
+    // without phase change): the buffer read after an odd step must hold zeros too
+    if (h->params.model == LBM_MODEL_PHASE_FIELD &&
+        cudaMemsetAsync(h->q[1], 0, h->N * sizeof(float), h->stream) != cudaSuccess)
+        return LBM_ECUDA;
     return do_init(h, phi0, T0, u0, p0);
 }
 
@@ -587,6 +600,9 @@ int lbm_set_state(lbm_handle *h, const void *src, size_t bytes, int32_t on_devic
     if (!h) return LBM_EINVAL;
     const int r = copy_state(h, const_cast<void *>(src), bytes, on_device, false);
     if (r != LBM_OK) return r;
+    if (h->params.model == LBM_MODEL_PHASE_FIELD &&
+        cudaMemsetAsync(h->q[h->cur ^ 1], 0, h->N * sizeof(float), h->stream) != cudaSuccess)
+        return LBM_ECUDA;
     h->steps = 0;
     if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return LBM_ECUDA;
     h->err_ready = 1;
@@ -655,7 +671,7 @@ int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
 static int adjoint_supported(const lbm_handle *h) {
     if (!h) return LBM_EINVAL;
     if (h->dim != 2 || h->params.storage != LBM_STORE_FP32 ||
-        h->params.model != LBM_MODEL_COUPLED)
+        h->params.model != LBM_MODEL_COUPLED || h->params.collision != LBM_COLLISION_BGK)
         return LBM_EUNSUPPORTED;
     return LBM_OK;
 }

@@ -31,7 +31,7 @@
 
 namespace lbm {
 
-template <typename S>
+template <typename S, bool TRT>
 __global__ void __launch_bounds__(TX * TY, 4)
 step2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
@@ -39,8 +39,8 @@ step2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
     __shared__ float sphi[SY * SX];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const bool fast = x0 >= 1 && x0 + TX + 1 <= P.n[0] && y0 >= 1 && y0 + TY + 1 <= P.n[1];
-    if (fast) step2d_tile<S, true>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
-    else step2d_tile<S, false>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+    if (fast) step2d_tile<S, true, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+    else step2d_tile<S, false, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
 }
 
 // ------------------------------------------------------------------ phi moment
@@ -177,8 +177,14 @@ cudaError_t launch_step2d(const void *pin, void *pout, float *phi_prev, const fl
                           float *q_out, const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
-    step2d_kernel<S><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
-                                             planes2d<S>(pin, pout, P));
+    // the two-relaxation-time collision is a separate instantiation, so the
+    // BGK kernel keeps its register allocation
+    if (P.trt)
+        step2d_kernel<S, true><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
+                                                       planes2d<S>(pin, pout, P));
+    else
+        step2d_kernel<S, false><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
+                                                        planes2d<S>(pin, pout, P));
     return cudaGetLastError();
 }
 

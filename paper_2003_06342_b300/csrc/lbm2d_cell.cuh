@@ -210,7 +210,9 @@ struct Coef2 {
 // working representation: stencils, closures, moments, production rate, the
 // three collisions and the push into pout.  FAST: no link of the cell wraps or
 // meets a wall.
-template <typename S, bool FAST>
+// TRT: the BGK relaxation (1 - om) v_i becomes
+// v_i - w+ (v_i + v_o)/2 - w- (v_i - v_o)/2 = a1 v_i + a2 v_o (o = opposite).
+template <typename S, bool FAST, bool TRT = false>
 __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const float f[9],
                                               const float g[9], const float s[9], float phip,
                                               float qp, int x, int y, size_t c,
@@ -272,33 +274,52 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     }
 
     const float ux = m.ux, uy = m.uy;
-    const float b_g = fmaf(-0.5f, om_g, 1.0f), b_f = fmaf(-0.5f, om_f, 1.0f);
-    const float b_s = fmaf(-0.5f, om_s, 1.0f);
+    // rates of the symmetric (p) and antisymmetric (m) parts: the BGK rate on
+    // both, or with TRT the BGK rate on the part carrying the transport
+    // coefficient (f: symmetric; g, s: antisymmetric) and the magic-parameter
+    // rate on the other
+    const float omp_f = om_f, omm_g = om_g, omm_s = om_s;
+    const float omm_f = TRT ? trt_other_rate(om_f, P.trt_magic[0]) : om_f;
+    const float omp_g = TRT ? trt_other_rate(om_g, P.trt_magic[1]) : om_g;
+    const float omp_s = TRT ? trt_other_rate(om_s, P.trt_magic[2]) : om_s;
+    const float b_g = fmaf(-0.5f, omp_g, 1.0f), b_f = fmaf(-0.5f, omp_f, 1.0f);
+    const float b_s = fmaf(-0.5f, omp_s, 1.0f);
+    const float bm_g = TRT ? fmaf(-0.5f, omm_g, 1.0f) : b_g;
+    const float bm_f = TRT ? fmaf(-0.5f, omm_f, 1.0f) : b_f;
     Coef2 k;
-    k.a_g = 1.0f - om_g; k.a_f = 1.0f - om_f; k.a_s = 1.0f - om_s;
+    k.a_g = 1.0f - omp_g; k.a_f = 1.0f - omp_f; k.a_s = 1.0f - omp_s;    // rest direction
     // g: F^g + P^g = w (iface e.n + q); g_eq - w phi_ref = w (phd + phi poly)
     const float iface = P.four_over_W * ph * (1.0f - ph);
-    k.Ag = fmaf(om_g, phd, b_g * q);
-    k.Bg = om_g * ph;
-    const float bgi = b_g * iface;
-    k.Vgx = fmaf(3.0f * k.Bg, ux, bgi * nx_);
-    k.Vgy = fmaf(3.0f * k.Bg, uy, bgi * ny_);
+    k.Ag = fmaf(omp_g, phd, b_g * q);
+    k.Bg = omp_g * ph;
+    const float Bgo = TRT ? omm_g * ph : k.Bg;
+    const float bgi = bm_g * iface;
+    k.Vgx = fmaf(3.0f * Bgo, ux, bgi * nx_);
+    k.Vgy = fmaf(3.0f * Bgo, uy, bgi * ny_);
     // f: f_eq = w (p + rho cs2 poly); F^f + P^f = w [(e.F - u.F + pf) + poly (e.H - u.H)]
     // with H = cs2 grad(rho) + F (Eq. Forcing with Gamma_i = w_i (1 + poly_i))
     const float hx = fmaf(L::cs2, m.grx, m.Fx), hy = fmaf(L::cs2, m.gry, m.Fy);
     const float hU = fmaf(ux, hx, uy * hy);
     const float uB = fmaf(ux, m.Fx, uy * m.Fy);
     // P^f_i / w_i = rho cs2 q kappa, here minus u.F
-    k.K0 = fmaf(om_f, m.p - P.set_ref[0], b_f * fmaf(rcs2 * q, P.kappa, -uB));
-    k.K1 = fmaf(om_f, rcs2, -b_f * hU);
+    k.K0 = fmaf(omp_f, m.p - P.set_ref[0], b_f * fmaf(rcs2 * q, P.kappa, -uB));
+    k.K1 = fmaf(omp_f, rcs2, -b_f * hU);
     k.Hx = b_f * hx; k.Hy = b_f * hy;
-    k.Vfx = fmaf(3.0f * k.K1, ux, b_f * m.Fx);
-    k.Vfy = fmaf(3.0f * k.K1, uy, b_f * m.Fy);
+    // the odd part: K1 and H with the antisymmetric rate
+    const float K1o = TRT ? fmaf(omm_f, rcs2, -bm_f * hU) : k.K1;
+    const float Hox = TRT ? bm_f * hx : k.Hx, Hoy = TRT ? bm_f * hy : k.Hy;
+    k.Vfx = fmaf(3.0f * K1o, ux, bm_f * m.Fx);
+    k.Vfy = fmaf(3.0f * K1o, uy, bm_f * m.Fy);
     // s: s_eq - w T_ref = w (Td + T poly); S^s = -w (L/Cp) D
-    k.As = fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D);
-    k.Bs = om_s * m.T;
+    k.As = fmaf(omp_s, m.Td, -b_s * P.L_over_Cp * D);
+    k.Bs = omp_s * m.T;
+    const float Bso = TRT ? omm_s * m.T : k.Bs;
     // __fmul_rn: W enters E +- W as a finished product, never fused into the sum
-    k.Wx = __fmul_rn(3.0f * k.Bs, ux); k.Wy = __fmul_rn(3.0f * k.Bs, uy);
+    k.Wx = __fmul_rn(3.0f * Bso, ux); k.Wy = __fmul_rn(3.0f * Bso, uy);
+    // TRT: out_i = a1 v_i + a2 v_o + ...
+    const float a1_f = 1.0f - 0.5f * (omp_f + omm_f), a2_f = 0.5f * (omm_f - omp_f);
+    const float a1_g = 1.0f - 0.5f * (omp_g + omm_g), a2_g = 0.5f * (omm_g - omp_g);
+    const float a1_s = 1.0f - 0.5f * (omp_s + omm_s), a2_s = 0.5f * (omm_s - omp_s);
 
     // even parts P_e of poly: rest, x axis, y axis, diagonals (1,1) and (-1,1)
     const float uxx = ux * ux, uyy = uy * uy, uxy = ux * uy;
@@ -313,25 +334,37 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
         fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)),
         fmaf(k.a_s, s[0], rep_mul<S>(0, 2, P) * fmaf(k.Bs, P0, k.As)), x, y, c, pout, P, PL);
     // a direction i with e = (ex, ey) and its opposite o
-    auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eVf, float eW) {
+    auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eHo, float eVf,
+                    float eW) {
         const float Eg = fmaf(k.Bg, Pe, k.Ag);
         const float Ef = fmaf(3.0f * cu, eH, fmaf(k.K1, Pe, k.K0));
-        const float Of = fmaf(Pe, eH, eVf);
+        const float Of = fmaf(Pe, eHo, eVf);
         const float Es = fmaf(k.Bs, Pe, k.As);
         const float mf = rep_mul<S>(i, 0, P), mg = rep_mul<S>(i, 1, P), ms = rep_mul<S>(i, 2, P);
-        push2d<S, FAST>(i, fmaf(k.a_f, f[i], mf * (Ef + Of)), fmaf(k.a_g, g[i], mg * (Eg + eVg)),
-                        fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P, PL);
-        push2d<S, FAST>(o, fmaf(k.a_f, f[o], mf * (Ef - Of)), fmaf(k.a_g, g[o], mg * (Eg - eVg)),
-                        fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P, PL);
+        if (!TRT) {
+            push2d<S, FAST>(i, fmaf(k.a_f, f[i], mf * (Ef + Of)), fmaf(k.a_g, g[i], mg * (Eg + eVg)),
+                            fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P, PL);
+            push2d<S, FAST>(o, fmaf(k.a_f, f[o], mf * (Ef - Of)), fmaf(k.a_g, g[o], mg * (Eg - eVg)),
+                            fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P, PL);
+        } else {
+            push2d<S, FAST>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], mf * (Ef + Of))),
+                            fmaf(a1_g, g[i], fmaf(a2_g, g[o], mg * (Eg + eVg))),
+                            fmaf(a1_s, s[i], fmaf(a2_s, s[o], ms * (Es + eW))), x, y, c, pout, P, PL);
+            push2d<S, FAST>(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], mf * (Ef - Of))),
+                            fmaf(a1_g, g[o], fmaf(a2_g, g[i], mg * (Eg - eVg))),
+                            fmaf(a1_s, s[o], fmaf(a2_s, s[i], ms * (Es - eW))), x, y, c, pout, P, PL);
+        }
     };
-    pair(1, 3, ux, Pxa, k.Vgx, k.Hx, k.Vfx, k.Wx);                               // (1, 0)
-    pair(2, 4, uy, Pya, k.Vgy, k.Hy, k.Vfy, k.Wy);                               // (0, 1)
+    pair(1, 3, ux, Pxa, k.Vgx, k.Hx, Hox, k.Vfx, k.Wx);                          // (1, 0)
+    pair(2, 4, uy, Pya, k.Vgy, k.Hy, Hoy, k.Vfy, k.Wy);                          // (0, 1)
     // the diagonal components are sums of products: __fadd_rn / __fsub_rn keep
     // the compiler from fusing one of the products into the sum
     pair(5, 7, __fadd_rn(ux, uy), fmaf(9.0f, uxy, Pd0), __fadd_rn(k.Vgx, k.Vgy),
-         __fadd_rn(k.Hx, k.Hy), __fadd_rn(k.Vfx, k.Vfy), __fadd_rn(k.Wx, k.Wy));          // (1, 1)
+         __fadd_rn(k.Hx, k.Hy), __fadd_rn(Hox, Hoy), __fadd_rn(k.Vfx, k.Vfy),
+         __fadd_rn(k.Wx, k.Wy));                                                 // (1, 1)
     pair(6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(k.Vgy, k.Vgx),
-         __fsub_rn(k.Hy, k.Hx), __fsub_rn(k.Vfy, k.Vfx), __fsub_rn(k.Wy, k.Wx));          // (-1, 1)
+         __fsub_rn(k.Hy, k.Hx), __fsub_rn(Hoy, Hox), __fsub_rn(k.Vfy, k.Vfx),
+         __fsub_rn(k.Wy, k.Wx));                                                 // (-1, 1)
 }
 
 // phi - phi_ref of one cell from its nine stored g values and lagged source
@@ -347,7 +380,7 @@ __device__ __forceinline__ float phid_cell2d(const S *__restrict__ pin, size_t c
 
 // The whole update of one tile.  FAST: the tile and its halo ring lie inside
 // the grid, so no halo cell and no streaming link wraps or meets a wall.
-template <typename S, bool FAST>
+template <typename S, bool FAST, bool TRT = false>
 __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__restrict__ pout,
                                             float *__restrict__ phi_prev,
                                             const float *__restrict__ q_in,
@@ -418,8 +451,8 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     __syncthreads();
     if (!active) return;
 
-    cell_update2d<S, FAST>(sphi + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y, c, pout,
-                           phi_prev, q_out, P, PL);
+    cell_update2d<S, FAST, TRT>(sphi + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y, c, pout,
+                                phi_prev, q_out, P, PL);
 }
 
 }  // namespace lbm

@@ -16,7 +16,7 @@
 
 namespace lbm {
 
-template <typename S>
+template <typename S, bool TRT>
 __global__ void __launch_bounds__(TX * TY, 2)
 step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
@@ -24,9 +24,9 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
     __shared__ float sphi[3 * PLANE];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int cls = tile_class3d(x0, y0, P);
-    if (cls == XY_IN) step3d_column<S, XY_IN>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
-    else if (cls == XY_WRAP) step3d_column<S, XY_WRAP>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
-    else step3d_column<S, XY_GEN>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+    if (cls == XY_IN) step3d_column<S, XY_IN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+    else if (cls == XY_WRAP) step3d_column<S, XY_WRAP, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+    else step3d_column<S, XY_GEN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
 }
 
 // ------------------------------------------------------------------ phi moment
@@ -165,8 +165,12 @@ cudaError_t launch_step3d(const void *pin, void *pout, float *phi_prev, const fl
                           float *q_out, const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, (P.n[2] + ZB - 1) / ZB);
-    step3d_kernel<S><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
-                                             planes3d<S>(pin, pout, P));
+    if (P.trt)
+        step3d_kernel<S, true><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
+                                                       planes3d<S>(pin, pout, P));
+    else
+        step3d_kernel<S, false><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
+                                                        planes3d<S>(pin, pout, P));
     return cudaGetLastError();
 }
 

@@ -391,7 +391,9 @@ __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int 
 // (algebraically Eq. LBE with theta_eq_bar = theta_eq - S/2 and the sources of
 // Eqs. Forcing, MicroProduction, SourceTerm_AllenCahn, Def_SourceTerms_Temp).
 // MODE (see push3d): how the links of this cell are pushed.
-template <typename S, int MODE>
+// TRT: see cell_update2d; the rest direction relaxes with the symmetric
+// rate, every other output is a1 v_i + a2 v_o + ... (o = opposite).
+template <typename S, int MODE, bool TRT = false>
 __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
                                                const float f[QF], const float s[QF],
                                                const float g[QG], float qp, float phip,
@@ -455,19 +457,31 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     }
 
     const float usq = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
-    const float b_g = fmaf(-0.5f, om_g, 1.0f), b_f = fmaf(-0.5f, om_f, 1.0f);
-    const float b_s = fmaf(-0.5f, om_s, 1.0f);
-    const float a_g = 1.0f - om_g, a_f = 1.0f - om_f, a_s = 1.0f - om_s;
+    // symmetric (p) and antisymmetric (m) rates: BGK, or TRT with the BGK rate
+    // on the part that carries the transport coefficient
+    const float omp_f = om_f, omm_g = om_g, omm_s = om_s;
+    const float omm_f = TRT ? trt_other_rate(om_f, P.trt_magic[0]) : om_f;
+    const float omp_g = TRT ? trt_other_rate(om_g, P.trt_magic[1]) : om_g;
+    const float omp_s = TRT ? trt_other_rate(om_s, P.trt_magic[2]) : om_s;
+    const float b_g = fmaf(-0.5f, omp_g, 1.0f), b_f = fmaf(-0.5f, omp_f, 1.0f);
+    const float b_s = fmaf(-0.5f, omp_s, 1.0f);
+    const float bm_g = TRT ? fmaf(-0.5f, omm_g, 1.0f) : b_g;
+    const float bm_f = TRT ? fmaf(-0.5f, omm_f, 1.0f) : b_f;
+    const float a_g = 1.0f - omp_g, a_f = 1.0f - omp_f, a_s = 1.0f - omp_s;
+    const float a1_f = 1.0f - 0.5f * (omp_f + omm_f), a2_f = 0.5f * (omm_f - omp_f);
+    const float a1_g = 1.0f - 0.5f * (omp_g + omm_g), a2_g = 0.5f * (omm_g - omp_g);
+    const float a1_s = 1.0f - 0.5f * (omp_s + omm_s), a2_s = 0.5f * (omm_s - omp_s);
 
     // phase field on D3Q7: poly = 4 e.u + 8 (e.u)^2 - 2 u^2
     {
         const float iface = P.four_over_W * ph * (1.0f - ph);
         // 16-bit storage: the set's scale folded into the coefficients
         const float sg = IsNarrow<S>::value ? P.set_sc[1] : 1.0f;
-        const float Ag = sg * fmaf(om_g, phd, b_g * q), Bg = sg * (om_g * ph);
-        const float bgi = sg * (b_g * iface);
-        const float Vg[3] = {fmaf(4.0f * Bg, ux, bgi * n0), fmaf(4.0f * Bg, uy, bgi * n1),
-                             fmaf(4.0f * Bg, uz, bgi * n2)};
+        const float Ag = sg * fmaf(omp_g, phd, b_g * q), Bg = sg * (omp_g * ph);
+        const float Bgo = TRT ? sg * (omm_g * ph) : Bg;
+        const float bgi = sg * (bm_g * iface);
+        const float Vg[3] = {fmaf(4.0f * Bgo, ux, bgi * n0), fmaf(4.0f * Bgo, uy, bgi * n1),
+                             fmaf(4.0f * Bgo, uz, bgi * n2)};
         const float usq2 = 2.0f * usq;
         push3d_g<S, MODE>(0, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)),
                             x, y, z, c, pout, P, PL);
@@ -476,8 +490,15 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
             const float ua = m.u[a];
             const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
             const float mg = rep_mul3<S, LG>(a + 1);
-            push3d_g<S, MODE>(a + 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
-            push3d_g<S, MODE>(a + 4, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
+            if (!TRT) {
+                push3d_g<S, MODE>(a + 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
+                push3d_g<S, MODE>(a + 4, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
+            } else {
+                push3d_g<S, MODE>(a + 1, fmaf(a1_g, g[a + 1], fmaf(a2_g, g[a + 4], mg * (Eg + Vg[a]))),
+                                  x, y, z, c, pout, P, PL);
+                push3d_g<S, MODE>(a + 4, fmaf(a1_g, g[a + 4], fmaf(a2_g, g[a + 1], mg * (Eg - Vg[a]))),
+                                  x, y, z, c, pout, P, PL);
+            }
         }
     }
 
@@ -491,16 +512,21 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     // P^f_i / w_i = rho cs2 q kappa, here minus u.F
     const float scf = IsNarrow<S>::value ? P.set_sc[0] : 1.0f;
     const float scs = IsNarrow<S>::value ? P.set_sc[2] : 1.0f;
-    const float K0 = scf * fmaf(om_f, m.p - P.set_ref[0], b_f * fmaf(rcs2 * q, P.kappa, -uB));
-    const float K1 = scf * fmaf(om_f, rcs2, -b_f * hU);
+    const float K0 = scf * fmaf(omp_f, m.p - P.set_ref[0], b_f * fmaf(rcs2 * q, P.kappa, -uB));
+    const float K1 = scf * fmaf(omp_f, rcs2, -b_f * hU);
     const float bf = scf * b_f;
     const float Hx = bf * hx, Hy = bf * hy, Hz = bf * hz;
-    const float Vfx = fmaf(3.0f * K1, ux, bf * m.F[0]);
-    const float Vfy = fmaf(3.0f * K1, uy, bf * m.F[1]);
-    const float Vfz = fmaf(3.0f * K1, uz, bf * m.F[2]);
-    const float As = scs * fmaf(om_s, m.Td, -b_s * P.L_over_Cp * D), Bs = scs * (om_s * m.T);
+    // the odd part: K1 and H with the antisymmetric rate
+    const float K1o = TRT ? scf * fmaf(omm_f, rcs2, -bm_f * hU) : K1;
+    const float bfo = TRT ? scf * bm_f : bf;
+    const float Hox = TRT ? bfo * hx : Hx, Hoy = TRT ? bfo * hy : Hy, Hoz = TRT ? bfo * hz : Hz;
+    const float Vfx = fmaf(3.0f * K1o, ux, bfo * m.F[0]);
+    const float Vfy = fmaf(3.0f * K1o, uy, bfo * m.F[1]);
+    const float Vfz = fmaf(3.0f * K1o, uz, bfo * m.F[2]);
+    const float As = scs * fmaf(omp_s, m.Td, -b_s * P.L_over_Cp * D), Bs = scs * (omp_s * m.T);
+    const float Bso = TRT ? scs * (omm_s * m.T) : Bs;
     // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
-    const float Wx = __fmul_rn(3.0f * Bs, ux), Wy = __fmul_rn(3.0f * Bs, uy), Wz = __fmul_rn(3.0f * Bs, uz);
+    const float Wx = __fmul_rn(3.0f * Bso, ux), Wy = __fmul_rn(3.0f * Bso, uy), Wz = __fmul_rn(3.0f * Bso, uz);
     push3d_fs<S, MODE>(0, fmaf(a_f, f[0], rep_mul3<S, LF>(0) * fmaf(K1, -usq15, K0)),
                             fmaf(a_s, s[0], rep_mul3<S, LF>(0) * fmaf(Bs, -usq15, As)), x, y, z, c,
                             pout, P, PL);
@@ -511,21 +537,29 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float cu = edot3(ex, ey, ez, ux, uy, uz);
         const float Pe = fmaf(4.5f * cu, cu, -usq15);
         const float eH = edot3(ex, ey, ez, Hx, Hy, Hz);
+        const float eHo = TRT ? edot3(ex, ey, ez, Hox, Hoy, Hoz) : eH;
         const float Ef = fmaf(3.0f * cu, eH, fmaf(K1, Pe, K0));
-        const float Of = fmaf(Pe, eH, edot3(ex, ey, ez, Vfx, Vfy, Vfz));
+        const float Of = fmaf(Pe, eHo, edot3(ex, ey, ez, Vfx, Vfy, Vfz));
         const float Es = fmaf(Bs, Pe, As);
         const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
         const float mf = rep_mul3<S, LF>(i), ms = mf;
-        push3d_fs<S, MODE>(i, fmaf(a_f, f[i], mf * (Ef + Of)), fmaf(a_s, s[i], ms * (Es + Os)),
-                                x, y, z, c, pout, P, PL);
-        push3d_fs<S, MODE>(o, fmaf(a_f, f[o], mf * (Ef - Of)), fmaf(a_s, s[o], ms * (Es - Os)),
-                                x, y, z, c, pout, P, PL);
+        if (!TRT) {
+            push3d_fs<S, MODE>(i, fmaf(a_f, f[i], mf * (Ef + Of)), fmaf(a_s, s[i], ms * (Es + Os)),
+                               x, y, z, c, pout, P, PL);
+            push3d_fs<S, MODE>(o, fmaf(a_f, f[o], mf * (Ef - Of)), fmaf(a_s, s[o], ms * (Es - Os)),
+                               x, y, z, c, pout, P, PL);
+        } else {
+            push3d_fs<S, MODE>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], mf * (Ef + Of))),
+                               fmaf(a1_s, s[i], fmaf(a2_s, s[o], ms * (Es + Os))), x, y, z, c, pout, P, PL);
+            push3d_fs<S, MODE>(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], mf * (Ef - Of))),
+                               fmaf(a1_s, s[o], fmaf(a2_s, s[i], ms * (Es - Os))), x, y, z, c, pout, P, PL);
+        }
     }
 }
 
 // One z-column of a 32x8 tile over layers [blockIdx.z * ZB, +ZB), every
 // value read with plain loads (see lbm3d.cu).
-template <typename S, int XY>
+template <typename S, int XY, bool TRT = false>
 __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__restrict__ pout,
                                               float *__restrict__ phi_prev,
                                               const float *__restrict__ q_in,
@@ -579,9 +613,9 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
             const float phip = phi_prev[c];
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY, TRT>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY_GEN, TRT>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
         }
 #pragma unroll
         for (int i = 0; i < QG; ++i) g[i] = gn[i];

@@ -180,7 +180,7 @@ __device__ __forceinline__ void ring_store(float *plane, const uint32_t *buf, in
 // z + 1; the copies of f/s(z + 1) and g(z + 2) are in flight, and when layer
 // z is done its stages receive f/s(z + 2) and g(z + 3): every copy is issued
 // at least one whole layer before it is awaited.
-template <typename S, int XY>
+template <typename S, int XY, bool TRT>
 __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S *__restrict__ pin,
                                            S *__restrict__ pout, float *__restrict__ phi_prev,
                                            const float *__restrict__ q_in, float *__restrict__ q_out,
@@ -265,9 +265,9 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const size_t c = (size_t)z * plane_cells + cxy;
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY, TRT>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY_GEN, TRT>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
         }
         __syncthreads();      // the stages of layer z and window slot (z - 1) % 3 are free
         if (z + Gm::NFS < zend) {
@@ -284,7 +284,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
     }
 }
 
-template <typename S>
+template <typename S, bool TRT>
 __global__ void __launch_bounds__(TX * TY, 2)
 step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ pin,
                   S *__restrict__ pout, float *__restrict__ phi_prev,
@@ -298,7 +298,7 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     __shared__ uint32_t rbuf[2 * RING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if (x0 + TX > P.n[0] || y0 + TY > P.n[1]) {          // ragged tile: plain loads
-        step3d_column<S, XY_GEN>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        step3d_column<S, XY_GEN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
         return;
     }
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -312,9 +312,9 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     // enough for the instruction cache (measured: FP32 +1.9%, FP16 +3.9%)
     const int cls = tile_class3d(x0, y0, P);
     if (cls != XY_GEN)
-        tma_column<S, XY_WRAP>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
+        tma_column<S, XY_WRAP, TRT>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
     else
-        tma_column<S, XY_GEN>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
+        tma_column<S, XY_GEN, TRT>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
 }
 
 // ------------------------------------------------------------------ host side
@@ -364,16 +364,23 @@ int make_tma_maps3d(TmaMaps3d *M, const DevParams &P, int elem_bytes, void *cons
     return 0;
 }
 
-template <typename S>
-static int blocks_per_sm_for() {
+template <typename S, bool TRT>
+static int blocks_per_sm_one() {
     int n = 0;
     const int dyn = Tma3Geom<S>::DYN;
-    if (cudaFuncSetAttribute(step3d_tma_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
+    if (cudaFuncSetAttribute(step3d_tma_kernel<S, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
         cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step3d_tma_kernel<S>, TX * TY, dyn) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step3d_tma_kernel<S, TRT>, TX * TY, dyn) != cudaSuccess)
         return 0;
     return n;
+}
+
+// both collision instantiations get the shared-memory limit
+template <typename S>
+static int blocks_per_sm_for() {
+    const int a = blocks_per_sm_one<S, false>(), b = blocks_per_sm_one<S, true>();
+    return a < b ? a : b;
 }
 
 int tma3d_blocks_per_sm(int elem_bytes) {
@@ -388,9 +395,12 @@ cudaError_t launch_step3d_tma(const TmaMaps3d &M, int par, const void *pin, void
                               const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, (P.n[2] + ZB - 1) / ZB);
-    step3d_tma_kernel<S><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, (const S *)pin, (S *)pout, phi_prev,
-                                                                q_in, q_out, par, err, P,
-                                                                planes3d<S>(pin, pout, P));
+    if (P.trt)
+        step3d_tma_kernel<S, true><<<grid, block, Tma3Geom<S>::DYN, st>>>(
+            M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes3d<S>(pin, pout, P));
+    else
+        step3d_tma_kernel<S, false><<<grid, block, Tma3Geom<S>::DYN, st>>>(
+            M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes3d<S>(pin, pout, P));
     return cudaGetLastError();
 }
 

@@ -108,6 +108,10 @@ struct DevParams {
     float enc_c[MAXQ_TOTAL], enc_s[MAXQ_TOTAL], dec_s[MAXQ_TOTAL];
     // per set (f, g, s): storage reference, 16-bit scale and its inverse
     float set_ref[3], set_sc[3], set_isc[3];
+    // two-relaxation-time collision: magic parameter of the f, g, s sets
+    // (read by the TRT instantiations of the step kernels only)
+    float trt_magic[3];
+    int trt;
 #ifdef LBM_CHECK_BOUNDS
     int *dbg;                          // device status word of the bounds checks
 #endif
@@ -284,6 +288,15 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// The second rate of the two-relaxation-time collision: given the rate om of
+// the part that carries the transport coefficient, the rate of the other part
+// from the magic parameter Lambda = (1/w+ - 1/2)(1/w- - 1/2), i.e.
+// w_other = b / (Lambda om + b/2) with b = 1 - om/2.
+__device__ __forceinline__ float trt_other_rate(float om, float magic) {
+    const float b = fmaf(-0.5f, om, 1.0f);
+    return b * rcp_approx(fmaf(magic, om, 0.5f * b));
 }
 
 // ---------------------------------------------------------------- closures

@@ -34,6 +34,9 @@ def make_params(d, storage="fp32", store_ref=None, store_scale=None):
     p.alpha_interp = int(d.get("alpha_interp", 0))
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p.model = int(d.get("model", 0))
+    coll = d.get("collision", 0)
+    p.collision = {"bgk": 0, "trt": 1}[coll] if isinstance(coll, str) else int(coll)
+    p.trt_magic[:] = [float(v) for v in d.get("trt_magic", (0.25, 0.25, 0.25))]
     return p
 
 

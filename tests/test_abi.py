@@ -75,6 +75,31 @@ def test_invalid_parameters_rejected(field, value):
     assert r == B.LBM_EINVAL
 
 
+def test_collision_option_validated():
+    w = W.film_boiling_2d(16, 16)
+    w.params.update(collision=1, trt_magic=(0.25, 3.0 / 16.0, 0.25))
+    assert _ws(w)[0] == B.LBM_OK
+    for bad in ((0.0, 0.25, 0.25), (0.25, -1.0, 0.25), (0.25, 0.25, float("inf"))):
+        w.params["trt_magic"] = bad
+        assert _ws(w)[0] == B.LBM_EINVAL, bad
+    w.params.update(collision=2, trt_magic=(0.25, 0.25, 0.25))
+    assert _ws(w)[0] == B.LBM_EINVAL
+    # the phase-field-only model and the adjoint are BGK only
+    v = W.vortex_disk(n=33)
+    v.params.update(collision=1, trt_magic=(0.25, 0.25, 0.25))
+    assert _ws(v)[0] == B.LBM_EUNSUPPORTED
+    w.params.update(collision=1)
+    r, nbytes, g, p, lat = _ws(w)
+    buf = (ctypes.c_uint8 * (nbytes + 512))()
+    base = (ctypes.addressof(buf) + 255) // 256 * 256
+    h = ctypes.c_void_p()
+    assert B.lib.lbm_create(ctypes.byref(g), lat, ctypes.byref(p), ctypes.c_void_p(base), nbytes,
+                            None, ctypes.byref(h)) == B.LBM_OK
+    a, sc = ctypes.c_size_t(), ctypes.c_size_t()
+    assert B.lib.lbm_adjoint_bytes(h, ctypes.byref(a), ctypes.byref(sc)) == B.LBM_EUNSUPPORTED
+    B.lib.lbm_destroy(h)
+
+
 def test_invalid_grids_rejected():
     w = W.film_boiling_2d(16, 16)
     w.periodic = (False, False)            # two wall axes

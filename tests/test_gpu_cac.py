@@ -109,3 +109,22 @@ def test_paper_cac_validations(make, sym_bound, mass_bound):
     print(w.name, "symmetric difference", sym, "mass drift", (m1 - m0) / m0)
     assert sym < sym_bound
     assert abs(m1 - m0) <= mass_bound * m0
+
+
+def test_odd_step_counts_read_a_zero_lagged_source():
+    """The phase-field kernel does not write the lagged source; after an odd
+    number of steps the moments read the second source buffer, which must
+    hold zeros even when the workspace memory held NaN before."""
+    w = W.vortex_disk(n=41)
+    u = [uu * 5.0 for uu in w.extra["u"]]
+    junk = torch.full((64 << 20,), float("nan"), device="cuda")   # 256 MB back to the cache
+    del junk
+    s = _solver(w, u=u, period=0.0)
+    s.step(7)
+    err = np.abs(_phi(s) - _oracle(w, 7, u=u, period=0.0)).max()
+    assert err < TOL, err
+    snap = s.get_state()
+    s.step(2)
+    s.set_state(snap)
+    s.step(1)
+    assert np.isfinite(_phi(s)).all()
