@@ -280,6 +280,20 @@ def run_device(args, world, rank, local):
                 "frac": bpc * w.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v)),
                 "traffic": profiled_traffic(f"step2d_{storage}_2048x4096")}
             del v
+        # the two-relaxation-time collision option on the same 2D workload
+        wt = dict(w.params, collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25))
+        for storage in ("fp32", "fp16"):
+            v = Solver(w.n, w.periodic, wt, storage=storage, device=dev, stream=stream)
+            v.init(w.phi0, w.T0, p0=w.p0)
+            v.step(20)
+            ms_v = step_kernel_ms(v, 500)
+            m_v = safe_reduce(v)
+            bpc = BYTES_PER_CELL[("2d", storage)]
+            variants[f"2d_{storage}_trt"] = {
+                "workload": w.name + ", TRT collision", "MLUPS": w.cells / ms_v / 1e3, "ms_per_step": ms_v,
+                "bytes_per_cell": bpc, "achieved_GBs": bpc * w.cells / ms_v / 1e6,
+                "frac": bpc * w.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v))}
+            del v
         w3 = W.c3_film_boiling_3d()
         best16 = ("tiled", 0.0)
         for storage in ("fp32", "fp16"):
@@ -301,6 +315,20 @@ def run_device(args, world, rank, local):
                 if storage == "fp16" and mlups > best16[1]:
                     best16 = (kern, mlups)
                 del v
+        # TRT in 3D (TMA-staged kernel)
+        w3t = dict(w3.params, collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25))
+        v = Solver(w3.n, w3.periodic, w3t, storage="fp32", device=dev, stream=stream)
+        v.set_kernel("tma")
+        v.init(w3.phi0, w3.T0, p0=w3.p0)
+        v.step(5)
+        ms_v = step_kernel_ms(v, 100)
+        m_v = safe_reduce(v)
+        bpc = BYTES_PER_CELL[("3d", "fp32")]
+        variants["3d_fp32_tma_trt"] = {
+            "workload": w3.name + ", TRT collision", "kernel": v.kernel(), "MLUPS": w3.cells / ms_v / 1e3,
+            "ms_per_step": ms_v, "bytes_per_cell": bpc, "achieved_GBs": bpc * w3.cells / ms_v / 1e6,
+            "frac": bpc * w3.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v))}
+        del v
         torch.cuda.empty_cache()
         # the 512 x 512 x 768 FP16 film (201 M cells, 36 GB of populations)
         w5 = W.c5_film_boiling_3d_large()
