@@ -156,8 +156,9 @@ int lbm_init(lbm_handle *h, const lbm_fields *in);
 /* Advance n >= 0 time steps: per step one fused kernel computing the moments
  * (Eqs. Moment_Phi, Velocity, Pressure, Moment_Temp), the phi stencils (Eqs.
  * Grad, Laplacian, ChemicalPotential), the production rate (Eq.
- * ProductionRate), the three BGK collisions with sources (Eq. LBE) and the
- * streaming with boundary links.  Asynchronous. */
+ * ProductionRate), the three collisions with sources (Eq. LBE, or the TRT
+ * option of lbm_params.collision) and the streaming with boundary links.
+ * Asynchronous. */
 int lbm_step(lbm_handle *h, int32_t n);
 
 /* Write phi, u, p and T of the current state (the moments of the step
