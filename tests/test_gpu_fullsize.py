@@ -1,0 +1,129 @@
+"""Parity at the full benchmark sizes, in the launch configuration bench.py
+times (2048 x 4096 2D film on the tiled kernel; 256 x 256 x 512 3D film on
+the TMA-staged kernel), on sampled cells.
+
+The oracle cannot step 8 M or 34 M cells in a test, but a cell's update over
+k steps depends only on the initial fields within a few cells of it (the push
+moves a value one cell per step and the phi stencils reach one more cell, so
+the fields at x after k steps depend on the initial fields within 2k + 2
+cells).  For each sampled cell the oracle therefore steps the window of
+radius r = 2k + 3 around it, cut from the same initial fields: periodic axes
+wrap, a window that meets a wall keeps that wall, and the window's own edges
+(wrapped or cut) are more than 2k + 2 cells from the sample.  The sampled
+cells include the interface band, cells next to both walls, periodic edges
+and the borders of the 32 x 8 tiles."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import model as M
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _samples(n, periodic, band, rng, count=24):
+    """Cell coordinates (x, y[, z]): random cells in the interface band along
+    the wall axis, cells next to each wall, periodic edges, tile borders."""
+    dim = len(n)
+    wall = [a for a in range(dim) if not periodic[a]][0]
+    out = []
+    for _ in range(count):
+        c = [int(rng.integers(0, n[a])) for a in range(dim)]
+        c[wall] = int(rng.integers(band[0], band[1]))
+        out.append(c)
+    for wv in (0, 1, n[wall] - 2, n[wall] - 1):
+        c = [int(rng.integers(0, n[a])) for a in range(dim)]
+        c[wall] = wv
+        out.append(c)
+    for a in range(dim):
+        if periodic[a]:
+            for v in (0, n[a] - 1, 31 if a == 0 else 7, 32 if a == 0 else 8):
+                c = [int(rng.integers(0, n[b])) for b in range(dim)]
+                c[a] = v
+                c[wall] = int(rng.integers(band[0], band[1]))
+                out.append(c)
+    return out
+
+
+def _window(w, cell, r):
+    """Window of the initial fields around `cell`, its grid and the cell's
+    position in it."""
+    idx, per, pos = [], [], []
+    for a, (c, n) in enumerate(zip(cell, w.n)):
+        m = 2 * r + 1
+        if w.periodic[a]:
+            idx.append([(c - r + k) % n for k in range(m)])
+            per.append(True)
+            pos.append(r)
+        else:
+            lo = min(max(c - r, 0), n - m)
+            idx.append(list(range(lo, lo + m)))
+            per.append(False)
+            pos.append(c - lo)
+    ix = np.ix_(*reversed(idx))                    # arrays are [z][y]x
+    cut = lambda f: np.ascontiguousarray(f[ix]) if f is not None else None
+    return cut(w.phi0), cut(w.T0), cut(w.p0), tuple(2 * r + 1 for _ in w.n), tuple(per), tuple(pos)
+
+
+def _oracle_at(w, cell, steps):
+    r = 2 * steps + 3
+    phi0, T0, p0, n, per, pos = _window(w, cell, r)
+    P, G = M.Params.from_dict(w.params), M.Grid(n, per)
+    st = M.run(M.init_state(phi0, T0, P, G, p0=p0), P, G, steps)
+    F = M.fields(st, P, G)
+    at = tuple(reversed(pos))
+    return dict(phi=float(F["phi"][at]), T=float(F["T"][at]), p=float(F["p"][at]),
+                u=[float(F["u"][a][at]) for a in range(len(n))])
+
+
+def _gpu_at(F, cells):
+    dim = len(cells[0])
+    idx = [torch.tensor([c[a] for c in cells], device=F["phi"].device) for a in reversed(range(dim))]
+    pick = lambda t: t[tuple(idx)].double().cpu().numpy()
+    return dict(phi=pick(F["phi"]), T=pick(F["T"]), p=pick(F["p"]), u=[pick(F["u"][a]) for a in range(dim)])
+
+
+def _check(w, kernel, steps, storage="fp32", tol=TOL, seed=0):
+    from paper_2003_06342_b300 import Solver
+    s = Solver(w.n, w.periodic, w.params, storage=storage)
+    s.set_kernel(kernel)
+    s.init(w.phi0, w.T0, p0=w.p0)
+    s.step(steps)
+    assert s.kernel() == kernel
+    dim = len(w.n)
+    wall = [a for a in range(dim) if not w.periodic[a]][0]
+    # the interface band: where phi0 crosses 1/2 along the wall axis
+    prof = w.phi0.mean(axis=tuple(range(dim - 1)))
+    mid = int(np.argmin(np.abs(prof - 0.5)))
+    cells = _samples(w.n, w.periodic, (max(mid - 12, 0), min(mid + 12, w.n[wall])), np.random.default_rng(seed))
+    got = _gpu_at(s.fields(), cells)
+    worst = {k: 0.0 for k in ("phi", "T", "p", "u")}
+    for j, cell in enumerate(cells):
+        ref = _oracle_at(w, cell, steps)
+        for k in ("phi", "T", "p"):
+            worst[k] = max(worst[k], abs(got[k][j] - ref[k]))
+        worst["u"] = max(worst["u"], max(abs(got["u"][a][j] - ref["u"][a]) for a in range(dim)))
+    print(w.name, kernel, storage, steps, len(cells), "cells", worst)
+    assert all(v < tol for v in worst.values()), worst
+
+
+def test_2d_2048x4096_tiled_fp32_sampled():
+    _check(W.c2_film_boiling(), "tiled", 3)
+
+
+def test_2d_2048x4096_tiled_fp32_sampled_20_steps():
+    _check(W.c2_film_boiling(), "tiled", 20, seed=1)
+
+
+def test_2d_2048x4096_tiled_fp16_sampled():
+    _check(W.c2_film_boiling(), "tiled", 3, storage="fp16", tol=5e-3)
+
+
+def test_3d_256x256x512_tma_fp32_sampled():
+    _check(W.c3_film_boiling_3d(), "tma", 2)
+
+
+def test_3d_256x256x512_tma_fp16_sampled():
+    _check(W.c3_film_boiling_3d(), "tma", 2, storage="fp16", tol=5e-3, seed=2)
