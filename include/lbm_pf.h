@@ -288,9 +288,11 @@ int lbm_adjoint_init(lbm_handle *h, const lbm_fields *init, const void *adj0, fl
 /* LBM_MODEL_PHASE_FIELD: the imposed velocity u(x) (ux, uy of `u`, same
  * layout and pointer rules as lbm_init) and its time factor: the velocity at
  * step n is u(x) cos(pi n / period) when period > 0 (the reversing vortex of
- * Sec. 4.1 uses period = 2 T_f), u(x) otherwise.  Call before lbm_init, which
- * then builds the populations with that velocity.  LBM_EUNSUPPORTED for the
- * coupled model. */
+ * Sec. 4.1 uses period = 2 T_f), u(x) otherwise, with n counted from
+ * lbm_init or lbm_set_state (the saved state holds no step count, so a
+ * resumed time-dependent run restarts its factor at n = 0).  Call before
+ * lbm_init, which then builds the populations with that velocity.
+ * LBM_EUNSUPPORTED for the coupled model. */
 int lbm_set_velocity(lbm_handle *h, const lbm_fields *u, double period);
 
 /* Allocation-free global sums (no counterpart in the paper).  For callers
