@@ -92,6 +92,7 @@ class Params:
                                       # "cac_eq": Eq. LBE_PhaseField_Eq_Alternative
     normal_eps: float = 1e-3          # n = grad phi / max(|grad phi|, normal_eps)
     collision: str = "bgk"            # "bgk": Eq. LBE; "trt": two relaxation rates
+    grad_scheme: str = "central"      # Eq. DerivDirec_Grad; "biased2": second-order biased
     trt_magic: tuple = (0.25, 0.25, 0.25)   # Lambda of the f, g, s sets (TRT only)
 
     @classmethod
@@ -103,6 +104,8 @@ class Params:
             keys["alpha_interp"] = "harmonic" if keys["alpha_interp"] else "linear"
         if "source_on" in keys:
             keys["source_on"] = bool(keys["source_on"])
+        if "grad_scheme" in keys and not isinstance(keys["grad_scheme"], str):
+            keys["grad_scheme"] = "biased2" if keys["grad_scheme"] else "central"
         if "collision" in keys and not isinstance(keys["collision"], str):
             keys["collision"] = "trt" if keys["collision"] else "bgk"
         if "trt_magic" in keys:
@@ -146,11 +149,11 @@ class Grid:
 # neighbour access and finite differences (Sec. 3.4)
 # ----------------------------------------------------------------------------
 
-def _pad(field, grid, lo_val, hi_val):
-    """One ghost layer on every axis: the wall's Dirichlet value on the wall
-    axis, wrapped values on periodic axes.  The wall axis is padded first, so
-    a ghost that is both beyond a wall and beyond a periodic edge holds the
-    wall value."""
+def _pad(field, grid, lo_val, hi_val, width=1):
+    """`width` ghost layers on every axis: the wall's Dirichlet value on the
+    wall axis, wrapped values on periodic axes.  The wall axis is padded
+    first, so a ghost that is both beyond a wall and beyond a periodic edge
+    holds the wall value."""
     out = field
     order = [a for a in range(grid.dim) if not grid.periodic[a]] + \
             [a for a in range(grid.dim) if grid.periodic[a]]
@@ -158,36 +161,48 @@ def _pad(field, grid, lo_val, hi_val):
         d = grid.tdim(a)
         size = out.shape[d]
         if grid.periodic[a]:
-            lo = out.narrow(d, size - 1, 1)
-            hi = out.narrow(d, 0, 1)
+            lo = out.index_select(d, torch.tensor([k % size for k in range(-width, 0)]))
+            hi = out.index_select(d, torch.tensor([k % size for k in range(width)]))
         else:
-            lo = torch.full_like(out.narrow(d, 0, 1), lo_val)
-            hi = torch.full_like(out.narrow(d, 0, 1), hi_val)
+            shape = list(out.shape)
+            shape[d] = width
+            lo = torch.full(shape, lo_val, dtype=out.dtype)
+            hi = torch.full(shape, hi_val, dtype=out.dtype)
         out = torch.cat([lo, out, hi], dim=d)
     return out
 
 
-def _at(padded, grid, e):
-    """Field value at x + e (|e_a| <= 1) read from the padded field."""
+def _at(padded, grid, e, width=1):
+    """Field value at x + e (|e_a| <= width) read from the padded field."""
     out = padded
     for a in range(grid.dim):
-        out = out.narrow(grid.tdim(a), 1 + int(e[a]), grid.n[a])
+        out = out.narrow(grid.tdim(a), width + int(e[a]), grid.n[a])
     return out
 
 
 def gradient_laplacian(phi, grid, P):
     """grad(phi) by Eqs. DerivDirec_Grad + Grad and lap(phi) by Eqs.
     DerivDirect_Laplacian + Laplacian, over the stencil lattice's directions
-    i = 1..Q-1, with prefactor 1/cs^2 of that lattice."""
+    i = 1..Q-1, with prefactor 1/cs^2 of that lattice.  With grad_scheme
+    "biased2" the directional derivative in Eq. Grad is the second-order
+    biased (upwind) difference of Sec. 3.4,
+    e_i . grad(phi) = [-phi(x + 2 e_i) + 4 phi(x + e_i) - 3 phi(x)] / 2,
+    read from two ghost layers; the Laplacian stays central."""
     lat = lattices_for(grid.dim)[2]
-    pad = _pad(phi, grid, P.phi_wall[0], P.phi_wall[1])
+    biased = P.grad_scheme == "biased2"
+    width = 2 if biased else 1
+    pad = _pad(phi, grid, P.phi_wall[0], P.phi_wall[1], width)
     grad = [torch.zeros_like(phi) for _ in range(grid.dim)]
     lap = torch.zeros_like(phi)
     for i in range(1, lat.Q):
         e = lat.e[i]
-        plus = _at(pad, grid, e)
-        minus = _at(pad, grid, -e)
-        directional = (plus - minus) / 2.0             # e_i . grad(phi)
+        plus = _at(pad, grid, e, width)
+        minus = _at(pad, grid, -e, width)
+        if biased:
+            plus2 = _at(pad, grid, 2 * e, width)
+            directional = (-plus2 + 4.0 * plus - 3.0 * phi) / 2.0
+        else:
+            directional = (plus - minus) / 2.0         # e_i . grad(phi)
         second = plus - 2.0 * phi + minus              # (e_i . grad)^2 phi
         for a in range(grid.dim):
             if e[a] != 0:
