@@ -90,7 +90,7 @@ typedef struct {
     int32_t storage;              /* LBM_STORE_*                                 */
     int32_t model;                /* LBM_MODEL_*                                 */
     int32_t collision;            /* LBM_COLLISION_*                             */
-    int32_t reserved;             /* set to 0                                    */
+    int32_t grad_scheme;          /* LBM_GRAD_*                                  */
     double trt_magic[3];          /* TRT magic parameter of the f, g, s sets     */
 } lbm_params;
 
@@ -107,6 +107,18 @@ typedef struct {
  * in 2D and 3D; the adjoint covers BGK only. */
 #define LBM_COLLISION_BGK 0
 #define LBM_COLLISION_TRT 1
+
+/* Directional derivative inside Eq. Grad (Sec. 3.4).  CENTRAL: Eq.
+ * DerivDirec_Grad (the paper's choice).  BIASED2: the second-order biased
+ * difference e_i.grad(phi) = [-phi(x + 2 e_i) + 4 phi(x + e_i) - 3 phi(x)]/2
+ * the paper names as the remedy for velocity profiles in low-density
+ * regions (the first-order one gives exactly the central gradient through
+ * Eq. Grad); two ghost layers, the wall's Dirichlet value beyond a wall.
+ * The Laplacian stays central.  BIASED2 is implemented for the 2D coupled
+ * model on the tiled kernel; the TMA kernel and the adjoint take CENTRAL
+ * only (LBM_EUNSUPPORTED). */
+#define LBM_GRAD_CENTRAL 0
+#define LBM_GRAD_BIASED2 1
 
 /* Models.  COUPLED: the three coupled schemes of Sec. 3 (the default).
  * PHASE_FIELD: the phase-field scheme alone (Sec. 3.2, no phase change) in a

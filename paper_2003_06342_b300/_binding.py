@@ -24,6 +24,8 @@ LBM_EBOUNDS = -7
 
 LBM_COLLISION_BGK = 0
 LBM_COLLISION_TRT = 1
+LBM_GRAD_CENTRAL = 0
+LBM_GRAD_BIASED2 = 1
 
 LBM_D2Q9 = 0
 LBM_D3Q19_D3Q7 = 1
@@ -60,7 +62,7 @@ class lbm_params(ctypes.Structure):
         ("store_ref", ctypes.c_double * 3), ("store_scale", ctypes.c_double * 3),
         ("source_on", ctypes.c_int32), ("visc_interp", ctypes.c_int32),
         ("alpha_interp", ctypes.c_int32), ("storage", ctypes.c_int32),
-        ("model", ctypes.c_int32), ("collision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("model", ctypes.c_int32), ("collision", ctypes.c_int32), ("grad_scheme", ctypes.c_int32),
         ("trt_magic", ctypes.c_double * 3),
     ]
 

@@ -90,6 +90,9 @@ int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
         if (dim != 2) return LBM_EUNSUPPORTED;
     }
     if (p->collision != LBM_COLLISION_BGK && p->collision != LBM_COLLISION_TRT) return LBM_EINVAL;
+    if (p->grad_scheme != LBM_GRAD_CENTRAL && p->grad_scheme != LBM_GRAD_BIASED2) return LBM_EINVAL;
+    if (p->grad_scheme == LBM_GRAD_BIASED2 && (dim != 2 || p->model != LBM_MODEL_COUPLED))
+        return LBM_EUNSUPPORTED;
     if (p->collision == LBM_COLLISION_TRT) {
         for (int s = 0; s < 3; ++s)
             if (!(p->trt_magic[s] > 0.0 && std::isfinite(p->trt_magic[s]))) return LBM_EINVAL;
@@ -165,7 +168,8 @@ void fill_devparams(lbm_handle *h) {
     d.dbg = h->err;
 #endif
     d.Cp_over_L2 = (float)(p.Cp / (p.L * p.L));
-    d.trt = p.collision == LBM_COLLISION_TRT ? 1 : 0;
+    d.opts = (p.collision == LBM_COLLISION_TRT ? OPT_TRT : 0) |
+             (p.grad_scheme == LBM_GRAD_BIASED2 ? OPT_BIASED : 0);
     for (int s = 0; s < 3; ++s) d.trt_magic[s] = (float)p.trt_magic[s];
     // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
     int k = 0;
@@ -650,6 +654,8 @@ int lbm_sync(lbm_handle *h) {
 int lbm_set_kernel(lbm_handle *h, int32_t kernel) {
     if (!h || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA) return LBM_EINVAL;
     if (kernel == LBM_KERNEL_TMA) {
+        // the biased gradient needs two ghost layers: tiled kernel only
+        if (h->params.grad_scheme != LBM_GRAD_CENTRAL) return LBM_EUNSUPPORTED;
         if (h->tma_state == 0) setup_tma(h);
         if (h->tma_state != 1) return LBM_EUNSUPPORTED;
     }
@@ -671,7 +677,8 @@ int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
 static int adjoint_supported(const lbm_handle *h) {
     if (!h) return LBM_EINVAL;
     if (h->dim != 2 || h->params.storage != LBM_STORE_FP32 ||
-        h->params.model != LBM_MODEL_COUPLED || h->params.collision != LBM_COLLISION_BGK)
+        h->params.model != LBM_MODEL_COUPLED || h->params.collision != LBM_COLLISION_BGK ||
+        h->params.grad_scheme != LBM_GRAD_CENTRAL)
         return LBM_EUNSUPPORTED;
     return LBM_OK;
 }

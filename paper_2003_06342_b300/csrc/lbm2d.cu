@@ -31,16 +31,21 @@
 
 namespace lbm {
 
-template <typename S, bool TRT>
+template <typename S, bool TRT, bool BIASED>
 __global__ void __launch_bounds__(TX * TY, 4)
 step2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
               const __grid_constant__ Planes2d<S> PL) {
-    __shared__ float sphi[SY * SX];
+    __shared__ float sphi[BIASED ? SYB * SXB : SY * SX];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const bool fast = x0 >= 1 && x0 + TX + 1 <= P.n[0] && y0 >= 1 && y0 + TY + 1 <= P.n[1];
-    if (fast) step2d_tile<S, true, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
-    else step2d_tile<S, false, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+    if (BIASED) {
+        if (fast) step2d_tile_biased<S, true, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+        else step2d_tile_biased<S, false, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+    } else {
+        if (fast) step2d_tile<S, true, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+        else step2d_tile<S, false, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+    }
 }
 
 // ------------------------------------------------------------------ phi moment
@@ -71,6 +76,28 @@ __device__ __forceinline__ void gather_nb2d(const float *__restrict__ phi, int x
     }
 }
 
+// With the biased option, grad(phi) from the phi field by the second-order
+// biased difference (two ghost layers: the wall value beyond a wall,
+// wrapped on periodic axes); nb holds the nine values one cell away.
+__device__ __forceinline__ void biased_grad_field2d(const float *__restrict__ phi, int x, int y,
+                                                    const float nb[9], const DevParams &P, float &gx,
+                                                    float &gy) {
+    const int nx = P.n[0], ny = P.n[1];
+    float q[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        int cx = x + 2 * L::ex(i), cy = y + 2 * L::ey(i);
+        const int kx = wrap_coord_far(cx, nx, P.periodic[0]);
+        const int ky = wrap_coord_far(cy, ny, P.periodic[1]);
+        if (kx >= 2) q[i] = P.phi_wall[kx - 2];
+        else if (ky >= 2) q[i] = P.phi_wall[ky - 2];
+        else q[i] = phi[(size_t)cy * nx + cx];
+    }
+    // D2Q9 order: 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE
+    biased_grad2d(nb[1], nb[3], nb[2], nb[4], nb[5], nb[6], nb[7], nb[8], q[1], q[3], q[2], q[4], q[5], q[6],
+                  q[7], q[8], gx, gy);
+}
+
 // ------------------------------------------------------------------ moments
 // Writes the requested fields (NULL pointers skipped) and, when partial is
 // non-NULL, one FP64 (mass, enthalpy) pair per block.
@@ -96,6 +123,7 @@ macro2d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
         Macro2 m;
         m.phi = nb[0];
         stencil2d(nb, m.gx, m.gy, m.lap);
+        if (P.opts & OPT_BIASED) biased_grad_field2d(phi_f, x, y, nb, P, m.gx, m.gy);
         moments2d(m, f, s, phi_prev[c] + P.g_ref, q_in[c], P);
         if (o_phi) o_phi[c] = m.phi;
         if (o_T) o_T[c] = m.T;
@@ -125,6 +153,7 @@ init2d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
     Macro2 m;
     m.phi = nb[0];
     stencil2d(nb, m.gx, m.gy, m.lap);
+    if (P.opts & OPT_BIASED) biased_grad_field2d(phi0, x, y, nb, P, m.gx, m.gy);
     closures2d(m, P);
     m.ux = ux0 ? ux0[c] : 0.0f;
     m.uy = uy0 ? uy0[c] : 0.0f;
@@ -179,12 +208,15 @@ cudaError_t launch_step2d(const void *pin, void *pout, float *phi_prev, const fl
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
     // the two-relaxation-time collision is a separate instantiation, so the
     // BGK kernel keeps its register allocation
-    if (P.trt)
-        step2d_kernel<S, true><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
-                                                       planes2d<S>(pin, pout, P));
-    else
-        step2d_kernel<S, false><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
-                                                        planes2d<S>(pin, pout, P));
+    const S *in = (const S *)pin;
+    S *out = (S *)pout;
+    const Planes2d<S> PL = planes2d<S>(pin, pout, P);
+    switch (P.opts & (OPT_TRT | OPT_BIASED)) {
+    case 0: step2d_kernel<S, false, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_TRT: step2d_kernel<S, true, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_BIASED: step2d_kernel<S, false, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    default: step2d_kernel<S, true, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    }
     return cudaGetLastError();
 }
 

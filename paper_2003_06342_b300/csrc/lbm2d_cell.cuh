@@ -87,6 +87,21 @@ __device__ __forceinline__ EqSrc eq_src2d(int i, const Macro2 &m, float nx_, flo
     return r;
 }
 
+// grad(phi) by Eq. Grad with the second-order biased directional difference
+// [-phi(x + 2e) + 4 phi(x + e) - 3 phi(x)] / 2 (Sec. 3.4), from the values one
+// (p*) and two (q*) cells away in each D2Q9 direction.  Pair-folded: a
+// direction and its opposite contribute w e (4 (p+ - p-) - (q+ - q-)) / 2.
+__device__ __forceinline__ void biased_grad2d(float pE, float pW, float pN, float pS, float pNE, float pNW,
+                                              float pSW, float pSE, float qE, float qW, float qN, float qS,
+                                              float qNE, float qNW, float qSW, float qSE, float &gx, float &gy) {
+    const float bx = 0.5f * fmaf(4.0f, pE - pW, -(qE - qW));
+    const float by = 0.5f * fmaf(4.0f, pN - pS, -(qN - qS));
+    const float bA = 0.5f * fmaf(4.0f, pNE - pSW, -(qNE - qSW));     // along (1, 1)
+    const float bB = 0.5f * fmaf(4.0f, pSE - pNW, -(qSE - qNW));     // along (1, -1)
+    gx = 3.0f * fmaf(1.0f / 9.0f, bx, (1.0f / 36.0f) * (bA + bB));
+    gy = 3.0f * fmaf(1.0f / 9.0f, by, (1.0f / 36.0f) * (bA - bB));
+}
+
 __device__ __forceinline__ void normal2d(float gx, float gy, float eps2, float &nx_, float &ny_) {
     const float d = sqrtf(fmaxf(gx * gx + gy * gy, eps2));
     nx_ = gx / d;
@@ -212,7 +227,9 @@ struct Coef2 {
 // meets a wall.
 // TRT: the BGK relaxation (1 - om) v_i becomes
 // v_i - w+ (v_i + v_o)/2 - w- (v_i - v_o)/2 = a1 v_i + a2 v_o (o = opposite).
-template <typename S, bool FAST, bool TRT = false>
+// BIASED: the gradient of Eq. Grad from the second-order biased difference
+// (the window then holds two rings around the tile).
+template <typename S, bool FAST, bool TRT = false, bool BIASED = false>
 __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const float f[9],
                                               const float g[9], const float s[9], float phip,
                                               float qp, int x, int y, size_t c,
@@ -230,8 +247,14 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     m.phi = ph;
     {
         const float dA = pNE - pSW, dB = pSE - pNW;
-        m.gx = 3.0f * fmaf(1.0f / 9.0f, pE - pW, (1.0f / 36.0f) * (dA + dB));
-        m.gy = 3.0f * fmaf(1.0f / 9.0f, pN - pS, (1.0f / 36.0f) * (dA - dB));
+        if (BIASED) {
+            const int p2 = 2 * pitch;
+            biased_grad2d(pE, pW, pN, pS, pNE, pNW, pSW, pSE, sp[2], sp[-2], sp[p2], sp[-p2], sp[p2 + 2],
+                          sp[p2 - 2], sp[-p2 - 2], sp[-p2 + 2], m.gx, m.gy);
+        } else {
+            m.gx = 3.0f * fmaf(1.0f / 9.0f, pE - pW, (1.0f / 36.0f) * (dA + dB));
+            m.gy = 3.0f * fmaf(1.0f / 9.0f, pN - pS, (1.0f / 36.0f) * (dA - dB));
+        }
         const float la = fmaf(-4.0f, phd, (pE + pW) + (pN + pS));
         const float ld = fmaf(-4.0f, phd, (pNE + pSW) + (pNW + pSE));
         m.lap = 6.0f * fmaf(1.0f / 9.0f, la, (1.0f / 36.0f) * ld);
@@ -453,6 +476,59 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
 
     cell_update2d<S, FAST, TRT>(sphi + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y, c, pout,
                                 phi_prev, q_out, P, PL);
+}
+
+// The update of one tile with the biased gradient: the phi window holds two
+// rings around the 32 x 8 tile ((TY + 4) x (TX + 4) values, formed with
+// plain loads; beyond a wall both ghost layers take the wall's Dirichlet
+// value, periodic axes wrap).  FAST: no streaming link of the tile wraps or
+// meets a wall.
+constexpr int SXB = TX + 4, SYB = TY + 4;
+
+template <typename S, bool FAST, bool TRT>
+__device__ __forceinline__ void step2d_tile_biased(const S *__restrict__ pin, S *__restrict__ pout,
+                                                   float *__restrict__ phi_prev,
+                                                   const float *__restrict__ q_in,
+                                                   float *__restrict__ q_out, const DevParams &P,
+                                                   float *sphi, int x0, int y0, const Planes2d<S> &PL) {
+    const int nx = P.n[0], ny = P.n[1];
+    const size_t N = (size_t)P.N;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = FAST || ((x < nx) && (y < ny));
+    const size_t c = active ? (size_t)y * nx + x : 0;
+    float f[9], g[9], s[9], phip = 0.0f, qp = 0.0f;
+    if (active) {
+        (void)in_bounds((long long)c, (long long)N, P);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = load_raw(PL.in[9 + i] + c);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
+        phip = phi_prev[c];
+        qp = q_in[c];
+        sphi[(ty + 2) * SXB + tx + 2] = fmaf(0.5f, qp, set_sum2d<S>(g, P.set_isc[1]));
+    }
+    for (int sidx = tid; sidx < SXB * SYB; sidx += TX * TY) {
+        const int sx = sidx % SXB, sy = sidx / SXB;
+        int cx = x0 + sx - 2, cy = y0 + sy - 2;
+        const bool inner = sx >= 2 && sx < TX + 2 && sy >= 2 && sy < TY + 2;
+        if (inner && cx < nx && cy < ny) continue;                   // owned by a thread
+        if (cx < -2 || cx > nx + 1 || cy < -2 || cy > ny + 1) { sphi[sidx] = 0.0f; continue; }
+        const int kx = wrap_coord_far(cx, nx, P.periodic[0]);
+        const int ky = wrap_coord_far(cy, ny, P.periodic[1]);
+        float v;
+        if (kx >= 2) v = P.phi_wall[kx - 2] - P.g_ref;
+        else if (ky >= 2) v = P.phi_wall[ky - 2] - P.g_ref;
+        else {
+            const size_t cc = (size_t)cy * nx + cx;
+            v = phid_cell2d<S>(pin, cc, N, q_in[cc], P);
+        }
+        sphi[sidx] = v;
+    }
+    __syncthreads();
+    if (!active) return;
+    cell_update2d<S, FAST, TRT, true>(sphi + (ty + 2) * SXB + tx + 2, SXB, f, g, s, phip, qp, x, y, c, pout,
+                                      phi_prev, q_out, P, PL);
 }
 
 }  // namespace lbm

@@ -379,7 +379,7 @@ cudaError_t launch_step2d_tma(const TmaMaps2d &M, int par, const void *pin, void
                               const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY * YC - 1) / (TY * YC));
-    if (P.trt)
+    if (P.opts & OPT_TRT)
         step2d_tma_kernel<S, true><<<grid, block, March2Geom<S>::DYN, st>>>(
             M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
     else

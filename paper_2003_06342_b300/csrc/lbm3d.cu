@@ -165,7 +165,7 @@ cudaError_t launch_step3d(const void *pin, void *pout, float *phi_prev, const fl
                           float *q_out, const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, (P.n[2] + ZB - 1) / ZB);
-    if (P.trt)
+    if (P.opts & OPT_TRT)
         step3d_kernel<S, true><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
                                                        planes3d<S>(pin, pout, P));
     else

@@ -395,7 +395,7 @@ cudaError_t launch_step3d_tma(const TmaMaps3d &M, int par, const void *pin, void
                               const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, (P.n[2] + ZB - 1) / ZB);
-    if (P.trt)
+    if (P.opts & OPT_TRT)
         step3d_tma_kernel<S, true><<<grid, block, Tma3Geom<S>::DYN, st>>>(
             M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes3d<S>(pin, pout, P));
     else

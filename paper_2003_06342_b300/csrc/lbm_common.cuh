@@ -111,7 +111,7 @@ struct DevParams {
     // two-relaxation-time collision: magic parameter of the f, g, s sets
     // (read by the TRT instantiations of the step kernels only)
     float trt_magic[3];
-    int trt;
+    int opts;                          // OPT_TRT | OPT_BIASED
 #ifdef LBM_CHECK_BOUNDS
     int *dbg;                          // device status word of the bounds checks
 #endif
@@ -134,6 +134,9 @@ __device__ __forceinline__ bool in_bounds(long long idx, long long lim, const De
     (void)idx; (void)lim; (void)P;
     return true;
 }
+
+// DevParams::opts: two-relaxation-time collision, biased gradient (Sec. 3.4)
+constexpr int OPT_TRT = 1, OPT_BIASED = 2;
 
 // ---------------------------------------------------------------- layout
 // Memory layout of a population buffer (and of the saved and the adjoint
@@ -340,6 +343,14 @@ __device__ __forceinline__ float production(float phi, float T, const DevParams 
 __device__ __forceinline__ int wrap_coord(int &c, int n, int periodic) {
     if (c >= 0 && c < n) return 0;
     if (periodic) { c = c < 0 ? c + n : c - n; return 1; }
+    return c < 0 ? 2 : 3;
+}
+
+// The same for a coordinate up to any distance outside [0, n) (the second
+// ghost layer of the biased gradient on an axis of one cell).
+__device__ __forceinline__ int wrap_coord_far(int &c, int n, int periodic) {
+    if (c >= 0 && c < n) return 0;
+    if (periodic) { c = ((c % n) + n) % n; return 1; }
     return c < 0 ? 2 : 3;
 }
 

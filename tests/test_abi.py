@@ -100,6 +100,20 @@ def test_collision_option_validated():
     B.lib.lbm_destroy(h)
 
 
+def test_gradient_option_validated():
+    w = W.film_boiling_2d(16, 16)
+    w.params.update(grad_scheme=1)
+    assert _ws(w)[0] == B.LBM_OK
+    w.params.update(grad_scheme=3)
+    assert _ws(w)[0] == B.LBM_EINVAL
+    w3 = W.film_boiling_3d(16, 8, 12, modes=1, z0=5.0)
+    w3.params.update(grad_scheme=1)
+    assert _ws(w3)[0] == B.LBM_EUNSUPPORTED            # 2D only
+    v = W.vortex_disk(n=33)
+    v.params.update(grad_scheme=1)
+    assert _ws(v)[0] == B.LBM_EUNSUPPORTED             # coupled model only
+
+
 def test_invalid_grids_rejected():
     w = W.film_boiling_2d(16, 16)
     w.periodic = (False, False)            # two wall axes
