@@ -16,7 +16,9 @@
 //      rate (Eq. ProductionRate) and the three BGK collisions in barred
 //      variables (Eq. LBE with Eqs. Feq_NS_Incompr, Forcing, MicroProduction,
 //      Geq_Allen-Cahn_Eq, SourceTerm_AllenCahn, Seq_Temp,
-//      Def_SourceTerms_Temp);
+//      Def_SourceTerms_Temp), or their two-relaxation-time form (TRT
+//      instantiation), with the central or the biased gradient (BIASED
+//      instantiation, a two-ring phi window);
 //      The temperature set is advanced as deviations sbar_i - w_i T_ref
 //      (the stored form), which keeps FP32 rounding relative to T - T_ref
 //      rather than to T;
@@ -206,8 +208,8 @@ cudaError_t launch_step2d(const void *pin, void *pout, float *phi_prev, const fl
                           float *q_out, const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
-    // the two-relaxation-time collision is a separate instantiation, so the
-    // BGK kernel keeps its register allocation
+    // the TRT collision and the biased gradient are separate instantiations,
+    // so the default kernel keeps its register allocation
     const S *in = (const S *)pin;
     S *out = (S *)pout;
     const Planes2d<S> PL = planes2d<S>(pin, pout, P);

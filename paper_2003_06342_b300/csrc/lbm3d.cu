@@ -8,7 +8,8 @@
 // its own cell of plane z+1 in registers for the next iteration.  The halo
 // ring's gbar and q are re-read from L2, so populations cross HBM once.
 // Everything else mirrors the 2D kernel (see lbm2d.cu): moments, closures,
-// production rate, three BGK collisions and push streaming with wall links.
+// production rate, three BGK (or TRT) collisions and push streaming with wall
+// links.
 #include "lbm_common.cuh"
 #include "lbm_kernels.h"
 #include "lbm3d.h"
