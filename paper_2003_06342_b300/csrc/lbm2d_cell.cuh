@@ -418,25 +418,31 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
 
     float f[9], g[9], s[9], phip = 0.0f, qp = 0.0f;
     (void)in_bounds(active ? (long long)c : 0, P.N, P);
-    // FAST: the ring cells' g and q are requested first, so their latency
-    // (an L2 hit: the neighbouring tiles load the same lines) overlaps the
-    // tile's own loads instead of following them
+    // FAST: the ring cells' g and q come from L2 (the neighbouring tiles load
+    // the same lines).  FP32 requests them before the tile's own values, so
+    // their latency overlaps the own loads; the 16-bit formats after them
+    // (measured: ring first is 3.8% faster for FP32, own first 2.4% / 4.4%
+    // faster for FP16 / BF16)
     constexpr int RING = 2 * SX + 2 * TY;
+    constexpr bool RING_FIRST = !IsNarrow<S>::value;
     float rv[9], rq = 0.0f;
     int rslot = 0;
-    if (FAST && tid < RING) {
-        int sx, sy;
-        if (tid < SX) { sx = tid; sy = 0; }
-        else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
-        else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
-        else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
-        rslot = sy * SX + sx;
-        const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
-        const bool ok = in_bounds((long long)cc, (long long)N, P);
+    auto load_ring = [&]() {
+        if (FAST && tid < RING) {
+            int sx, sy;
+            if (tid < SX) { sx = tid; sy = 0; }
+            else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
+            else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
+            else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
+            rslot = sy * SX + sx;
+            const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
+            const bool ok = in_bounds((long long)cc, (long long)N, P);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) rv[i] = ok ? load_raw(PL.in[9 + i] + cc) : 0.0f;
-        rq = ok ? q_in[cc] : 0.0f;
-    }
+            for (int i = 0; i < 9; ++i) rv[i] = ok ? load_raw(PL.in[9 + i] + cc) : 0.0f;
+            rq = ok ? q_in[cc] : 0.0f;
+        }
+    };
+    if (RING_FIRST) load_ring();
     if (active) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = load_raw(PL.in[9 + i] + c);
@@ -446,6 +452,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
         qp = q_in[c];
         sphi[(ty + 1) * SX + tx + 1] = fmaf(0.5f, qp, set_sum2d<S>(g, P.set_isc[1]));   // phi - phi_ref
     }
+    if (!RING_FIRST) load_ring();
     if (FAST) {
         // the 2*SX + 2*TY halo cells, one per thread (same arithmetic as
         // phid_cell2d)
