@@ -59,27 +59,34 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
     const size_t c = active ? (size_t)y * nx + x : 0;
     const float isc = P.set_isc[1];
 
+    // the ring's g values come from L2: requested before the tile's own for
+    // FP32, after them for the 16-bit formats (measured +1.6% / +2.6%)
     constexpr int RING = 2 * SX + 2 * TY;
+    constexpr bool RING_FIRST = !IsNarrow<S>::value;
     float rv[9];
     int rslot = 0;
-    if (FAST && tid < RING) {
-        int sx, sy;
-        if (tid < SX) { sx = tid; sy = 0; }
-        else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
-        else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
-        else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
-        rslot = sy * SX + sx;
-        const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
+    auto load_ring = [&]() {
+        if (FAST && tid < RING) {
+            int sx, sy;
+            if (tid < SX) { sx = tid; sy = 0; }
+            else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
+            else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
+            else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
+            rslot = sy * SX + sx;
+            const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) rv[i] = load_raw(PL.in[9 + i] + cc);
-        (void)in_bounds((long long)cc, (long long)N, P);
-    }
+            for (int i = 0; i < 9; ++i) rv[i] = load_raw(PL.in[9 + i] + cc);
+            (void)in_bounds((long long)cc, (long long)N, P);
+        }
+    };
+    if (RING_FIRST) load_ring();
     float g[9];
     if (active) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = load_raw(PL.in[9 + i] + c);
         sphi[(ty + 1) * SX + tx + 1] = set_sum2d<S>(g, isc);          // phi - phi_ref
     }
+    if (!RING_FIRST) load_ring();
     if (FAST) {
         if (tid < RING) sphi[rslot] = set_sum2d<S>(rv, isc);
     } else {
