@@ -557,9 +557,9 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     }
 }
 
-// One z-column of a 32x8 tile over layers [blockIdx.z * ZB, +ZB), every
+// One z-column of a 32x8 tile over layers [blockIdx.z * ZBLK, +ZBLK), every
 // value read with plain loads (see lbm3d.cu).
-template <typename S, int XY, bool TRT = false>
+template <typename S, int XY, bool TRT = false, int ZBLK = ZB>
 __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__restrict__ pout,
                                               float *__restrict__ phi_prev,
                                               const float *__restrict__ q_in,
@@ -568,8 +568,8 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int zbeg = blockIdx.z * ZB;
-    const int zend = min(zbeg + ZB, nz);
+    const int zbeg = blockIdx.z * ZBLK;
+    const int zend = min(zbeg + ZBLK, nz);
     const int x = x0 + tx, y = y0 + ty;
     const bool col = XY != XY_GEN || ((x < nx) && (y < ny));
     const size_t cxy = col ? (size_t)y * nx + x : 0;
