@@ -114,9 +114,9 @@ typedef struct {
  * the paper names as the remedy for velocity profiles in low-density
  * regions (the first-order one gives exactly the central gradient through
  * Eq. Grad); two ghost layers, the wall's Dirichlet value beyond a wall.
- * The Laplacian stays central.  BIASED2 is implemented for the 2D coupled
- * model on the tiled kernel; the TMA kernel and the adjoint take CENTRAL
- * only (LBM_EUNSUPPORTED). */
+ * The Laplacian stays central.  BIASED2 is implemented for the coupled model
+ * on the tiled kernels (2D and 3D; in 3D AUTO then selects the tiled kernel);
+ * the TMA kernels and the adjoint take CENTRAL only (LBM_EUNSUPPORTED). */
 #define LBM_GRAD_CENTRAL 0
 #define LBM_GRAD_BIASED2 1
 

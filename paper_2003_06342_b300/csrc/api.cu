@@ -91,8 +91,7 @@ int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
     }
     if (p->collision != LBM_COLLISION_BGK && p->collision != LBM_COLLISION_TRT) return LBM_EINVAL;
     if (p->grad_scheme != LBM_GRAD_CENTRAL && p->grad_scheme != LBM_GRAD_BIASED2) return LBM_EINVAL;
-    if (p->grad_scheme == LBM_GRAD_BIASED2 && (dim != 2 || p->model != LBM_MODEL_COUPLED))
-        return LBM_EUNSUPPORTED;
+    if (p->grad_scheme == LBM_GRAD_BIASED2 && p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
     if (p->collision == LBM_COLLISION_TRT) {
         for (int s = 0; s < 3; ++s)
             if (!(p->trt_magic[s] > 0.0 && std::isfinite(p->trt_magic[s]))) return LBM_EINVAL;
@@ -246,11 +245,12 @@ int do_step(lbm_handle *h) {
         if (h->kernel_choice == LBM_KERNEL_TMA) return LBM_EUNSUPPORTED;
     }
     // 3D: AUTO resolves to the TMA-staged kernel whenever it is available
-    if (h->dim == 3 && h->kernel_choice != LBM_KERNEL_TILED) {
-        if (h->tma_state == 0) setup_tma(h);
-    }
+    // (not with the biased gradient, which the tiled kernel alone implements)
+    const bool tma3 = h->dim == 3 && h->kernel_choice != LBM_KERNEL_TILED &&
+                      h->params.grad_scheme == LBM_GRAD_CENTRAL;
+    if (tma3 && h->tma_state == 0) setup_tma(h);
     if (h->dim == 3 && h->kernel_choice == LBM_KERNEL_TMA && h->tma_state != 1) return LBM_EUNSUPPORTED;
-    if (h->dim == 3 && h->kernel_choice != LBM_KERNEL_TILED && h->tma_state == 1) {
+    if (tma3 && h->tma_state == 1) {
         switch (h->params.storage) {
         case LBM_STORE_FP32: e = launch_step3d_tma<float>(h->maps3, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
         case LBM_STORE_FP16: e = launch_step3d_tma<__half>(h->maps3, h->cur, h->pops[h->cur], h->pops[nxt], h->phi_prev, h->q[h->cur], h->q[nxt], h->err, h->dp, h->stream); break;
@@ -668,7 +668,8 @@ int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
     if (h->dim == 3 && h->kernel_choice == LBM_KERNEL_AUTO && h->tma_state == 0)
         setup_tma(const_cast<lbm_handle *>(h));
     const bool tma = h->kernel_choice == LBM_KERNEL_TMA ||
-                     (h->dim == 3 && h->kernel_choice == LBM_KERNEL_AUTO);
+                     (h->dim == 3 && h->kernel_choice == LBM_KERNEL_AUTO &&
+                      h->params.grad_scheme == LBM_GRAD_CENTRAL);
     if (tma && h->tma_state == 1) *kernel = LBM_KERNEL_TMA;
     else *kernel = LBM_KERNEL_TILED;
     return LBM_OK;

@@ -17,17 +17,23 @@
 
 namespace lbm {
 
-template <typename S, bool TRT>
+template <typename S, bool TRT, bool BIASED>
 __global__ void __launch_bounds__(TX * TY, 2)
 step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
               const __grid_constant__ Planes3d<S> PL) {
-    __shared__ float sphi[3 * PLANE];
+    __shared__ float sphi[BIASED ? 5 * PLANEB : 3 * PLANE];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int cls = tile_class3d(x0, y0, P);
-    if (cls == XY_IN) step3d_column<S, XY_IN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
-    else if (cls == XY_WRAP) step3d_column<S, XY_WRAP, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
-    else step3d_column<S, XY_GEN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+    if (BIASED) {
+        if (cls == XY_IN) step3d_column_biased<S, XY_IN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        else if (cls == XY_WRAP) step3d_column_biased<S, XY_WRAP, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        else step3d_column_biased<S, XY_GEN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+    } else {
+        if (cls == XY_IN) step3d_column<S, XY_IN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        else if (cls == XY_WRAP) step3d_column<S, XY_WRAP, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        else step3d_column<S, XY_GEN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+    }
 }
 
 // ------------------------------------------------------------------ phi moment
@@ -55,6 +61,36 @@ __device__ __forceinline__ void gather_nb3d(const float *__restrict__ phi, int x
     }
 }
 
+// With the biased option, grad(phi) from the phi field by the second-order
+// biased difference of Eq. Grad (two ghost layers: the wall value beyond a
+// wall, wrapped on periodic axes); nb holds the values one cell away.
+__device__ __forceinline__ void biased_grad_field3d(const float *__restrict__ phi, int x, int y, int z,
+                                                    const float nb[QF], const DevParams &P, float g[3]) {
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    float q[QF];
+#pragma unroll
+    for (int i = 1; i < QF; ++i) {
+        int cx = x + 2 * LF::ex(i), cy = y + 2 * LF::ey(i), cz = z + 2 * LF::ez(i);
+        const int kx = wrap_coord_far(cx, nx, P.periodic[0]);
+        const int ky = wrap_coord_far(cy, ny, P.periodic[1]);
+        const int kz = wrap_coord_far(cz, nz, P.periodic[2]);
+        if (kx >= 2) q[i] = P.phi_wall[kx - 2];
+        else if (ky >= 2) q[i] = P.phi_wall[ky - 2];
+        else if (kz >= 2) q[i] = P.phi_wall[kz - 2];
+        else q[i] = phi[((size_t)cz * ny + cy) * nx + cx];
+    }
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = half19(k), o = LF::opp(i);
+        const float d = 0.5f * fmaf(4.0f, nb[i] - nb[o], -(q[i] - q[o]));
+        if (LF::ex(i) != 0) gx += sgnv(LF::ex(i), d) * LF::w(i);
+        if (LF::ey(i) != 0) gy += sgnv(LF::ey(i), d) * LF::w(i);
+        if (LF::ez(i) != 0) gz += sgnv(LF::ez(i), d) * LF::w(i);
+    }
+    g[0] = 3.0f * gx; g[1] = 3.0f * gy; g[2] = 3.0f * gz;
+}
+
 template <typename S>
 __global__ void __launch_bounds__(256)
 macro3d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
@@ -77,6 +113,7 @@ macro3d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
         Macro3 m;
         m.phi = nb[0];
         stencil3d(nb, m.g, m.lap);
+        if (P.opts & OPT_BIASED) biased_grad_field3d(phi_f, x, y, z, nb, P, m.g);
         moments3d(m, f, s, phi_prev[c] + P.g_ref, q_in[c], P);
         if (o_phi) o_phi[c] = m.phi;
         if (o_T) o_T[c] = m.T;
@@ -106,6 +143,7 @@ init3d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
     Macro3 m;
     m.phi = nb[0];
     stencil3d(nb, m.g, m.lap);
+    if (P.opts & OPT_BIASED) biased_grad_field3d(phi0, x, y, z, nb, P, m.g);
     closures3d(m, P);
     m.u[0] = ux0 ? ux0[c] : 0.0f;
     m.u[1] = uy0 ? uy0[c] : 0.0f;
@@ -166,12 +204,15 @@ cudaError_t launch_step3d(const void *pin, void *pout, float *phi_prev, const fl
                           float *q_out, const DevParams &P, cudaStream_t st) {
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, (P.n[2] + ZB - 1) / ZB);
-    if (P.opts & OPT_TRT)
-        step3d_kernel<S, true><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
-                                                       planes3d<S>(pin, pout, P));
-    else
-        step3d_kernel<S, false><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, phi_prev, q_in, q_out, P,
-                                                        planes3d<S>(pin, pout, P));
+    const S *in = (const S *)pin;
+    S *out = (S *)pout;
+    const Planes3d<S> PL = planes3d<S>(pin, pout, P);
+    switch (P.opts & (OPT_TRT | OPT_BIASED)) {
+    case 0: step3d_kernel<S, false, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_TRT: step3d_kernel<S, true, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_BIASED: step3d_kernel<S, false, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    default: step3d_kernel<S, true, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    }
     return cudaGetLastError();
 }
 

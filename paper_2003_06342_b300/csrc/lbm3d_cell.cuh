@@ -11,6 +11,8 @@ using LF = D3Q19L;   // f and s
 using LG = D3Q7L;    // g
 constexpr int TX = 32, TY = 8, SX = TX + 2, SY = TY + 2, PLANE = SX * SY;
 constexpr int ZB = 32;                       // z planes per block
+// window of the biased gradient: two rings around the tile, five planes
+constexpr int SXB = TX + 4, SYB = TY + 4, PLANEB = SXB * SYB;
 constexpr int QF = 19, QG = 7;
 constexpr int G0 = QF, S0 = QF + QG;         // flat plane number of g_0 and of s_0
 
@@ -393,7 +395,10 @@ __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int 
 // MODE (see push3d): how the links of this cell are pushed.
 // TRT: see cell_update2d; the rest direction relaxes with the symmetric
 // rate, every other output is a1 v_i + a2 v_o + ... (o = opposite).
-template <typename S, int MODE, bool TRT = false>
+// BIASED: sphi holds five planes of two-ring windows (plane p in slot
+// (p + 2) % 5) and the gradient of Eq. Grad uses the second-order biased
+// difference [-phi(x + 2e) + 4 phi(x + e) - 3 phi(x)] / 2 (Sec. 3.4).
+template <typename S, int MODE, bool TRT = false, bool BIASED = false>
 __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
                                                const float f[QF], const float s[QF],
                                                const float g[QG], float qp, float phip,
@@ -401,25 +406,47 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
                                                float *__restrict__ q_out, const DevParams &P,
                                                const Planes3d<S> &PL) {
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int centre = (ty + 1) * SX + tx + 1;
-    const float *pl[3] = {sphi + (z % 3) * PLANE + centre, sphi + ((z + 1) % 3) * PLANE + centre,
-                          sphi + ((z + 2) % 3) * PLANE + centre};   // planes z-1, z, z+1
     Macro3 m;
-    const float phd = pl[1][0];              // the window holds phi - phi_ref
+    float phd, gx = 0.0f, gy = 0.0f, gz = 0.0f, la = 0.0f, ld = 0.0f;
+    if constexpr (!BIASED) {
+        const int centre = (ty + 1) * SX + tx + 1;
+        const float *pl[3] = {sphi + (z % 3) * PLANE + centre, sphi + ((z + 1) % 3) * PLANE + centre,
+                              sphi + ((z + 2) % 3) * PLANE + centre};   // planes z-1, z, z+1
+        phd = pl[1][0];                      // the window holds phi - phi_ref
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = half19(k);
+            const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
+            const float a = pl[1 + ez][ey * SX + ex], b = pl[1 - ez][-ey * SX - ex];
+            const float d = a - b, sm = a + b;
+            if (ex != 0) gx += sgnv(ex, d) * LF::w(i);
+            if (ey != 0) gy += sgnv(ey, d) * LF::w(i);
+            if (ez != 0) gz += sgnv(ez, d) * LF::w(i);
+            if (i <= 6) la += sm; else ld += sm;
+        }
+    } else {
+        const int centre = (ty + 2) * SXB + tx + 2;
+        const float *pl[5];                  // planes z-2 .. z+2
+#pragma unroll
+        for (int k = 0; k < 5; ++k) pl[k] = sphi + ((z + k) % 5) * PLANEB + centre;
+        phd = pl[2][0];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = half19(k);
+            const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
+            const int o1 = ey * SXB + ex;
+            const float a = pl[2 + ez][o1], b = pl[2 - ez][-o1];
+            const float a2 = pl[2 + 2 * ez][2 * o1], b2 = pl[2 - 2 * ez][-2 * o1];
+            // a direction and its opposite: w e (4 (a - b) - (a2 - b2)) / 2
+            const float d = 0.5f * fmaf(4.0f, a - b, -(a2 - b2)), sm = a + b;
+            if (ex != 0) gx += sgnv(ex, d) * LF::w(i);
+            if (ey != 0) gy += sgnv(ey, d) * LF::w(i);
+            if (ez != 0) gz += sgnv(ez, d) * LF::w(i);
+            if (i <= 6) la += sm; else ld += sm;
+        }
+    }
     const float ph = phd + P.g_ref;
     m.phi = ph;
-    float gx = 0.0f, gy = 0.0f, gz = 0.0f, la = 0.0f, ld = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int i = half19(k);
-        const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
-        const float a = pl[1 + ez][ey * SX + ex], b = pl[1 - ez][-ey * SX - ex];
-        const float d = a - b, sm = a + b;
-        if (ex != 0) gx += sgnv(ex, d) * LF::w(i);
-        if (ey != 0) gy += sgnv(ey, d) * LF::w(i);
-        if (ez != 0) gz += sgnv(ez, d) * LF::w(i);
-        if (i <= 6) la += sm; else ld += sm;
-    }
     m.g[0] = 3.0f * gx; m.g[1] = 3.0f * gy; m.g[2] = 3.0f * gz;
     m.lap = 6.0f * fmaf(1.0f / 18.0f, fmaf(-6.0f, phd, la), (1.0f / 36.0f) * fmaf(-12.0f, phd, ld));
     closures3d(m, P);
@@ -621,6 +648,67 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
         for (int i = 0; i < QG; ++i) g[i] = gn[i];
         qcur = qnext;
         __syncthreads();   // plane (z - 1) % 3 is overwritten next iteration
+    }
+}
+
+// phi - phi_ref of window slot (sx, sy) of plane z of the two-ring window:
+// the wall's Dirichlet value beyond a wall, wrapped on periodic axes (to any
+// distance, for axes shorter than the ring)
+template <typename S>
+__device__ __forceinline__ float window_phid_b(int cx, int cy, int cz, const S *__restrict__ pin,
+                                               const float *__restrict__ q_in, const DevParams &P) {
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const int kx = wrap_coord_far(cx, nx, P.periodic[0]);
+    const int ky = wrap_coord_far(cy, ny, P.periodic[1]);
+    const int kz = wrap_coord_far(cz, nz, P.periodic[2]);
+    if (kx >= 2) return P.phi_wall[kx - 2] - P.g_ref;
+    if (ky >= 2) return P.phi_wall[ky - 2] - P.g_ref;
+    if (kz >= 2) return P.phi_wall[kz - 2] - P.g_ref;
+    return phid_at<S>(pin, q_in, ((size_t)cz * ny + cy) * nx + cx, (size_t)P.N, P);
+}
+
+// One z-column with the biased gradient: a rolling window of five planes,
+// each of the tile and two rings, every value formed from plain loads.
+// XY: the tile class, used for the push of interior layers as in
+// step3d_column.
+template <typename S, int XY, bool TRT>
+__device__ __forceinline__ void step3d_column_biased(const S *__restrict__ pin, S *__restrict__ pout,
+                                                     float *__restrict__ phi_prev,
+                                                     const float *__restrict__ q_in,
+                                                     float *__restrict__ q_out, const DevParams &P,
+                                                     float *sphi, const Planes3d<S> &PL) {
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int zbeg = blockIdx.z * ZB;
+    const int zend = min(zbeg + ZB, nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool col = (x < nx) && (y < ny);
+    const size_t cxy = col ? (size_t)y * nx + x : 0;
+    const size_t plane_cells = (size_t)nx * ny;
+    auto fill = [&](int p) {                 // plane p into slot (p + 2) % 5
+        float *pl = sphi + ((p + 2 + 5 * 4) % 5) * PLANEB;
+        for (int sidx = tid; sidx < PLANEB; sidx += TX * TY)
+            pl[sidx] = window_phid_b<S>(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, pin, q_in, P);
+    };
+    for (int p = zbeg - 2; p <= zbeg + 1; ++p) fill(p);
+    for (int z = zbeg; z < zend; ++z) {
+        fill(z + 2);
+        __syncthreads();
+        if (col) {
+            const size_t c = (size_t)z * plane_cells + cxy;
+            float f[QF], s[QF], g[QG];
+#pragma unroll
+            for (int i = 0; i < QG; ++i) g[i] = load_raw(PL.in[G0 + i] + c);
+#pragma unroll
+            for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
+            const float qp = q_in[c], phip = phi_prev[c];
+            if (XY != XY_GEN && z >= 1 && z + 1 < nz)
+                layer_update3d<S, XY, TRT, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+            else
+                layer_update3d<S, XY_GEN, TRT, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+        }
+        __syncthreads();   // slot (z - 2 + 2) % 5 is refilled next iteration
     }
 }
 

@@ -108,7 +108,7 @@ def test_gradient_option_validated():
     assert _ws(w)[0] == B.LBM_EINVAL
     w3 = W.film_boiling_3d(16, 8, 12, modes=1, z0=5.0)
     w3.params.update(grad_scheme=1)
-    assert _ws(w3)[0] == B.LBM_EUNSUPPORTED            # 2D only
+    assert _ws(w3)[0] == B.LBM_OK
     v = W.vortex_disk(n=33)
     v.params.update(grad_scheme=1)
     assert _ws(v)[0] == B.LBM_EUNSUPPORTED             # coupled model only

@@ -2,7 +2,9 @@
 the GPU against the FP64 oracle with grad_scheme "biased2": parity within
 1e-5 on geometries that take every ghost path (walls on y and on x with two
 ghost layers, periodic boxes, a one-cell periodic axis that wraps twice,
-ragged tiles), combined with TRT, and with 16-bit storage."""
+ragged tiles, 3D with walls on z and a periodic axis shorter than the rings),
+combined with TRT, and with 16-bit storage; in 3D AUTO selects the tiled
+kernel."""
 import numpy as np
 import pytest
 
@@ -30,6 +32,12 @@ CASES = [
     ("stefan_walls_x", lambda: _b(W.stefan_1d(nx=90, ny=2)), 80),
     ("one_cell_axis", lambda: _b(W.stefan_1d(nx=40, ny=1)), 40),
     ("film_trt", lambda: _b(_film(67, 45), collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25)), 30),
+    # 3D: walls on z, ragged x / y tiles, several z blocks of 32 layers
+    ("film_3d_ragged", lambda: _b(W.film_boiling_3d(37, 10, 41, modes=2, z0=12.0, phi_wall=(1.0, 0.0))), 12),
+    # a periodic axis of three cells, shorter than the two rings
+    ("film_3d_thin_y", lambda: _b(W.film_boiling_3d(40, 3, 20, modes=1, z0=7.0, phi_wall=(1.0, 0.0))), 12),
+    ("film_3d_trt", lambda: _b(W.film_boiling_3d(33, 9, 17, modes=1, z0=6.0, phi_wall=(1.0, 0.0)),
+                               collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25)), 10),
 ]
 
 
@@ -62,4 +70,15 @@ def test_biased_fp16_close_to_fp32_and_tma_refused():
     assert np.abs(fa["phi"] - fb["phi"]).max() < 5e-3
     with pytest.raises(LBMError) as e:
         a.set_kernel("tma")
+    assert e.value.code == LBM_EUNSUPPORTED
+
+
+def test_biased_3d_runs_on_the_tiled_kernel():
+    w = _b(W.film_boiling_3d(64, 16, 40, modes=1, z0=12.0, phi_wall=(1.0, 0.0)))
+    s = gpu_solver(w, storage="fp16")
+    assert s.kernel() == "tiled"              # AUTO picks the tiled kernel
+    s.step(5)
+    assert np.isfinite(gpu_fields(s)["phi"]).all()
+    with pytest.raises(LBMError) as e:
+        s.set_kernel("tma")
     assert e.value.code == LBM_EUNSUPPORTED
