@@ -3,7 +3,8 @@
 // The conservative Allen-Cahn scheme of Sec. 3.2 without phase change (q = 0)
 // and with the velocity u(x) c(n) prescribed instead of computed from f --
 // the setting of the paper's CAC validations (Sec. 4.1).  One launch per step
-// over 32x8 tiles, the same organisation as step2d_kernel for the g set only:
+// over tiles of 64 x 4 (FP32) or 32 x 4 cells (16-bit), the same organisation
+// as step2d_kernel for the g set only:
 // the tile's 9 g planes are loaded (the halo ring's first, so their L2
 // latency overlaps the own loads), phi - phi_ref of the tile and its ring
 // goes to shared memory, then each cell forms grad(phi) (Eqs. DerivDirec_Grad,
@@ -46,11 +47,13 @@ __device__ __forceinline__ void cac_push2d(int i, float v, int x, int y, size_t 
     }
 }
 
-template <typename S, bool FAST>
+template <typename S, bool FAST, class T>
 __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restrict__ pout,
                                            const float *__restrict__ vel, float factor,
                                            const DevParams &P, float *sphi, int x0, int y0,
                                            const Planes2d<S> &PL) {
+    constexpr int TX = T::TX, TY = T::TY, SX = T::SX, SY = T::SY;
+    static_assert(T::RING <= T::NT, "one halo-ring cell per thread");
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -150,25 +153,30 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
     pair(6, 8, fmaf(-9.0f, uxy, Pd0), __fsub_rn(Vgy, Vgx));
 }
 
+// Tile per storage, chosen by measurement on the 4096^2 vortex (one thread
+// per cell, 2048 threads per SM, 32 registers): FP32 64 x 4 (67.1k MLUPS
+// against 65.2k for 32 x 8), 16-bit 32 x 4 (82.6k against 80.6k).
+template <typename S> struct CacTile { using T = Tile2<32, 4>; };
+template <> struct CacTile<float> { using T = Tile2<64, 4>; };
+
 template <typename S>
-// eight blocks per SM (32 registers, a few bytes of spill): the full 64 warps
-// hide the latency of this light kernel (measured 4 -> 8 blocks: FP32 68% ->
-// 81% of the HBM peak, FP16 39% -> 55%)
-__global__ void __launch_bounds__(TX * TY, 8)
+__global__ void __launch_bounds__(CacTile<S>::T::NT, 2048 / CacTile<S>::T::NT)
 cac2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, const float *__restrict__ vel,
              float factor, const DevParams P, const __grid_constant__ Planes2d<S> PL) {
-    __shared__ float sphi[SY * SX];
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const bool fast = x0 >= 1 && x0 + TX + 1 <= P.n[0] && y0 >= 1 && y0 + TY + 1 <= P.n[1];
-    if (fast) cac_tile2d<S, true>(pin, pout, vel, factor, P, sphi, x0, y0, PL);
-    else cac_tile2d<S, false>(pin, pout, vel, factor, P, sphi, x0, y0, PL);
+    using T = typename CacTile<S>::T;
+    __shared__ float sphi[T::SY * T::SX];
+    const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
+    const bool fast = x0 >= 1 && x0 + T::TX + 1 <= P.n[0] && y0 >= 1 && y0 + T::TY + 1 <= P.n[1];
+    if (fast) cac_tile2d<S, true, T>(pin, pout, vel, factor, P, sphi, x0, y0, PL);
+    else cac_tile2d<S, false, T>(pin, pout, vel, factor, P, sphi, x0, y0, PL);
 }
 
 template <typename S>
 cudaError_t launch_cac2d(const void *pin, void *pout, const float *vel, float factor,
                          const DevParams &P, cudaStream_t st) {
-    dim3 block(TX, TY);
-    dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
+    using T = typename CacTile<S>::T;
+    dim3 block(T::TX, T::TY);
+    dim3 grid((P.n[0] + T::TX - 1) / T::TX, (P.n[1] + T::TY - 1) / T::TY);
     cac2d_kernel<S><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, vel, factor, P,
                                             planes2d<S>(pin, pout, P));
     return cudaGetLastError();

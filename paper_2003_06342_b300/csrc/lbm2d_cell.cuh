@@ -401,17 +401,37 @@ __device__ __forceinline__ float phid_cell2d(const S *__restrict__ pin, size_t c
     return fmaf(0.5f, qv, set_sum2d<S>(v, P.set_isc[1]));
 }
 
-// The whole update of one tile.  FAST: the tile and its halo ring lie inside
-// the grid, so no halo cell and no streaming link wraps or meets a wall.
-template <typename S, bool FAST, bool TRT = false>
+// Geometry of a tile of the tiled 2D kernels: TX_ x TY_ cells, one thread
+// each, and a phi window with a one-cell halo ring of RING cells.
+template <int TX_, int TY_> struct Tile2 {
+    static constexpr int TX = TX_, TY = TY_, SX = TX_ + 2, SY = TY_ + 2, NT = TX_ * TY_;
+    static constexpr int RING = 2 * SX + 2 * TY_;
+};
+using Tile2Default = Tile2<TX, TY>;
+
+// window slot (sx, sy) of ring cell r: the top row, the bottom row, then the
+// left and right columns
+template <class T>
+__device__ __forceinline__ void ring_slot(int r, int &sx, int &sy) {
+    if (r < T::SX) { sx = r; sy = 0; }
+    else if (r < 2 * T::SX) { sx = r - T::SX; sy = T::SY - 1; }
+    else if (r < 2 * T::SX + T::TY) { sx = 0; sy = 1 + r - 2 * T::SX; }
+    else { sx = T::SX - 1; sy = 1 + r - 2 * T::SX - T::TY; }
+}
+
+// The whole update of one tile of geometry T (blockDim = T::TX x T::TY).
+// FAST: the tile and its halo ring lie inside the grid, so no halo cell and
+// no streaming link wraps or meets a wall.
+template <typename S, bool FAST, bool TRT = false, class T = Tile2Default>
 __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__restrict__ pout,
                                             float *__restrict__ phi_prev,
                                             const float *__restrict__ q_in,
                                             float *__restrict__ q_out, const DevParams &P,
                                             float *sphi, int x0, int y0, const Planes2d<S> &PL) {
+    constexpr int SXT = T::SX, SYT = T::SY, TXT = T::TX, TYT = T::TY, NT = T::NT, RING = T::RING;
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TXT + tx;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = FAST || ((x < nx) && (y < ny));
     const size_t c = active ? (size_t)y * nx + x : 0;
@@ -419,22 +439,19 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     float f[9], g[9], s[9], phip = 0.0f, qp = 0.0f;
     (void)in_bounds(active ? (long long)c : 0, P.N, P);
     // FAST: the ring cells' g and q come from L2 (the neighbouring tiles load
-    // the same lines).  FP32 requests them before the tile's own values, so
-    // their latency overlaps the own loads; the 16-bit formats after them
-    // (measured: ring first is 3.8% faster for FP32, own first 2.4% / 4.4%
-    // faster for FP16 / BF16)
-    constexpr int RING = 2 * SX + 2 * TY;
+    // the same lines), one ring cell per thread held in registers.  FP32
+    // requests them before the tile's own values, so their latency overlaps
+    // the own loads; the 16-bit formats after them (measured on 32 x 8 tiles:
+    // ring first is 3.8% faster for FP32, own first 2.4% / 4.4% faster for
+    // FP16 / BF16).  Ring cells beyond the block's thread count follow.
     constexpr bool RING_FIRST = !IsNarrow<S>::value;
     float rv[9], rq = 0.0f;
     int rslot = 0;
     auto load_ring = [&]() {
         if (FAST && tid < RING) {
             int sx, sy;
-            if (tid < SX) { sx = tid; sy = 0; }
-            else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
-            else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
-            else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
-            rslot = sy * SX + sx;
+            ring_slot<T>(tid, sx, sy);
+            rslot = sy * SXT + sx;
             const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
             const bool ok = in_bounds((long long)cc, (long long)N, P);
 #pragma unroll
@@ -450,20 +467,28 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
         for (int i = 0; i < 9; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
         phip = phi_prev[c];
         qp = q_in[c];
-        sphi[(ty + 1) * SX + tx + 1] = fmaf(0.5f, qp, set_sum2d<S>(g, P.set_isc[1]));   // phi - phi_ref
+        sphi[(ty + 1) * SXT + tx + 1] = fmaf(0.5f, qp, set_sum2d<S>(g, P.set_isc[1]));   // phi - phi_ref
     }
     if (!RING_FIRST) load_ring();
     if (FAST) {
-        // the 2*SX + 2*TY halo cells, one per thread (same arithmetic as
-        // phid_cell2d)
+        // the ring's halo cells (same arithmetic as phid_cell2d)
         if (tid < RING) sphi[rslot] = fmaf(0.5f, rq, set_sum2d<S>(rv, P.set_isc[1]));
+        if (RING > NT) {
+            for (int r = tid + NT; r < RING; r += NT) {
+                int sx, sy;
+                ring_slot<T>(r, sx, sy);
+                const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
+                const bool ok = in_bounds((long long)cc, (long long)N, P);
+                sphi[sy * SXT + sx] = ok ? phid_cell2d<S>(pin, cc, N, q_in[cc], P) : 0.0f;
+            }
+        }
     } else {
         // halo ring and ragged-tile slots: phi at the (wrapped) neighbour
         // cell, or the wall's Dirichlet value beyond a wall
-        for (int sidx = tid; sidx < SX * SY; sidx += TX * TY) {
-            const int sx = sidx % SX, sy = sidx / SX;
+        for (int sidx = tid; sidx < SXT * SYT; sidx += NT) {
+            const int sx = sidx % SXT, sy = sidx / SXT;
             int cx = x0 + sx - 1, cy = y0 + sy - 1;
-            const bool inner = sx >= 1 && sx <= TX && sy >= 1 && sy <= TY;
+            const bool inner = sx >= 1 && sx <= TXT && sy >= 1 && sy <= TYT;
             if (inner && cx < nx && cy < ny) continue;               // owned by a thread
             if (cx < -1 || cx > nx || cy < -1 || cy > ny) { sphi[sidx] = 0.0f; continue; }
             const int kx = wrap_coord(cx, nx, P.periodic[0]);
@@ -481,23 +506,22 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     __syncthreads();
     if (!active) return;
 
-    cell_update2d<S, FAST, TRT>(sphi + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y, c, pout,
+    cell_update2d<S, FAST, TRT>(sphi + (ty + 1) * SXT + tx + 1, SXT, f, g, s, phip, qp, x, y, c, pout,
                                 phi_prev, q_out, P, PL);
 }
 
 // The update of one tile with the biased gradient: the phi window holds two
-// rings around the 32 x 8 tile ((TY + 4) x (TX + 4) values, formed with
+// rings around the tile ((TY + 4) x (TX + 4) values, formed with
 // plain loads; beyond a wall both ghost layers take the wall's Dirichlet
 // value, periodic axes wrap).  FAST: no streaming link of the tile wraps or
 // meets a wall.
-constexpr int SXB = TX + 4, SYB = TY + 4;
-
-template <typename S, bool FAST, bool TRT>
+template <typename S, bool FAST, bool TRT, class T = Tile2Default>
 __device__ __forceinline__ void step2d_tile_biased(const S *__restrict__ pin, S *__restrict__ pout,
                                                    float *__restrict__ phi_prev,
                                                    const float *__restrict__ q_in,
                                                    float *__restrict__ q_out, const DevParams &P,
                                                    float *sphi, int x0, int y0, const Planes2d<S> &PL) {
+    constexpr int TX = T::TX, TY = T::TY, SXB = TX + 4, SYB = TY + 4;
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
