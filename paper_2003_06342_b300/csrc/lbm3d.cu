@@ -1,7 +1,7 @@
 // 3D kernels: D3Q19 for f and s, D3Q7 for the phase field g (Sec. 3
 // lattices), stencils over the D3Q19 neighbours with factor 1/cs^2 = 3.
 //
-// The step kernel marches each 32x8 (x, y) column tile through a range of z
+// The step kernel marches each 32x4 (x, y) column tile through a range of z
 // planes.  Shared memory holds a rolling window of three planes of
 // phi^n = sum_i gbar_i + q^{n-1}/2 (tile plus a one-cell halo ring): before
 // layer z is updated, plane z+1 is computed; each thread keeps the gbar of
@@ -18,7 +18,7 @@
 namespace lbm {
 
 template <typename S, bool TRT, bool BIASED>
-__global__ void __launch_bounds__(TX * TY, 2)
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
 step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
               const __grid_constant__ Planes3d<S> PL) {

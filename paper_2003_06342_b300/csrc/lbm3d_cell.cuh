@@ -9,7 +9,7 @@ namespace lbm {
 
 using LF = D3Q19L;   // f and s
 using LG = D3Q7L;    // g
-constexpr int TX = 32, TY = 8, SX = TX + 2, SY = TY + 2, PLANE = SX * SY;
+constexpr int TX = 32, TY = 4, SX = TX + 2, SY = TY + 2, PLANE = SX * SY;
 constexpr int ZB = 32;                       // z planes per block
 // window of the biased gradient: two rings around the tile, five planes
 constexpr int SXB = TX + 4, SYB = TY + 4, PLANEB = SXB * SYB;
@@ -193,7 +193,7 @@ __device__ __forceinline__ float phi_at(const S *__restrict__ pin, const float *
     return phid_at<S>(pin, q_in, cc, N, P) + P.g_ref;
 }
 
-// Classes of a 32x8 column tile.  XY_IN: the tile and its halo ring lie
+// Classes of a 32x4 column tile.  XY_IN: the tile and its halo ring lie
 // inside the grid in x and y.  XY_WRAP: the tile lies inside the grid and its
 // ring crosses only periodic x / y boundaries (so every x / y link of its
 // cells lands on a grid cell after the periodic wrap).  XY_GEN: anything
@@ -584,7 +584,7 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     }
 }
 
-// One z-column of a 32x8 tile over layers [blockIdx.z * ZBLK, +ZBLK), every
+// One z-column of a 32x4 tile over layers [blockIdx.z * ZBLK, +ZBLK), every
 // value read with plain loads (see lbm3d.cu).
 template <typename S, int XY, bool TRT = false, int ZBLK = ZB>
 __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__restrict__ pout,

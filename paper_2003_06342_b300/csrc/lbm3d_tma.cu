@@ -1,13 +1,13 @@
 // 3D step with every tile layer staged by bulk tensor copies.
 //
-// Same update as step3d_kernel (lbm3d.cu): each block marches a 32x8 column
+// Same update as step3d_kernel (lbm3d.cu): each block marches a 32x4 column
 // tile through ZBT layers.  One thread issues cp.async.bulk.tensor copies of
 // the tile's layers into shared-memory stages:
-//   f/s stage  (f_i, s_i) pair planes 32 x 8 x 1 x 19 from (x0, y0, L, 0)
+//   f/s stage  (f_i, s_i) pair planes 32 x 4 x 1 x 19 from (x0, y0, L, 0)
 //                                          4D map (x, y, z, pair plane)
-//              phi^{n-1} 32 x 8 x 1    from (x0, y0, L)       3D map (x, y, z)
-//   g stage    g planes 32 x 8 x 1 x 7  from (x0, y0, L, 0)   4D map (x, y, z, g plane)
-//              q^{n-1}  32 x 8 x 1     from (x0, y0, L)
+//              phi^{n-1} 32 x 4 x 1    from (x0, y0, L)       3D map (x, y, z)
+//   g stage    g planes 32 x 4 x 1 x 7  from (x0, y0, L, 0)   4D map (x, y, z, g plane)
+//              q^{n-1}  32 x 4 x 1     from (x0, y0, L)
 // each completing on its own mbarrier (a box row of pairs is two whole
 // 128-byte lines of FP32, or one of 16-bit values).  Two f/s stages and three g stages
 // rotate so that every copy is issued a whole layer before it is needed: while
@@ -288,7 +288,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
 }
 
 template <typename S, bool TRT>
-__global__ void __launch_bounds__(TX * TY, 2)
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
 step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ pin,
                   S *__restrict__ pout, float *__restrict__ phi_prev,
                   const float *__restrict__ q_in, float *__restrict__ q_out, int par, int *err,

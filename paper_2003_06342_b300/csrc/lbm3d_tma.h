@@ -8,16 +8,16 @@
 namespace lbm {
 
 // Tensor maps of the two population buffers as (x, y, z, plane): `fs` over
-// the (f_i, s_i) pair planes (one element = one pair) with a 32 x 8 x 1 x 19
+// the (f_i, s_i) pair planes (one element = one pair) with a 32 x 4 x 1 x 19
 // box (the f and s sets of one tile layer), `g` over the g planes with a
-// 32 x 8 x 1 x 7 box; of the two lagged-source buffers and of phi^{n-1}
-// (32 x 8 x 1 boxes); index = which buffer is read.
+// 32 x 4 x 1 x 7 box; of the two lagged-source buffers and of phi^{n-1}
+// (32 x 4 x 1 boxes); index = which buffer is read.
 struct TmaMaps3d {
     CUtensorMap fs[2], g[2], q[2], pp;
 };
 
 // Row, plane and population-plane strides are multiples of 16 bytes and the
-// grid holds at least one whole 32 x 8 tile.
+// grid holds at least one whole 32 x 4 tile.
 bool tma3d_eligible(const DevParams &P, int elem_bytes);
 // Encode the maps; 0 on success.
 int make_tma_maps3d(TmaMaps3d *M, const DevParams &P, int elem_bytes, void *const pops[2],
