@@ -78,18 +78,23 @@ adj_terminal2d_kernel(const float *__restrict__ st, const float *__restrict__ ta
 // ------------------------------------------------------------------ step A
 // two blocks per SM: 128 registers, no spills (at one block the kernel is
 // latency bound with 8 warps per SM)
-__global__ void __launch_bounds__(256, 2)
+// tile of kernel A: 32 x ADJ_TY cells, one thread each (128 registers, 512
+// threads per SM)
+constexpr int ADJ_TY = 4;
+
+__global__ void __launch_bounds__(32 * ADJ_TY, 16 / ADJ_TY)
 adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_next,
                     float *__restrict__ lam, float *__restrict__ cst, double *dparams,
                     const DevParams P) {
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
-    // one 32x8 tile per block; phi - phi_ref of the tile and its one-cell ring
-    // in shared memory (each window value formed once, not once per neighbour)
-    constexpr int WX = 34, WY = 10;
+    // one 32 x ADJ_TY tile per block; phi - phi_ref of the tile and its
+    // one-cell ring in shared memory (each window value formed once, not once
+    // per neighbour)
+    constexpr int WX = 34, WY = ADJ_TY + 2;
     __shared__ float sphi[WX * WY];
     const int tiles_x = (nx + 31) / 32;
-    const int x0 = (int)(blockIdx.x % tiles_x) * 32, y0 = (int)(blockIdx.x / tiles_x) * 8;
+    const int x0 = (int)(blockIdx.x % tiles_x) * 32, y0 = (int)(blockIdx.x / tiles_x) * ADJ_TY;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < nx && y < ny;
@@ -506,9 +511,9 @@ cudaError_t launch_adj_terminal2d(const float *st, const float *target, float *a
 
 cudaError_t launch_adj_step2d(const float *st, const float *lam_next, float *lam, float *cst,
                               double *dparams, const DevParams &P, cudaStream_t stream) {
-    const int tiles = ((P.n[0] + 31) / 32) * ((P.n[1] + 7) / 8);
+    const int tiles = ((P.n[0] + 31) / 32) * ((P.n[1] + ADJ_TY - 1) / ADJ_TY);
     const int nb = (int)((P.N + 255) / 256);
-    adj_step2d_a_kernel<<<tiles, 256, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
+    adj_step2d_a_kernel<<<tiles, 32 * ADJ_TY, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
     adj_step2d_b_kernel<<<nb, 256, 0, stream>>>(cst, lam, P);
     return cudaGetLastError();
 }
