@@ -125,7 +125,8 @@ typedef struct {
  * velocity field imposed with lbm_set_velocity -- the setting of the CAC
  * validations of Sec. 4.1; the flow and temperature populations are not
  * stepped, lbm_get_fields returns phi (u, p and T are not meaningful) and
- * source_on must be 0.  2D only. */
+ * source_on must be 0.  2D (D2Q9) and 3D (the D3Q7 phase-field lattice of
+ * the coupled model, on the tiled kernel). */
 #define LBM_MODEL_COUPLED      0
 #define LBM_MODEL_PHASE_FIELD  1
 
@@ -297,8 +298,8 @@ int lbm_adjoint_steps(lbm_handle *h, const void *states, size_t stride, int32_t 
 int lbm_adjoint_init(lbm_handle *h, const lbm_fields *init, const void *adj0, float *dT0,
                      double *d_dparams);
 
-/* LBM_MODEL_PHASE_FIELD: the imposed velocity u(x) (ux, uy of `u`, same
- * layout and pointer rules as lbm_init) and its time factor: the velocity at
+/* LBM_MODEL_PHASE_FIELD: the imposed velocity u(x) (ux, uy and in 3D uz of
+ * `u`, same layout and pointer rules as lbm_init) and its time factor: the velocity at
  * step n is u(x) cos(pi n / period) when period > 0 (the reversing vortex of
  * Sec. 4.1 uses period = 2 T_f), u(x) otherwise, with n counted from
  * lbm_init or lbm_set_state (the saved state holds no step count, so a

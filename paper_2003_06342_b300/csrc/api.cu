@@ -85,10 +85,7 @@ int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
         return LBM_EINVAL;
     if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16) return LBM_EINVAL;
     if (p->model != LBM_MODEL_COUPLED && p->model != LBM_MODEL_PHASE_FIELD) return LBM_EINVAL;
-    if (p->model == LBM_MODEL_PHASE_FIELD) {
-        if (p->source_on) return LBM_EINVAL;          // no phase change in this model
-        if (dim != 2) return LBM_EUNSUPPORTED;
-    }
+    if (p->model == LBM_MODEL_PHASE_FIELD && p->source_on) return LBM_EINVAL;   // no phase change
     if (p->collision != LBM_COLLISION_BGK && p->collision != LBM_COLLISION_TRT) return LBM_EINVAL;
     if (p->grad_scheme != LBM_GRAD_CENTRAL && p->grad_scheme != LBM_GRAD_BIASED2) return LBM_EINVAL;
     if (p->grad_scheme == LBM_GRAD_BIASED2 && p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
@@ -221,10 +218,20 @@ int do_step(lbm_handle *h) {
     if (h->params.model == LBM_MODEL_PHASE_FIELD) {
         const double n = (double)h->steps;
         const float factor = h->vel_period > 0.0 ? (float)std::cos(M_PI * n / h->vel_period) : 1.0f;
-        switch (h->params.storage) {
-        case LBM_STORE_FP32: e = launch_cac2d<float>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
-        case LBM_STORE_FP16: e = launch_cac2d<__half>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
-        default: e = launch_cac2d<__nv_bfloat16>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
+        if (h->dim == 2) {
+            switch (h->params.storage) {
+            case LBM_STORE_FP32: e = launch_cac2d<float>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
+            case LBM_STORE_FP16: e = launch_cac2d<__half>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
+            default: e = launch_cac2d<__nv_bfloat16>(h->pops[h->cur], h->pops[nxt], h->vel, factor, h->dp, h->stream); break;
+            }
+        } else {
+            // the lagged-source buffers hold zeros in this model
+            const float *qz = h->q[h->cur];
+            switch (h->params.storage) {
+            case LBM_STORE_FP32: e = launch_cac3d<float>(h->pops[h->cur], h->pops[nxt], qz, h->vel, factor, h->dp, h->stream); break;
+            case LBM_STORE_FP16: e = launch_cac3d<__half>(h->pops[h->cur], h->pops[nxt], qz, h->vel, factor, h->dp, h->stream); break;
+            default: e = launch_cac3d<__nv_bfloat16>(h->pops[h->cur], h->pops[nxt], qz, h->vel, factor, h->dp, h->stream); break;
+            }
         }
         if (e != cudaSuccess) return LBM_ECUDA;
         h->cur = nxt;
@@ -422,6 +429,19 @@ int lbm_set_stream(lbm_handle *h, void *stream) {
     return LBM_OK;
 }
 
+// The phase-field-only kernels write the g planes alone: copy the current
+// population buffer into the other one, so that the flow and temperature
+// planes read after an odd number of steps hold the initial values (finite
+// moments, reductions and state checks) instead of whatever the workspace
+// held.
+static int mirror_unstepped(lbm_handle *h) {
+    const size_t bytes = (size_t)h->Qtot * h->N * h->elem;
+    if (cudaMemcpyAsync(h->pops[h->cur ^ 1], h->pops[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream) !=
+        cudaSuccess)
+        return LBM_ECUDA;
+    return LBM_OK;
+}
+
 int lbm_init(lbm_handle *h, const lbm_fields *in) {
     if (!h || !in || !in->phi || !in->T) return LBM_EINVAL;
     const float *phi0, *T0, *p0, *u0[3] = {nullptr, nullptr, nullptr};
@@ -436,6 +456,7 @@ int lbm_init(lbm_handle *h, const lbm_fields *in) {
         // the populations start from the imposed velocity (factor 1 at n = 0)
         u0[0] = h->vel_set ? h->vel : nullptr;
         u0[1] = h->vel_set ? h->vel + h->N : nullptr;
+        if (h->dim == 3) u0[2] = h->vel_set ? h->vel + 2 * h->N : nullptr;
     }
     h->cur = 0;
     h->steps = 0;
@@ -446,7 +467,9 @@ int lbm_init(lbm_handle *h, const lbm_fields *in) {
     if (h->params.model == LBM_MODEL_PHASE_FIELD &&
         cudaMemsetAsync(h->q[1], 0, h->N * sizeof(float), h->stream) != cudaSuccess)
         return LBM_ECUDA;
-    return do_init(h, phi0, T0, u0, p0);
+    const int r0 = do_init(h, phi0, T0, u0, p0);
+    if (r0 != LBM_OK || h->params.model != LBM_MODEL_PHASE_FIELD) return r0;
+    return mirror_unstepped(h);
 }
 
 // the periodic state check after a step, when one is due
@@ -604,9 +627,12 @@ int lbm_set_state(lbm_handle *h, const void *src, size_t bytes, int32_t on_devic
     if (!h) return LBM_EINVAL;
     const int r = copy_state(h, const_cast<void *>(src), bytes, on_device, false);
     if (r != LBM_OK) return r;
-    if (h->params.model == LBM_MODEL_PHASE_FIELD &&
-        cudaMemsetAsync(h->q[h->cur ^ 1], 0, h->N * sizeof(float), h->stream) != cudaSuccess)
-        return LBM_ECUDA;
+    if (h->params.model == LBM_MODEL_PHASE_FIELD) {
+        if (cudaMemsetAsync(h->q[h->cur ^ 1], 0, h->N * sizeof(float), h->stream) != cudaSuccess)
+            return LBM_ECUDA;
+        const int rm = mirror_unstepped(h);
+        if (rm != LBM_OK) return rm;
+    }
     h->steps = 0;
     if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return LBM_ECUDA;
     h->err_ready = 1;
@@ -667,9 +693,10 @@ int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
     if (!h || !kernel) return LBM_EINVAL;
     if (h->dim == 3 && h->kernel_choice == LBM_KERNEL_AUTO && h->tma_state == 0)
         setup_tma(const_cast<lbm_handle *>(h));
-    const bool tma = h->kernel_choice == LBM_KERNEL_TMA ||
-                     (h->dim == 3 && h->kernel_choice == LBM_KERNEL_AUTO &&
-                      h->params.grad_scheme == LBM_GRAD_CENTRAL);
+    const bool tma = h->params.model == LBM_MODEL_COUPLED &&
+                     (h->kernel_choice == LBM_KERNEL_TMA ||
+                      (h->dim == 3 && h->kernel_choice == LBM_KERNEL_AUTO &&
+                       h->params.grad_scheme == LBM_GRAD_CENTRAL));
     if (tma && h->tma_state == 1) *kernel = LBM_KERNEL_TMA;
     else *kernel = LBM_KERNEL_TILED;
     return LBM_OK;
@@ -711,10 +738,10 @@ int lbm_adjoint_step(lbm_handle *h, const void *state, const void *adj_next, voi
 }
 
 int lbm_set_velocity(lbm_handle *h, const lbm_fields *u, double period) {
-    if (!h || !u || !u->ux || (h->dim >= 2 && !u->uy)) return LBM_EINVAL;
+    if (!h || !u || !u->ux || !u->uy || (h->dim == 3 && !u->uz)) return LBM_EINVAL;
     if (h->params.model != LBM_MODEL_PHASE_FIELD) return LBM_EUNSUPPORTED;
     if (!std::isfinite(period) || period < 0.0) return LBM_EINVAL;
-    const void *src[2] = {u->ux, u->uy};
+    const void *src[3] = {u->ux, u->uy, u->uz};
     for (int a = 0; a < h->dim; ++a) {
         const float *dev;
         const int r = stage_in(h, src[a], u->on_device, u->dtype, a, &dev);

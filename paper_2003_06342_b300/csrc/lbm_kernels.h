@@ -44,6 +44,12 @@ template <typename S>
 cudaError_t launch_cac2d(const void *pin, void *pout, const float *vel, float factor,
                          const DevParams &P, cudaStream_t st);
 
+// 3D phase field alone (cac3d.cu): vel holds ux, uy, uz (N floats each);
+// q_zero is a lagged-source buffer of zeros (no phase change)
+template <typename S>
+cudaError_t launch_cac3d(const void *pin, void *pout, const float *q_zero, const float *vel, float factor,
+                         const DevParams &P, cudaStream_t st);
+
 // periodic state check (health.cu): bit 4 of *err when phi leaves
 // [1/2 - excess, 1/2 + excess] or phi / the lagged source is not finite
 template <typename S>

@@ -213,8 +213,12 @@ def test_phase_field_model_validation():
     g3 = B.lbm_grid()
     g3.nx, g3.ny, g3.nz = 8, 8, 8
     g3.periodic[:] = [1, 1, 1]
+    size3, size3c = ctypes.c_size_t(), ctypes.c_size_t()
     assert B.lib.lbm_workspace_bytes(ctypes.byref(g3), B.LBM_D3Q19_D3Q7, ctypes.byref(p),
-                                     ctypes.byref(size_c)) == B.LBM_EUNSUPPORTED
+                                     ctypes.byref(size3)) == B.LBM_OK
+    assert B.lib.lbm_workspace_bytes(ctypes.byref(g3), B.LBM_D3Q19_D3Q7, ctypes.byref(pc),
+                                     ctypes.byref(size3c)) == B.LBM_OK
+    assert size3.value >= size3c.value + 3 * 8 * 8 * 8 * 4          # three velocity planes
     # lbm_set_velocity belongs to the phase-field model only
     buf = (ctypes.c_uint8 * (size.value + 512))()
     base = (ctypes.addressof(buf) + 255) // 256 * 256

@@ -128,3 +128,83 @@ def test_odd_step_counts_read_a_zero_lagged_source():
     s.set_state(snap)
     s.step(1)
     assert np.isfinite(_phi(s)).all()
+
+
+def _extruded_vortex(n, nz, speed):
+    """The 2D vortex disk repeated along a thin periodic z axis (the thin 3D
+    domain of the paper's CAC tests), uz = 0."""
+    w = W.vortex_disk(n=n)
+    phi0 = np.repeat(w.phi0[None], nz, axis=0)
+    u = [np.repeat(uu[None] * speed, nz, axis=0) for uu in w.extra["u"]] + [np.zeros_like(phi0)]
+    return w.params, (n, n, nz), (True, True, True), phi0, u
+
+
+def _sphere_in_rotation(nx, ny, nz, speed):
+    """A sphere in a solid-body rotation about a tilted axis, walls on z
+    (phi = 0 beyond both), so every velocity component and the wall links are
+    exercised."""
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    c = np.array([nx / 2.0, ny / 2.0, nz / 2.0])
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    phi0 = 0.5 * (1.0 + np.tanh(2.0 * (min(nx, ny, nz) * 0.3 - r) / 6.0))
+    axis = np.array([0.3, 0.4, 1.0]) / np.linalg.norm([0.3, 0.4, 1.0])
+    d = np.stack([x - c[0], y - c[1], z - c[2]])
+    u = [speed * (axis[1] * d[2] - axis[2] * d[1]), speed * (axis[2] * d[0] - axis[0] * d[2]),
+         speed * (axis[0] * d[1] - axis[1] * d[0])]
+    params = dict(W.cac_params(), phi_wall=(0.0, 0.0))
+    return params, (nx, ny, nz), (True, True, False), phi0, u
+
+
+CASES_3D = [
+    ("vortex_thin_z", lambda: _extruded_vortex(41, 4, 5.0), 30.0, 30),
+    ("sphere_walls_z", lambda: _sphere_in_rotation(37, 21, 18, 2e-3), 0.0, 30),
+]
+
+
+@pytest.mark.parametrize("name,make,period,steps", CASES_3D, ids=[c[0] for c in CASES_3D])
+def test_phase_field_model_3d_matches_oracle(name, make, period, steps):
+    from paper_2003_06342_b300 import Solver
+    params, n, periodic, phi0, u = make()
+    P, G = M.Params.from_dict(params), M.Grid(n, periodic)
+    ref = C.phase_field(C.run(C.init_state(phi0, u, P, G, period), u, P, G, steps, period)).numpy()
+    s = Solver(n, periodic, params)
+    s.set_velocity(u, period)
+    s.init(phi0, np.ones_like(phi0))
+    assert s.kernel() == "tiled"
+    s.step(steps)
+    err = np.abs(_phi(s) - ref).max()
+    print(name, "max |phi - oracle|", err)
+    assert err < TOL
+    if all(periodic):
+        m0, _ = s.reduce()
+        assert abs(m0 - float(phi0.sum())) <= 2e-5 * float(phi0.sum())
+
+
+def test_phase_field_model_3d_16bit():
+    from paper_2003_06342_b300 import Solver
+    params, n, periodic, phi0, u = _sphere_in_rotation(37, 21, 18, 2e-3)
+    out = {}
+    for storage in ("fp32", "fp16"):
+        s = Solver(n, periodic, params, storage=storage)
+        s.set_velocity(u, 0.0)
+        s.init(phi0, np.ones_like(phi0))
+        s.step(40)
+        out[storage] = _phi(s)
+    assert np.abs(out["fp32"] - out["fp16"]).max() < 5e-3
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_unstepped_planes_stay_defined(storage):
+    """The phase-field kernels write only the g planes; after an odd number of
+    steps the moments read the other buffer's flow and temperature planes,
+    which hold the initial values (not the NaN the workspace held before), so
+    the FP64 sums and the state check stay finite."""
+    w = W.vortex_disk(n=41)
+    junk = torch.full((64 << 20,), float("nan"), device="cuda")
+    del junk
+    s = _solver(w, storage=storage, period=0.0)
+    s.set_health_check(1, 0.6)
+    s.step(3)
+    mass, energy = s.reduce()
+    assert np.isfinite(mass) and np.isfinite(energy)
+    s.sync()
