@@ -250,6 +250,7 @@ def run_device(args, world, rank, local):
     result = {
         "ms": ms, "wall_s": wall, "launches": launches, "cells": w.cells, "mass": mass,
         "energy": energy, "clocks": clk.summary(), "peak": peak, "peak_kind": peak_kind,
+        "device": {"gpu": torch.cuda.get_device_name(dev), "host_cores": os.cpu_count()},
     }
 
     # roofline of the dominant kernel: step launches alone, same stream
@@ -671,6 +672,7 @@ def main():
                      "kernel": "step2d_kernel<float>", "bytes_per_cell": bpc,
                      "step_ms": r["step_ms"], "peak_kind": r["peak_kind"]},
         "clocks": r["clocks"],
+        "device": r["device"],
         "gpu_launches": r["launches"],
         "finite": r["finite"],
         "variants": r["variants"],
