@@ -94,6 +94,7 @@ class Params:
     collision: str = "bgk"            # "bgk": Eq. LBE; "trt": two relaxation rates
     grad_scheme: str = "central"      # Eq. DerivDirec_Grad; "biased2": second-order biased
     trt_magic: tuple = (0.25, 0.25, 0.25)   # Lambda of the f, g, s sets (TRT only)
+    mrt_rates: tuple = (1.4, 1.4, 1.2)      # s_e, s_eps, s_q of the flow set (MRT only)
 
     @classmethod
     def from_dict(cls, d):
@@ -107,7 +108,9 @@ class Params:
         if "grad_scheme" in keys and not isinstance(keys["grad_scheme"], str):
             keys["grad_scheme"] = "biased2" if keys["grad_scheme"] else "central"
         if "collision" in keys and not isinstance(keys["collision"], str):
-            keys["collision"] = "trt" if keys["collision"] else "bgk"
+            keys["collision"] = {0: "bgk", 1: "trt", 2: "mrt"}[int(keys["collision"])]
+        if "mrt_rates" in keys:
+            keys["mrt_rates"] = tuple(float(v) for v in keys["mrt_rates"])
         if "trt_magic" in keys:
             keys["trt_magic"] = tuple(float(v) for v in keys["trt_magic"])
         for k in ("gravity", "body_force", "phi_wall", "T_wall"):
@@ -420,6 +423,44 @@ def _relax_trt(pops, eq_bar, S, tau, magic, lat, transport_odd):
     return out
 
 
+def mrt_basis(lat):
+    """Moment basis of the D2Q9 multiple-relaxation-time collision, built from
+    the lattice vectors (rows: rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy):
+    e = 3|c|^2 - 4, eps = 4 - 21|c|^2/2 + 9|c|^4/2, q_a = (3|c|^2 - 5) c_a,
+    p_xx = c_x^2 - c_y^2, p_xy = c_x c_y.  The rows are orthogonal."""
+    rows = []
+    for i in range(lat.Q):
+        cx, cy = float(lat.e[i][0]), float(lat.e[i][1])
+        c2 = cx * cx + cy * cy
+        rows.append([1.0, 3.0 * c2 - 4.0, 4.0 - 10.5 * c2 + 4.5 * c2 * c2, cx, (3.0 * c2 - 5.0) * cx,
+                     cy, (3.0 * c2 - 5.0) * cy, cx * cx - cy * cy, cx * cy])
+    return torch.tensor(rows, dtype=F64).T          # (moment, direction)
+
+
+def _relax_mrt(pops, eq_bar, S, tau, rates, lat):
+    """Multiple-relaxation-time collision of the flow set (the "next" MRT
+    row; not in the paper): with d = theta - eq_bar in moment space m = M d,
+    theta*_i = theta_i - (M^-1 diag(s) M d)_i + S_i.  The conserved moments
+    and the stress moments relax with the BGK rate 1/(tau + 1/2) (the
+    viscosity), e and eps with s_e and s_eps, and the odd moments j and q
+    with s_q; with every rate equal to the BGK rate this is Eq. LBE, and with
+    s_e = s_eps = 1/(tau + 1/2) it is the TRT collision whose antisymmetric
+    rate is s_q."""
+    Mb = mrt_basis(lat)
+    om = 1.0 / (tau + 0.5)
+    s_e, s_eps, s_q = rates
+    d = torch.stack([pops[i] - eq_bar[i] for i in range(lat.Q)])          # (Q, *grid)
+    m = torch.tensordot(Mb, d, dims=1)                                    # (9, *grid)
+    norms = (Mb * Mb).sum(dim=1)
+    shape = (-1,) + (1,) * (m.dim() - 1)
+    om_t = om if torch.is_tensor(om) else torch.full_like(m[0], om)
+    s = [om_t, torch.full_like(om_t, s_e), torch.full_like(om_t, s_eps), torch.full_like(om_t, s_q),
+         torch.full_like(om_t, s_q), torch.full_like(om_t, s_q), torch.full_like(om_t, s_q), om_t, om_t]
+    relaxed = torch.stack([s[k] * m[k] for k in range(9)]) / norms.reshape(shape)
+    r = torch.tensordot(Mb.T, relaxed, dims=1)                            # M^-1 = M^T diag(1/norms)
+    return [pops[i] - r[i] + S[i] for i in range(lat.Q)]
+
+
 def collide(st, M, q, P, grid):
     """Post-collision populations of the three sets at time n."""
     Lf, Lg, _ = lattices_for(grid.dim)
@@ -442,7 +483,13 @@ def collide(st, M, q, P, grid):
     f_bar = [f_eq[i] - 0.5 * f_S[i] for i in range(Lf.Q)]
     s_eq, s_S, tau_s = E["s"]
     s_bar = [s_eq[i] - 0.5 * s_S[i] for i in range(Lf.Q)]
-    if P.collision == "trt":
+    if P.collision == "mrt":
+        if grid.dim != 2:
+            raise ValueError("the MRT collision is defined for D2Q9")
+        f_out = _relax_mrt(st["f"], f_bar, f_S, tau_f, P.mrt_rates, Lf)
+        g_out = [_relax(st["g"][i], g_bar[i], g_src[i], tau_g) for i in range(Lg.Q)]
+        s_out = [_relax(st["s"][i], s_bar[i], s_S[i], tau_s) for i in range(Lf.Q)]
+    elif P.collision == "trt":
         mf, mg, ms = P.trt_magic
         f_out = _relax_trt(st["f"], f_bar, f_S, tau_f, mf, Lf, transport_odd=False)
         g_out = _relax_trt(st["g"], g_bar, g_src, tau_g, mg, Lg, transport_odd=True)

@@ -1,0 +1,65 @@
+"""Pins of the oracle's multiple-relaxation-time collision of the flow set
+(collision = "mrt", D2Q9), each against something other than the MRT code:
+
+* with every rate equal to the BGK rate it is the BGK step of Eq. LBE;
+* with s_e = s_eps = the BGK rate and s_q the TRT antisymmetric rate of a
+  magic parameter Lambda it is the TRT step (a different code path);
+* with s_q = 8 (2 - s_nu)/(8 - s_nu) (Lambda = 3/16) the steady Poiseuille
+  profile between half-way bounce-back walls is the exact parabola, also
+  with s_e and s_eps away from the BGK rate, while BGK is off by percents."""
+import numpy as np
+
+import workloads as W
+from oracle import model as M
+
+
+def _droplet_fields(**over):
+    w = W.droplet_2d(24, 6.0, T_offset=0.04, T_noise=0.01, corr_len=4.0)
+    base = dict(w.params, nu_l=0.1, nu_g=0.1, alpha_l=0.05, alpha_g=0.05)
+    base.update(over)
+    P, G = M.Params.from_dict(base), M.Grid(w.n, w.periodic)
+    return M.fields(M.run(M.init_state(w.phi0, w.T0, P, G), P, G, 12), P, G)
+
+
+def _close(a, b, tol=1e-13):
+    return all(float((a[k] - b[k]).abs().max()) < tol for k in ("phi", "T", "p"))
+
+
+def test_mrt_with_equal_rates_is_bgk():
+    om = 1.0 / (0.1 * 3.0 + 0.5)
+    bgk = _droplet_fields(collision="bgk")
+    mrt = _droplet_fields(collision="mrt", mrt_rates=(om, om, om))
+    assert _close(bgk, mrt)
+    other = _droplet_fields(collision="mrt", mrt_rates=(1.1, 1.3, 1.2))
+    assert float((other["phi"] - bgk["phi"]).abs().max()) > 1e-9
+
+
+def test_mrt_reduces_to_trt():
+    cs2 = 1.0 / 3.0
+    tau_f, tau_g, tau_s = 0.1 / cs2, 0.08 / cs2, 0.05 / cs2
+    lam = 0.3
+    om = 1.0 / (tau_f + 0.5)
+    s_q = 1.0 / (lam / tau_f + 0.5)
+    trt = _droplet_fields(collision="trt", M_phi=0.08, trt_magic=(lam, tau_g * tau_g, tau_s * tau_s))
+    mrt = _droplet_fields(collision="mrt", M_phi=0.08, mrt_rates=(om, om, s_q))
+    assert _close(trt, mrt)
+
+
+def _poiseuille(collision, rates, nu=0.5, H=8, G=1e-5, steps=1500):
+    params = W.base_params(rho_l=1.0, rho_g=1.0, nu_l=nu, nu_g=nu, alpha_l=0.05, alpha_g=0.05,
+                           sigma=0.0, gravity=(0.0, 0.0, 0.0), body_force=(G, 0.0, 0.0), source_on=0,
+                           phi_wall=(0.0, 0.0), T_wall=(1.0, 1.0), collision=collision, mrt_rates=rates)
+    P, Gd = M.Params.from_dict(params), M.Grid((2, H), (True, False))
+    st = M.run(M.init_state(np.zeros((H, 2)), np.ones((H, 2)), P, Gd), P, Gd, steps)
+    u = M.fields(st, P, Gd)["u"][0][:, 0].numpy()
+    y = np.arange(H)
+    exact = G / (2 * nu) * (y + 0.5) * (H - 0.5 - y)
+    return float(np.abs(u - exact).max() / exact.max())
+
+
+def test_mrt_magic_rate_gives_the_exact_poiseuille_profile():
+    s_nu = 1.0 / (0.5 * 3.0 + 0.5)
+    s_q = 8.0 * (2.0 - s_nu) / (8.0 - s_nu)
+    assert _poiseuille("mrt", (1.1, 1.3, s_q)) < 1e-10
+    assert _poiseuille("mrt", (1.1, 1.3, 1.9)) > 1e-3
+    assert _poiseuille("bgk", (1.0, 1.0, 1.0)) > 1e-2
