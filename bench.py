@@ -297,6 +297,20 @@ def run_device(args, world, rank, local):
                 "bytes_per_cell": bpc, "achieved_GBs": bpc * w.cells / ms_v / 1e6,
                 "frac": bpc * w.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v))}
             del v
+        # the multiple-relaxation-time collision of the flow set on the same 2D workload
+        wm = dict(w.params, collision="mrt", mrt_rates=(1.4, 1.4, 1.2))
+        for storage in ("fp32", "fp16"):
+            v = Solver(w.n, w.periodic, wm, storage=storage, device=dev, stream=stream)
+            v.init(w.phi0, w.T0, p0=w.p0)
+            v.step(20)
+            ms_v = step_kernel_ms(v, 500)
+            m_v = safe_reduce(v)
+            bpc = BYTES_PER_CELL[("2d", storage)]
+            variants[f"2d_{storage}_mrt"] = {
+                "workload": w.name + ", MRT collision of the flow set", "MLUPS": w.cells / ms_v / 1e3,
+                "ms_per_step": ms_v, "bytes_per_cell": bpc, "achieved_GBs": bpc * w.cells / ms_v / 1e6,
+                "frac": bpc * w.cells / ms_v / 1e6 / peak, "finite": bool(np.isfinite(m_v))}
+            del v
         # the second-order biased gradient option (two-ring phi window)
         wb = dict(w.params, grad_scheme="biased2")
         v = Solver(w.n, w.periodic, wb, storage="fp32", device=dev, stream=stream)

@@ -63,7 +63,7 @@ class lbm_params(ctypes.Structure):
         ("source_on", ctypes.c_int32), ("visc_interp", ctypes.c_int32),
         ("alpha_interp", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("model", ctypes.c_int32), ("collision", ctypes.c_int32), ("grad_scheme", ctypes.c_int32),
-        ("trt_magic", ctypes.c_double * 3),
+        ("trt_magic", ctypes.c_double * 3), ("mrt_rates", ctypes.c_double * 3),
     ]
 
 

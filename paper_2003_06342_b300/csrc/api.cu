@@ -86,13 +86,20 @@ int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
     if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16) return LBM_EINVAL;
     if (p->model != LBM_MODEL_COUPLED && p->model != LBM_MODEL_PHASE_FIELD) return LBM_EINVAL;
     if (p->model == LBM_MODEL_PHASE_FIELD && p->source_on) return LBM_EINVAL;   // no phase change
-    if (p->collision != LBM_COLLISION_BGK && p->collision != LBM_COLLISION_TRT) return LBM_EINVAL;
+    if (p->collision != LBM_COLLISION_BGK && p->collision != LBM_COLLISION_TRT &&
+        p->collision != LBM_COLLISION_MRT)
+        return LBM_EINVAL;
     if (p->grad_scheme != LBM_GRAD_CENTRAL && p->grad_scheme != LBM_GRAD_BIASED2) return LBM_EINVAL;
     if (p->grad_scheme == LBM_GRAD_BIASED2 && p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
     if (p->collision == LBM_COLLISION_TRT) {
         for (int s = 0; s < 3; ++s)
             if (!(p->trt_magic[s] > 0.0 && std::isfinite(p->trt_magic[s]))) return LBM_EINVAL;
         if (p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
+    }
+    if (p->collision == LBM_COLLISION_MRT) {
+        for (int k = 0; k < 3; ++k)
+            if (!(p->mrt_rates[k] > 0.0 && p->mrt_rates[k] < 2.0)) return LBM_EINVAL;
+        if (dim != 2 || p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
     }
     const double vals[] = {p->rho_l, p->rho_g, p->nu_l, p->nu_g, p->alpha_l, p->alpha_g, p->sigma,
                            p->W, p->M_phi, p->A, p->theta_I, p->L, p->Cp, p->T_sat,
@@ -165,8 +172,10 @@ void fill_devparams(lbm_handle *h) {
 #endif
     d.Cp_over_L2 = (float)(p.Cp / (p.L * p.L));
     d.opts = (p.collision == LBM_COLLISION_TRT ? OPT_TRT : 0) |
+             (p.collision == LBM_COLLISION_MRT ? OPT_MRT : 0) |
              (p.grad_scheme == LBM_GRAD_BIASED2 ? OPT_BIASED : 0);
     for (int s = 0; s < 3; ++s) d.trt_magic[s] = (float)p.trt_magic[s];
+    for (int k = 0; k < 3; ++k) d.mrt_rates[k] = (float)p.mrt_rates[k];
     // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
     int k = 0;
     for (int set = 0; set < 3; ++set) {

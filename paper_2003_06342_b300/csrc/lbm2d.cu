@@ -18,8 +18,9 @@
 //      variables (Eq. LBE with Eqs. Feq_NS_Incompr, Forcing, MicroProduction,
 //      Geq_Allen-Cahn_Eq, SourceTerm_AllenCahn, Seq_Temp,
 //      Def_SourceTerms_Temp), or their two-relaxation-time form (TRT
-//      instantiation), with the central or the biased gradient (BIASED
-//      instantiation, a two-ring phi window);
+//      instantiation), or the multiple-relaxation-time collision of the
+//      flow set with BGK for g and s (MRT instantiation), with the central
+//      or the biased gradient (BIASED instantiation, a two-ring phi window);
 //      The temperature set is advanced as deviations sbar_i - w_i T_ref
 //      (the stored form), which keeps FP32 rounding relative to T - T_ref
 //      rather than to T;
@@ -41,7 +42,7 @@ namespace lbm {
 template <typename S, bool BIASED> struct StepTile { using T = Tile2<64, 4>; };
 template <> struct StepTile<float, false> { using T = Tile2<32, 4>; };
 
-template <typename S, bool TRT, bool BIASED>
+template <typename S, int COLL, bool BIASED>
 __global__ void __launch_bounds__(StepTile<S, BIASED>::T::NT, 1024 / StepTile<S, BIASED>::T::NT)
 step2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
@@ -51,21 +52,21 @@ step2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
     const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
     const bool fast = x0 >= 1 && x0 + T::TX + 1 <= P.n[0] && y0 >= 1 && y0 + T::TY + 1 <= P.n[1];
     if (BIASED) {
-        if (fast) step2d_tile_biased<S, true, TRT, T>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
-        else step2d_tile_biased<S, false, TRT, T>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+        if (fast) step2d_tile_biased<S, true, COLL, T>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+        else step2d_tile_biased<S, false, COLL, T>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
     } else {
-        if (fast) step2d_tile<S, true, TRT, T>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
-        else step2d_tile<S, false, TRT, T>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+        if (fast) step2d_tile<S, true, COLL, T>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
+        else step2d_tile<S, false, COLL, T>(pin, pout, phi_prev, q_in, q_out, P, sphi, x0, y0, PL);
     }
 }
 
-template <typename S, bool TRT, bool BIASED>
+template <typename S, int COLL, bool BIASED>
 static void launch_step2d_one(const S *in, S *out, float *phi_prev, const float *q_in, float *q_out,
                               const DevParams &P, const Planes2d<S> &PL, cudaStream_t st) {
     using T = typename StepTile<S, BIASED>::T;
     const dim3 block(T::TX, T::TY);
     const dim3 grid((P.n[0] + T::TX - 1) / T::TX, (P.n[1] + T::TY - 1) / T::TY);
-    step2d_kernel<S, TRT, BIASED><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL);
+    step2d_kernel<S, COLL, BIASED><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL);
 }
 
 // ------------------------------------------------------------------ phi moment
@@ -224,16 +225,23 @@ __global__ void streammap2d_kernel(int32_t *src, int8_t *kind, const DevParams P
 template <typename S>
 cudaError_t launch_step2d(const void *pin, void *pout, float *phi_prev, const float *q_in,
                           float *q_out, const DevParams &P, cudaStream_t st) {
-    // the TRT collision and the biased gradient are separate instantiations,
+    // the TRT and MRT collisions and the biased gradient are separate instantiations,
     // so the default kernel keeps its register allocation
     const S *in = (const S *)pin;
     S *out = (S *)pout;
     const Planes2d<S> PL = planes2d<S>(pin, pout, P);
-    switch (P.opts & (OPT_TRT | OPT_BIASED)) {
-    case 0: launch_step2d_one<S, false, false>(in, out, phi_prev, q_in, q_out, P, PL, st); break;
-    case OPT_TRT: launch_step2d_one<S, true, false>(in, out, phi_prev, q_in, q_out, P, PL, st); break;
-    case OPT_BIASED: launch_step2d_one<S, false, true>(in, out, phi_prev, q_in, q_out, P, PL, st); break;
-    default: launch_step2d_one<S, true, true>(in, out, phi_prev, q_in, q_out, P, PL, st); break;
+    switch (P.opts & (OPT_TRT | OPT_MRT | OPT_BIASED)) {
+    case 0: launch_step2d_one<S, COLL_BGK, false>(in, out, phi_prev, q_in, q_out, P, PL, st); break;
+    case OPT_TRT: launch_step2d_one<S, COLL_TRT, false>(in, out, phi_prev, q_in, q_out, P, PL, st); break;
+    case OPT_MRT: launch_step2d_one<S, COLL_MRT, false>(in, out, phi_prev, q_in, q_out, P, PL, st); break;
+    case OPT_BIASED: launch_step2d_one<S, COLL_BGK, true>(in, out, phi_prev, q_in, q_out, P, PL, st); break;
+    case OPT_TRT | OPT_BIASED:
+        launch_step2d_one<S, COLL_TRT, true>(in, out, phi_prev, q_in, q_out, P, PL, st);
+        break;
+    case OPT_MRT | OPT_BIASED:
+        launch_step2d_one<S, COLL_MRT, true>(in, out, phi_prev, q_in, q_out, P, PL, st);
+        break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

@@ -225,17 +225,25 @@ struct Coef2 {
 // working representation: stencils, closures, moments, production rate, the
 // three collisions and the push into pout.  FAST: no link of the cell wraps or
 // meets a wall.
-// TRT: the BGK relaxation (1 - om) v_i becomes
+// COLL selects the collision of Eq. LBE (COLL_BGK) or one of two extensions
+// outside the paper.  COLL_TRT: the BGK relaxation (1 - om) v_i becomes
 // v_i - w+ (v_i + v_o)/2 - w- (v_i - v_o)/2 = a1 v_i + a2 v_o (o = opposite).
+// COLL_MRT (flow set only; g and s keep BGK): with d = f - f_eq_bar and the
+// orthogonal D2Q9 moment basis M (rows rho, e, eps, j_x, q_x, j_y, q_y, p_xx,
+// p_xy), f*_i = f_i - (M^-1 diag(s) M d)_i + S_i, the conserved and stress
+// moments relaxed at the BGK rate om, e and eps at s_e and s_eps, j and q at
+// s_q; computed as the BGK update plus -(M^-1 diag(s - om) M d)_i, which
+// involves only the six moments e, eps, j_x, q_x, j_y, q_y.
 // BIASED: the gradient of Eq. Grad from the second-order biased difference
 // (the window then holds two rings around the tile).
-template <typename S, bool FAST, bool TRT = false, bool BIASED = false>
+template <typename S, bool FAST, int COLL = COLL_BGK, bool BIASED = false>
 __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const float f[9],
                                               const float g[9], const float s[9], float phip,
                                               float qp, int x, int y, size_t c,
                                               S *__restrict__ pout, float *__restrict__ phi_prev,
                                               float *__restrict__ q_out, const DevParams &P,
                                               const Planes2d<S> &PL) {
+    constexpr bool TRT = COLL == COLL_TRT, MRT = COLL == COLL_MRT;
     // stencils, pair-folded: each (i, opposite) pair of Eqs. Grad and
     // Laplacian contributes w_i e_i (phi_i - phi_i') and 2 w_i (phi_i + phi_i' - 2 phi)
     // the window holds phi - phi_ref; differences are unaffected by the shift
@@ -351,9 +359,73 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     const float Pxa = fmaf(3.0f, uxx, -1.5f * uyy), Pya = fmaf(3.0f, uyy, -1.5f * uxx);
     const float Pd0 = 3.0f * usq;
 
+    // MRT: correction per direction of the flow set, in the working
+    // representation (zero and never formed for BGK and TRT)
+    float cf[9];
+    if (MRT) {
+        // f_eq_bar - w ref per weight: the coefficient form above at om = 1 and
+        // b = -1/2, since om f_eq + (1 - om/2) S = f_eq - S/2 there
+        const float K0b = fmaf(-0.5f, fmaf(rcs2 * q, P.kappa, -uB), m.p - P.set_ref[0]);
+        const float K1b = fmaf(0.5f, hU, rcs2);
+        const float Hbx = __fmul_rn(-0.5f, hx), Hby = __fmul_rn(-0.5f, hy);
+        const float Vbx = fmaf(3.0f * K1b, ux, -0.5f * m.Fx), Vby = fmaf(3.0f * K1b, uy, -0.5f * m.Fy);
+        // d_i = f_i - f_eq_bar_i (population units)
+        float dd[9];
+        auto dev = [&](int i, float eqw) {
+            return IsNarrow<S>::value ? __fmul_rn(L::w(i), fmaf(f[i], P.set_isc[0], -eqw))
+                                      : fmaf(-L::w(i), eqw, f[i]);
+        };
+        dd[0] = dev(0, fmaf(K1b, P0, K0b));
+        auto dpair = [&](int i, int o, float cu, float Pe, float eHb, float eVb) {
+            const float Eb = fmaf(3.0f * cu, eHb, fmaf(K1b, Pe, K0b));
+            const float Ob = fmaf(Pe, eHb, eVb);
+            dd[i] = dev(i, Eb + Ob);
+            dd[o] = dev(o, Eb - Ob);
+        };
+        dpair(1, 3, ux, Pxa, Hbx, Vbx);
+        dpair(2, 4, uy, Pya, Hby, Vby);
+        dpair(5, 7, __fadd_rn(ux, uy), fmaf(9.0f, uxy, Pd0), __fadd_rn(Hbx, Hby), __fadd_rn(Vbx, Vby));
+        dpair(6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(Hby, Hbx), __fsub_rn(Vby, Vbx));
+        // the six non-BGK moments of d (e5 = (1,1), e6 = (-1,1), e7 = (-1,-1), e8 = (1,-1))
+        const float sa = (dd[1] + dd[3]) + (dd[2] + dd[4]);
+        const float sd = (dd[5] + dd[7]) + (dd[6] + dd[8]);
+        const float me = fmaf(2.0f, sd, fmaf(-4.0f, dd[0], -sa));
+        const float meps = fmaf(4.0f, dd[0], fmaf(-2.0f, sa, sd));
+        const float ax = dd[1] - dd[3], ay = dd[2] - dd[4];
+        const float dx = (dd[5] - dd[7]) + (dd[8] - dd[6]), dy = (dd[5] - dd[7]) - (dd[8] - dd[6]);
+        const float mjx = ax + dx, mjy = ay + dy;
+        const float mqx = fmaf(-2.0f, ax, dx), mqy = fmaf(-2.0f, ay, dy);
+        // (s_k - om) / |row k|^2 with |e|^2 = |eps|^2 = 36, |j|^2 = 6, |q|^2 = 12
+        const float ce = __fmul_rn(P.mrt_rates[0] - om_f, 1.0f / 36.0f);
+        const float cp = __fmul_rn(P.mrt_rates[1] - om_f, 1.0f / 36.0f);
+        const float cj = __fmul_rn(P.mrt_rates[2] - om_f, 1.0f / 6.0f);
+        const float cq = __fmul_rn(P.mrt_rates[2] - om_f, 1.0f / 12.0f);
+        // -(M^-1 diag(s - om) M d)_i by direction class
+        const float r0 = 4.0f * fmaf(ce, me, -cp * meps);
+        const float rA = fmaf(ce, me, 2.0f * cp * meps);
+        const float rD = -fmaf(2.0f * ce, me, cp * meps);
+        const float Ox = fmaf(2.0f * cq, mqx, -cj * mjx), Oy = fmaf(2.0f * cq, mqy, -cj * mjy);
+        const float Bx = -fmaf(cj, mjx, cq * mqx), By = -fmaf(cj, mjy, cq * mqy);
+        // to the working representation: x 1 (FP32), x scale / w_i (16-bit)
+        const float k0 = IsNarrow<S>::value ? P.set_sc[0] * 2.25f : 1.0f;
+        const float kA = IsNarrow<S>::value ? P.set_sc[0] * 9.0f : 1.0f;
+        const float kD = IsNarrow<S>::value ? P.set_sc[0] * 36.0f : 1.0f;
+        // __fmul_rn / __fadd_rn: no product here is fused into a later sum, so
+        // every kernel that runs this update produces the same bits
+        cf[0] = __fmul_rn(k0, r0);
+        cf[1] = __fmul_rn(kA, rA + Ox); cf[3] = __fmul_rn(kA, rA - Ox);
+        cf[2] = __fmul_rn(kA, rA + Oy); cf[4] = __fmul_rn(kA, rA - Oy);
+        cf[5] = __fmul_rn(kD, rD + (Bx + By)); cf[7] = __fmul_rn(kD, rD - (Bx + By));
+        cf[6] = __fmul_rn(kD, rD + (By - Bx)); cf[8] = __fmul_rn(kD, rD - (By - Bx));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cf[i] = 0.0f;
+    }
+
     // rest
     push2d<S, FAST>(0,
-        fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)),
+        MRT ? __fadd_rn(fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)), cf[0])
+            : fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)),
         fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)),
         fmaf(k.a_s, s[0], rep_mul<S>(0, 2, P) * fmaf(k.Bs, P0, k.As)), x, y, c, pout, P, PL);
     // a direction i with e = (ex, ey) and its opposite o
@@ -364,7 +436,12 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
         const float Of = fmaf(Pe, eHo, eVf);
         const float Es = fmaf(k.Bs, Pe, k.As);
         const float mf = rep_mul<S>(i, 0, P), mg = rep_mul<S>(i, 1, P), ms = rep_mul<S>(i, 2, P);
-        if (!TRT) {
+        if (MRT) {
+            push2d<S, FAST>(i, __fadd_rn(fmaf(k.a_f, f[i], mf * (Ef + Of)), cf[i]), fmaf(k.a_g, g[i], mg * (Eg + eVg)),
+                            fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P, PL);
+            push2d<S, FAST>(o, __fadd_rn(fmaf(k.a_f, f[o], mf * (Ef - Of)), cf[o]), fmaf(k.a_g, g[o], mg * (Eg - eVg)),
+                            fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P, PL);
+        } else if (!TRT) {
             push2d<S, FAST>(i, fmaf(k.a_f, f[i], mf * (Ef + Of)), fmaf(k.a_g, g[i], mg * (Eg + eVg)),
                             fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P, PL);
             push2d<S, FAST>(o, fmaf(k.a_f, f[o], mf * (Ef - Of)), fmaf(k.a_g, g[o], mg * (Eg - eVg)),
@@ -422,7 +499,7 @@ __device__ __forceinline__ void ring_slot(int r, int &sx, int &sy) {
 // The whole update of one tile of geometry T (blockDim = T::TX x T::TY).
 // FAST: the tile and its halo ring lie inside the grid, so no halo cell and
 // no streaming link wraps or meets a wall.
-template <typename S, bool FAST, bool TRT = false, class T = Tile2Default>
+template <typename S, bool FAST, int COLL = COLL_BGK, class T = Tile2Default>
 __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__restrict__ pout,
                                             float *__restrict__ phi_prev,
                                             const float *__restrict__ q_in,
@@ -506,7 +583,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
     __syncthreads();
     if (!active) return;
 
-    cell_update2d<S, FAST, TRT>(sphi + (ty + 1) * SXT + tx + 1, SXT, f, g, s, phip, qp, x, y, c, pout,
+    cell_update2d<S, FAST, COLL>(sphi + (ty + 1) * SXT + tx + 1, SXT, f, g, s, phip, qp, x, y, c, pout,
                                 phi_prev, q_out, P, PL);
 }
 
@@ -515,7 +592,7 @@ __device__ __forceinline__ void step2d_tile(const S *__restrict__ pin, S *__rest
 // plain loads; beyond a wall both ghost layers take the wall's Dirichlet
 // value, periodic axes wrap).  FAST: no streaming link of the tile wraps or
 // meets a wall.
-template <typename S, bool FAST, bool TRT, class T = Tile2Default>
+template <typename S, bool FAST, int COLL, class T = Tile2Default>
 __device__ __forceinline__ void step2d_tile_biased(const S *__restrict__ pin, S *__restrict__ pout,
                                                    float *__restrict__ phi_prev,
                                                    const float *__restrict__ q_in,
@@ -558,7 +635,7 @@ __device__ __forceinline__ void step2d_tile_biased(const S *__restrict__ pin, S 
     }
     __syncthreads();
     if (!active) return;
-    cell_update2d<S, FAST, TRT, true>(sphi + (ty + 2) * SXB + tx + 2, SXB, f, g, s, phip, qp, x, y, c, pout,
+    cell_update2d<S, FAST, COLL, true>(sphi + (ty + 2) * SXB + tx + 2, SXB, f, g, s, phip, qp, x, y, c, pout,
                                       phi_prev, q_out, P, PL);
 }
 

@@ -159,7 +159,7 @@ __device__ __forceinline__ void ring2_store(float *win, const uint32_t *buf, int
     win[slot] = fmaf(0.5f, __uint_as_float(buf[9 * RING2 + tid]), set_sum2d<S>(v, P.set_isc[1]));
 }
 
-template <typename S, bool TRT>
+template <typename S, int COLL>
 __global__ void __launch_bounds__(TX * TY, 3)
 step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ pin,
                   S *__restrict__ pout, float *__restrict__ phi_prev,
@@ -182,7 +182,7 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
 
     if (!xin) {     // strip at (or beyond) the x edges: generic tiles, plain loads
         for (int c = 0; c < nc; ++c) {
-            step2d_tile<S, false, TRT>(pin, pout, phi_prev, q_in, q_out, P, win[0], x0, ybeg + c * TY, PL);
+            step2d_tile<S, false, COLL>(pin, pout, phi_prev, q_in, q_out, P, win[0], x0, ybeg + c * TY, PL);
             __syncthreads();
         }
         return;
@@ -278,12 +278,12 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
             const float qp = ((const float *)(bg + Gm::OFF_Q))[tid];
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const int x = x0 + tx, y = y0 + ty;
-            cell_update2d<S, true, TRT>(W + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y,
+            cell_update2d<S, true, COLL>(W + (ty + 1) * SX + tx + 1, SX, f, g, s, phip, qp, x, y,
                                    (size_t)y * nx + x, pout, phi_prev, q_out, P, PL);
         } else {
             // first or last rows of the grid (or a ragged chunk): generic tile
             // on the same window buffer, so the next chunk can take its top row
-            step2d_tile<S, false, TRT>(pin, pout, phi_prev, q_in, q_out, P, W, x0, y0, PL);
+            step2d_tile<S, false, COLL>(pin, pout, phi_prev, q_in, q_out, P, W, x0, y0, PL);
         }
         __syncthreads();      // the stages of chunk c and window c - 1 are free again
         if (c + Gm::NFS < nc) {
@@ -348,23 +348,25 @@ int make_tma_maps2d(TmaMaps2d *M, const DevParams &P, int elem_bytes, void *cons
     return 0;
 }
 
-template <typename S, bool TRT>
+template <typename S, int COLL>
 static int blocks_per_sm_one2() {
     int n = 0;
     const int dyn = March2Geom<S>::DYN;
-    if (cudaFuncSetAttribute(step2d_tma_kernel<S, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
+    if (cudaFuncSetAttribute(step2d_tma_kernel<S, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
         cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step2d_tma_kernel<S, TRT>, TX * TY, dyn) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step2d_tma_kernel<S, COLL>, TX * TY, dyn) != cudaSuccess)
         return 0;
     return n;
 }
 
-// both collision instantiations get the shared-memory limit
+// every collision instantiation gets the shared-memory limit
 template <typename S>
 static int blocks_per_sm_for2() {
-    const int a = blocks_per_sm_one2<S, false>(), b = blocks_per_sm_one2<S, true>();
-    return a < b ? a : b;
+    const int a = blocks_per_sm_one2<S, COLL_BGK>(), b = blocks_per_sm_one2<S, COLL_TRT>();
+    const int c = blocks_per_sm_one2<S, COLL_MRT>();
+    const int ab = a < b ? a : b;
+    return ab < c ? ab : c;
 }
 
 int tma2d_blocks_per_sm(int elem_bytes) {
@@ -380,10 +382,13 @@ cudaError_t launch_step2d_tma(const TmaMaps2d &M, int par, const void *pin, void
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY * YC - 1) / (TY * YC));
     if (P.opts & OPT_TRT)
-        step2d_tma_kernel<S, true><<<grid, block, March2Geom<S>::DYN, st>>>(
+        step2d_tma_kernel<S, COLL_TRT><<<grid, block, March2Geom<S>::DYN, st>>>(
+            M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
+    else if (P.opts & OPT_MRT)
+        step2d_tma_kernel<S, COLL_MRT><<<grid, block, March2Geom<S>::DYN, st>>>(
             M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
     else
-        step2d_tma_kernel<S, false><<<grid, block, March2Geom<S>::DYN, st>>>(
+        step2d_tma_kernel<S, COLL_BGK><<<grid, block, March2Geom<S>::DYN, st>>>(
             M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
     return cudaGetLastError();
 }

@@ -111,7 +111,10 @@ struct DevParams {
     // two-relaxation-time collision: magic parameter of the f, g, s sets
     // (read by the TRT instantiations of the step kernels only)
     float trt_magic[3];
-    int opts;                          // OPT_TRT | OPT_BIASED
+    // multiple-relaxation-time collision of the flow set: rates s_e, s_eps
+    // and s_q (read by the MRT instantiations of the 2D step kernels only)
+    float mrt_rates[3];
+    int opts;                          // OPT_TRT | OPT_MRT | OPT_BIASED
 #ifdef LBM_CHECK_BOUNDS
     int *dbg;                          // device status word of the bounds checks
 #endif
@@ -135,8 +138,11 @@ __device__ __forceinline__ bool in_bounds(long long idx, long long lim, const De
     return true;
 }
 
-// DevParams::opts: two-relaxation-time collision, biased gradient (Sec. 3.4)
-constexpr int OPT_TRT = 1, OPT_BIASED = 2;
+// DevParams::opts: two-relaxation-time collision, biased gradient (Sec. 3.4),
+// multiple-relaxation-time collision of the flow set (2D)
+constexpr int OPT_TRT = 1, OPT_BIASED = 2, OPT_MRT = 4;
+// collision instantiation of the step kernels
+constexpr int COLL_BGK = 0, COLL_TRT = 1, COLL_MRT = 2;
 
 // ---------------------------------------------------------------- layout
 // Memory layout of a population buffer (and of the saved and the adjoint

@@ -35,8 +35,9 @@ def make_params(d, storage="fp32", store_ref=None, store_scale=None):
     p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     p.model = int(d.get("model", 0))
     coll = d.get("collision", 0)
-    p.collision = {"bgk": 0, "trt": 1}[coll] if isinstance(coll, str) else int(coll)
+    p.collision = {"bgk": 0, "trt": 1, "mrt": 2}[coll] if isinstance(coll, str) else int(coll)
     p.trt_magic[:] = [float(v) for v in d.get("trt_magic", (0.25, 0.25, 0.25))]
+    p.mrt_rates[:] = [float(v) for v in d.get("mrt_rates", (1.4, 1.4, 1.2))]
     gs = d.get("grad_scheme", 0)
     p.grad_scheme = {"central": 0, "biased2": 1}[gs] if isinstance(gs, str) else int(gs)
     return p

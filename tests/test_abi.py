@@ -82,8 +82,20 @@ def test_collision_option_validated():
     for bad in ((0.0, 0.25, 0.25), (0.25, -1.0, 0.25), (0.25, 0.25, float("inf"))):
         w.params["trt_magic"] = bad
         assert _ws(w)[0] == B.LBM_EINVAL, bad
-    w.params.update(collision=2, trt_magic=(0.25, 0.25, 0.25))
+    w.params.update(collision=3, trt_magic=(0.25, 0.25, 0.25))
     assert _ws(w)[0] == B.LBM_EINVAL
+    # MRT of the flow set: rates in (0, 2), D2Q9 and the coupled model only
+    w.params.update(collision=2, mrt_rates=(1.4, 1.4, 1.2))
+    assert _ws(w)[0] == B.LBM_OK
+    for bad in ((0.0, 1.4, 1.2), (1.4, 2.0, 1.2), (1.4, 1.4, float("nan"))):
+        w.params["mrt_rates"] = bad
+        assert _ws(w)[0] == B.LBM_EINVAL, bad
+    w3 = W.film_boiling_3d(8, 8, 8, modes=1, z0=3.0)
+    w3.params.update(collision=2, mrt_rates=(1.4, 1.4, 1.2))
+    assert _ws(w3)[0] == B.LBM_EUNSUPPORTED
+    vm = W.vortex_disk(n=33)
+    vm.params.update(collision=2, mrt_rates=(1.4, 1.4, 1.2))
+    assert _ws(vm)[0] == B.LBM_EUNSUPPORTED
     # the phase-field-only model and the adjoint are BGK only
     v = W.vortex_disk(n=33)
     v.params.update(collision=1, trt_magic=(0.25, 0.25, 0.25))

@@ -1,0 +1,134 @@
+"""The multiple-relaxation-time collision of the flow set (LBM_COLLISION_MRT,
+D2Q9) on the GPU against the FP64 oracle's MRT step (oracle.model with
+collision = "mrt"): parity within 1e-5 on walled, periodic and ragged 2D
+grids, the 16-bit storages within their own bound, the TMA-staged kernel
+equal to the tiled one bit for bit, the exact Poiseuille profile at the
+magic rate s_q = 8 (2 - s_nu)/(8 - s_nu), and the unsupported cases."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+from _parity import gpu_fields, gpu_solver, max_errors, oracle_fields
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _mrt(w, rates=(1.4, 1.3, 1.2)):
+    w.params.update(collision="mrt", mrt_rates=rates)
+    return w
+
+
+def _film(nx, ny, **kw):
+    return W.film_boiling_2d(nx, ny, rho_ratio=10.0, y0=ny / 3.0, amplitude=2.0, phi_wall=(1.0, 0.0), **kw)
+
+
+CASES = [
+    ("film_ragged", lambda: _mrt(_film(100, 70)), 40),
+    ("droplet_periodic", lambda: _mrt(W.droplet_2d(48, 12.0, T_offset=0.05), (1.1, 1.6, 1.8)), 40),
+    ("stefan_x_walls", lambda: _mrt(W.stefan_1d(nx=90, ny=2), (1.0, 1.2, 1.5)), 80),
+    ("film_biased", lambda: _mrt(_film(70, 45, grad_scheme="biased2")), 30),
+]
+
+
+@pytest.mark.parametrize("name,make,steps", CASES, ids=[c[0] for c in CASES])
+def test_mrt_parity_with_oracle(name, make, steps):
+    w = make()
+    ref = oracle_fields(w, steps)
+    s = gpu_solver(w)
+    s.step(steps)
+    err = max_errors(gpu_fields(s), ref)
+    print(name, err)
+    assert all(v < TOL for v in err.values()), err
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_mrt_16bit_storage_near_oracle(storage):
+    # the same bound the BGK step meets with 16-bit storage on this film
+    w = _mrt(_film(64, 48))
+    ref = oracle_fields(w, 20)
+    err = max_errors(gpu_fields(_stepped(gpu_solver(w, storage=storage), 20)), ref)
+    bgk = _film(64, 48)
+    ref_b = oracle_fields(bgk, 20)
+    err_b = max_errors(gpu_fields(_stepped(gpu_solver(bgk, storage=storage), 20)), ref_b)
+    print(storage, "mrt", err, "bgk", err_b)
+    assert all(err[k] < 4.0 * err_b[k] + 1e-5 for k in err), (err, err_b)
+
+
+def _stepped(s, n):
+    s.step(n)
+    return s
+
+
+def test_mrt_differs_from_bgk_and_equal_rates_match_bgk():
+    w = _film(64, 40)
+    a = gpu_solver(w)
+    b = gpu_solver(_mrt(_film(64, 40)))
+    a.step(20)
+    b.step(20)
+    fa, fb = gpu_fields(a), gpu_fields(b)
+    assert np.abs(fa["phi"] - fb["phi"]).max() > 1e-7
+    # every rate at the BGK rate: equal to the BGK kernel within FP32 rounding
+    om = 1.0 / (3.0 * 0.1 + 0.5)
+    wl = W.droplet_2d(40, 10.0, T_offset=0.04)
+    wl.params.update(nu_l=0.1, nu_g=0.1)
+    c = gpu_solver(wl)
+    wm = W.droplet_2d(40, 10.0, T_offset=0.04)
+    wm.params.update(nu_l=0.1, nu_g=0.1, collision="mrt", mrt_rates=(om, om, om))
+    d = gpu_solver(wm)
+    c.step(30)
+    d.step(30)
+    err = max_errors(gpu_fields(c), gpu_fields(d))
+    assert all(v < 1e-6 for v in err.values()), err
+
+
+TMA_CASES = [("2d_fp32", "fp32"), ("2d_fp16", "fp16"), ("2d_bf16", "bf16")]
+
+
+@pytest.mark.parametrize("name,storage", TMA_CASES, ids=[c[0] for c in TMA_CASES])
+def test_mrt_tma_matches_tiled_bit_for_bit(name, storage):
+    w = _mrt(_film(128, 96))
+    a = gpu_solver(w, storage=storage)
+    b = gpu_solver(w, storage=storage)
+    a.set_kernel("tma")
+    b.set_kernel("tiled")
+    a.step(20)
+    b.step(20)
+    sa, sb = a.get_state(), b.get_state()
+    torch.cuda.synchronize()
+    assert torch.equal(sa, sb), name
+
+
+def _poiseuille_error(rates, nu=0.5, H=8, G=1e-5, steps=1500):
+    params = W.base_params(rho_l=1.0, rho_g=1.0, nu_l=nu, nu_g=nu, alpha_l=0.05, alpha_g=0.05, sigma=0.0,
+                           gravity=(0.0, 0.0, 0.0), body_force=(G, 0.0, 0.0), source_on=0,
+                           phi_wall=(0.0, 0.0), T_wall=(1.0, 1.0), collision="mrt", mrt_rates=rates)
+    from paper_2003_06342_b300 import Solver
+    s = Solver((2, H), (True, False), params)
+    s.init(np.zeros((H, 2)), np.ones((H, 2)))
+    s.step(steps)
+    u = s.fields()["u"][0].double().cpu().numpy()[:, 0]
+    y = np.arange(H)
+    exact = G / (2 * nu) * (y + 0.5) * (H - 0.5 - y)
+    return float(np.abs(u - exact).max() / exact.max())
+
+
+def test_mrt_magic_rate_poiseuille_on_gpu():
+    s_nu = 1.0 / (0.5 * 3.0 + 0.5)
+    s_q = 8.0 * (2.0 - s_nu) / (8.0 - s_nu)
+    err_magic, err_off = _poiseuille_error((1.1, 1.3, s_q)), _poiseuille_error((1.1, 1.3, 1.9))
+    print("poiseuille rel err MRT magic", err_magic, "off", err_off)
+    assert err_magic < 1e-4
+    assert err_off > 1e-3
+
+
+def test_mrt_unsupported_cases():
+    from paper_2003_06342_b300 import Solver
+    w3 = _mrt(W.film_boiling_3d(16, 8, 12, modes=1, z0=4.0, phi_wall=(1.0, 0.0)))
+    with pytest.raises(RuntimeError):
+        Solver(w3.n, w3.periodic, w3.params)
+    w = _mrt(_film(32, 24), rates=(1.4, 2.0, 1.2))
+    with pytest.raises(RuntimeError):
+        Solver(w.n, w.periodic, w.params)
