@@ -95,6 +95,8 @@ class Params:
     grad_scheme: str = "central"      # Eq. DerivDirec_Grad; "biased2": second-order biased
     trt_magic: tuple = (0.25, 0.25, 0.25)   # Lambda of the f, g, s sets (TRT only)
     mrt_rates: tuple = (1.4, 1.4, 1.2)      # s_e, s_eps, s_q of the flow set (MRT only)
+    # s_e, s_eps, s_q, s_p of the phase-field set (MRT only; 0: the BGK rate)
+    mrt_rates_g: tuple = (0.0, 0.0, 0.0, 0.0)
 
     @classmethod
     def from_dict(cls, d):
@@ -109,8 +111,9 @@ class Params:
             keys["grad_scheme"] = "biased2" if keys["grad_scheme"] else "central"
         if "collision" in keys and not isinstance(keys["collision"], str):
             keys["collision"] = {0: "bgk", 1: "trt", 2: "mrt"}[int(keys["collision"])]
-        if "mrt_rates" in keys:
-            keys["mrt_rates"] = tuple(float(v) for v in keys["mrt_rates"])
+        for k in ("mrt_rates", "mrt_rates_g"):
+            if k in keys:
+                keys[k] = tuple(float(v) for v in keys[k])
         if "trt_magic" in keys:
             keys["trt_magic"] = tuple(float(v) for v in keys["trt_magic"])
         for k in ("gravity", "body_force", "phi_wall", "T_wall"):
@@ -437,28 +440,45 @@ def mrt_basis(lat):
     return torch.tensor(rows, dtype=F64).T          # (moment, direction)
 
 
-def _relax_mrt(pops, eq_bar, S, tau, rates, lat):
-    """Multiple-relaxation-time collision of the flow set (the "next" MRT
-    row; not in the paper): with d = theta - eq_bar in moment space m = M d,
-    theta*_i = theta_i - (M^-1 diag(s) M d)_i + S_i.  The conserved moments
-    and the stress moments relax with the BGK rate 1/(tau + 1/2) (the
-    viscosity), e and eps with s_e and s_eps, and the odd moments j and q
-    with s_q; with every rate equal to the BGK rate this is Eq. LBE, and with
-    s_e = s_eps = 1/(tau + 1/2) it is the TRT collision whose antisymmetric
-    rate is s_q."""
+def _relax_moments(pops, eq_bar, S, rates, lat):
+    """Collision in the moment space of mrt_basis: with d = theta - eq_bar and
+    m = M d, theta*_i = theta_i - (M^-1 diag(s) M d)_i + S_i, where `rates`
+    holds the nine rates s_k (scalars or per-cell tensors) in basis order
+    rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy."""
     Mb = mrt_basis(lat)
-    om = 1.0 / (tau + 0.5)
-    s_e, s_eps, s_q = rates
     d = torch.stack([pops[i] - eq_bar[i] for i in range(lat.Q)])          # (Q, *grid)
     m = torch.tensordot(Mb, d, dims=1)                                    # (9, *grid)
     norms = (Mb * Mb).sum(dim=1)
     shape = (-1,) + (1,) * (m.dim() - 1)
-    om_t = om if torch.is_tensor(om) else torch.full_like(m[0], om)
-    s = [om_t, torch.full_like(om_t, s_e), torch.full_like(om_t, s_eps), torch.full_like(om_t, s_q),
-         torch.full_like(om_t, s_q), torch.full_like(om_t, s_q), torch.full_like(om_t, s_q), om_t, om_t]
+    s = [r if torch.is_tensor(r) else torch.full_like(m[0], r) for r in rates]
     relaxed = torch.stack([s[k] * m[k] for k in range(9)]) / norms.reshape(shape)
     r = torch.tensordot(Mb.T, relaxed, dims=1)                            # M^-1 = M^T diag(1/norms)
     return [pops[i] - r[i] + S[i] for i in range(lat.Q)]
+
+
+def _relax_mrt(pops, eq_bar, S, tau, rates, lat):
+    """Multiple-relaxation-time collision of the flow set (the "next" MRT
+    row; not in the paper).  The conserved moments and the stress moments
+    relax with the BGK rate 1/(tau + 1/2) (the viscosity), e and eps with
+    s_e and s_eps, and the odd moments j and q with s_q; with every rate
+    equal to the BGK rate this is Eq. LBE, and with s_e = s_eps =
+    1/(tau + 1/2) it is the TRT collision whose antisymmetric rate is s_q."""
+    om = 1.0 / (tau + 0.5)
+    s_e, s_eps, s_q = rates
+    return _relax_moments(pops, eq_bar, S, [om, s_e, s_eps, s_q, s_q, s_q, s_q, om, om], lat)
+
+
+def _relax_mrt_g(pops, eq_bar, S, tau, rates, lat):
+    """Multiple-relaxation-time collision of the phase-field set (not in the
+    paper): phi and the fluxes j relax with the BGK rate 1/(tau_g + 1/2),
+    which carries the mobility M_phi, so the model's transport coefficient
+    is that of Eq. LBE; e, eps, q and the stress moments p_xx, p_xy take
+    s_e, s_eps, s_q and s_p (a rate of 0 stands for the BGK rate).  With
+    s_q = the BGK rate and s_e = s_eps = s_p = w+ this is the TRT collision
+    of g (odd moments at the mobility rate, even ones at w+)."""
+    om = 1.0 / (tau + 0.5)
+    s_e, s_eps, s_q, s_p = [om if r == 0.0 else r for r in rates]
+    return _relax_moments(pops, eq_bar, S, [om, s_e, s_eps, om, s_q, om, s_q, s_p, s_p], lat)
 
 
 def collide(st, M, q, P, grid):
@@ -487,7 +507,7 @@ def collide(st, M, q, P, grid):
         if grid.dim != 2:
             raise ValueError("the MRT collision is defined for D2Q9")
         f_out = _relax_mrt(st["f"], f_bar, f_S, tau_f, P.mrt_rates, Lf)
-        g_out = [_relax(st["g"][i], g_bar[i], g_src[i], tau_g) for i in range(Lg.Q)]
+        g_out = _relax_mrt_g(st["g"], g_bar, g_src, tau_g, P.mrt_rates_g, Lg)
         s_out = [_relax(st["s"][i], s_bar[i], s_S[i], tau_s) for i in range(Lf.Q)]
     elif P.collision == "trt":
         mf, mg, ms = P.trt_magic

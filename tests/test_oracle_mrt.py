@@ -63,3 +63,49 @@ def test_mrt_magic_rate_gives_the_exact_poiseuille_profile():
     assert _poiseuille("mrt", (1.1, 1.3, s_q)) < 1e-10
     assert _poiseuille("mrt", (1.1, 1.3, 1.9)) > 1e-3
     assert _poiseuille("bgk", (1.0, 1.0, 1.0)) > 1e-2
+
+
+# ---- the phase-field set (mrt_rates_g = s_e, s_eps, s_q, s_p; 0: the BGK rate)
+
+def test_mrt_g_default_rates_are_bgk_and_other_rates_differ():
+    om = 1.0 / (0.1 * 3.0 + 0.5)
+    bgk = _droplet_fields(collision="bgk")
+    mrt = _droplet_fields(collision="mrt", mrt_rates=(om, om, om))
+    om_g = 1.0 / (bgk_tau_g() + 0.5)
+    explicit = _droplet_fields(collision="mrt", mrt_rates=(om, om, om), mrt_rates_g=(om_g, om_g, om_g, om_g))
+    assert _close(bgk, mrt) and _close(bgk, explicit)
+    other = _droplet_fields(collision="mrt", mrt_rates=(om, om, om), mrt_rates_g=(1.2, 1.5, 1.1, 1.7))
+    assert float((other["phi"] - bgk["phi"]).abs().max()) > 1e-9
+
+
+def bgk_tau_g(M_phi=None):
+    w = W.droplet_2d(24, 6.0)
+    return (M_phi if M_phi is not None else w.params["M_phi"]) * 3.0
+
+
+def test_mrt_g_reduces_to_trt_g_with_the_source_off():
+    # TRT of g: odd moments at the mobility rate, even ones at w+ = 1/(Lambda/tau_g + 1/2);
+    # the same collision as MRT of g with s_q = BGK rate and s_e = s_eps = s_p = w+,
+    # once phi's own moment of d vanishes (source off)
+    cs2 = 1.0 / 3.0
+    tau_f, tau_g, tau_s = 0.1 / cs2, 0.08 / cs2, 0.05 / cs2
+    lam = 0.3
+    wp = 1.0 / (lam / tau_g + 0.5)
+    om_f = 1.0 / (tau_f + 0.5)
+    trt = _droplet_fields(collision="trt", M_phi=0.08, source_on=0,
+                          trt_magic=(tau_f * tau_f, lam, tau_s * tau_s))
+    mrt = _droplet_fields(collision="mrt", M_phi=0.08, source_on=0, mrt_rates=(om_f, om_f, om_f),
+                          mrt_rates_g=(wp, wp, 0.0, wp))
+    assert _close(trt, mrt)
+
+
+def test_mrt_g_conserves_phi_mass_with_the_source_off():
+    w = W.droplet_2d(24, 6.0, T_offset=0.04, T_noise=0.01, corr_len=4.0)
+    params = dict(w.params, nu_l=0.1, nu_g=0.1, alpha_l=0.05, alpha_g=0.05, source_on=0,
+                  collision="mrt", mrt_rates=(1.3, 1.1, 1.6), mrt_rates_g=(1.2, 1.6, 1.05, 1.8))
+    P, G = M.Params.from_dict(params), M.Grid(w.n, w.periodic)
+    st = M.init_state(w.phi0, w.T0, P, G)
+    m0 = float(M.fields(st, P, G)["phi"].sum())
+    st = M.run(st, P, G, 40)
+    m1 = float(M.fields(st, P, G)["phi"].sum())
+    assert abs(m1 - m0) < 1e-11 * abs(m0)
