@@ -93,6 +93,7 @@ typedef struct {
     int32_t grad_scheme;          /* LBM_GRAD_*                                  */
     double trt_magic[3];          /* TRT magic parameter of the f, g, s sets     */
     double mrt_rates[3];          /* MRT rates s_e, s_eps, s_q of the f set      */
+    double mrt_rates_g[4];        /* MRT rates s_e, s_eps, s_q, s_p of the g set */
 } lbm_params;
 
 /* Collision operators.  BGK: Eq. LBE (the paper's scheme, the default).
@@ -108,19 +109,25 @@ typedef struct {
  * in 2D and 3D; the adjoint covers BGK only. */
 #define LBM_COLLISION_BGK 0
 #define LBM_COLLISION_TRT 1
-/* MRT: multiple relaxation times for the flow set f (not in the paper; the
- * multiple-relaxation-time extension its outlook names), g and s keep BGK.
- * With d = f - f_eq_bar expressed in the orthogonal D2Q9 moment basis (rho,
- * e = 3|c|^2 - 4, eps = 4 - 21|c|^2/2 + 9|c|^4/2, j_x, q_x = (3|c|^2 - 5) c_x,
- * j_y, q_y, p_xx = c_x^2 - c_y^2, p_xy = c_x c_y), the moments rho, p_xx and
- * p_xy relax at the BGK rate 1/(tau_f + 1/2) (the viscosity), e and eps at
- * mrt_rates[0] and [1], j and q at mrt_rates[2]; each rate in (0, 2), else
- * LBM_EINVAL.  Equal rates give BGK; s_e = s_eps = 1/(tau_f + 1/2) gives the
- * TRT collision of f with antisymmetric rate s_q; s_q = 8 (2 - s_nu)/(8 - s_nu)
- * puts the half-way bounce-back wall at the middle of the link for Poiseuille
- * flow.  MRT is implemented for LBM_MODEL_COUPLED on D2Q9 (tiled and TMA
- * kernels); D3Q19_D3Q7 and the phase-field model return LBM_EUNSUPPORTED;
- * the adjoint covers BGK only. */
+/* MRT: multiple relaxation times for the flow set f and the phase-field set
+ * g (not in the paper; the multiple-relaxation-time extension its outlook
+ * names); s keeps BGK.  With d = theta - theta_eq_bar expressed in the
+ * orthogonal D2Q9 moment basis (rho, e = 3|c|^2 - 4, eps = 4 - 21|c|^2/2 +
+ * 9|c|^4/2, j_x, q_x = (3|c|^2 - 5) c_x, j_y, q_y, p_xx = c_x^2 - c_y^2,
+ * p_xy = c_x c_y):
+ *   f: rho, p_xx and p_xy relax at the BGK rate 1/(tau_f + 1/2) (the
+ *      viscosity), e and eps at mrt_rates[0] and [1], j and q at
+ *      mrt_rates[2]; each rate in (0, 2), else LBM_EINVAL.  Equal rates give
+ *      BGK; s_e = s_eps = 1/(tau_f + 1/2) gives the TRT collision of f with
+ *      antisymmetric rate s_q; s_q = 8 (2 - s_nu)/(8 - s_nu) puts the
+ *      half-way bounce-back wall at the middle of the link for Poiseuille
+ *      flow.
+ *   g: phi and j relax at the BGK rate 1/(tau_g + 1/2) (the mobility), e,
+ *      eps, q and p_xx, p_xy at mrt_rates_g[0..3]; each rate 0 (meaning the
+ *      BGK rate, so all zeros keep g on BGK) or in (0, 2), else LBM_EINVAL.
+ * MRT is implemented for LBM_MODEL_COUPLED on D2Q9 (tiled and TMA kernels);
+ * D3Q19_D3Q7 and the phase-field model return LBM_EUNSUPPORTED; the adjoint
+ * covers BGK only. */
 #define LBM_COLLISION_MRT 2
 
 /* Directional derivative inside Eq. Grad (Sec. 3.4).  CENTRAL: Eq.

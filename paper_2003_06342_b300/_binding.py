@@ -64,6 +64,7 @@ class lbm_params(ctypes.Structure):
         ("alpha_interp", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("model", ctypes.c_int32), ("collision", ctypes.c_int32), ("grad_scheme", ctypes.c_int32),
         ("trt_magic", ctypes.c_double * 3), ("mrt_rates", ctypes.c_double * 3),
+        ("mrt_rates_g", ctypes.c_double * 4),
     ]
 
 

@@ -99,6 +99,9 @@ int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
     if (p->collision == LBM_COLLISION_MRT) {
         for (int k = 0; k < 3; ++k)
             if (!(p->mrt_rates[k] > 0.0 && p->mrt_rates[k] < 2.0)) return LBM_EINVAL;
+        for (int k = 0; k < 4; ++k)
+            if (!(p->mrt_rates_g[k] == 0.0 || (p->mrt_rates_g[k] > 0.0 && p->mrt_rates_g[k] < 2.0)))
+                return LBM_EINVAL;
         if (dim != 2 || p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
     }
     const double vals[] = {p->rho_l, p->rho_g, p->nu_l, p->nu_g, p->alpha_l, p->alpha_g, p->sigma,
@@ -176,6 +179,7 @@ void fill_devparams(lbm_handle *h) {
              (p.grad_scheme == LBM_GRAD_BIASED2 ? OPT_BIASED : 0);
     for (int s = 0; s < 3; ++s) d.trt_magic[s] = (float)p.trt_magic[s];
     for (int k = 0; k < 3; ++k) d.mrt_rates[k] = (float)p.mrt_rates[k];
+    for (int k = 0; k < 4; ++k) d.mrt_rates_g[k] = p.mrt_rates_g[k] == 0.0 ? d.om_g : (float)p.mrt_rates_g[k];
     // codec constants, planes ordered f (Qf), g (Qg), s (Qf)
     int k = 0;
     for (int set = 0; set < 3; ++set) {

@@ -19,7 +19,7 @@
 //      Geq_Allen-Cahn_Eq, SourceTerm_AllenCahn, Seq_Temp,
 //      Def_SourceTerms_Temp), or their two-relaxation-time form (TRT
 //      instantiation), or the multiple-relaxation-time collision of the
-//      flow set with BGK for g and s (MRT instantiation), with the central
+//      flow and phase-field sets with BGK for s (MRT instantiation), with the central
 //      or the biased gradient (BIASED instantiation, a two-ring phi window);
 //      The temperature set is advanced as deviations sbar_i - w_i T_ref
 //      (the stored form), which keeps FP32 rounding relative to T - T_ref

@@ -220,6 +220,61 @@ struct Coef2 {
     float As, Bs, Wx, Wy;
 };
 
+// MRT correction of one D2Q9 set: -(M^-1 diag(s - om) M d)_i for the
+// non-conserved moments of the orthogonal basis (rows rho, e, eps, j_x, q_x,
+// j_y, q_y, p_xx, p_xy; squared norms 9, 36, 36, 6, 12, 6, 12, 4, 4), given
+// d_i = theta_i - theta_eq_bar_i in population units and the rate
+// differences s_k - om of e, eps, j (J: else j keeps om), q and the stress
+// moments (PS: else they keep om).  The result is in the set's working
+// representation (x 1 for FP32, x scale / w_i for 16-bit storage);
+// __fmul_rn / __fadd_rn keep every product out of later sums, so each kernel
+// that runs this correction produces the same bits.
+template <typename S, bool J, bool PS>
+__device__ __forceinline__ void mrt_correction2d(const float dd[9], float de, float dp, float dj,
+                                                 float dqs, float sc, float out[9]) {
+    // with J (flow set) the q rate is the j rate: dqs carries s_p - om of the
+    // stress moments instead (PS, phase-field set), whose q rate is dj
+    const float ce = __fmul_rn(de, 1.0f / 36.0f), cp = __fmul_rn(dp, 1.0f / 36.0f);
+    const float cj = J ? __fmul_rn(dj, 1.0f / 6.0f) : 0.0f;
+    const float cq = __fmul_rn(dj, 1.0f / 12.0f);
+    const float cs = PS ? __fmul_rn(dqs, 0.25f) : 0.0f;
+    // moments of d (e5 = (1,1), e6 = (-1,1), e7 = (-1,-1), e8 = (1,-1))
+    const float s13 = dd[1] + dd[3], s24 = dd[2] + dd[4];
+    const float s57 = dd[5] + dd[7], s68 = dd[6] + dd[8];
+    const float sa = s13 + s24, sd = s57 + s68;
+    const float me = fmaf(2.0f, sd, fmaf(-4.0f, dd[0], -sa));
+    const float meps = fmaf(4.0f, dd[0], fmaf(-2.0f, sa, sd));
+    const float ax = dd[1] - dd[3], ay = dd[2] - dd[4];
+    const float dx = (dd[5] - dd[7]) + (dd[8] - dd[6]), dy = (dd[5] - dd[7]) - (dd[8] - dd[6]);
+    const float mqx = fmaf(-2.0f, ax, dx), mqy = fmaf(-2.0f, ay, dy);
+    // by direction class: rest, axis (even, odd), diagonal (even, odd)
+    const float r0 = 4.0f * fmaf(ce, me, -cp * meps);
+    const float rA = fmaf(ce, me, 2.0f * cp * meps);
+    const float rD = -fmaf(2.0f * ce, me, cp * meps);
+    float Ox = __fmul_rn(2.0f * cq, mqx), Oy = __fmul_rn(2.0f * cq, mqy);
+    float Bx = __fmul_rn(-cq, mqx), By = __fmul_rn(-cq, mqy);
+    if (J) {
+        const float mjx = ax + dx, mjy = ay + dy;
+        Ox = fmaf(2.0f * cq, mqx, -cj * mjx);
+        Oy = fmaf(2.0f * cq, mqy, -cj * mjy);
+        Bx = -fmaf(cj, mjx, cq * mqx);
+        By = -fmaf(cj, mjy, cq * mqy);
+    }
+    // stress moments: p_xx = +1 on x-axis links, -1 on y-axis links; p_xy = +1
+    // on the (1,1) / (-1,-1) diagonals, -1 on the others
+    const float pxx = PS ? __fmul_rn(cs, s13 - s24) : 0.0f;
+    const float pxy = PS ? __fmul_rn(cs, s57 - s68) : 0.0f;
+    const float rAx = PS ? rA - pxx : rA, rAy = PS ? rA + pxx : rA;
+    const float rD57 = PS ? rD - pxy : rD, rD68 = PS ? rD + pxy : rD;
+    const bool nar = IsNarrow<S>::value;
+    const float k0 = nar ? sc * 2.25f : 1.0f, kA = nar ? sc * 9.0f : 1.0f, kD = nar ? sc * 36.0f : 1.0f;
+    out[0] = __fmul_rn(k0, r0);
+    out[1] = __fmul_rn(kA, rAx + Ox); out[3] = __fmul_rn(kA, rAx - Ox);
+    out[2] = __fmul_rn(kA, rAy + Oy); out[4] = __fmul_rn(kA, rAy - Oy);
+    out[5] = __fmul_rn(kD, rD57 + (Bx + By)); out[7] = __fmul_rn(kD, rD57 - (Bx + By));
+    out[6] = __fmul_rn(kD, rD68 + (By - Bx)); out[8] = __fmul_rn(kD, rD68 - (By - Bx));
+}
+
 // Update of one cell from a window of phi - phi_ref (`sp` points at the
 // cell, rows `pitch` floats apart) and the cell's own populations in the
 // working representation: stencils, closures, moments, production rate, the
@@ -228,12 +283,13 @@ struct Coef2 {
 // COLL selects the collision of Eq. LBE (COLL_BGK) or one of two extensions
 // outside the paper.  COLL_TRT: the BGK relaxation (1 - om) v_i becomes
 // v_i - w+ (v_i + v_o)/2 - w- (v_i - v_o)/2 = a1 v_i + a2 v_o (o = opposite).
-// COLL_MRT (flow set only; g and s keep BGK): with d = f - f_eq_bar and the
-// orthogonal D2Q9 moment basis M (rows rho, e, eps, j_x, q_x, j_y, q_y, p_xx,
-// p_xy), f*_i = f_i - (M^-1 diag(s) M d)_i + S_i, the conserved and stress
-// moments relaxed at the BGK rate om, e and eps at s_e and s_eps, j and q at
-// s_q; computed as the BGK update plus -(M^-1 diag(s - om) M d)_i, which
-// involves only the six moments e, eps, j_x, q_x, j_y, q_y.
+// COLL_MRT (flow and phase-field sets; s keeps BGK): with d = theta -
+// theta_eq_bar and the orthogonal D2Q9 moment basis M (rows rho, e, eps, j_x,
+// q_x, j_y, q_y, p_xx, p_xy), theta*_i = theta_i - (M^-1 diag(s) M d)_i + S_i;
+// for f the conserved and stress moments relax at the BGK rate om_f, e and
+// eps at s_e and s_eps, j and q at s_q; for g phi and j relax at om_g (the
+// mobility), e, eps, q and the stress moments at their own rates.  Computed
+// as the BGK update plus -(M^-1 diag(s - om) M d)_i (mrt_correction2d).
 // BIASED: the gradient of Eq. Grad from the second-order biased difference
 // (the window then holds two rings around the tile).
 template <typename S, bool FAST, int COLL = COLL_BGK, bool BIASED = false>
@@ -359,9 +415,9 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     const float Pxa = fmaf(3.0f, uxx, -1.5f * uyy), Pya = fmaf(3.0f, uyy, -1.5f * uxx);
     const float Pd0 = 3.0f * usq;
 
-    // MRT: correction per direction of the flow set, in the working
-    // representation (zero and never formed for BGK and TRT)
-    float cf[9];
+    // MRT: correction per direction of the flow and phase-field sets, in the
+    // working representation (zero and never formed for BGK and TRT)
+    float cf[9], cg[9];
     if (MRT) {
         // f_eq_bar - w ref per weight: the coefficient form above at om = 1 and
         // b = -1/2, since om f_eq + (1 - om/2) S = f_eq - S/2 there
@@ -371,62 +427,60 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
         const float Vbx = fmaf(3.0f * K1b, ux, -0.5f * m.Fx), Vby = fmaf(3.0f * K1b, uy, -0.5f * m.Fy);
         // d_i = f_i - f_eq_bar_i (population units)
         float dd[9];
-        auto dev = [&](int i, float eqw) {
+        auto devf = [&](int i, float eqw) {
             return IsNarrow<S>::value ? __fmul_rn(L::w(i), fmaf(f[i], P.set_isc[0], -eqw))
                                       : fmaf(-L::w(i), eqw, f[i]);
         };
-        dd[0] = dev(0, fmaf(K1b, P0, K0b));
+        dd[0] = devf(0, fmaf(K1b, P0, K0b));
         auto dpair = [&](int i, int o, float cu, float Pe, float eHb, float eVb) {
             const float Eb = fmaf(3.0f * cu, eHb, fmaf(K1b, Pe, K0b));
             const float Ob = fmaf(Pe, eHb, eVb);
-            dd[i] = dev(i, Eb + Ob);
-            dd[o] = dev(o, Eb - Ob);
+            dd[i] = devf(i, Eb + Ob);
+            dd[o] = devf(o, Eb - Ob);
         };
         dpair(1, 3, ux, Pxa, Hbx, Vbx);
         dpair(2, 4, uy, Pya, Hby, Vby);
         dpair(5, 7, __fadd_rn(ux, uy), fmaf(9.0f, uxy, Pd0), __fadd_rn(Hbx, Hby), __fadd_rn(Vbx, Vby));
         dpair(6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(Hby, Hbx), __fsub_rn(Vby, Vbx));
-        // the six non-BGK moments of d (e5 = (1,1), e6 = (-1,1), e7 = (-1,-1), e8 = (1,-1))
-        const float sa = (dd[1] + dd[3]) + (dd[2] + dd[4]);
-        const float sd = (dd[5] + dd[7]) + (dd[6] + dd[8]);
-        const float me = fmaf(2.0f, sd, fmaf(-4.0f, dd[0], -sa));
-        const float meps = fmaf(4.0f, dd[0], fmaf(-2.0f, sa, sd));
-        const float ax = dd[1] - dd[3], ay = dd[2] - dd[4];
-        const float dx = (dd[5] - dd[7]) + (dd[8] - dd[6]), dy = (dd[5] - dd[7]) - (dd[8] - dd[6]);
-        const float mjx = ax + dx, mjy = ay + dy;
-        const float mqx = fmaf(-2.0f, ax, dx), mqy = fmaf(-2.0f, ay, dy);
-        // (s_k - om) / |row k|^2 with |e|^2 = |eps|^2 = 36, |j|^2 = 6, |q|^2 = 12
-        const float ce = __fmul_rn(P.mrt_rates[0] - om_f, 1.0f / 36.0f);
-        const float cp = __fmul_rn(P.mrt_rates[1] - om_f, 1.0f / 36.0f);
-        const float cj = __fmul_rn(P.mrt_rates[2] - om_f, 1.0f / 6.0f);
-        const float cq = __fmul_rn(P.mrt_rates[2] - om_f, 1.0f / 12.0f);
-        // -(M^-1 diag(s - om) M d)_i by direction class
-        const float r0 = 4.0f * fmaf(ce, me, -cp * meps);
-        const float rA = fmaf(ce, me, 2.0f * cp * meps);
-        const float rD = -fmaf(2.0f * ce, me, cp * meps);
-        const float Ox = fmaf(2.0f * cq, mqx, -cj * mjx), Oy = fmaf(2.0f * cq, mqy, -cj * mjy);
-        const float Bx = -fmaf(cj, mjx, cq * mqx), By = -fmaf(cj, mjy, cq * mqy);
-        // to the working representation: x 1 (FP32), x scale / w_i (16-bit)
-        const float k0 = IsNarrow<S>::value ? P.set_sc[0] * 2.25f : 1.0f;
-        const float kA = IsNarrow<S>::value ? P.set_sc[0] * 9.0f : 1.0f;
-        const float kD = IsNarrow<S>::value ? P.set_sc[0] * 36.0f : 1.0f;
-        // __fmul_rn / __fadd_rn: no product here is fused into a later sum, so
-        // every kernel that runs this update produces the same bits
-        cf[0] = __fmul_rn(k0, r0);
-        cf[1] = __fmul_rn(kA, rA + Ox); cf[3] = __fmul_rn(kA, rA - Ox);
-        cf[2] = __fmul_rn(kA, rA + Oy); cf[4] = __fmul_rn(kA, rA - Oy);
-        cf[5] = __fmul_rn(kD, rD + (Bx + By)); cf[7] = __fmul_rn(kD, rD - (Bx + By));
-        cf[6] = __fmul_rn(kD, rD + (By - Bx)); cf[8] = __fmul_rn(kD, rD - (By - Bx));
+        // e, eps, j and q relax at their own rates; rho, p_xx, p_xy at om_f
+        mrt_correction2d<S, true, false>(dd, P.mrt_rates[0] - om_f, P.mrt_rates[1] - om_f,
+                                         P.mrt_rates[2] - om_f, 0.0f, P.set_sc[0], cf);
+
+        // g_eq_bar - w phi_ref per weight: (phd - q/2) + phi P_e + e.(3 phi u - iface n / 2)
+        const float Agb = fmaf(-0.5f, q, phd);
+        const float hif = __fmul_rn(-0.5f, iface);
+        const float Vgbx = fmaf(3.0f * ph, ux, __fmul_rn(hif, nx_));
+        const float Vgby = fmaf(3.0f * ph, uy, __fmul_rn(hif, ny_));
+        auto devg = [&](int i, float eqw) {
+            return IsNarrow<S>::value ? __fmul_rn(L::w(i), fmaf(g[i], P.set_isc[1], -eqw))
+                                      : fmaf(-L::w(i), eqw, g[i]);
+        };
+        dd[0] = devg(0, fmaf(ph, P0, Agb));
+        auto gpair = [&](int i, int o, float Pe, float eV) {
+            const float Eb = fmaf(ph, Pe, Agb);
+            dd[i] = devg(i, Eb + eV);
+            dd[o] = devg(o, Eb - eV);
+        };
+        gpair(1, 3, Pxa, Vgbx);
+        gpair(2, 4, Pya, Vgby);
+        gpair(5, 7, fmaf(9.0f, uxy, Pd0), __fadd_rn(Vgbx, Vgby));
+        gpair(6, 8, fmaf(-9.0f, uxy, Pd0), __fsub_rn(Vgby, Vgbx));
+        // phi and j relax at om_g (the mobility); e, eps, q, p_xx, p_xy at
+        // their own rates (the host stores om_g for a rate given as 0)
+        mrt_correction2d<S, false, true>(dd, P.mrt_rates_g[0] - om_g, P.mrt_rates_g[1] - om_g,
+                                         P.mrt_rates_g[2] - om_g, P.mrt_rates_g[3] - om_g,
+                                         P.set_sc[1], cg);
     } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) cf[i] = 0.0f;
+        for (int i = 0; i < 9; ++i) cf[i] = cg[i] = 0.0f;
     }
 
     // rest
     push2d<S, FAST>(0,
         MRT ? __fadd_rn(fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)), cf[0])
             : fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)),
-        fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)),
+        MRT ? __fadd_rn(fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)), cg[0])
+            : fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)),
         fmaf(k.a_s, s[0], rep_mul<S>(0, 2, P) * fmaf(k.Bs, P0, k.As)), x, y, c, pout, P, PL);
     // a direction i with e = (ex, ey) and its opposite o
     auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eHo, float eVf,
@@ -437,9 +491,11 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
         const float Es = fmaf(k.Bs, Pe, k.As);
         const float mf = rep_mul<S>(i, 0, P), mg = rep_mul<S>(i, 1, P), ms = rep_mul<S>(i, 2, P);
         if (MRT) {
-            push2d<S, FAST>(i, __fadd_rn(fmaf(k.a_f, f[i], mf * (Ef + Of)), cf[i]), fmaf(k.a_g, g[i], mg * (Eg + eVg)),
+            push2d<S, FAST>(i, __fadd_rn(fmaf(k.a_f, f[i], mf * (Ef + Of)), cf[i]),
+                            __fadd_rn(fmaf(k.a_g, g[i], mg * (Eg + eVg)), cg[i]),
                             fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P, PL);
-            push2d<S, FAST>(o, __fadd_rn(fmaf(k.a_f, f[o], mf * (Ef - Of)), cf[o]), fmaf(k.a_g, g[o], mg * (Eg - eVg)),
+            push2d<S, FAST>(o, __fadd_rn(fmaf(k.a_f, f[o], mf * (Ef - Of)), cf[o]),
+                            __fadd_rn(fmaf(k.a_g, g[o], mg * (Eg - eVg)), cg[o]),
                             fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P, PL);
         } else if (!TRT) {
             push2d<S, FAST>(i, fmaf(k.a_f, f[i], mf * (Ef + Of)), fmaf(k.a_g, g[i], mg * (Eg + eVg)),

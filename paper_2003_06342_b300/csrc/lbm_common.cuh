@@ -114,6 +114,8 @@ struct DevParams {
     // multiple-relaxation-time collision of the flow set: rates s_e, s_eps
     // and s_q (read by the MRT instantiations of the 2D step kernels only)
     float mrt_rates[3];
+    // and of the phase-field set: s_e, s_eps, s_q, s_p (om_g stored for a 0)
+    float mrt_rates_g[4];
     int opts;                          // OPT_TRT | OPT_MRT | OPT_BIASED
 #ifdef LBM_CHECK_BOUNDS
     int *dbg;                          // device status word of the bounds checks

@@ -38,6 +38,7 @@ def make_params(d, storage="fp32", store_ref=None, store_scale=None):
     p.collision = {"bgk": 0, "trt": 1, "mrt": 2}[coll] if isinstance(coll, str) else int(coll)
     p.trt_magic[:] = [float(v) for v in d.get("trt_magic", (0.25, 0.25, 0.25))]
     p.mrt_rates[:] = [float(v) for v in d.get("mrt_rates", (1.4, 1.4, 1.2))]
+    p.mrt_rates_g[:] = [float(v) for v in d.get("mrt_rates_g", (0.0, 0.0, 0.0, 0.0))]
     gs = d.get("grad_scheme", 0)
     p.grad_scheme = {"central": 0, "biased2": 1}[gs] if isinstance(gs, str) else int(gs)
     return p

@@ -90,6 +90,13 @@ def test_collision_option_validated():
     for bad in ((0.0, 1.4, 1.2), (1.4, 2.0, 1.2), (1.4, 1.4, float("nan"))):
         w.params["mrt_rates"] = bad
         assert _ws(w)[0] == B.LBM_EINVAL, bad
+    w.params["mrt_rates"] = (1.4, 1.4, 1.2)
+    w.params["mrt_rates_g"] = (0.0, 1.5, 0.0, 1.2)          # 0: the BGK rate
+    assert _ws(w)[0] == B.LBM_OK
+    for bad in ((-0.1, 1.5, 1.0, 1.2), (1.0, 2.0, 1.0, 1.0), (1.0, 1.0, float("inf"), 1.0)):
+        w.params["mrt_rates_g"] = bad
+        assert _ws(w)[0] == B.LBM_EINVAL, bad
+    w.params["mrt_rates_g"] = (0.0, 0.0, 0.0, 0.0)
     w3 = W.film_boiling_3d(8, 8, 8, modes=1, z0=3.0)
     w3.params.update(collision=2, mrt_rates=(1.4, 1.4, 1.2))
     assert _ws(w3)[0] == B.LBM_EUNSUPPORTED

@@ -1,9 +1,11 @@
-"""The multiple-relaxation-time collision of the flow set (LBM_COLLISION_MRT,
-D2Q9) on the GPU against the FP64 oracle's MRT step (oracle.model with
-collision = "mrt"): parity within 1e-5 on walled, periodic and ragged 2D
-grids, the 16-bit storages within their own bound, the TMA-staged kernel
-equal to the tiled one bit for bit, the exact Poiseuille profile at the
-magic rate s_q = 8 (2 - s_nu)/(8 - s_nu), and the unsupported cases."""
+"""The multiple-relaxation-time collision of the flow and phase-field sets
+(LBM_COLLISION_MRT, D2Q9) on the GPU against the FP64 oracle's MRT step
+(oracle.model with collision = "mrt"): parity within 1e-5 on walled,
+periodic and ragged 2D grids, with g on BGK or on its own MRT rates; the
+16-bit storages within their own bound; the TMA-staged kernel equal to the
+tiled one bit for bit; phi mass conserved with the source off; the exact
+Poiseuille profile at the magic rate s_q = 8 (2 - s_nu)/(8 - s_nu); and the
+unsupported cases."""
 import numpy as np
 import pytest
 import torch
@@ -16,9 +18,12 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def _mrt(w, rates=(1.4, 1.3, 1.2)):
-    w.params.update(collision="mrt", mrt_rates=rates)
+def _mrt(w, rates=(1.4, 1.3, 1.2), rates_g=(0.0, 0.0, 0.0, 0.0)):
+    w.params.update(collision="mrt", mrt_rates=rates, mrt_rates_g=rates_g)
     return w
+
+
+G_RATES = (1.2, 1.5, 1.1, 1.7)
 
 
 def _film(nx, ny, **kw):
@@ -30,6 +35,11 @@ CASES = [
     ("droplet_periodic", lambda: _mrt(W.droplet_2d(48, 12.0, T_offset=0.05), (1.1, 1.6, 1.8)), 40),
     ("stefan_x_walls", lambda: _mrt(W.stefan_1d(nx=90, ny=2), (1.0, 1.2, 1.5)), 80),
     ("film_biased", lambda: _mrt(_film(70, 45, grad_scheme="biased2")), 30),
+    # the phase-field set on MRT too (a rate of 0 is the BGK rate)
+    ("film_ragged_g", lambda: _mrt(_film(100, 70), rates_g=G_RATES), 40),
+    ("droplet_periodic_g", lambda: _mrt(W.droplet_2d(48, 12.0, T_offset=0.05), (1.1, 1.6, 1.8),
+                                        (0.0, 1.3, 1.6, 0.0)), 40),
+    ("film_biased_g", lambda: _mrt(_film(70, 45, grad_scheme="biased2"), rates_g=G_RATES), 30),
 ]
 
 
@@ -47,7 +57,7 @@ def test_mrt_parity_with_oracle(name, make, steps):
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 def test_mrt_16bit_storage_near_oracle(storage):
     # the same bound the BGK step meets with 16-bit storage on this film
-    w = _mrt(_film(64, 48))
+    w = _mrt(_film(64, 48), rates_g=G_RATES)
     ref = oracle_fields(w, 20)
     err = max_errors(gpu_fields(_stepped(gpu_solver(w, storage=storage), 20)), ref)
     bgk = _film(64, 48)
@@ -84,12 +94,13 @@ def test_mrt_differs_from_bgk_and_equal_rates_match_bgk():
     assert all(v < 1e-6 for v in err.values()), err
 
 
-TMA_CASES = [("2d_fp32", "fp32"), ("2d_fp16", "fp16"), ("2d_bf16", "bf16")]
+TMA_CASES = [("2d_fp32", "fp32", (0.0,) * 4), ("2d_fp16", "fp16", (0.0,) * 4), ("2d_bf16", "bf16", (0.0,) * 4),
+             ("2d_fp32_g", "fp32", G_RATES), ("2d_fp16_g", "fp16", G_RATES), ("2d_bf16_g", "bf16", G_RATES)]
 
 
-@pytest.mark.parametrize("name,storage", TMA_CASES, ids=[c[0] for c in TMA_CASES])
-def test_mrt_tma_matches_tiled_bit_for_bit(name, storage):
-    w = _mrt(_film(128, 96))
+@pytest.mark.parametrize("name,storage,rates_g", TMA_CASES, ids=[c[0] for c in TMA_CASES])
+def test_mrt_tma_matches_tiled_bit_for_bit(name, storage, rates_g):
+    w = _mrt(_film(128, 96), rates_g=rates_g)
     a = gpu_solver(w, storage=storage)
     b = gpu_solver(w, storage=storage)
     a.set_kernel("tma")
@@ -132,3 +143,14 @@ def test_mrt_unsupported_cases():
     w = _mrt(_film(32, 24), rates=(1.4, 2.0, 1.2))
     with pytest.raises(RuntimeError):
         Solver(w.n, w.periodic, w.params)
+
+
+def test_mrt_g_conserves_phi_mass_with_the_source_off():
+    w = _mrt(W.droplet_2d(64, 16.0, T_offset=0.05), rates_g=G_RATES)
+    w.params.update(source_on=0)
+    s = gpu_solver(w)
+    m0, _ = s.reduce()
+    s.step(200)
+    m1, _ = s.reduce()
+    print("phi mass", m0, m1)
+    assert abs(m1 - m0) / m0 < 1e-5
