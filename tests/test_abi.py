@@ -250,3 +250,33 @@ def test_phase_field_model_validation():
     f.on_device, f.dtype = 0, 1
     assert B.lib.lbm_set_velocity(h, ctypes.byref(f), 0.0) == B.LBM_EUNSUPPORTED
     B.lib.lbm_destroy(h)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every field of lbm_grid, lbm_params and lbm_fields sits at the same
+    offset, and each struct has the same size, in the C header (compiled with
+    the host C compiler) and in the ctypes binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = (B.lbm_grid, B.lbm_params, B.lbm_fields)
+    body = ""
+    for st in structs:
+        t = st.__name__
+        body += "".join(f'    printf("{t}.{f[0]} %zu\\n", offsetof({t}, {f[0]}));\n' for f in st._fields_)
+        body += f'    printf("{t}.sizeof %zu\\n", sizeof({t}));\n'
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "lbm_pf.h"\nint main(void) {\n'
+                   f'{body}    return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for st in structs:
+        t = st.__name__
+        for f in st._fields_:
+            assert int(out[f"{t}.{f[0]}"]) == getattr(st, f[0]).offset, (t, f[0])
+        assert int(out[f"{t}.sizeof"]) == ctypes.sizeof(st), t
