@@ -224,20 +224,20 @@ struct Coef2 {
 // non-conserved moments of the orthogonal basis (rows rho, e, eps, j_x, q_x,
 // j_y, q_y, p_xx, p_xy; squared norms 9, 36, 36, 6, 12, 6, 12, 4, 4), given
 // d_i = theta_i - theta_eq_bar_i in population units and the rate
-// differences s_k - om of e, eps, j (J: else j keeps om), q and the stress
-// moments (PS: else they keep om).  The result is in the set's working
-// representation (x 1 for FP32, x scale / w_i for 16-bit storage);
-// __fmul_rn / __fadd_rn keep every product out of later sums, so each kernel
-// that runs this correction produces the same bits.
+// differences s_k - om:
+//   de: e,  dp: eps,  dq: q (and j when J: the flow set relaxes j with q),
+//   ds: the stress moments p_xx, p_xy (read when PS: the phase-field set).
+// Without J, j keeps om; without PS, p_xx and p_xy keep om.  The result is
+// in the set's working representation (x 1 for FP32, x scale / w_i for
+// 16-bit storage); __fmul_rn / __fadd_rn keep every product out of later
+// sums, so each kernel that runs this correction produces the same bits.
 template <typename S, bool J, bool PS>
-__device__ __forceinline__ void mrt_correction2d(const float dd[9], float de, float dp, float dj,
-                                                 float dqs, float sc, float out[9]) {
-    // with J (flow set) the q rate is the j rate: dqs carries s_p - om of the
-    // stress moments instead (PS, phase-field set), whose q rate is dj
+__device__ __forceinline__ void mrt_correction2d(const float dd[9], float de, float dp, float dq,
+                                                 float ds, float sc, float out[9]) {
     const float ce = __fmul_rn(de, 1.0f / 36.0f), cp = __fmul_rn(dp, 1.0f / 36.0f);
-    const float cj = J ? __fmul_rn(dj, 1.0f / 6.0f) : 0.0f;
-    const float cq = __fmul_rn(dj, 1.0f / 12.0f);
-    const float cs = PS ? __fmul_rn(dqs, 0.25f) : 0.0f;
+    const float cj = J ? __fmul_rn(dq, 1.0f / 6.0f) : 0.0f;
+    const float cq = __fmul_rn(dq, 1.0f / 12.0f);
+    const float cs = PS ? __fmul_rn(ds, 0.25f) : 0.0f;
     // moments of d (e5 = (1,1), e6 = (-1,1), e7 = (-1,-1), e8 = (1,-1))
     const float s13 = dd[1] + dd[3], s24 = dd[2] + dd[4];
     const float s57 = dd[5] + dd[7], s68 = dd[6] + dd[8];
