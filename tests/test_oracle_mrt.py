@@ -109,3 +109,20 @@ def test_mrt_g_conserves_phi_mass_with_the_source_off():
     st = M.run(st, P, G, 40)
     m1 = float(M.fields(st, P, G)["phi"].sum())
     assert abs(m1 - m0) < 1e-11 * abs(m0)
+
+
+def test_mrt_keeps_the_tanh_interface_stationary():
+    # a flat two-interface slab at rest is the CAC equilibrium (Sec. 3.2):
+    # with every MRT rate away from the BGK one the profile stays in place
+    # within the bound the BGK step meets
+    n, Wd = 48, 4.0
+    params = W.base_params(rho_l=1.0, rho_g=1.0, nu_l=0.1, nu_g=0.1, sigma=0.0, W=Wd, M_phi=0.08,
+                           gravity=(0.0, 0.0, 0.0), source_on=0, collision="mrt",
+                           mrt_rates=(1.3, 1.1, 1.6), mrt_rates_g=(1.2, 1.5, 1.1, 1.7))
+    y = np.arange(n) + 0.5
+    prof = 0.5 * (1 + np.tanh(2 * (y - 12) / Wd)) - 0.5 * (1 + np.tanh(2 * (y - 36) / Wd))
+    phi0 = np.broadcast_to(prof[:, None], (n, 3)).copy()
+    P, G = M.Params.from_dict(params), M.Grid((3, n), (True, True))
+    st = M.run(M.init_state(phi0, np.ones_like(phi0), P, G), P, G, 800)
+    drift = float(np.abs(M.fields(st, P, G)["phi"].numpy() - phi0).max())
+    assert drift < 1e-2, drift
