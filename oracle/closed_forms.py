@@ -14,8 +14,8 @@
 * Laplace law, Sec. 4.1 (Eq. LaplaceLaw): p_in - p_out = sigma / R in 2D.
 * Coefficient A of Eq. ProductionRate from the four integrals of App. B
   (Eqs. Def_A, Def_Integrals, OurFunctions), evaluated by quadrature.
-* Film-boiling characteristic numbers, Sec. 5.1 (Eq. Critical_wavelength,
-  Grashof, Prandtl, Jacob numbers and the time scale t_s).
+(The film-boiling characteristic numbers of Sec. 5.1 belong to the package's
+unit conversion, which tests them against the printed values.)
 """
 import math
 
@@ -104,19 +104,3 @@ def coefficient_A(W=2.0 * math.sqrt(2.0)):
     """Eq. Def_A: A = (G + J U) / (2 I)."""
     I, J, G, U = A_integrals(W)
     return (G + J * U) / (2.0 * I)
-
-
-# ----------------------------------------------------------------------------
-# film boiling numbers (Sec. 5.1)
-# ----------------------------------------------------------------------------
-
-def film_boiling_numbers(rho_l, rho_g, nu_g, alpha_g, sigma, g_y, Cp, L, T_w, T_sat):
-    lam_s = math.sqrt(sigma / ((rho_l - rho_g) * g_y))
-    return dict(
-        lambda_s=lam_s,
-        lambda_c=2.0 * math.pi * lam_s,
-        Gr=rho_g * g_y * (rho_l - rho_g) * lam_s ** 3 / (rho_g ** 2 * nu_g ** 2),
-        Pr=nu_g / alpha_g,
-        Ja=Cp * (T_w - T_sat) / L,
-        t_s=math.sqrt(lam_s / g_y),
-    )

@@ -24,7 +24,16 @@ def test_characteristic_numbers():
     fb = GOLD["film_boiling"]
     ph = fb["physical"]
     n = units.film_boiling_numbers(ph["rho_l"], ph["rho_g"], ph["nu_g"], ph["alpha_g"], ph["sigma"],
-                                   ph["g_y"], 1.0, 1.0, 1.0 + ph["theta_w"], 1.0)
+                                   ph["g_y"], 1.0, ph["L_over_Cp"], 1.0 + ph["theta_w"], 1.0)
+    # printed truncated to four significant figures (lambda_s = 0.0435855
+    # appears as 4.358e-2, lambda_c = 0.273856 as 0.2738)
     assert abs(n["lambda_s"] - fb["lambda_s"]) / fb["lambda_s"] < 2e-4
-    assert abs(n["Pr"] - 0.2) < 1e-12 and abs(n["Ja"] - 0.025) < 1e-12
+    assert abs(n["lambda_c"] - fb["lambda_c"]) / fb["lambda_c"] < 5e-4
+    assert abs(n["Pr"] - fb["Pr"]) < 1e-12 and abs(n["Pr"] - 0.2) < 1e-12
+    assert abs(n["Ja"] - fb["Ja"]) < 1e-12 and abs(n["Ja"] - 0.025) < 1e-12
     assert abs(n["t_s"] - fb["t_s"]) < 5e-5
+    # the paper's Gr follows from its rounded lambda_s = 4.358e-2
+    Gr_rounded = ph["rho_g"] * ph["g_y"] * (ph["rho_l"] - ph["rho_g"]) * fb["lambda_s"] ** 3 \
+        / (ph["rho_g"] ** 2 * ph["nu_g"] ** 2)
+    assert abs(Gr_rounded - fb["Gr"]) / fb["Gr"] < 1e-4
+    assert abs(n["Gr"] - fb["Gr"]) / fb["Gr"] < 1e-3
