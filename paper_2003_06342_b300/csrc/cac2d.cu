@@ -138,14 +138,14 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
     const float P0 = -1.5f * usq;
     const float Pxa = fmaf(3.0f, uxx, -1.5f * uyy), Pya = fmaf(3.0f, uyy, -1.5f * uxx);
     const float Pd0 = 3.0f * usq;
-    auto mul = [&](int i) { return IsNarrow<S>::value ? P.set_sc[1] : L::w(i); };
+    // increments in the working representation (split-weight product for FP32)
+    auto rep = [&](int i, float v) { return IsNarrow<S>::value ? P.set_sc[1] * v : weighted<L>(i, v); };
 
-    cac_push2d<S, FAST>(0, fmaf(a_g, g[0], mul(0) * fmaf(Bg, P0, Ag)), x, y, c, pout, P, PL);
+    cac_push2d<S, FAST>(0, fmaf(a_g, g[0], rep(0, fmaf(Bg, P0, Ag))), x, y, c, pout, P, PL);
     auto pair = [&](int i, int o, float Pe, float eV) {
         const float E = fmaf(Bg, Pe, Ag);
-        const float m = mul(i);
-        cac_push2d<S, FAST>(i, fmaf(a_g, g[i], m * (E + eV)), x, y, c, pout, P, PL);
-        cac_push2d<S, FAST>(o, fmaf(a_g, g[o], m * (E - eV)), x, y, c, pout, P, PL);
+        cac_push2d<S, FAST>(i, fmaf(a_g, g[i], rep(i, E + eV)), x, y, c, pout, P, PL);
+        cac_push2d<S, FAST>(o, fmaf(a_g, g[o], rep(i, E - eV)), x, y, c, pout, P, PL);
     };
     pair(1, 3, Pxa, Vgx);
     pair(2, 4, Pya, Vgy);

@@ -165,6 +165,14 @@ __device__ __forceinline__ float rep_mul(int i, int set, const DevParams &P) {
     return IsNarrow<S>::value ? P.set_sc[set] : L::w(i);
 }
 
+// A per-weight increment x taken to the working representation: w_i x (the
+// split-weight product of weighted()) for FP32, x times the set's scale for
+// 16-bit storage.
+template <typename S>
+__device__ __forceinline__ float to_rep(int i, int set, float x, const DevParams &P) {
+    return IsNarrow<S>::value ? P.set_sc[set] * x : weighted<L>(i, x);
+}
+
 // Push of direction i's three post-collision values (working representation)
 // from cell c = (x, y).  FAST: the link neither wraps nor meets a wall.
 template <typename S, bool FAST>
@@ -477,11 +485,11 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
 
     // rest
     push2d<S, FAST>(0,
-        MRT ? __fadd_rn(fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)), cf[0])
-            : fmaf(k.a_f, f[0], rep_mul<S>(0, 0, P) * fmaf(k.K1, P0, k.K0)),
-        MRT ? __fadd_rn(fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)), cg[0])
-            : fmaf(k.a_g, g[0], rep_mul<S>(0, 1, P) * fmaf(k.Bg, P0, k.Ag)),
-        fmaf(k.a_s, s[0], rep_mul<S>(0, 2, P) * fmaf(k.Bs, P0, k.As)), x, y, c, pout, P, PL);
+        MRT ? __fadd_rn(fmaf(k.a_f, f[0], to_rep<S>(0, 0, fmaf(k.K1, P0, k.K0), P)), cf[0])
+            : fmaf(k.a_f, f[0], to_rep<S>(0, 0, fmaf(k.K1, P0, k.K0), P)),
+        MRT ? __fadd_rn(fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)), cg[0])
+            : fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)),
+        fmaf(k.a_s, s[0], to_rep<S>(0, 2, fmaf(k.Bs, P0, k.As), P)), x, y, c, pout, P, PL);
     // a direction i with e = (ex, ey) and its opposite o
     auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eHo, float eVf,
                     float eW) {
@@ -489,26 +497,29 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
         const float Ef = fmaf(3.0f * cu, eH, fmaf(k.K1, Pe, k.K0));
         const float Of = fmaf(Pe, eHo, eVf);
         const float Es = fmaf(k.Bs, Pe, k.As);
-        const float mf = rep_mul<S>(i, 0, P), mg = rep_mul<S>(i, 1, P), ms = rep_mul<S>(i, 2, P);
+        // w_i = w_o: the increments of i and o share the weight of i
+        auto rf = [&](float v) { return to_rep<S>(i, 0, v, P); };
+        auto rg = [&](float v) { return to_rep<S>(i, 1, v, P); };
+        auto rs = [&](float v) { return to_rep<S>(i, 2, v, P); };
         if (MRT) {
-            push2d<S, FAST>(i, __fadd_rn(fmaf(k.a_f, f[i], mf * (Ef + Of)), cf[i]),
-                            __fadd_rn(fmaf(k.a_g, g[i], mg * (Eg + eVg)), cg[i]),
-                            fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P, PL);
-            push2d<S, FAST>(o, __fadd_rn(fmaf(k.a_f, f[o], mf * (Ef - Of)), cf[o]),
-                            __fadd_rn(fmaf(k.a_g, g[o], mg * (Eg - eVg)), cg[o]),
-                            fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P, PL);
+            push2d<S, FAST>(i, __fadd_rn(fmaf(k.a_f, f[i], rf(Ef + Of)), cf[i]),
+                            __fadd_rn(fmaf(k.a_g, g[i], rg(Eg + eVg)), cg[i]),
+                            fmaf(k.a_s, s[i], rs(Es + eW)), x, y, c, pout, P, PL);
+            push2d<S, FAST>(o, __fadd_rn(fmaf(k.a_f, f[o], rf(Ef - Of)), cf[o]),
+                            __fadd_rn(fmaf(k.a_g, g[o], rg(Eg - eVg)), cg[o]),
+                            fmaf(k.a_s, s[o], rs(Es - eW)), x, y, c, pout, P, PL);
         } else if (!TRT) {
-            push2d<S, FAST>(i, fmaf(k.a_f, f[i], mf * (Ef + Of)), fmaf(k.a_g, g[i], mg * (Eg + eVg)),
-                            fmaf(k.a_s, s[i], ms * (Es + eW)), x, y, c, pout, P, PL);
-            push2d<S, FAST>(o, fmaf(k.a_f, f[o], mf * (Ef - Of)), fmaf(k.a_g, g[o], mg * (Eg - eVg)),
-                            fmaf(k.a_s, s[o], ms * (Es - eW)), x, y, c, pout, P, PL);
+            push2d<S, FAST>(i, fmaf(k.a_f, f[i], rf(Ef + Of)), fmaf(k.a_g, g[i], rg(Eg + eVg)),
+                            fmaf(k.a_s, s[i], rs(Es + eW)), x, y, c, pout, P, PL);
+            push2d<S, FAST>(o, fmaf(k.a_f, f[o], rf(Ef - Of)), fmaf(k.a_g, g[o], rg(Eg - eVg)),
+                            fmaf(k.a_s, s[o], rs(Es - eW)), x, y, c, pout, P, PL);
         } else {
-            push2d<S, FAST>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], mf * (Ef + Of))),
-                            fmaf(a1_g, g[i], fmaf(a2_g, g[o], mg * (Eg + eVg))),
-                            fmaf(a1_s, s[i], fmaf(a2_s, s[o], ms * (Es + eW))), x, y, c, pout, P, PL);
-            push2d<S, FAST>(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], mf * (Ef - Of))),
-                            fmaf(a1_g, g[o], fmaf(a2_g, g[i], mg * (Eg - eVg))),
-                            fmaf(a1_s, s[o], fmaf(a2_s, s[i], ms * (Es - eW))), x, y, c, pout, P, PL);
+            push2d<S, FAST>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], rf(Ef + Of))),
+                            fmaf(a1_g, g[i], fmaf(a2_g, g[o], rg(Eg + eVg))),
+                            fmaf(a1_s, s[i], fmaf(a2_s, s[o], rs(Es + eW))), x, y, c, pout, P, PL);
+            push2d<S, FAST>(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], rf(Ef - Of))),
+                            fmaf(a1_g, g[o], fmaf(a2_g, g[i], rg(Eg - eVg))),
+                            fmaf(a1_s, s[o], fmaf(a2_s, s[i], rs(Es - eW))), x, y, c, pout, P, PL);
         }
     };
     pair(1, 3, ux, Pxa, k.Vgx, k.Hx, Hox, k.Vfx, k.Wx);                          // (1, 0)

@@ -300,6 +300,13 @@ __device__ __forceinline__ float rep_mul3(int i) {
     return IsNarrow<S>::value ? 1.0f : Lt::w(i);
 }
 
+// The per-weight increment x in the working representation: w_i x as the
+// split-weight product of weighted() for FP32, x itself for 16-bit values.
+template <typename S, class Lt>
+__device__ __forceinline__ float rep3(int i, float x) {
+    return IsNarrow<S>::value ? x : weighted<Lt>(i, x);
+}
+
 // Push from cell c = (x, y, z).  MODE XY_IN: the link stays inside the grid;
 // XY_WRAP: it may cross a periodic x / y boundary but not a z edge or a wall;
 // XY_GEN: anything.  Through a wall a value comes back to c in the opposite
@@ -510,20 +517,20 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Vg[3] = {fmaf(4.0f * Bgo, ux, bgi * n0), fmaf(4.0f * Bgo, uy, bgi * n1),
                              fmaf(4.0f * Bgo, uz, bgi * n2)};
         const float usq2 = 2.0f * usq;
-        push3d_g<S, MODE>(0, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)),
+        push3d_g<S, MODE>(0, fmaf(a_g, g[0], rep3<S, LG>(0, fmaf(Bg, -usq2, Ag))),
                             x, y, z, c, pout, P, PL);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const float ua = m.u[a];
             const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
-            const float mg = rep_mul3<S, LG>(a + 1);
+            auto rg = [&](float v) { return rep3<S, LG>(a + 1, v); };
             if (!TRT) {
-                push3d_g<S, MODE>(a + 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
-                push3d_g<S, MODE>(a + 4, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
+                push3d_g<S, MODE>(a + 1, fmaf(a_g, g[a + 1], rg(Eg + Vg[a])), x, y, z, c, pout, P, PL);
+                push3d_g<S, MODE>(a + 4, fmaf(a_g, g[a + 4], rg(Eg - Vg[a])), x, y, z, c, pout, P, PL);
             } else {
-                push3d_g<S, MODE>(a + 1, fmaf(a1_g, g[a + 1], fmaf(a2_g, g[a + 4], mg * (Eg + Vg[a]))),
+                push3d_g<S, MODE>(a + 1, fmaf(a1_g, g[a + 1], fmaf(a2_g, g[a + 4], rg(Eg + Vg[a]))),
                                   x, y, z, c, pout, P, PL);
-                push3d_g<S, MODE>(a + 4, fmaf(a1_g, g[a + 4], fmaf(a2_g, g[a + 1], mg * (Eg - Vg[a]))),
+                push3d_g<S, MODE>(a + 4, fmaf(a1_g, g[a + 4], fmaf(a2_g, g[a + 1], rg(Eg - Vg[a]))),
                                   x, y, z, c, pout, P, PL);
             }
         }
@@ -554,8 +561,8 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float Bso = TRT ? scs * (omm_s * m.T) : Bs;
     // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
     const float Wx = __fmul_rn(3.0f * Bso, ux), Wy = __fmul_rn(3.0f * Bso, uy), Wz = __fmul_rn(3.0f * Bso, uz);
-    push3d_fs<S, MODE>(0, fmaf(a_f, f[0], rep_mul3<S, LF>(0) * fmaf(K1, -usq15, K0)),
-                            fmaf(a_s, s[0], rep_mul3<S, LF>(0) * fmaf(Bs, -usq15, As)), x, y, z, c,
+    push3d_fs<S, MODE>(0, fmaf(a_f, f[0], rep3<S, LF>(0, fmaf(K1, -usq15, K0))),
+                            fmaf(a_s, s[0], rep3<S, LF>(0, fmaf(Bs, -usq15, As))), x, y, z, c,
                             pout, P, PL);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -569,17 +576,18 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Of = fmaf(Pe, eHo, edot3(ex, ey, ez, Vfx, Vfy, Vfz));
         const float Es = fmaf(Bs, Pe, As);
         const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
-        const float mf = rep_mul3<S, LF>(i), ms = mf;
+        // w_i = w_o: the increments of i and o share the weight of i
+        auto rf = [&](float v) { return rep3<S, LF>(i, v); };
         if (!TRT) {
-            push3d_fs<S, MODE>(i, fmaf(a_f, f[i], mf * (Ef + Of)), fmaf(a_s, s[i], ms * (Es + Os)),
+            push3d_fs<S, MODE>(i, fmaf(a_f, f[i], rf(Ef + Of)), fmaf(a_s, s[i], rf(Es + Os)),
                                x, y, z, c, pout, P, PL);
-            push3d_fs<S, MODE>(o, fmaf(a_f, f[o], mf * (Ef - Of)), fmaf(a_s, s[o], ms * (Es - Os)),
+            push3d_fs<S, MODE>(o, fmaf(a_f, f[o], rf(Ef - Of)), fmaf(a_s, s[o], rf(Es - Os)),
                                x, y, z, c, pout, P, PL);
         } else {
-            push3d_fs<S, MODE>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], mf * (Ef + Of))),
-                               fmaf(a1_s, s[i], fmaf(a2_s, s[o], ms * (Es + Os))), x, y, z, c, pout, P, PL);
-            push3d_fs<S, MODE>(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], mf * (Ef - Of))),
-                               fmaf(a1_s, s[o], fmaf(a2_s, s[i], ms * (Es - Os))), x, y, z, c, pout, P, PL);
+            push3d_fs<S, MODE>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], rf(Ef + Of))),
+                               fmaf(a1_s, s[i], fmaf(a2_s, s[o], rf(Es + Os))), x, y, z, c, pout, P, PL);
+            push3d_fs<S, MODE>(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], rf(Ef - Of))),
+                               fmaf(a1_s, s[o], fmaf(a2_s, s[i], rf(Es - Os))), x, y, z, c, pout, P, PL);
         }
     }
 }

@@ -86,14 +86,16 @@ def test_parity_with_oracle(name, make, steps):
 
 
 def test_parity_c1_1000_steps():
-    """The 128 x 256 film-boiling case for 1000 steps.
+    """The 128 x 256 film-boiling case for 1000 steps: phi, T, u and p within
+    1e-5 of the FP64 oracle.
 
-    u and p must stay within 1e-5.  For phi and T that bound lies below what
-    FP32 arithmetic can deliver on this trajectory: the oracle's own step run
-    in float32 already drifts from float64 by the amounts stored in
-    tests/golden/c1_fp32_floor.json (written by make_fp32_floor.py from the
-    oracle alone; about 2e-5 in phi at the interface and 8e-5 in T).  phi and
-    T must therefore stay within max(1e-5, 2 x that floor)."""
+    For context the test prints what plain FP32 arithmetic costs on this
+    trajectory: the oracle's own step run in float32 drifts from float64 by
+    the amounts in tests/golden/c1_fp32_floor.json (written from the oracle
+    alone; 1.9e-5 in phi, 8.4e-5 in T).  The kernels multiply by each lattice
+    weight as a two-float product (the rounded float32 weights do not sum to
+    one, a bias that accumulates step after step) and advance T as a
+    deviation from T_sat, which keeps them inside the bound."""
     floor = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c1_fp32_floor.json")))
     w = W.c1_parity()
     ref = oracle_fields(w, w.steps)
@@ -101,10 +103,8 @@ def test_parity_c1_1000_steps():
     s.step(w.steps)
     got = gpu_fields(s)
     err = max_errors(got, ref)
-    print("c1 1000-step errors", err, "fp32 floor", floor)
-    assert err["u"] < TOL and err["p"] < TOL, err
-    assert err["phi"] < max(TOL, 2.0 * floor["phi"]), (err, floor)
-    assert err["T"] < max(TOL, 2.0 * floor["T"]), (err, floor)
+    print("c1 1000-step errors", err, "plain-fp32 oracle", floor)
+    assert all(v < TOL for v in err.values()), err
 
 
 def test_reductions_match_oracle():
