@@ -344,12 +344,39 @@ int lbm_set_velocity(lbm_handle *h, const lbm_fields *u, double period);
  * device memory that every GPU loading the library holds until exit; hence
  * n_cells is limited to 16,777,216 and larger sizes return LBM_ENOMEM.  The
  * first call on a device looks up that array's device address (with the
- * device current) and caches it; make that first call before any stream
- * capture.  All calls share the array: calls whose kernels overlap on the GPU
- * race and must be ordered by the caller.  Errors: LBM_EINVAL (NULL pointer,
- * n_cells < 1, non-positive density), LBM_ENOMEM, LBM_ECUDA. */
+ * device current) and caches it for the life of the process; make that first
+ * call before any stream capture.  A device reset (cudaDeviceReset, or a
+ * primary context released and created again) reloads the module and leaves
+ * the cached address stale: do not call this entry point on a device after
+ * resetting it.  All calls share the array: calls whose kernels overlap on
+ * the GPU race and must be ordered by the caller.  Errors: LBM_EINVAL (NULL
+ * pointer, n_cells < 1, non-positive density), LBM_ENOMEM, LBM_EUNSUPPORTED
+ * (current device ordinal 64 or above), LBM_ECUDA. */
 int lbm_field_sums_noalloc(const float *phi, const float *T, int64_t n_cells, double rho_l,
                            double rho_g, double Cp, double L, double *d_out, void *stream);
+
+/* Column blocks of the state, for a slab domain decomposition along x (the
+ * paper's implementation section: one sub-domain per GPU, neighbouring
+ * sub-domains trade ghost layers every time step).  A block is the complete
+ * stored state of columns [x0, x0 + ncols) over every y (and z): the Qtot
+ * population planes in the handle's storage precision (each plane rows x
+ * ncols values, rows = ny nz, x fastest; f, s of a direction as two planes,
+ * then the g planes), zero-padded to a multiple of 16 bytes, followed by phi^{n-1}
+ * and the lagged source as two planes of rows x ncols floats.
+ * lbm_columns_bytes gives the size of a block of ncols columns.
+ * lbm_pack_columns copies the block into dst, lbm_unpack_columns overwrites
+ * the handle's state with src; both are device buffers owned by the caller,
+ * 16-byte aligned, and both calls are queued on the handle's stream (the
+ * caller orders them against other streams).  A decomposition built on these
+ * calls gives each sub-domain h ghost columns on both sides (h = 2 for the
+ * central gradient, 3 for the biased one) and, after every step, unpacks the
+ * neighbours' h outermost owned columns into them; the owned columns then
+ * evolve exactly as in the undivided grid.  Errors: LBM_EINVAL (NULL, a
+ * misaligned buffer, columns outside [0, nx)), LBM_EUNSUPPORTED
+ * (LBM_MODEL_PHASE_FIELD), LBM_ECUDA. */
+int lbm_columns_bytes(const lbm_handle *h, int32_t ncols, size_t *bytes);
+int lbm_pack_columns(lbm_handle *h, int32_t x0, int32_t ncols, void *dst);
+int lbm_unpack_columns(lbm_handle *h, int32_t x0, int32_t ncols, const void *src);
 
 /* Release the handle (not the workspace, which the caller owns). */
 void lbm_destroy(lbm_handle *h);

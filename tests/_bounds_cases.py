@@ -23,6 +23,17 @@ def _film3d(nx, ny, nz, z0):
     return W.film_boiling_3d(nx, ny, nz, modes=1, z0=z0, phi_wall=(1.0, 0.0))
 
 
+def _opt(w, **extra):
+    """The workload with the collision / gradient options of rows f2, f3."""
+    w.params.update(**extra)
+    return w
+
+
+TRT = dict(collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25))
+MRT_G = dict(collision="mrt", mrt_rates=(1.4, 1.4, 1.2), mrt_rates_g=(1.3, 1.2, 1.1, 1.25))
+BIASED = dict(grad_scheme="biased2")
+
+
 # name, workload, storage, kernel, steps
 STEP_CASES = [
     ("2d_tiled_fp32_ragged_walls", lambda: _film(100, 70), "fp32", "tiled", 12),
@@ -35,6 +46,17 @@ STEP_CASES = [
     ("3d_tiled_fp16_tiny_z", lambda: _film3d(9, 9, 5, 2.0), "fp16", "tiled", 6),
     ("3d_tma_fp32_ragged", lambda: _film3d(44, 13, 37, 12.0), "fp32", "tma", 6),
     ("3d_tma_fp16_z_blocks", lambda: _film3d(64, 24, 70, 20.0), "fp16", "tma", 6),
+    # the separately instantiated collision and gradient options
+    ("2d_tiled_biased_ragged_walls", lambda: _opt(_film(100, 70), **BIASED), "fp32", "tiled", 12),
+    ("2d_tiled_biased_one_cell_axis", lambda: _opt(W.stefan_1d(nx=40, ny=1), **BIASED), "fp16", "tiled", 12),
+    ("3d_tiled_biased_ragged", lambda: _opt(_film3d(44, 13, 37, 12.0), **BIASED), "fp32", "tiled", 6),
+    ("3d_tiled_biased_tiny_z", lambda: _opt(_film3d(9, 9, 5, 2.0), **BIASED), "fp32", "tiled", 6),
+    ("2d_tiled_mrt_ragged", lambda: _opt(_film(100, 70), **MRT_G), "fp32", "tiled", 12),
+    ("2d_tiled_mrt_periodic", lambda: _opt(W.droplet_2d(48, 12.0, T_offset=0.05), **MRT_G), "fp16", "tiled", 12),
+    ("2d_tma_mrt_ragged_y", lambda: _opt(_film(96, 83), **MRT_G), "fp32", "tma", 12),
+    ("2d_tiled_trt_ragged", lambda: _opt(_film(100, 70), **TRT), "bf16", "tiled", 12),
+    ("3d_tma_trt_ragged", lambda: _opt(_film3d(44, 13, 37, 12.0), **TRT), "fp32", "tma", 6),
+    ("3d_tiled_trt_fp16", lambda: _opt(_film3d(44, 13, 37, 12.0), **TRT), "fp16", "tiled", 6),
 ]
 
 # name, grid size, storage, velocity factor, reversal period, steps
@@ -78,6 +100,23 @@ def run_adjoint_case():
     return np.concatenate([[J, g["L"], g["M_phi"], g["sigma"]], g["T0"].double().cpu().numpy().ravel()])
 
 
+def run_noalloc_case():
+    """The allocation-free sums on a ragged size (not a multiple of the
+    256-cell block)."""
+    import ctypes
+    from paper_2003_06342_b300 import _binding as B
+    n = 100003
+    g = torch.Generator().manual_seed(7)
+    phi = torch.rand(n, generator=g, dtype=torch.float32).cuda()
+    T = (1.0 + 0.1 * torch.rand(n, generator=g, dtype=torch.float32)).cuda()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    B.check(B.lib.lbm_field_sums_noalloc(ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(T.data_ptr()), n,
+                                         10.0, 1.0, 1.0, 1.0, ctypes.c_void_p(out.data_ptr()), None),
+            "lbm_field_sums_noalloc")
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
 def run_all():
     out = {}
     for name, make, storage, kernel, steps in STEP_CASES:
@@ -85,6 +124,7 @@ def run_all():
     for name, n, storage, speed, period, steps in CAC_CASES:
         out[name] = run_cac_case(n, storage, speed, period, steps)
     out["adjoint"] = run_adjoint_case()
+    out["noalloc"] = run_noalloc_case()
     return out
 
 

@@ -54,3 +54,12 @@ def test_adjoint_kernels_checked(debug_results):
     dbg = debug_results["adjoint"]
     assert np.all(np.isfinite(dbg))
     assert np.allclose(rel, dbg, rtol=1e-6, atol=1e-12 * np.abs(rel).max())
+
+
+def test_noalloc_sums_ragged_both_builds(debug_results):
+    """The allocation-free sums on a ragged size in both builds.  Its kernel
+    has no handle and so no status word: its only indexed loads sit behind the
+    guard c < n, and this case checks that a ragged last block gives the same
+    FP64 sums (fixed summation order) in both builds."""
+    rel = BC.run_noalloc_case()
+    assert np.array_equal(rel, debug_results["noalloc"])

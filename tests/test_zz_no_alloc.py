@@ -54,3 +54,18 @@ def test_noalloc_rejects_oversize_and_bad_args():
     assert B.lib.lbm_field_sums_noalloc(p, p, 16777216 + 1, 1.0, 1.0, 1.0, 1.0, o, None) == B.LBM_ENOMEM
     assert B.lib.lbm_field_sums_noalloc(p, p, 0, 1.0, 1.0, 1.0, 1.0, o, None) == B.LBM_EINVAL
     assert B.lib.lbm_field_sums_noalloc(None, p, 4, 1.0, 1.0, 1.0, 1.0, o, None) == B.LBM_EINVAL
+
+
+def test_noalloc_at_the_cell_limit():
+    """16,777,216 cells, the size that fills the whole static array: with
+    phi = 1 and T = 0 both sums are exact in FP64 (mass = n, enthalpy =
+    n rho_g L)."""
+    n = 16777216
+    phi = torch.ones(n, dtype=torch.float32, device="cuda")
+    T = torch.zeros(n, dtype=torch.float32, device="cuda")
+    params = dict(rho_l=10.0, rho_g=2.0, Cp=1.0, L=0.75)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        m, e = _noalloc_sums(dict(phi=phi, T=T), params, stream)
+        assert m == float(n)
+        assert e == float(n) * 2.0 * 0.75
