@@ -23,7 +23,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbmpf.so")
 LIB_DEBUG = os.path.join(LIBDIR, "liblbmpf_debug.so")
 SOURCES = ["api.cu", "lbm2d.cu", "lbm3d.cu", "reduce.cu", "noalloc.cu", "adjoint2d.cu", "lbm2d_tma.cu",
-           "lbm3d_tma.cu", "cac2d.cu", "cac3d.cu", "health.cu"]
+           "lbm3d_tma.cu", "cac2d.cu", "cac3d.cu", "health.cu", "columns.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

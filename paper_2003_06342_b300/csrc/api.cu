@@ -800,6 +800,35 @@ int lbm_adjoint_init(lbm_handle *h, const lbm_fields *init, const void *adj0, fl
                                          (const float *)adj0, dT0, d_dparams, h->dp, h->stream));
 }
 
+int lbm_columns_bytes(const lbm_handle *h, int32_t ncols, size_t *bytes) {
+    if (!h || !bytes || ncols < 1 || ncols > h->grid.nx) return LBM_EINVAL;
+    const long long cells = (long long)ncols * h->grid.ny * h->grid.nz;
+    *bytes = columns_pop_bytes(cells, h->Qtot, h->elem) + 2 * (size_t)cells * sizeof(float);
+    return LBM_OK;
+}
+
+static int columns(lbm_handle *h, int32_t x0, int32_t ncols, void *buf, bool pack) {
+    if (!h || !buf || ncols < 1 || x0 < 0 || x0 > h->grid.nx - ncols) return LBM_EINVAL;
+    if (h->params.model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
+    if ((uintptr_t)buf % 16 != 0) return LBM_EINVAL;
+    const long long rows = (long long)h->grid.ny * h->grid.nz;
+    cudaError_t e;
+    switch (h->params.storage) {
+    case LBM_STORE_FP32: e = launch_columns<float>(h->pops[h->cur], h->phi_prev, h->q[h->cur], buf, x0, ncols, h->grid.nx, rows, (long long)h->N, h->Qf, h->Qtot, pack, h->stream); break;
+    case LBM_STORE_FP16: e = launch_columns<__half>(h->pops[h->cur], h->phi_prev, h->q[h->cur], buf, x0, ncols, h->grid.nx, rows, (long long)h->N, h->Qf, h->Qtot, pack, h->stream); break;
+    default: e = launch_columns<__nv_bfloat16>(h->pops[h->cur], h->phi_prev, h->q[h->cur], buf, x0, ncols, h->grid.nx, rows, (long long)h->N, h->Qf, h->Qtot, pack, h->stream); break;
+    }
+    return cuda_status(e);
+}
+
+int lbm_pack_columns(lbm_handle *h, int32_t x0, int32_t ncols, void *dst) {
+    return columns(h, x0, ncols, dst, true);
+}
+
+int lbm_unpack_columns(lbm_handle *h, int32_t x0, int32_t ncols, const void *src) {
+    return columns(h, x0, ncols, const_cast<void *>(src), false);
+}
+
 void lbm_destroy(lbm_handle *h) { delete h; }
 
 }  // extern "C"

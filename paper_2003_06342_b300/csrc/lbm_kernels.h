@@ -71,6 +71,15 @@ cudaError_t launch_init2d(const float *phi0, const float *T0, const float *ux0, 
                           const DevParams &P, cudaStream_t st);
 cudaError_t launch_streammap2d(int32_t *src, int8_t *kind, const DevParams &P, cudaStream_t st);
 
+// column blocks of the state (columns.cu): copy the populations, phi^{n-1}
+// and the lagged source of columns [x0, x0 + ncols) (every y and z; rows =
+// ny nz) to (pack) or from (unpack) buf: Qtot planes of rows x ncols stored
+// values, padded to 16 bytes, then two planes of rows x ncols floats
+size_t columns_pop_bytes(long long cells, int Qtot, size_t elem);
+template <typename S>
+cudaError_t launch_columns(void *pops, float *phi_prev, float *q, void *buf, int x0, int ncols, int nx,
+                           long long rows, long long N, int Qf, int Qtot, bool pack, cudaStream_t st);
+
 // reductions (reduce.cu): sum nblocks (a, b) pairs into out[0..1]
 cudaError_t launch_final_sum2(const double *partial, int nblocks, double *out, cudaStream_t st);
 // float -> float copy with optional double conversion helpers

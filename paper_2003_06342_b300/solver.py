@@ -238,6 +238,30 @@ class Solver:
                                     1 if buf.is_cuda else 0), "lbm_set_state")
         return self
 
+    def columns_bytes(self, ncols):
+        n = ctypes.c_size_t()
+        B.check(B.lib.lbm_columns_bytes(self._h, int(ncols), ctypes.byref(n)), "lbm_columns_bytes")
+        return n.value
+
+    def pack_columns(self, x0, ncols, out=None):
+        """The stored state of columns [x0, x0 + ncols) as a uint8 CUDA tensor
+        (queued on the solver's stream)."""
+        nb = self.columns_bytes(ncols)
+        if out is None:
+            out = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        B.check(B.lib.lbm_pack_columns(self._h, int(x0), int(ncols), ctypes.c_void_p(out.data_ptr())),
+                "lbm_pack_columns")
+        return out
+
+    def unpack_columns(self, x0, ncols, buf):
+        """Overwrite columns [x0, x0 + ncols) of the state with a block from
+        pack_columns (a uint8 CUDA tensor of columns_bytes(ncols) bytes)."""
+        if buf.numel() < self.columns_bytes(ncols) or not buf.is_cuda:
+            raise ValueError("unpack_columns needs a CUDA buffer of columns_bytes(ncols) bytes")
+        B.check(B.lib.lbm_unpack_columns(self._h, int(x0), int(ncols), ctypes.c_void_p(buf.data_ptr())),
+                "lbm_unpack_columns")
+        return self
+
     def stream_map(self, which=0):
         Q = self.Qf if which == 0 else self.Qg
         src = torch.empty((Q, self.cells), dtype=torch.int32, device=self.device)
