@@ -237,14 +237,20 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
             const float seq = Td * G + Tref * Gw;
             // s
             l_s[i] = a_s * ls[i];
-            l_om_s += (-s[i] + seq) * ls[i];
+            // the non-equilibrium parts below are small differences of
+            // values of size w_i: their weight products are formed as the
+            // forward step forms them (weighted(), no bias from the float
+            // weights)
+            l_om_s += (weighted<L>(i, fmaf(T, poly, Td)) - s[i]) * ls[i];
             const float l_seq = om_s * ls[i];
             l_bsw += w * ls[i];
             l_Td += G * l_seq;
             float l_G = Td * l_seq, l_Gw = Tref * l_seq;
             // f
             l_f[i] = a_f * lf[i];
-            l_om_f += (-f[i] + feq - 0.5f * fS) * lf[i];
+            l_om_f += (weighted<L>(i, fmaf(rcs2, poly, p) - 0.5f * fmaf(poly, eA - uA,
+                                                                     fmaf(1.0f + poly, eB - uB, pf)))
+                       - f[i]) * lf[i];
             const float l_feq = om_f * lf[i], l_fS = b_f * lf[i];
             l_Gw += (eA - uA) * l_fS;
             l_G += (eB - uB) * l_fS;
@@ -259,7 +265,8 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
             float l_poly = w * rcs2 * l_feq;
             // g
             l_g[i] = a_g * lg[i];
-            l_om_g += (-g[i] + geqd - 0.5f * Sg) * lg[i];
+            l_om_g += (weighted<L>(i, fmaf(ph, poly, phd) - 0.5f * (i == 0 ? q : fmaf(iface, en, q)))
+                       - g[i]) * lg[i];
             l_phd += om_g * G * lg[i];
             l_G += om_g * phd * lg[i];
             l_Gw += om_g * gref * lg[i];

@@ -128,3 +128,77 @@ def test_segment_calls_match_single_steps():
     torch.cuda.synchronize()
     assert torch.equal(res, l1)
     assert torch.allclose(d1, d2, rtol=1e-12, atol=0.0)
+
+
+# Grids that span several tiles of the reverse kernel (32 x 4 cells) in both
+# directions, step counts that the checkpoint interval does not divide, and
+# targets that differ from the initial phase field.
+MULTI_TILE_CASES = [
+    ("film_walls_96x40", lambda: W.film_boiling_2d(96, 40, rho_ratio=5.0, y0=13.0, amplitude=1.5,
+                                                   phi_wall=(1.0, 0.0), theta_I=0.05),
+     30, 7, lambda phi: np.roll(phi, 3, axis=1)),
+    ("droplet_periodic_80", lambda: W.droplet_2d(80, 14.0, T_offset=0.04, T_noise=0.01, corr_len=6.0),
+     30, 8, lambda phi: np.roll(phi, (2, 3), axis=(0, 1))),
+]
+
+
+def _compare(g, g_ref, J, J_ref, tol=TOL, J_tol=1e-4):
+    print("J", J, J_ref, {k: (g[k], g_ref[k]) for k in ("L", "M_phi", "sigma")})
+    for k in ("L", "M_phi", "sigma"):
+        assert abs(g[k] - g_ref[k]) <= tol * abs(g_ref[k]) + 1e-12, (k, g[k], g_ref[k])
+    dT = g["T0"].double().cpu().numpy()
+    dT_ref = g_ref["T0"].numpy()
+    err = np.abs(dT - dT_ref).max() / np.abs(dT_ref).max()
+    assert err <= tol, err
+    assert abs(J - J_ref) <= J_tol * abs(J_ref), (J, J_ref)
+    return err
+
+
+@pytest.mark.parametrize("name,make,steps,K,target", MULTI_TILE_CASES, ids=[c[0] for c in MULTI_TILE_CASES])
+def test_gpu_adjoint_multi_tile_matches_oracle(name, make, steps, K, target):
+    from paper_2003_06342_b300.adjoint import gradients
+    w = make()
+    tgt = target(w.phi0)
+    G = M.Grid(w.n, w.periodic)
+    J_ref, g_ref = A.gradients(w.phi0, w.T0, w.params, G, steps, tgt, p0=w.p0, segment=10)
+    J, g = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, tgt, steps, K=K, p0=w.p0)
+    err = _compare(g, g_ref, J, J_ref)
+    print(name, {k: (g[k], g_ref[k]) for k in ("L", "M_phi", "sigma")}, "T0 rel err", err)
+
+
+def test_gpu_adjoint_multi_tile_matches_central_differences():
+    """The 96 x 40 walled film: the CUDA gradients against central
+    differences of J on the FP64 oracle's forward map."""
+    from paper_2003_06342_b300.adjoint import gradients
+    name, make, steps, K, target = MULTI_TILE_CASES[0]
+    w = make()
+    tgt = target(w.phi0)
+    G = M.Grid(w.n, w.periodic)
+    J, g = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, tgt, steps, K=K, p0=w.p0)
+    for k in ("L", "M_phi", "sigma"):
+        h = 1e-5 * abs(w.params[k])
+        fd = A.central_difference(w.phi0, w.T0, w.params, G, steps, tgt, k, h, p0=w.p0)
+        assert abs(g[k] - fd) <= TOL * abs(fd), (k, g[k], fd)
+    d = np.random.Generator(np.random.PCG64(12)).standard_normal(w.T0.shape)
+    fd = A.central_difference(w.phi0, w.T0, w.params, G, steps, tgt, "T0", 1e-4, direction=d, p0=w.p0)
+    ad = float((g["T0"].double().cpu().numpy() * d).sum())
+    assert abs(ad - fd) <= TOL * abs(fd), (ad, fd)
+
+
+def test_gpu_adjoint_reduced_droplet_job():
+    """The evaporating-droplet gradient job at reduced size: 128^2 periodic
+    box, radius 10, 200 steps, checkpoint every 20, against a target
+    displaced by two cells.  GPU gradients within 1e-4 relative of the
+    oracle's reverse mode.  (With the large job's target, a run with L x 1.05,
+    M_phi x 0.95 and sigma x 1.1, the misfit at this size is only ~1e-3 per
+    interface cell, so the FP32 forward trajectory alone, ~1e-6 from the FP64
+    one, moves J and its gradients by several 1e-4.)"""
+    from paper_2003_06342_b300.adjoint import gradients
+    w = W.droplet_2d(128, 10.0, seed=3, corr_len=4.0)
+    steps = 200
+    G = M.Grid(w.n, w.periodic)
+    tgt = np.roll(w.phi0, 2, axis=1)
+    J_ref, g_ref = A.gradients(w.phi0, w.T0, w.params, G, steps, tgt, segment=20)
+    J, g = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, tgt, steps, K=20)
+    err = _compare(g, g_ref, J, J_ref)
+    print("droplet 128", {k: (g[k], g_ref[k]) for k in ("L", "M_phi", "sigma")}, "T0 rel err", err)
