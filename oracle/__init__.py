@@ -18,11 +18,13 @@ lattice       D2Q9 / D3Q7 / D3Q19 tables (Sec. 3, lattice definitions).
 model         one time step, initialisation, moments, streaming map and the
               global reductions (Sec. 2 model, Sec. 3 schemes, App. C).
 closed_forms  Stefan solution (Sec. 4.2), layered Poiseuille (Sec. 4.1),
-              Laplace law, coefficient A (App. B), film-boiling numbers (Sec. 5).
+              Laplace law, coefficient A (App. B).
 adjoint       reverse-mode gradient of a final-time phase-field misfit, by
               torch autograd through ``model.step`` (no hand derivation).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test except the
 fully coupled film-boiling trajectory, whose parity is pinned only through its
-components and invariants (the paper prints no field values for it).
+components and invariants (the paper prints no field values for it): phase
+mass balance with the source on, the enthalpy invariant of the temperature
+scheme, the energy sum's hand value, stationarity of a flat interface.
 """
