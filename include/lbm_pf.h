@@ -355,6 +355,17 @@ int lbm_set_velocity(lbm_handle *h, const lbm_fields *u, double period);
 int lbm_field_sums_noalloc(const float *phi, const float *T, int64_t n_cells, double rho_l,
                            double rho_g, double Cp, double L, double *d_out, void *stream);
 
+/* Test hook of the bounded waits (no counterpart in the paper).  Every
+ * mbarrier wait of the TMA-staged step kernels polls at most 4,194,304 times
+ * before the block gives up, waits for the bulk copies it has issued,
+ * records the timeout in the handle's status word and returns; lbm_sync then
+ * reports LBM_ETIMEOUT.  This call sets the poll limit of the first wait of
+ * every block (the later waits keep the default) on the current device and
+ * for the whole process: 0 makes every block give up at once, which is how
+ * the timeout path is tested without a stalled copy; a negative value
+ * restores the default.  Error: LBM_ECUDA. */
+int lbm_set_first_wait_limit(int32_t polls);
+
 /* Column blocks of the state, for a slab domain decomposition along x (the
  * paper's implementation section: one sub-domain per GPU, neighbouring
  * sub-domains trade ghost layers every time step).  A block is the complete

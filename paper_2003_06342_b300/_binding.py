@@ -113,6 +113,7 @@ SIGNATURES = {
     "lbm_step_record": (ctypes.c_int, [H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t]),
     "lbm_set_velocity": (ctypes.c_int, [H, P(lbm_fields), ctypes.c_double]),
     "lbm_set_health_check": (ctypes.c_int, [H, ctypes.c_int32, ctypes.c_float]),
+    "lbm_set_first_wait_limit": (ctypes.c_int, [ctypes.c_int32]),
     "lbm_columns_bytes": (ctypes.c_int, [H, ctypes.c_int32, P(ctypes.c_size_t)]),
     "lbm_pack_columns": (ctypes.c_int, [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "lbm_unpack_columns": (ctypes.c_int, [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),

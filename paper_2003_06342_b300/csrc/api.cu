@@ -800,6 +800,12 @@ int lbm_adjoint_init(lbm_handle *h, const lbm_fields *init, const void *adj0, fl
                                          (const float *)adj0, dT0, d_dparams, h->dp, h->stream));
 }
 
+int lbm_set_first_wait_limit(int32_t polls) {
+    if (set_first_wait_limit2d(polls) != cudaSuccess) return LBM_ECUDA;
+    if (set_first_wait_limit3d(polls) != cudaSuccess) return LBM_ECUDA;
+    return LBM_OK;
+}
+
 int lbm_columns_bytes(const lbm_handle *h, int32_t ncols, size_t *bytes) {
     if (!h || !bytes || ncols < 1 || ncols > h->grid.nx) return LBM_EINVAL;
     const long long cells = (long long)ncols * h->grid.ny * h->grid.nz;

@@ -90,10 +90,22 @@ __device__ __forceinline__ float staged_phid2(const unsigned char *gstage, int k
     return fmaf(0.5f, ((const float *)(gstage + Gm::OFF_Q))[k], set_sum2d<S>(v, P.set_isc[1]));
 }
 
+// Polls allowed to the first mbarrier wait of every block (all later waits
+// take WAIT_LIMIT).  The default is WAIT_LIMIT; the timeout test lowers it to
+// zero through set_first_wait_limit2d, so that every block gives up at its
+// first stage, waits for the copies it issued, records the timeout in the
+// status word and returns (no copy is left in flight).
+static __device__ int first_wait_limit = WAIT_LIMIT;
+
+cudaError_t set_first_wait_limit2d(int polls) {
+    const int v = polls < 0 ? WAIT_LIMIT : polls;
+    return cudaMemcpyToSymbol(first_wait_limit, &v, sizeof(int));
+}
+
 struct StageBits {
     uint32_t par = 0u, pend = 0u;     // parity awaited next / copies in flight, per barrier
-    __device__ __forceinline__ bool wait(uint64_t *bars, int b) {
-        const bool ok = mbar_wait_bounded(&bars[b], (par >> b) & 1u);
+    __device__ __forceinline__ bool wait(uint64_t *bars, int b, int limit = WAIT_LIMIT) {
+        const bool ok = mbar_wait_bounded(&bars[b], (par >> b) & 1u, limit);
         if (ok) { par ^= 1u << b; pend &= ~(1u << b); }
         return ok;
     }
@@ -211,7 +223,7 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
         for (int k = 0; k < Gm::NFS; ++k)
             if (k < nc) issue_fs2<S>(fs_base + k * Gm::FS_STAGE, &barF[k], maps, par, x0, ybeg + k * TY);
     }
-    bool ok = G.wait(barG, 0);
+    bool ok = G.wait(barG, 0, first_wait_limit);
 
     int fb = 0, gb = 0;                     // stages of chunk c
     for (int c = 0; c < nc; ++c) {

@@ -86,12 +86,24 @@ __device__ __forceinline__ float staged_phid(const unsigned char *gstage, int ow
     return fmaf(0.5f, ((const float *)(gstage + Gm::OFF_Q))[own], set_sum7<S>(v, P.set_isc[1]));
 }
 
+// Polls allowed to the first mbarrier wait of every block (all later waits
+// take WAIT_LIMIT).  The default is WAIT_LIMIT; the timeout test lowers it to
+// zero through set_first_wait_limit3d, so that every block gives up at its
+// first stage, waits for the copies it issued, records the timeout in the
+// status word and returns (no copy is left in flight).
+static __device__ int first_wait_limit = WAIT_LIMIT;
+
+cudaError_t set_first_wait_limit3d(int polls) {
+    const int v = polls < 0 ? WAIT_LIMIT : polls;
+    return cudaMemcpyToSymbol(first_wait_limit, &v, sizeof(int));
+}
+
 // Stage bookkeeping: bit b of `par_*` = parity awaited next on barrier b,
 // bit b of `pend_*` = copies issued on barrier b and not yet seen complete.
 struct StageSet {
     uint32_t par = 0u, pend = 0u;
-    __device__ __forceinline__ bool wait(uint64_t *bars, int b) {
-        const bool ok = mbar_wait_bounded(&bars[b], (par >> b) & 1u);
+    __device__ __forceinline__ bool wait(uint64_t *bars, int b, int limit = WAIT_LIMIT) {
+        const bool ok = mbar_wait_bounded(&bars[b], (par >> b) & 1u, limit);
         if (ok) { par ^= 1u << b; pend &= ~(1u << b); }
         return ok;
     }
@@ -219,7 +231,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
 
     // window: plane zbeg - 1 with plain loads, plane zbeg from its g stage
     fill_plane<S, XY_GEN>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
-    bool ok = G.wait(barG, 0);
+    bool ok = G.wait(barG, 0, first_wait_limit);
     fill_plane<S, XY>(sphi, (zbeg + 1) % 3, zbeg, true, true, staged_phid<S>(g_base, tid, P), pin,
                        q_in, x0, y0, tid, tx, ty, P);
     if (PRE && zbeg + 1 < nz)

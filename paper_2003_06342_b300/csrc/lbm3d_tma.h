@@ -25,6 +25,10 @@ int make_tma_maps3d(TmaMaps3d *M, const DevParams &P, int elem_bytes, void *cons
 // Set the kernel's dynamic shared-memory limit; resident blocks per SM (0 on failure).
 int tma3d_blocks_per_sm(int elem_bytes);
 
+// Polls of the first mbarrier wait of every block (negative: the default
+// WAIT_LIMIT), on the current device; the timeout test's hook.
+cudaError_t set_first_wait_limit3d(int polls);
+
 template <typename S>
 cudaError_t launch_step3d_tma(const TmaMaps3d &M, int par, const void *pin, void *pout,
                               float *phi_prev, const float *q_in, float *q_out, int *err,
