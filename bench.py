@@ -490,10 +490,10 @@ def run_device(args, world, rank, local):
 # adjoint scalars
 ADJ_SURVEY_BYTES_PER_CELL = 352
 # what the two-kernel adjoint step moves: kernel A reads the state (29
-# planes), the next adjoint state (29) and writes the adjoint state (29) and
-# nine stencil contributions; kernel B reads those contributions and updates
-# 10 adjoint planes
-ADJ_BYTES_PER_CELL = 4 * (29 + 29 + 29 + 9) + 4 * (9 + 10 + 10)
+# planes) and the next adjoint state (30: 29 planes and the phi adjoint) and
+# writes the adjoint state's 29 planes and four stencil-contribution planes;
+# kernel B reads those four and writes the phi adjoint
+ADJ_BYTES_PER_CELL = 4 * (29 + 30 + 29 + 4) + 4 * (4 + 1)
 
 
 def adjoint_variant(dev, peak, steps=2000, K=100):
@@ -518,7 +518,11 @@ def adjoint_variant(dev, peak, steps=2000, K=100):
     J, g = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, target, steps, K=K, device=dev)
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
-    # the adjoint-step kernels alone, on one state
+    job_name, job_cells = w.name, w.cells
+    # the adjoint-step kernels alone, on one state of the same droplet at
+    # 2048 x 2048 (4.2 M cells, 1.6 GB moved per reverse step: larger than L2)
+    torch.cuda.empty_cache()
+    w = W.c4_droplet(2048)
     s = Solver(w.n, w.periodic, w.params, device=dev)
     s.init(w.phi0, w.T0)
     state = s.get_state().clone()
@@ -540,8 +544,9 @@ def adjoint_variant(dev, peak, steps=2000, K=100):
     e1.record(s.stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / reps
-    return {"workload": w.name + " (2000 steps, checkpoint every 100)",
-            "MLUPS": w.cells * steps / dt / 1e6, "seconds": dt,
+    return {"workload": job_name + " (2000 steps, checkpoint every 100)",
+            "MLUPS": job_cells * steps / dt / 1e6, "seconds": dt,
+            "reverse_step_workload": w.name,
             "what": "forward with checkpoints + reverse with segment recomputation, per forward step",
             "J": J, "dJ_dL": g["L"], "dJ_dM_phi": g["M_phi"], "dJ_dsigma": g["sigma"],
             "dJ_dT0_norm": float(g["T0"].norm()),

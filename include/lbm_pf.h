@@ -287,11 +287,16 @@ int lbm_sync(lbm_handle *h);
  * sources of Sec. 3; the loss is J = 1/2 sum (phi^N - phi_target)^2).
  * States are device buffers in the lbm_get_state layout (float32: the nine
  * (f_i, s_i) pair planes, 2N values each with f_i at 2(iN + x) and s_i at
- * 2(iN + x) + 1, the nine g planes, phi^{n-1}, lagged source); an adjoint
- * state has the same layout and holds dJ/d(stored value).  Other lattices and storages return
- * LBM_EUNSUPPORTED. */
+ * 2(iN + x) + 1, the nine g planes, phi^{n-1}, lagged source).  An adjoint
+ * state has the same 29 planes followed by a 30th, lambda_phi = dJ/dphi^n:
+ * the derivative of J with respect to a stored g_i(x) is plane 9 + i plus
+ * lambda_phi(x), with respect to the lagged source(x) plane 28 plus
+ * lambda_phi(x)/2, with respect to every other stored value its own plane
+ * (phi^n = sum_i g_i + q^{n-1}/2 is kept as one term instead of being spread
+ * over ten planes).  Other lattices and storages return LBM_EUNSUPPORTED. */
 
-/* Bytes of one adjoint state and of the per-step scratch (9 planes). */
+/* Bytes of one adjoint state (30 planes of N floats) and of the per-step
+ * scratch (4 planes). */
 int lbm_adjoint_bytes(const lbm_handle *h, size_t *adj_state_bytes, size_t *scratch_bytes);
 
 /* Seed: adj = dJ/dX^N for the state X^N; adds J to *d_J (device double). */

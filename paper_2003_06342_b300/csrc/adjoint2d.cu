@@ -10,12 +10,18 @@
 //      a bounced link maps back with +1 for f and -1 for the anti-bounce-back
 //      sets g, s); back-propagate by hand through the collision, sources,
 //      production rate, moments, closures and stencils.  Writes the adjoint
-//      of x's own populations, of phi^{n-1} and of q^{n-1}, plus the nine
-//      stencil contributions c_j(x) = dJ/dphi^n(x + e_j), and accumulates
+//      of x's own populations, of phi^{n-1} and of q^{n-1}, plus four planes
+//      that give every stencil contribution c_j(x) = dJ/dphi^n(x + e_j)
+//      (the own-cell part c_0 and the adjoints of grad phi and lap phi;
+//      c_j = 3 w_j e_j.l_grad + 6 w_j l_lap for j >= 1), and accumulates
 //      dJ/dL, dJ/dM_phi, dJ/dsigma (FP64 block sums, one atomic per block).
 //   B. per cell y: lambda_phi(y) = sum_j c_j(y - e_j) (transpose of the
-//      stencil gather), then the transpose of phi^n = sum_i g_i + q/2:
-//      every g_i(y) gains lambda_phi(y), q^{n-1}(y) gains lambda_phi(y)/2.
+//      stencil gather) into plane 29 of the adjoint state.
+// The transpose of phi^n = sum_i g_i + q^{n-1}/2 is left implicit: the
+// adjoint of g_i(y) is plane 9 + i plus lambda_phi(y), that of q^{n-1}(y)
+// plane 28 plus lambda_phi(y)/2, and each reader (kernel A of the next
+// reverse step when it pulls, the init kernel) adds the share itself, so B
+// moves 20 bytes per cell instead of rewriting ten adjoint planes.
 // The terminal kernel seeds Lambda^N for J = 1/2 sum (phi^N - phi_target)^2,
 // and the init kernel maps Lambda^0 to dJ/dT_0 (and the init's share of
 // dJ/dL, dJ/dsigma) through the barred-equilibrium initialisation.
@@ -38,19 +44,31 @@ __device__ __forceinline__ size_t st_idx(int k, size_t c, size_t N) {
                                                                               : (size_t)k * N + c;
 }
 
+// plane of an adjoint state holding lambda_phi = dJ/dphi^n: the adjoint of a
+// stored g_i adds it, that of the lagged source half of it
+constexpr int LPHI = 29;
+
 // the (f_i, s_i) pair of cell c as one 8-byte load
 __device__ __forceinline__ float2 pair_at(const float *__restrict__ buf, int i, size_t c, size_t N) {
     return __ldg(reinterpret_cast<const float2 *>(buf) + ((size_t)i * N + c));
+}
+
+// phi - phi_ref from a cell's nine g deviations and its lagged source
+__device__ __forceinline__ float phid_sum(const float g[9], float q) {
+    float v = g[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) v = __fadd_rn(v, g[i]);
+    return fmaf(0.5f, q, v);
 }
 
 __device__ __forceinline__ float phid_cell(const float *__restrict__ st, size_t c, size_t N,
                                            const DevParams &P) {
     // phi - phi_ref of a cell from the stored state (g planes 9..17 hold
     // deviations, the lagged source is plane 28)
-    float v = st[st_idx(9, c, N)];
+    float g[9];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) v += st[st_idx(9 + i, c, N)];
-    return v + 0.5f * st[st_idx(28, c, N)];
+    for (int i = 0; i < 9; ++i) g[i] = st[st_idx(9 + i, c, N)];
+    return phid_sum(g, st[st_idx(28, c, N)]);
 }
 
 __device__ __forceinline__ float edot2(int ex, int ey, float a, float b) {
@@ -68,8 +86,7 @@ adj_terminal2d_kernel(const float *__restrict__ st, const float *__restrict__ ta
     if (c < N) {
         const float r = phid_cell(st, c, N, P) + P.g_ref - target[c];
         for (int k = 0; k < 29; ++k) adj[st_idx(k, c, N)] = 0.0f;
-        for (int i = 0; i < 9; ++i) adj[st_idx(9 + i, c, N)] = r;
-        adj[st_idx(28, c, N)] = 0.5f * r;
+        adj[(size_t)LPHI * N + c] = r;           // dJ/dphi^N
         part = 0.5 * (double)r * (double)r;
     }
     block_sum3_atomic(part, 0.0, 0.0, J);
@@ -82,44 +99,29 @@ adj_terminal2d_kernel(const float *__restrict__ st, const float *__restrict__ ta
 // threads per SM)
 constexpr int ADJ_TY = 4;
 
-__global__ void __launch_bounds__(32 * ADJ_TY, 16 / ADJ_TY)
-adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_next,
-                    float *__restrict__ lam, float *__restrict__ cst, double *dparams,
-                    const DevParams P) {
+constexpr int ADJ_WX = 34, ADJ_WY = ADJ_TY + 2;
+
+// The reverse step of one 32 x ADJ_TY tile.  FAST: the tile and its one-cell
+// ring lie inside the grid, so no pulled link and no ring cell wraps or meets
+// a wall.  Adds the cell's dJ/dL, dJ/dM_phi, dJ/dsigma terms to dL, dM, dS.
+template <bool FAST>
+__device__ __forceinline__ void adj_a_tile(const float *__restrict__ st, const float *__restrict__ lam_next,
+                                           float *__restrict__ lam, float *__restrict__ cst,
+                                           const DevParams &P, float *sphi, int x0, int y0,
+                                           float &dL, float &dM, float &dS) {
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
-    // one 32 x ADJ_TY tile per block; phi - phi_ref of the tile and its
-    // one-cell ring in shared memory (each window value formed once, not once
-    // per neighbour)
-    constexpr int WX = 34, WY = ADJ_TY + 2;
-    __shared__ float sphi[WX * WY];
-    const int tiles_x = (nx + 31) / 32;
-    const int x0 = (int)(blockIdx.x % tiles_x) * 32, y0 = (int)(blockIdx.x / tiles_x) * ADJ_TY;
+    // phi - phi_ref of the tile and its one-cell ring in shared memory (each
+    // window value formed once, not once per neighbour)
+    constexpr int WX = ADJ_WX, WY = ADJ_WY;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < nx && y < ny;
     const size_t c = active ? (size_t)y * nx + x : 0;
-    for (int sidx = threadIdx.x; sidx < WX * WY; sidx += blockDim.x) {
-        int cx = x0 + sidx % WX - 1, cy = y0 + sidx / WX - 1;
-        if (cx > nx || cy > ny) { sphi[sidx] = 0.0f; continue; }     // beyond a ragged tile
-        const int kx = wrap_coord(cx, nx, P.periodic[0]);
-        const int ky = wrap_coord(cy, ny, P.periodic[1]);
-        sphi[sidx] = kx >= 2 ? P.phi_wall[kx - 2] - P.g_ref
-                   : (ky >= 2 ? P.phi_wall[ky - 2] - P.g_ref : phid_cell(st, (size_t)cy * nx + cx, N, P));
-    }
-    __syncthreads();
-    float dL = 0.0f, dM = 0.0f, dS = 0.0f;        // this cell's terms (FP32)
+    // the cell's own stored state first: its window slot comes from the g
+    // values it needs anyway, the ring and ragged slots from plain loads
+    float f[9], g[9], s[9], phip = 0.0f, qp = 0.0f;
     if (active) {
-        // ---------------- forward recomputation
-        float nb[9];
-        bool ghost[9];
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            nb[j] = sphi[(ty + 1 + L::ey(j)) * WX + tx + 1 + L::ex(j)];
-            int cx = x + L::ex(j), cy = y + L::ey(j);
-            ghost[j] = wrap_coord(cx, nx, P.periodic[0]) >= 2 || wrap_coord(cy, ny, P.periodic[1]) >= 2;
-        }
-        float f[9], g[9], s[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float2 fs = pair_at(st, i, c, N);
@@ -127,8 +129,75 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
             g[i] = st[st_idx(9 + i, c, N)];
             s[i] = fs.y;
         }
-        const float phip = st[st_idx(27, c, N)];
-        const float qp = st[st_idx(28, c, N)];
+        phip = st[st_idx(27, c, N)];
+        qp = st[st_idx(28, c, N)];
+        sphi[(ty + 1) * WX + tx + 1] = phid_sum(g, qp);
+    }
+    float lf[9], lg[9], ls[9], l_phip_new = 0.0f, l_q_new = 0.0f;
+    if (active) {
+        // ---------------- adjoints of the pushed values (pull of Lambda^{n+1})
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            // the adjoint of a g value at its target cell adds that cell's
+            // lambda_phi (plane LPHI)
+            if (FAST) {
+                const size_t d = c + (long long)L::ey(i) * nx + L::ex(i);
+                const float2 fs = pair_at(lam_next, i, d, N);
+                lf[i] = fs.x;
+                lg[i] = lam_next[st_idx(9 + i, d, N)] + lam_next[(size_t)LPHI * N + d];
+                ls[i] = fs.y;
+                continue;
+            }
+            int dx = x + L::ex(i), dy = y + L::ey(i);
+            const int kx = wrap_coord(dx, nx, P.periodic[0]);
+            const int ky = wrap_coord(dy, ny, P.periodic[1]);
+            if (kx >= 2 || ky >= 2) {
+                const int o = L::opp(i);
+                const float2 fs = pair_at(lam_next, o, c, N);
+                lf[i] = fs.x;
+                lg[i] = -(lam_next[st_idx(9 + o, c, N)] + lam_next[(size_t)LPHI * N + c]);
+                ls[i] = -fs.y;
+            } else {
+                const size_t d = (size_t)dy * nx + dx;
+                const float2 fs = pair_at(lam_next, i, d, N);
+                lf[i] = fs.x;
+                lg[i] = lam_next[st_idx(9 + i, d, N)] + lam_next[(size_t)LPHI * N + d];
+                ls[i] = fs.y;
+            }
+        }
+        l_phip_new = lam_next[st_idx(27, c, N)];
+        l_q_new = fmaf(0.5f, lam_next[(size_t)LPHI * N + c], lam_next[st_idx(28, c, N)]);
+
+    }
+    if (FAST) {
+        // the ring: the top and bottom rows, then the left and right columns
+        constexpr int RING = 2 * WX + 2 * ADJ_TY;
+        const int r = threadIdx.x;
+        if (r < RING) {
+            int wx, wy;
+            if (r < WX) { wx = r; wy = 0; }
+            else if (r < 2 * WX) { wx = r - WX; wy = WY - 1; }
+            else if (r < 2 * WX + ADJ_TY) { wx = 0; wy = 1 + r - 2 * WX; }
+            else { wx = WX - 1; wy = 1 + r - 2 * WX - ADJ_TY; }
+            sphi[wy * WX + wx] = phid_cell(st, (size_t)(y0 + wy - 1) * nx + (x0 + wx - 1), N, P);
+        }
+    } else
+    for (int sidx = threadIdx.x; sidx < WX * WY; sidx += blockDim.x) {
+        int cx = x0 + sidx % WX - 1, cy = y0 + sidx / WX - 1;
+        const int wx = sidx % WX, wy = sidx / WX;
+        if (wx >= 1 && wx <= 32 && wy >= 1 && wy <= ADJ_TY && cx < nx && cy < ny) continue;  // owned
+        if (cx > nx || cy > ny) { sphi[sidx] = 0.0f; continue; }     // beyond a ragged tile
+        const int kx = wrap_coord(cx, nx, P.periodic[0]);
+        const int ky = wrap_coord(cy, ny, P.periodic[1]);
+        sphi[sidx] = kx >= 2 ? P.phi_wall[kx - 2] - P.g_ref
+                   : (ky >= 2 ? P.phi_wall[ky - 2] - P.g_ref : phid_cell(st, (size_t)cy * nx + cx, N, P));
+    }
+    __syncthreads();
+    if (active) {
+        // ---------------- forward recomputation
+        float nb[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) nb[j] = sphi[(ty + 1 + L::ey(j)) * WX + tx + 1 + L::ex(j)];
         const float phd = nb[0];
         const float ph = phd + P.g_ref;
         const float nE = nb[1], nN = nb[2], nW = nb[3], nS = nb[4];
@@ -191,30 +260,6 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         const float a_s = 1.0f - om_s, b_s = 1.0f - 0.5f * om_s;
         const float Tref = P.s_ref, gref = P.g_ref;
 
-        // ---------------- adjoints of the pushed values (pull of Lambda^{n+1})
-        float lf[9], lg[9], ls[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            int dx = x + L::ex(i), dy = y + L::ey(i);
-            const int kx = wrap_coord(dx, nx, P.periodic[0]);
-            const int ky = wrap_coord(dy, ny, P.periodic[1]);
-            if (kx >= 2 || ky >= 2) {
-                const int o = L::opp(i);
-                const float2 fs = pair_at(lam_next, o, c, N);
-                lf[i] = fs.x;
-                lg[i] = -lam_next[st_idx(9 + o, c, N)];
-                ls[i] = -fs.y;
-            } else {
-                const size_t d = (size_t)dy * nx + dx;
-                const float2 fs = pair_at(lam_next, i, d, N);
-                lf[i] = fs.x;
-                lg[i] = lam_next[st_idx(9 + i, d, N)];
-                ls[i] = fs.y;
-            }
-        }
-        const float l_phip_new = lam_next[st_idx(27, c, N)];
-        const float l_q_new = lam_next[st_idx(28, c, N)];
-
         // ---------------- reverse sweep
         float l_f[9], l_g[9], l_s[9];
         float l_om_g = 0.f, l_om_f = 0.f, l_om_s = 0.f, l_bsw = 0.f, l_Td = 0.f, l_p = 0.f;
@@ -229,12 +274,7 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
             const float poly = cu * (3.0f + 4.5f * cu) - usq15;
             const float G = w + w * poly, Gw = w * poly;
             const float en = edot2(ex, ey, n0, n1);
-            const float Sg = w * (i == 0 ? q : iface * en + q);
-            const float geqd = phd * G + gref * Gw;
-            const float feq = w * (p + rcs2 * poly);
             const float eA = edot2(ex, ey, gAx, gAy), eB = edot2(ex, ey, Fx, Fy);
-            const float fS = Gw * (eA - uA) + G * (eB - uB) + w * pf;
-            const float seq = Td * G + Tref * Gw;
             // s
             l_s[i] = a_s * ls[i];
             // the non-equilibrium parts below are small differences of
@@ -380,19 +420,13 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         l_pc += P.drho * l_rho;
         if (inside) l_ph += l_pc;
         l_phd += l_ph;
-        // stencil transpose: contributions to phi^n at x + e_j
-        float cj[9];
-        cj[0] = l_phd - 24.0f * (w1 + w5) * l_lap;
-        cj[1] = 3.0f * w1 * l_gx + 6.0f * w1 * l_lap;                        // E
-        cj[3] = -3.0f * w1 * l_gx + 6.0f * w1 * l_lap;                       // W
-        cj[2] = 3.0f * w1 * l_gy + 6.0f * w1 * l_lap;                        // N
-        cj[4] = -3.0f * w1 * l_gy + 6.0f * w1 * l_lap;                       // S
-        cj[5] = 3.0f * w5 * (l_gx + l_gy) + 6.0f * w5 * l_lap;               // NE
-        cj[7] = -3.0f * w5 * (l_gx + l_gy) + 6.0f * w5 * l_lap;              // SW
-        cj[8] = 3.0f * w5 * (l_gx - l_gy) + 6.0f * w5 * l_lap;               // SE
-        cj[6] = -3.0f * w5 * (l_gx - l_gy) + 6.0f * w5 * l_lap;              // NW
-#pragma unroll
-        for (int j = 0; j < 9; ++j) cst[j * N + c] = ghost[j] ? 0.0f : cj[j];
+        // stencil transpose: the own-cell contribution to phi^n and the
+        // adjoints of grad phi and lap phi, from which kernel B forms the
+        // contribution 3 w_j e_j.(l_gx, l_gy) + 6 w_j l_lap to phi^n(x + e_j)
+        cst[c] = l_phd - 24.0f * (w1 + w5) * l_lap;
+        cst[N + c] = l_gx;
+        cst[2 * N + c] = l_gy;
+        cst[3 * N + c] = l_lap;
         // sums and moments into own populations
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -406,29 +440,66 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
         // latent heat: Lc = L / Cp (d/dL = 1/Cp), Cl = Cp / L (d/dL = -Cp/L^2)
         dL += l_Lc * P.inv_Cp - l_Cl * P.Cp_over_L2;
     }
+}
+
+__global__ void __launch_bounds__(32 * ADJ_TY, 16 / ADJ_TY)
+adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_next,
+                    float *__restrict__ lam, float *__restrict__ cst, double *dparams,
+                    const DevParams P) {
+    __shared__ float sphi[ADJ_WX * ADJ_WY];
+    const int nx = P.n[0], ny = P.n[1];
+    const int tiles_x = (nx + 31) / 32;
+    const int x0 = (int)(blockIdx.x % tiles_x) * 32, y0 = (int)(blockIdx.x / tiles_x) * ADJ_TY;
+    const bool fast = x0 >= 1 && x0 + 33 <= nx && y0 >= 1 && y0 + ADJ_TY + 1 <= ny;
+    float dL = 0.0f, dM = 0.0f, dS = 0.0f;        // this cell's terms (FP32)
+    if (fast) adj_a_tile<true>(st, lam_next, lam, cst, P, sphi, x0, y0, dL, dM, dS);
+    else adj_a_tile<false>(st, lam_next, lam, cst, P, sphi, x0, y0, dL, dM, dS);
     block_sum3f_atomic(dL, dM, dS, dparams);
 }
 
 // ------------------------------------------------------------------ step B
+// One row segment of 256 cells per block (grid: x segments, rows).  Cells
+// whose eight neighbours all lie inside the grid take fixed offsets; the
+// others wrap periodic axes and skip neighbours beyond a wall.
 __global__ void __launch_bounds__(256)
 adj_step2d_b_kernel(const float *__restrict__ cst, float *__restrict__ lam, const DevParams P) {
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
-    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    const int x = (int)(c % nx), y = (int)(c / nx);
-    float lphi = 0.0f;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    const size_t c = (size_t)y * nx + x;
+    // lambda_phi(y) = c_0(y) + sum_{j >= 1} c_j(y - e_j) over the cells
+    // y - e_j that exist (none beyond a wall; periodic axes wrap), with
+    // c_j = 3 w_j e_j.(l_gx, l_gy) + 6 w_j l_lap from the four planes of A
+    const float *lgx = cst + N, *lgy = cst + 2 * N, *llap = cst + 3 * N;
+    float lphi = cst[c];
+    if (x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny) {
+        // all eight sources exist: c_j(y - e_j) with fixed offsets; the axis
+        // and diagonal weights factored out
+        const size_t up = c + nx, dn = c - nx;
+        // sources y - e_j: e = +x -> c - 1, -x -> c + 1, +y -> dn, -y -> up
+        const float ax = __ldg(lgx + c - 1) - __ldg(lgx + c + 1);
+        const float ay = __ldg(lgy + dn) - __ldg(lgy + up);
+        const float al = (__ldg(llap + c - 1) + __ldg(llap + c + 1)) + (__ldg(llap + dn) + __ldg(llap + up));
+        // diagonals: (1,1) from dn - 1, (-1,1) from dn + 1, (-1,-1) from up + 1, (1,-1) from up - 1
+        const float dx = (__ldg(lgx + dn - 1) - __ldg(lgx + up + 1)) + (__ldg(lgx + up - 1) - __ldg(lgx + dn + 1));
+        const float dy = (__ldg(lgy + dn - 1) - __ldg(lgy + up + 1)) + (__ldg(lgy + dn + 1) - __ldg(lgy + up - 1));
+        const float dl = (__ldg(llap + dn - 1) + __ldg(llap + up + 1)) + (__ldg(llap + dn + 1) + __ldg(llap + up - 1));
+        lphi += fmaf(3.0f / 9.0f, ax + ay, fmaf(6.0f / 9.0f, al, fmaf(3.0f / 36.0f, dx + dy, (6.0f / 36.0f) * dl)));
+    } else {
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        int sx = x - L::ex(j), sy = y - L::ey(j);
-        const int kx = wrap_coord(sx, nx, P.periodic[0]);
-        const int ky = wrap_coord(sy, ny, P.periodic[1]);
-        if (kx >= 2 || ky >= 2) continue;        // no such cell
-        lphi += cst[j * N + (size_t)sy * nx + sx];
+        for (int j = 1; j < 9; ++j) {
+            int sx = x - L::ex(j), sy = y - L::ey(j);
+            const int kx = wrap_coord(sx, nx, P.periodic[0]);
+            const int ky = wrap_coord(sy, ny, P.periodic[1]);
+            if (kx >= 2 || ky >= 2) continue;        // no such cell
+            const size_t sc = (size_t)sy * nx + sx;
+            const float w = L::w(j);
+            lphi += fmaf(3.0f * w, edot2(L::ex(j), L::ey(j), __ldg(lgx + sc), __ldg(lgy + sc)),
+                         6.0f * w * __ldg(llap + sc));
+        }
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) lam[st_idx(9 + i, c, N)] += lphi;
-    lam[st_idx(28, c, N)] += 0.5f * lphi;
+    lam[(size_t)LPHI * N + c] = lphi;
 }
 
 // ------------------------------------------------------------------ init
@@ -475,14 +546,17 @@ adj_init2d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
         const float D = (ux * gx + uy * gy) + ph * q * P.kappa;
         const float rcs2 = rho * L::cs2;
         const float usq15 = 1.5f * (ux * ux + uy * uy);
-        float l_q = lam[st_idx(28, c, N)], l_Td = 0.0f, l_Lc = 0.0f, l_Fx = 0.0f, l_Fy = 0.0f;
+        // the adjoint of g_i adds lambda_phi, that of the lagged source half of it
+        const float lphi = lam[(size_t)LPHI * N + c];
+        float l_q = fmaf(0.5f, lphi, lam[st_idx(28, c, N)]), l_Td = 0.0f, l_Lc = 0.0f, l_Fx = 0.0f, l_Fy = 0.0f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float w = L::w(i);
             const float cu = edot2(L::ex(i), L::ey(i), ux, uy);
             const float poly = cu * (3.0f + 4.5f * cu) - usq15;
             const float G = w + w * poly;
-            const float lf = lam[st_idx(i, c, N)], lg = lam[st_idx(9 + i, c, N)], ls = lam[st_idx(18 + i, c, N)];
+            const float lf = lam[st_idx(i, c, N)], lg = lam[st_idx(9 + i, c, N)] + lphi;
+            const float ls = lam[st_idx(18 + i, c, N)];
             // f_i = feq - fS/2, fS contains G (e - u).F + w rcs2 q kappa
             l_Fx += -0.5f * G * ((float)L::ex(i) - ux) * lf;
             l_Fy += -0.5f * G * ((float)L::ey(i) - uy) * lf;
@@ -519,9 +593,8 @@ cudaError_t launch_adj_terminal2d(const float *st, const float *target, float *a
 cudaError_t launch_adj_step2d(const float *st, const float *lam_next, float *lam, float *cst,
                               double *dparams, const DevParams &P, cudaStream_t stream) {
     const int tiles = ((P.n[0] + 31) / 32) * ((P.n[1] + ADJ_TY - 1) / ADJ_TY);
-    const int nb = (int)((P.N + 255) / 256);
     adj_step2d_a_kernel<<<tiles, 32 * ADJ_TY, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
-    adj_step2d_b_kernel<<<nb, 256, 0, stream>>>(cst, lam, P);
+    adj_step2d_b_kernel<<<dim3((P.n[0] + 255) / 256, P.n[1]), 256, 0, stream>>>(cst, lam, P);
     return cudaGetLastError();
 }
 

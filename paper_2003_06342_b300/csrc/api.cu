@@ -727,8 +727,9 @@ static int adjoint_supported(const lbm_handle *h) {
 int lbm_adjoint_bytes(const lbm_handle *h, size_t *adj_state_bytes, size_t *scratch_bytes) {
     const int r = adjoint_supported(h);
     if (r != LBM_OK) return r;
-    if (adj_state_bytes) *adj_state_bytes = (size_t)(h->Qtot + 2) * h->N * sizeof(float);
-    if (scratch_bytes) *scratch_bytes = (size_t)9 * h->N * sizeof(float);
+    // the state's 29 planes and lambda_phi
+    if (adj_state_bytes) *adj_state_bytes = (size_t)(h->Qtot + 3) * h->N * sizeof(float);
+    if (scratch_bytes) *scratch_bytes = (size_t)4 * h->N * sizeof(float);   // four stencil planes
     return LBM_OK;
 }
 
