@@ -300,13 +300,10 @@ __device__ __forceinline__ void mrt_correction2d(const float dd[9], float de, fl
 // as the BGK update plus -(M^-1 diag(s - om) M d)_i (mrt_correction2d).
 // BIASED: the gradient of Eq. Grad from the second-order biased difference
 // (the window then holds two rings around the tile).
-template <typename S, bool FAST, int COLL = COLL_BGK, bool BIASED = false>
-__device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const float f[9],
-                                              const float g[9], const float s[9], float phip,
-                                              float qp, int x, int y, size_t c,
-                                              S *__restrict__ pout, float *__restrict__ phi_prev,
-                                              float *__restrict__ q_out, const DevParams &P,
-                                              const Planes2d<S> &PL) {
+template <typename S, int COLL, bool BIASED, class Sink>
+__device__ __forceinline__ void cell_core2d(const float *sp, int pitch, const float f[9],
+                                            const float g[9], const float s[9], float phip,
+                                            float qp, const DevParams &P, Sink &sink) {
     constexpr bool TRT = COLL == COLL_TRT, MRT = COLL == COLL_MRT;
     // stencils, pair-folded: each (i, opposite) pair of Eqs. Grad and
     // Laplacian contributes w_i e_i (phi_i - phi_i') and 2 w_i (phi_i + phi_i' - 2 phi)
@@ -363,10 +360,7 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     const float om_g = P.om_g;
     const float D = fmaf(ph * q, P.kappa, (phd - phip) + ug);
 
-    if (in_bounds((long long)c, P.N, P)) {
-        phi_prev[c] = phd;      // stored as phi - phi_ref
-        q_out[c] = q;
-    }
+    sink.scalars(phd, q);      // phi^{n-1} stored as phi - phi_ref
 
     const float ux = m.ux, uy = m.uy;
     // rates of the symmetric (p) and antisymmetric (m) parts: the BGK rate on
@@ -484,12 +478,12 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     }
 
     // rest
-    push2d<S, FAST>(0,
+    sink.put(0,
         MRT ? __fadd_rn(fmaf(k.a_f, f[0], to_rep<S>(0, 0, fmaf(k.K1, P0, k.K0), P)), cf[0])
             : fmaf(k.a_f, f[0], to_rep<S>(0, 0, fmaf(k.K1, P0, k.K0), P)),
         MRT ? __fadd_rn(fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)), cg[0])
             : fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)),
-        fmaf(k.a_s, s[0], to_rep<S>(0, 2, fmaf(k.Bs, P0, k.As), P)), x, y, c, pout, P, PL);
+        fmaf(k.a_s, s[0], to_rep<S>(0, 2, fmaf(k.Bs, P0, k.As), P)));
     // a direction i with e = (ex, ey) and its opposite o
     auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eHo, float eVf,
                     float eW) {
@@ -502,24 +496,24 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
         auto rg = [&](float v) { return to_rep<S>(i, 1, v, P); };
         auto rs = [&](float v) { return to_rep<S>(i, 2, v, P); };
         if (MRT) {
-            push2d<S, FAST>(i, __fadd_rn(fmaf(k.a_f, f[i], rf(Ef + Of)), cf[i]),
+            sink.put(i, __fadd_rn(fmaf(k.a_f, f[i], rf(Ef + Of)), cf[i]),
                             __fadd_rn(fmaf(k.a_g, g[i], rg(Eg + eVg)), cg[i]),
-                            fmaf(k.a_s, s[i], rs(Es + eW)), x, y, c, pout, P, PL);
-            push2d<S, FAST>(o, __fadd_rn(fmaf(k.a_f, f[o], rf(Ef - Of)), cf[o]),
+                            fmaf(k.a_s, s[i], rs(Es + eW)));
+            sink.put(o, __fadd_rn(fmaf(k.a_f, f[o], rf(Ef - Of)), cf[o]),
                             __fadd_rn(fmaf(k.a_g, g[o], rg(Eg - eVg)), cg[o]),
-                            fmaf(k.a_s, s[o], rs(Es - eW)), x, y, c, pout, P, PL);
+                            fmaf(k.a_s, s[o], rs(Es - eW)));
         } else if (!TRT) {
-            push2d<S, FAST>(i, fmaf(k.a_f, f[i], rf(Ef + Of)), fmaf(k.a_g, g[i], rg(Eg + eVg)),
-                            fmaf(k.a_s, s[i], rs(Es + eW)), x, y, c, pout, P, PL);
-            push2d<S, FAST>(o, fmaf(k.a_f, f[o], rf(Ef - Of)), fmaf(k.a_g, g[o], rg(Eg - eVg)),
-                            fmaf(k.a_s, s[o], rs(Es - eW)), x, y, c, pout, P, PL);
+            sink.put(i, fmaf(k.a_f, f[i], rf(Ef + Of)), fmaf(k.a_g, g[i], rg(Eg + eVg)),
+                            fmaf(k.a_s, s[i], rs(Es + eW)));
+            sink.put(o, fmaf(k.a_f, f[o], rf(Ef - Of)), fmaf(k.a_g, g[o], rg(Eg - eVg)),
+                            fmaf(k.a_s, s[o], rs(Es - eW)));
         } else {
-            push2d<S, FAST>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], rf(Ef + Of))),
+            sink.put(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], rf(Ef + Of))),
                             fmaf(a1_g, g[i], fmaf(a2_g, g[o], rg(Eg + eVg))),
-                            fmaf(a1_s, s[i], fmaf(a2_s, s[o], rs(Es + eW))), x, y, c, pout, P, PL);
-            push2d<S, FAST>(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], rf(Ef - Of))),
+                            fmaf(a1_s, s[i], fmaf(a2_s, s[o], rs(Es + eW))));
+            sink.put(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], rf(Ef - Of))),
                             fmaf(a1_g, g[o], fmaf(a2_g, g[i], rg(Eg - eVg))),
-                            fmaf(a1_s, s[o], fmaf(a2_s, s[i], rs(Es - eW))), x, y, c, pout, P, PL);
+                            fmaf(a1_s, s[o], fmaf(a2_s, s[i], rs(Es - eW))));
         }
     };
     pair(1, 3, ux, Pxa, k.Vgx, k.Hx, Hox, k.Vfx, k.Wx);                          // (1, 0)
@@ -532,6 +526,42 @@ __device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const 
     pair(6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(k.Vgy, k.Vgx),
          __fsub_rn(k.Hy, k.Hx), __fsub_rn(Hoy, Hox), __fsub_rn(k.Vfy, k.Vfx),
          __fsub_rn(k.Wy, k.Wx));                                                 // (-1, 1)
+}
+
+
+// Where a cell update's results go: PushSink2 pushes them into the other
+// population buffer and writes phi^{n-1} and the lagged source (the tiled and
+// TMA kernels); a sink gets scalars(phd, q) once and put(i, f, g, s) for every
+// direction i.
+template <typename S, bool FAST>
+struct PushSink2 {
+    int x, y;
+    size_t c;
+    S *__restrict__ pout;
+    float *__restrict__ phi_prev;
+    float *__restrict__ q_out;
+    const DevParams &P;
+    const Planes2d<S> &PL;
+    __device__ __forceinline__ void scalars(float phd, float q) {
+        if (in_bounds((long long)c, P.N, P)) {
+            phi_prev[c] = phd;
+            q_out[c] = q;
+        }
+    }
+    __device__ __forceinline__ void put(int i, float vf, float vg, float vs) {
+        push2d<S, FAST>(i, vf, vg, vs, x, y, c, pout, P, PL);
+    }
+};
+
+template <typename S, bool FAST, int COLL = COLL_BGK, bool BIASED = false>
+__device__ __forceinline__ void cell_update2d(const float *sp, int pitch, const float f[9],
+                                              const float g[9], const float s[9], float phip,
+                                              float qp, int x, int y, size_t c,
+                                              S *__restrict__ pout, float *__restrict__ phi_prev,
+                                              float *__restrict__ q_out, const DevParams &P,
+                                              const Planes2d<S> &PL) {
+    PushSink2<S, FAST> sink{x, y, c, pout, phi_prev, q_out, P, PL};
+    cell_core2d<S, COLL, BIASED>(sp, pitch, f, g, s, phip, qp, P, sink);
 }
 
 // phi - phi_ref of one cell from its nine stored g values and lagged source

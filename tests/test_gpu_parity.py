@@ -157,12 +157,21 @@ def test_mass_conservation_source_off_gpu():
     assert abs(m1 - m0) / m0 < 1e-5
 
 
+def _trt(w):
+    w.params.update(collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25))
+    return w
+
+
 TMA_CASES = [
     ("film_walls_fp32", lambda: _film(128, 96), "fp32", 40),
     ("film_walls_ragged_y", lambda: _film(96, 83), "fp32", 25),
     ("droplet_periodic_fp32", lambda: W.droplet_2d(96, 20.0, T_offset=0.05), "fp32", 40),
     ("film_walls_fp16", lambda: _film(128, 96), "fp16", 40),
     ("film_walls_bf16", lambda: _film(128, 96), "bf16", 20),
+    # 16-bit widths with interior 64-cell tiles of the tiled kernel, and TRT
+    ("film_walls_fp16_wide", lambda: _film(320, 72), "fp16", 30),
+    ("droplet_periodic_fp16", lambda: W.droplet_2d(256, 40.0, T_offset=0.05), "fp16", 30),
+    ("film_trt_fp16_wide", lambda: _trt(_film(256, 64)), "fp16", 20),
     # 3D: periodic x, y (edge tiles wrap), walls in z, several z blocks of 32
     # layers, and a grid whose last tiles are ragged in x and y
     ("film3d_fp32", lambda: W.film_boiling_3d(64, 24, 70, modes=2, z0=20.0, phi_wall=(1.0, 0.0)), "fp32", 12),
