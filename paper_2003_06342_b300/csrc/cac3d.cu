@@ -5,8 +5,13 @@
 // velocity u(x) c(n) prescribed -- the CAC validations of Sec. 4.1 run on
 // thin 3D domains.  Each block marches a 32x4 column tile through ZB layers
 // with the rolling three-plane phi window of step3d_kernel: before layer z is
-// updated, plane z+1 is formed (the own cell's g of plane z+1 stays in
-// registers for the next layer, the halo ring comes from L2).  Per cell:
+// updated, plane z+1 is formed.  With FP32 storage, on tiles that need no wall
+// test, the loads run a layer ahead: while layer z is updated, the own cells' g of plane z+2 and
+// the imposed velocity of layer z+1 are in flight in registers and the halo
+// ring of plane z+2 is being copied into shared memory with cp.async (the
+// per-layer work is small, so without the lookahead every layer waited for
+// its loads).  There is no phase change, so phi = sum_i g_i and no lagged
+// source is read.  Per cell:
 // grad(phi) by Eqs. DerivDirec_Grad and Grad over the D3Q19 neighbours, the
 // normal, Gamma(u) (Eq. FunctionGamma) and the collision of Eq. LBE with the
 // source F^g of Eq. SourceTerm_AllenCahn in the even / odd form of the
@@ -17,15 +22,94 @@
 #include "lbm_common.cuh"
 #include "lbm_kernels.h"
 #include "lbm3d_cell.cuh"
+#include "tma_util.cuh"
 
 namespace lbm {
+
+namespace {
+
+// Halo ring of the phi window (one cell per thread r < CRING), fetched a
+// layer ahead with 4-byte cp.async copies into shared memory: the 7 g values
+// of ring cell r in words buf[i * CRING + r].  A 16-bit value is fetched as
+// the aligned 32-bit word that holds it (the workspace is 256-byte aligned).
+constexpr int CRING = 2 * SX + 2 * TY;
+constexpr int CRING_WORDS = QG * CRING;
+
+__device__ __forceinline__ void cac_cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+template <int XY>
+__device__ __forceinline__ size_t cac_ring_cell(int r, int z, int x0, int y0, const DevParams &P, int &slot) {
+    const int nx = P.n[0], ny = P.n[1];
+    int sx, sy;
+    if (r < SX) { sx = r; sy = 0; }
+    else if (r < 2 * SX) { sx = r - SX; sy = SY - 1; }
+    else if (r < 2 * SX + TY) { sx = 0; sy = 1 + r - 2 * SX; }
+    else { sx = SX - 1; sy = 1 + r - 2 * SX - TY; }
+    slot = sy * SX + sx;
+    int cx = x0 + sx - 1, cy = y0 + sy - 1;
+    if (XY == XY_WRAP) {
+        cx = cx < 0 ? cx + nx : (cx >= nx ? cx - nx : cx);
+        cy = cy < 0 ? cy + ny : (cy >= ny ? cy - ny : cy);
+    }
+    return ((size_t)z * ny + cy) * nx + cx;
+}
+
+// issue the ring copies of plane z (one commit group per call)
+template <typename S, int XY>
+__device__ __forceinline__ void cac_ring_prefetch(uint32_t *buf, const S *__restrict__ pin, int z, int x0,
+                                                  int y0, int tid, const DevParams &P) {
+    if (tid < CRING) {
+        int slot;
+        const size_t cc = cac_ring_cell<XY>(tid, z, x0, y0, P, slot);
+        const size_t N = (size_t)P.N;
+        if (in_bounds((long long)cc, (long long)N, P)) {
+#pragma unroll
+            for (int i = 0; i < QG; ++i) {
+                const size_t e = off_g(QF, i, cc, N);
+                const S *src = pin + (IsNarrow<S>::value ? (e & ~(size_t)1) : e);
+                cac_cp_async4(&buf[i * CRING + tid], src);
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// phi - phi_ref of ring cell tid of plane z from its fetched words
+template <typename S, int XY>
+__device__ __forceinline__ void cac_ring_store(float *plane, const uint32_t *buf, int z, int x0, int y0,
+                                               int tid, const DevParams &P) {
+    if (tid >= CRING) return;
+    int slot;
+    const size_t cc = cac_ring_cell<XY>(tid, z, x0, y0, P, slot);
+    const size_t N = (size_t)P.N;
+    float v[QG];
+#pragma unroll
+    for (int i = 0; i < QG; ++i) {
+        const uint32_t w = buf[i * CRING + tid];
+        if (IsNarrow<S>::value) {
+            const size_t e = off_g(QF, i, cc, N);
+            const unsigned short h = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
+            S val;
+            memcpy(&val, &h, 2);
+            v[i] = widen(val);
+        } else {
+            v[i] = __uint_as_float(w);
+        }
+    }
+    plane[slot] = set_sum7<S>(v, P.set_isc[1]);
+}
+
+}  // namespace
 
 // update of one cell of layer z from the phi window (planes z-1, z, z+1 in
 // slots z % 3, (z+1) % 3, (z+2) % 3) and its g values (working representation)
 template <typename S, int MODE>
 __device__ __forceinline__ void cac3d_cell(const float *sphi, int z, int x, int y, size_t c,
                                            const float g[QG], const float *__restrict__ vel, float factor,
-                                           S *__restrict__ pout, const DevParams &P, const Planes3d<S> &PL) {
+                                           const float uin[3], bool have_u, S *__restrict__ pout,
+                                           const DevParams &P, const Planes3d<S> &PL) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const size_t N = (size_t)P.N;
     const int centre = (ty + 1) * SX + tx + 1;
@@ -46,7 +130,9 @@ __device__ __forceinline__ void cac3d_cell(const float *sphi, int z, int x, int 
     gx *= 3.0f; gy *= 3.0f; gz *= 3.0f;
     const float inv_d = rsqrt_approx(fmaxf(fmaf(gz, gz, fmaf(gy, gy, gx * gx)), P.eps2));
     const float n[3] = {gx * inv_d, gy * inv_d, gz * inv_d};
-    const float u[3] = {vel[c] * factor, vel[N + c] * factor, vel[2 * N + c] * factor};
+    // the imposed velocity (already loaded a layer ahead when have_u)
+    const float u[3] = {(have_u ? uin[0] : vel[c]) * factor, (have_u ? uin[1] : vel[N + c]) * factor,
+                        (have_u ? uin[2] : vel[2 * N + c]) * factor};
     const float usq = fmaf(u[2], u[2], fmaf(u[1], u[1], u[0] * u[0]));
 
     const float om = P.om_g, a_g = 1.0f - om, b_g = fmaf(-0.5f, om, 1.0f);
@@ -71,7 +157,7 @@ template <typename S, int XY>
 __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__restrict__ pout,
                                              const float *__restrict__ q_zero, const float *__restrict__ vel,
                                              float factor, const DevParams &P, float *sphi,
-                                             const Planes3d<S> &PL) {
+                                             uint32_t (*rbuf)[CRING_WORDS], const Planes3d<S> &PL) {
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -81,30 +167,72 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
     const bool col = XY != XY_GEN || ((x < nx) && (y < ny));
     const size_t cxy = col ? (size_t)y * nx + x : 0;
     const size_t plane_cells = (size_t)nx * ny;
+    const size_t N = (size_t)P.N;
     const float isc = P.set_isc[1];
+    // lookahead on tiles that need no wall test (q = 0: phi = sum_i g_i), FP32
+    // storage: with 16-bit storage it measured 3% slower than without
+    // (609 against 589 us on 1024 x 1024 x 32), so those keep the plain march
+    constexpr bool PRE = XY != XY_GEN && !IsNarrow<S>::value;
 
-    float g[QG];
+    // gn: the own g of plane z + 1 as stored (a 16-bit value is widened only
+    // where it is used, so the load it came from is not waited for early)
+    float g[QG], u[3] = {0.0f, 0.0f, 0.0f};
+    S gn[QG];
     {
         float ph = 0.0f;
         if (col) {
             const size_t c = zbeg * plane_cells + cxy;
 #pragma unroll
             for (int i = 0; i < QG; ++i) g[i] = load_raw(PL.in[G0 + i] + c);
-            ph = fmaf(0.5f, q_zero[c], set_sum7<S>(g, isc));
+            ph = PRE ? set_sum7<S>(g, isc) : fmaf(0.5f, q_zero[c], set_sum7<S>(g, isc));
+            if (PRE) for (int a = 0; a < 3; ++a) u[a] = vel[a * N + c];
         }
         fill_plane<S, XY>(sphi, (zbeg + 1) % 3, zbeg, true, col, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
         fill_plane<S, XY_GEN>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
+        if (PRE && zbeg + 1 < nz) {
+            const size_t c = (size_t)(zbeg + 1) * plane_cells + cxy;
+#pragma unroll
+            for (int i = 0; i < QG; ++i) gn[i] = __ldg(PL.in[G0 + i] + c);
+            cac_ring_prefetch<S, XY>(rbuf[(zbeg + 1) & 1], pin, zbeg + 1, x0, y0, tid, P);
+        }
     }
     for (int z = zbeg; z < zend; ++z) {
-        float gn[QG];
-        {
+        S gnn[QG];
+        float un[3] = {0.0f, 0.0f, 0.0f};
+        if (PRE) {
+            // in flight during this layer: plane z + 2 and the velocity of z + 1
+            if (z + 2 < nz) {
+                const size_t c2 = (size_t)(z + 2) * plane_cells + cxy;
+#pragma unroll
+                for (int i = 0; i < QG; ++i) gnn[i] = __ldg(PL.in[G0 + i] + c2);
+                cac_ring_prefetch<S, XY>(rbuf[z & 1], pin, z + 2, x0, y0, tid, P);
+            }
+            if (z + 1 < zend) {
+                const size_t c1 = (size_t)(z + 1) * plane_cells + cxy;
+                for (int a = 0; a < 3; ++a) un[a] = vel[a * N + c1];
+            }
+            // plane z + 1 (in range: its own values and ring arrived a layer ago)
+            if (z + 1 < nz) {
+                float *plane = sphi + ((z + 2) % 3) * PLANE;
+                float v[QG];
+#pragma unroll
+                for (int i = 0; i < QG; ++i) v[i] = widen(gn[i]);
+                plane[(ty + 1) * SX + tx + 1] = set_sum7<S>(v, isc);
+                if (z + 2 < nz) asm volatile("cp.async.wait_group 1;" ::: "memory");
+                else asm volatile("cp.async.wait_group 0;" ::: "memory");
+                cac_ring_store<S, XY>(plane, rbuf[(z + 1) & 1], z + 1, x0, y0, tid, P);
+            } else {
+                fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
+            }
+        } else {
             float ph = 0.0f;
             const bool ok = col && (z + 1 < nz);
             if (ok) {
                 const size_t c = (size_t)(z + 1) * plane_cells + cxy;
+                float v[QG];
 #pragma unroll
-                for (int i = 0; i < QG; ++i) gn[i] = load_raw(PL.in[G0 + i] + c);
-                ph = fmaf(0.5f, q_zero[c], set_sum7<S>(gn, isc));
+                for (int i = 0; i < QG; ++i) { gn[i] = __ldg(PL.in[G0 + i] + c); v[i] = widen(gn[i]); }
+                ph = fmaf(0.5f, q_zero[c], set_sum7<S>(v, isc));
             }
             fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, ok, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
         }
@@ -112,14 +240,16 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
         if (col) {
             const size_t c = (size_t)z * plane_cells + cxy;
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                cac3d_cell<S, XY>(sphi, z, x, y, c, g, vel, factor, pout, P, PL);
+                cac3d_cell<S, XY>(sphi, z, x, y, c, g, vel, factor, u, PRE, pout, P, PL);
             else
-                cac3d_cell<S, XY_GEN>(sphi, z, x, y, c, g, vel, factor, pout, P, PL);
+                cac3d_cell<S, XY_GEN>(sphi, z, x, y, c, g, vel, factor, u, PRE, pout, P, PL);
         }
 #pragma unroll
-        for (int i = 0; i < QG; ++i) g[i] = gn[i];
-        __syncthreads();   // plane (z - 1) % 3 is overwritten next iteration
+        for (int i = 0; i < QG; ++i) { g[i] = widen(gn[i]); if (PRE) gn[i] = gnn[i]; }
+        if (PRE) for (int a = 0; a < 3; ++a) u[a] = un[a];
+        __syncthreads();   // plane (z - 1) % 3 and ring buffer z & 1 are reused next iteration
     }
+    if (PRE) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 template <typename S>
@@ -128,11 +258,12 @@ cac3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, const float *__res
              const float *__restrict__ vel, float factor, const DevParams P,
              const __grid_constant__ Planes3d<S> PL) {
     __shared__ float sphi[3 * PLANE];
+    __shared__ uint32_t rbuf[2][CRING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int cls = tile_class3d(x0, y0, P);
-    if (cls == XY_IN) cac3d_column<S, XY_IN>(pin, pout, q_zero, vel, factor, P, sphi, PL);
-    else if (cls == XY_WRAP) cac3d_column<S, XY_WRAP>(pin, pout, q_zero, vel, factor, P, sphi, PL);
-    else cac3d_column<S, XY_GEN>(pin, pout, q_zero, vel, factor, P, sphi, PL);
+    if (cls == XY_IN) cac3d_column<S, XY_IN>(pin, pout, q_zero, vel, factor, P, sphi, rbuf, PL);
+    else if (cls == XY_WRAP) cac3d_column<S, XY_WRAP>(pin, pout, q_zero, vel, factor, P, sphi, rbuf, PL);
+    else cac3d_column<S, XY_GEN>(pin, pout, q_zero, vel, factor, P, sphi, rbuf, PL);
 }
 
 template <typename S>
