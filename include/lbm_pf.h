@@ -137,8 +137,10 @@ typedef struct {
  * regions (the first-order one gives exactly the central gradient through
  * Eq. Grad); two ghost layers, the wall's Dirichlet value beyond a wall.
  * The Laplacian stays central.  BIASED2 is implemented for the coupled model
- * on the tiled kernels (2D and 3D; in 3D AUTO then selects the tiled kernel);
- * the TMA kernels and the adjoint take CENTRAL only (LBM_EUNSUPPORTED). */
+ * on the tiled kernels (2D and 3D) and on the 3D TMA kernel for grids without
+ * ragged tiles (n_x a multiple of 32, n_y of 4; there AUTO selects it for
+ * 16-bit storage and the tiled kernel for FP32, the faster of each pair); the
+ * 2D TMA kernel and the adjoint take CENTRAL only (LBM_EUNSUPPORTED). */
 #define LBM_GRAD_CENTRAL 0
 #define LBM_GRAD_BIASED2 1
 

@@ -190,12 +190,86 @@ __device__ __forceinline__ void ring_store(float *plane, const uint32_t *buf, in
     plane[slot] = fmaf(0.5f, __uint_as_float(buf[QG * RING_CELLS + tid]), set_sum7<S>(v, P.set_isc[1]));
 }
 
+// ---- the biased gradient's window: five planes of the tile and two rings.
+// A window plane is fetched whole a layer ahead with cp.async (its own cells
+// too: the g stage of that layer is still in flight when the plane is needed).
+
+// slot of the two-ring window at (cx, cy, cz): the grid cell (wrapped over
+// periodic axes, up to two cells out), or -1 beyond a wall with the wall's
+// value in wall_val (the cases of window_phid_b)
+__device__ __forceinline__ long long bwin_cell(int cx, int cy, int cz, const DevParams &P, float &wall_val) {
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    // x and y: this kernel runs on n_x >= 32, n_y >= 4, so a slot is at most
+    // one period out and one add or subtract wraps it
+    const int kx = (cx >= 0 && cx < nx) ? 0 : (P.periodic[0] ? (cx += cx < 0 ? nx : -nx, 1) : (cx < 0 ? 2 : 3));
+    const int ky = (cy >= 0 && cy < ny) ? 0 : (P.periodic[1] ? (cy += cy < 0 ? ny : -ny, 1) : (cy < 0 ? 2 : 3));
+    const int kz = (cz >= 0 && cz < nz) ? 0 : wrap_coord_far(cz, nz, P.periodic[2]);
+    wall_val = 0.0f;
+    if (kx >= 2) { wall_val = P.phi_wall[kx - 2] - P.g_ref; return -1; }
+    if (ky >= 2) { wall_val = P.phi_wall[ky - 2] - P.g_ref; return -1; }
+    if (kz >= 2) { wall_val = P.phi_wall[kz - 2] - P.g_ref; return -1; }
+    return ((long long)cz * ny + cy) * nx + cx;
+}
+
+// words of one fetched window plane: slot k's 7 g values in words
+// i * PLANEB + k, its lagged source in word 7 PLANEB + k
+constexpr int BWIN_WORDS = (QG + 1) * PLANEB;
+
+// issue the copies of window plane p for the slots this thread handles (one
+// commit group); a 16-bit value comes as the aligned 32-bit word holding it
+template <typename S>
+__device__ __forceinline__ void bwin_prefetch(uint32_t *buf, const S *__restrict__ pin,
+                                              const float *__restrict__ q_in, int p, int x0, int y0,
+                                              int tid, const DevParams &P) {
+    const size_t N = (size_t)P.N;
+    for (int sidx = tid; sidx < PLANEB; sidx += TX * TY) {
+        float wv;
+        const long long cc = bwin_cell(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, P, wv);
+        if (cc < 0 || !in_bounds(cc, (long long)N, P)) continue;
+#pragma unroll
+        for (int i = 0; i < QG; ++i) {
+            const size_t e = off_g(QF, i, (size_t)cc, N);
+            cp_async4(&buf[i * PLANEB + sidx], pin + (IsNarrow<S>::value ? (e & ~(size_t)1) : e));
+        }
+        cp_async4(&buf[QG * PLANEB + sidx], q_in + cc);
+    }
+    cp_async_commit();
+}
+
+// phi - phi_ref of window plane p's slots handled by this thread, from the
+// words it fetched (same arithmetic as phid_at)
+template <typename S>
+__device__ __forceinline__ void bwin_store(float *pl, const uint32_t *buf, int p, int x0, int y0, int tid,
+                                           const DevParams &P) {
+    const size_t N = (size_t)P.N;
+    for (int sidx = tid; sidx < PLANEB; sidx += TX * TY) {
+        float wv;
+        const long long cc = bwin_cell(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, P, wv);
+        if (cc < 0) { pl[sidx] = wv; continue; }
+        float v[QG];
+#pragma unroll
+        for (int i = 0; i < QG; ++i) {
+            const uint32_t w = buf[i * PLANEB + sidx];
+            if (IsNarrow<S>::value) {
+                const size_t e = off_g(QF, i, (size_t)cc, N);
+                const unsigned short h = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
+                S val;
+                memcpy(&val, &h, 2);
+                v[i] = widen(val);
+            } else {
+                v[i] = __uint_as_float(w);
+            }
+        }
+        pl[sidx] = fmaf(0.5f, __uint_as_float(buf[QG * PLANEB + sidx]), set_sum7<S>(v, P.set_isc[1]));
+    }
+}
+
 // Layer z uses f/s stage (z - zbeg) % 2 and g stage (z - zbeg) % 3.  In
 // iteration z the block needs the f/s stage of z and the g stages of z and
 // z + 1; the copies of f/s(z + 1) and g(z + 2) are in flight, and when layer
 // z is done its stages receive f/s(z + 2) and g(z + 3): every copy is issued
 // at least one whole layer before it is awaited.
-template <typename S, int XY, bool TRT>
+template <typename S, int XY, bool TRT, bool BIASED>
 __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S *__restrict__ pin,
                                            S *__restrict__ pout, float *__restrict__ phi_prev,
                                            const float *__restrict__ q_in, float *__restrict__ q_out,
@@ -227,6 +301,73 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             if ((G.pend >> k) & 1u) issue_g<S>(g_base + k * Gm::G_STAGE, &barG[k], M, par, x0, y0, zbeg + k);
         for (int k = 0; k < Gm::NFS; ++k)
             if ((F.pend >> k) & 1u) issue_fs<S>(fs_base + k * Gm::FS_STAGE, &barF[k], M, par, x0, y0, zbeg + k);
+    }
+
+    if (BIASED) {
+        // the two-ring window: planes zbeg - 2 .. zbeg + 1 with plain loads
+        // (slot of plane p: (p + 2) mod 5), plane zbeg + 2 fetched
+        for (int p = zbeg - 2; p <= zbeg + 1; ++p) {
+            float *pl = sphi + ((p + 2 + 5 * 4) % 5) * PLANEB;
+            for (int sidx = tid; sidx < PLANEB; sidx += TX * TY)
+                pl[sidx] = window_phid_b<S>(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, pin, q_in, P);
+        }
+        bwin_prefetch<S>(rbuf, pin, q_in, zbeg + 2, x0, y0, tid, P);
+        bool ok = G.wait(barG, 0, first_wait_limit);
+        int fb = 0, gb = 0;
+        for (int z = zbeg; z < zend; ++z) {
+            const int gn = gb == Gm::NG - 1 ? 0 : gb + 1;
+            if (z > zbeg) ok = G.wait(barG, gb) && ok;        // g stage of layer z
+            ok = F.wait(barF, fb) && ok;
+            // window plane z + 2 (fetched a layer ago); plane z + 3 in flight
+            if (z + 1 < zend) {
+                bwin_prefetch<S>(rbuf + ((z - zbeg + 1) & 1) * BWIN_WORDS, pin, q_in, z + 3, x0, y0, tid, P);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                cp_async_wait_all();
+            }
+            bwin_store<S>(sphi + ((z + 4) % 5) * PLANEB, rbuf + ((z - zbeg) & 1) * BWIN_WORDS, z + 2, x0, y0,
+                          tid, P);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicOr(err, 1);
+                cp_async_wait_all();
+                F.drain(barF, Gm::NFS);              // copies that may still land
+                G.drain(barG, Gm::NG);
+                return;
+            }
+            {
+                const unsigned char *b = fs_base + fb * Gm::FS_STAGE;
+                const unsigned char *bg = g_base + gb * Gm::G_STAGE;
+                const auto *FSp = (const typename PairOf<S>::T *)(b + Gm::OFF_FS);
+                const S *Gp = (const S *)(bg + Gm::OFF_G);
+                float f[QF], s[QF], g[QG];
+#pragma unroll
+                for (int i = 0; i < QF; ++i) unpack_pair(FSp[i * Gm::CELLS + tid], f[i], s[i]);
+#pragma unroll
+                for (int i = 0; i < QG; ++i) g[i] = widen(Gp[i * Gm::CELLS + tid]);
+                const float qp = ((const float *)(bg + Gm::OFF_Q))[tid];
+                const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
+                const size_t c = (size_t)z * plane_cells + cxy;
+                if (XY != XY_GEN && z >= 1 && z + 1 < nz)
+                    layer_update3d<S, XY, TRT, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out,
+                                                     P, PL);
+                else
+                    layer_update3d<S, XY_GEN, TRT, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev,
+                                                         q_out, P, PL);
+            }
+            __syncthreads();      // the stages of layer z and window slot of plane z - 2 are free
+            if (z + Gm::NFS < zend) {
+                if (tid == 0)
+                    issue_fs<S>(fs_base + fb * Gm::FS_STAGE, &barF[fb], M, par, x0, y0, z + Gm::NFS);
+                F.pend |= 1u << fb;
+            }
+            if (z + Gm::NG <= zlast) {
+                if (tid == 0) issue_g<S>(g_base + gb * Gm::G_STAGE, &barG[gb], M, par, x0, y0, z + Gm::NG);
+                G.pend |= 1u << gb;
+            }
+            fb ^= 1;
+            gb = gn;
+        }
+        return;
     }
 
     // window: plane zbeg - 1 with plain loads, plane zbeg from its g stage
@@ -299,7 +440,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
     }
 }
 
-template <typename S, bool TRT>
+template <typename S, bool TRT, bool BIASED>
 __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
 step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ pin,
                   S *__restrict__ pout, float *__restrict__ phi_prev,
@@ -309,10 +450,17 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     // bulk tensor copies want 128-byte aligned destinations
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t barF[Tma3Geom<S>::NFS], barG[Tma3Geom<S>::NG];
-    __shared__ float sphi[3 * PLANE];
-    __shared__ uint32_t rbuf[2 * RING_WORDS];
+    // the biased gradient: a five-plane two-ring window, two fetched planes
+    __shared__ float sphi[BIASED ? 5 * PLANEB : 3 * PLANE];
+    __shared__ uint32_t rbuf[BIASED ? 2 * BWIN_WORDS : 2 * RING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if (x0 + TX > P.n[0] || y0 + TY > P.n[1]) {          // ragged tile: plain loads
+        if (BIASED) {
+            // the host runs this kernel with the biased gradient only on grids
+            // without ragged tiles; record the broken precondition
+            if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(err, 2);
+            return;
+        }
         step3d_column<S, XY_GEN, TRT, Tma3Geom<S>::ZBT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
         return;
     }
@@ -327,9 +475,9 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     // enough for the instruction cache (measured: FP32 +1.9%, FP16 +3.9%)
     const int cls = tile_class3d(x0, y0, P);
     if (cls != XY_GEN)
-        tma_column<S, XY_WRAP, TRT>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
+        tma_column<S, XY_WRAP, TRT, BIASED>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
     else
-        tma_column<S, XY_GEN, TRT>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
+        tma_column<S, XY_GEN, TRT, BIASED>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
 }
 
 // ------------------------------------------------------------------ host side
@@ -379,22 +527,25 @@ int make_tma_maps3d(TmaMaps3d *M, const DevParams &P, int elem_bytes, void *cons
     return 0;
 }
 
-template <typename S, bool TRT>
+template <typename S, bool TRT, bool BIASED>
 static int blocks_per_sm_one() {
     int n = 0;
     const int dyn = Tma3Geom<S>::DYN;
-    if (cudaFuncSetAttribute(step3d_tma_kernel<S, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(step3d_tma_kernel<S, TRT, BIASED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dyn) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step3d_tma_kernel<S, TRT>, TX * TY, dyn) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step3d_tma_kernel<S, TRT, BIASED>, TX * TY, dyn) !=
+        cudaSuccess)
         return 0;
     return n;
 }
 
-// both collision instantiations get the shared-memory limit
+// every collision and gradient instantiation gets the shared-memory limit;
+// the central-gradient ones decide whether the kernel runs at all
 template <typename S>
 static int blocks_per_sm_for() {
-    const int a = blocks_per_sm_one<S, false>(), b = blocks_per_sm_one<S, true>();
+    const int a = blocks_per_sm_one<S, false, false>(), b = blocks_per_sm_one<S, true, false>();
+    if (blocks_per_sm_one<S, false, true>() < 1 || blocks_per_sm_one<S, true, true>() < 1) return 0;
     return a < b ? a : b;
 }
 
@@ -411,12 +562,23 @@ cudaError_t launch_step3d_tma(const TmaMaps3d &M, int par, const void *pin, void
     dim3 block(TX, TY);
     constexpr int zb = Tma3Geom<S>::ZBT;
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, (P.n[2] + zb - 1) / zb);
-    if (P.opts & OPT_TRT)
-        step3d_tma_kernel<S, true><<<grid, block, Tma3Geom<S>::DYN, st>>>(
-            M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes3d<S>(pin, pout, P));
-    else
-        step3d_tma_kernel<S, false><<<grid, block, Tma3Geom<S>::DYN, st>>>(
-            M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes3d<S>(pin, pout, P));
+    const Planes3d<S> PL = planes3d<S>(pin, pout, P);
+    const S *in = (const S *)pin;
+    S *out = (S *)pout;
+    switch (P.opts & (OPT_TRT | OPT_BIASED)) {
+    case 0:
+        step3d_tma_kernel<S, false, false><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, q_out, par, err, P, PL);
+        break;
+    case OPT_TRT:
+        step3d_tma_kernel<S, true, false><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, q_out, par, err, P, PL);
+        break;
+    case OPT_BIASED:
+        step3d_tma_kernel<S, false, true><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, q_out, par, err, P, PL);
+        break;
+    default:
+        step3d_tma_kernel<S, true, true><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, q_out, par, err, P, PL);
+        break;
+    }
     return cudaGetLastError();
 }
 

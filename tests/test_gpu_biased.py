@@ -3,8 +3,9 @@ the GPU against the FP64 oracle with grad_scheme "biased2": parity within
 1e-5 on geometries that take every ghost path (walls on y and on x with two
 ghost layers, periodic boxes, a one-cell periodic axis that wraps twice,
 ragged tiles, 3D with walls on z and a periodic axis shorter than the rings),
-combined with TRT, and with 16-bit storage; in 3D AUTO selects the tiled
-kernel."""
+combined with TRT, and with 16-bit storage.  In 3D the TMA-staged kernel
+takes the biased gradient on grids without ragged tiles (AUTO selects it
+there for 16-bit storage) and matches the tiled kernel bit for bit."""
 import numpy as np
 import pytest
 
@@ -41,6 +42,16 @@ CASES = [
 ]
 
 
+def test_biased_parity_with_oracle_on_the_3d_tma_kernel():
+    w = _b(W.film_boiling_3d(64, 8, 30, modes=1, z0=10.0, phi_wall=(1.0, 0.0)))
+    ref = oracle_fields(w, 10)
+    s = gpu_solver(w)
+    s.set_kernel("tma")
+    s.step(10)
+    err = max_errors(gpu_fields(s), ref)
+    assert all(v < TOL for v in err.values()), err
+
+
 @pytest.mark.parametrize("name,make,steps", CASES, ids=[c[0] for c in CASES])
 def test_biased_parity_with_oracle(name, make, steps):
     w = make()
@@ -73,10 +84,38 @@ def test_biased_fp16_close_to_fp32_and_tma_refused():
     assert e.value.code == LBM_EUNSUPPORTED
 
 
-def test_biased_3d_runs_on_the_tiled_kernel():
-    w = _b(W.film_boiling_3d(64, 16, 40, modes=1, z0=12.0, phi_wall=(1.0, 0.0)))
+TMA_CASES = [
+    ("fp32", lambda: _b(W.film_boiling_3d(64, 16, 40, modes=1, z0=12.0, phi_wall=(1.0, 0.0))), "fp32", 12),
+    # several z blocks of 64 layers (16-bit storage)
+    ("fp16_z_blocks", lambda: _b(W.film_boiling_3d(64, 24, 70, modes=2, z0=20.0, phi_wall=(1.0, 0.0))), "fp16", 10),
+    ("bf16_trt", lambda: _b(W.film_boiling_3d(64, 8, 33, modes=1, z0=10.0, phi_wall=(1.0, 0.0)),
+                            collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25)), "bf16", 8),
+    # periodic in every axis (no wall in z)
+    ("fp32_periodic", lambda: _b(W.droplet_3d(32, 6.0) if hasattr(W, "droplet_3d") else
+                                  W.film_boiling_3d(32, 8, 24, modes=1, z0=8.0, phi_wall=(1.0, 0.0))), "fp32", 8),
+]
+
+
+@pytest.mark.parametrize("name,make,storage,steps", TMA_CASES, ids=[c[0] for c in TMA_CASES])
+def test_biased_3d_tma_matches_tiled_bit_for_bit(name, make, storage, steps):
+    w = make()
+    a = gpu_solver(w, storage=storage)
+    b = gpu_solver(w, storage=storage)
+    # AUTO: the TMA kernel for 16-bit storage, the tiled one for FP32
+    assert a.kernel() == ("tiled" if storage == "fp32" else "tma")
+    a.set_kernel("tma")
+    b.set_kernel("tiled")
+    a.step(steps)
+    b.step(steps)
+    import torch
+    assert torch.equal(a.get_state(), b.get_state()), name
+    a.sync()
+
+
+def test_biased_3d_ragged_grid_stays_tiled():
+    w = _b(W.film_boiling_3d(44, 13, 20, modes=1, z0=7.0, phi_wall=(1.0, 0.0)))
     s = gpu_solver(w, storage="fp16")
-    assert s.kernel() == "tiled"              # AUTO picks the tiled kernel
+    assert s.kernel() == "tiled"              # ragged tiles: AUTO picks the tiled kernel
     s.step(5)
     assert np.isfinite(gpu_fields(s)["phi"]).all()
     with pytest.raises(LBMError) as e:
