@@ -139,8 +139,8 @@ typedef struct {
  * The Laplacian stays central.  BIASED2 is implemented for the coupled model
  * on the tiled kernels (2D and 3D) and on the 3D TMA kernel for grids without
  * ragged tiles (n_x a multiple of 32, n_y of 4; there AUTO selects it for
- * 16-bit storage and the tiled kernel for FP32, the faster of each pair); the
- * 2D TMA kernel and the adjoint take CENTRAL only (LBM_EUNSUPPORTED). */
+ * 16-bit storage and the tiled kernel for FP32, the faster of each pair) and
+ * in the adjoint; the 2D TMA kernel takes CENTRAL only (LBM_EUNSUPPORTED). */
 #define LBM_GRAD_CENTRAL 0
 #define LBM_GRAD_BIASED2 1
 

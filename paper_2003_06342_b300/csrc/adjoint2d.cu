@@ -26,7 +26,9 @@
 // and the init kernel maps Lambda^0 to dJ/dT_0 (and the init's share of
 // dJ/dL, dJ/dsigma) through the barred-equilibrium initialisation.
 // Derivatives of the clip of phi to [0, 1] and of the regularised norm are
-// taken piecewise (zero / 1/eps on the flat branches).
+// taken piecewise (zero / 1/eps on the flat branches).  With the biased
+// gradient (LBM_GRAD_BIASED2) the window holds two rings and kernel B also
+// gathers from the cells two links away.
 #include "lbm_common.cuh"
 #include "lbm_kernels.h"
 #include "adjoint.h"
@@ -99,21 +101,29 @@ adj_terminal2d_kernel(const float *__restrict__ st, const float *__restrict__ ta
 // threads per SM)
 constexpr int ADJ_TY = 4;
 
-constexpr int ADJ_WX = 34, ADJ_WY = ADJ_TY + 2;
+// phi window of a tile with R rings (R = 1 for the central gradient, 2 for
+// the biased one)
+template <int R> struct AdjWin {
+    static constexpr int WX = 32 + 2 * R, WY = ADJ_TY + 2 * R;
+};
+constexpr int ADJ_WMAX = AdjWin<2>::WX * AdjWin<2>::WY;
 
-// The reverse step of one 32 x ADJ_TY tile.  FAST: the tile and its one-cell
-// ring lie inside the grid, so no pulled link and no ring cell wraps or meets
-// a wall.  Adds the cell's dJ/dL, dJ/dM_phi, dJ/dsigma terms to dL, dM, dS.
-template <bool FAST>
+// The reverse step of one 32 x ADJ_TY tile.  FAST: the tile and its rings lie
+// inside the grid, so no pulled link and no window cell wraps or meets a
+// wall.  BIASED: the gradient of Eq. Grad from the second-order biased
+// difference (two rings).  Adds the cell's dJ/dL, dJ/dM_phi, dJ/dsigma terms
+// to dL, dM, dS.
+template <bool FAST, bool BIASED>
 __device__ __forceinline__ void adj_a_tile(const float *__restrict__ st, const float *__restrict__ lam_next,
                                            float *__restrict__ lam, float *__restrict__ cst,
                                            const DevParams &P, float *sphi, int x0, int y0,
                                            float &dL, float &dM, float &dS) {
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
-    // phi - phi_ref of the tile and its one-cell ring in shared memory (each
-    // window value formed once, not once per neighbour)
-    constexpr int WX = ADJ_WX, WY = ADJ_WY;
+    // phi - phi_ref of the tile and its rings in shared memory (each window
+    // value formed once, not once per neighbour)
+    constexpr int R = BIASED ? 2 : 1;
+    constexpr int WX = AdjWin<R>::WX, WY = AdjWin<R>::WY;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < nx && y < ny;
@@ -131,7 +141,7 @@ __device__ __forceinline__ void adj_a_tile(const float *__restrict__ st, const f
         }
         phip = st[st_idx(27, c, N)];
         qp = st[st_idx(28, c, N)];
-        sphi[(ty + 1) * WX + tx + 1] = phid_sum(g, qp);
+        sphi[(ty + R) * WX + tx + R] = phid_sum(g, qp);
     }
     float lf[9], lg[9], ls[9], l_phip_new = 0.0f, l_q_new = 0.0f;
     if (active) {
@@ -169,7 +179,7 @@ __device__ __forceinline__ void adj_a_tile(const float *__restrict__ st, const f
         l_q_new = fmaf(0.5f, lam_next[(size_t)LPHI * N + c], lam_next[st_idx(28, c, N)]);
 
     }
-    if (FAST) {
+    if (FAST && !BIASED) {
         // the ring: the top and bottom rows, then the left and right columns
         constexpr int RING = 2 * WX + 2 * ADJ_TY;
         const int r = threadIdx.x;
@@ -181,31 +191,49 @@ __device__ __forceinline__ void adj_a_tile(const float *__restrict__ st, const f
             else { wx = WX - 1; wy = 1 + r - 2 * WX - ADJ_TY; }
             sphi[wy * WX + wx] = phid_cell(st, (size_t)(y0 + wy - 1) * nx + (x0 + wx - 1), N, P);
         }
-    } else
-    for (int sidx = threadIdx.x; sidx < WX * WY; sidx += blockDim.x) {
-        int cx = x0 + sidx % WX - 1, cy = y0 + sidx / WX - 1;
-        const int wx = sidx % WX, wy = sidx / WX;
-        if (wx >= 1 && wx <= 32 && wy >= 1 && wy <= ADJ_TY && cx < nx && cy < ny) continue;  // owned
-        if (cx > nx || cy > ny) { sphi[sidx] = 0.0f; continue; }     // beyond a ragged tile
-        const int kx = wrap_coord(cx, nx, P.periodic[0]);
-        const int ky = wrap_coord(cy, ny, P.periodic[1]);
-        sphi[sidx] = kx >= 2 ? P.phi_wall[kx - 2] - P.g_ref
-                   : (ky >= 2 ? P.phi_wall[ky - 2] - P.g_ref : phid_cell(st, (size_t)cy * nx + cx, N, P));
+    } else {
+        for (int sidx = threadIdx.x; sidx < WX * WY; sidx += blockDim.x) {
+            const int wx = sidx % WX, wy = sidx / WX;
+            int cx = x0 + wx - R, cy = y0 + wy - R;
+            if (wx >= R && wx < 32 + R && wy >= R && wy < ADJ_TY + R && cx < nx && cy < ny) continue;  // owned
+            if (FAST) {
+                sphi[sidx] = phid_cell(st, (size_t)cy * nx + cx, N, P);
+                continue;
+            }
+            if (cx > nx + R - 1 || cy > ny + R - 1) { sphi[sidx] = 0.0f; continue; }   // beyond a ragged tile
+            const int kx = wrap_coord_far(cx, nx, P.periodic[0]);
+            const int ky = wrap_coord_far(cy, ny, P.periodic[1]);
+            sphi[sidx] = kx >= 2 ? P.phi_wall[kx - 2] - P.g_ref
+                       : (ky >= 2 ? P.phi_wall[ky - 2] - P.g_ref : phid_cell(st, (size_t)cy * nx + cx, N, P));
+        }
     }
     __syncthreads();
     if (active) {
         // ---------------- forward recomputation
+        const float *sp = sphi + (ty + R) * WX + tx + R;
         float nb[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) nb[j] = sphi[(ty + 1 + L::ey(j)) * WX + tx + 1 + L::ex(j)];
+        for (int j = 0; j < 9; ++j) nb[j] = sp[L::ey(j) * WX + L::ex(j)];
         const float phd = nb[0];
         const float ph = phd + P.g_ref;
         const float nE = nb[1], nN = nb[2], nW = nb[3], nS = nb[4];
         const float nNE = nb[5], nNW = nb[6], nSW = nb[7], nSE = nb[8];
         const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
         const float dA = nNE - nSW, dB = nSE - nNW;
-        const float gx = 3.0f * (w1 * (nE - nW) + w5 * (dA + dB));
-        const float gy = 3.0f * (w1 * (nN - nS) + w5 * (dA - dB));
+        float gx, gy;
+        if (BIASED) {
+            // Eq. Grad with [-phi(x + 2e) + 4 phi(x + e) - 3 phi(x)] / 2, pair-folded
+            const int W2 = 2 * WX;
+            const float bx = 0.5f * fmaf(4.0f, nE - nW, -(sp[2] - sp[-2]));
+            const float by = 0.5f * fmaf(4.0f, nN - nS, -(sp[W2] - sp[-W2]));
+            const float bA = 0.5f * fmaf(4.0f, dA, -(sp[W2 + 2] - sp[-W2 - 2]));
+            const float bB = 0.5f * fmaf(4.0f, dB, -(sp[-W2 + 2] - sp[W2 - 2]));
+            gx = 3.0f * fmaf(w1, bx, w5 * (bA + bB));
+            gy = 3.0f * fmaf(w1, by, w5 * (bA - bB));
+        } else {
+            gx = 3.0f * (w1 * (nE - nW) + w5 * (dA + dB));
+            gy = 3.0f * (w1 * (nN - nS) + w5 * (dA - dB));
+        }
         const float lap = 6.0f * (w1 * ((nE + nW) + (nN + nS) - 4.0f * phd)
                                 + w5 * ((nNE + nSW) + (nNW + nSE) - 4.0f * phd));
         const bool inside = ph > 0.0f && ph < 1.0f;
@@ -442,18 +470,20 @@ __device__ __forceinline__ void adj_a_tile(const float *__restrict__ st, const f
     }
 }
 
+template <bool BIASED>
 __global__ void __launch_bounds__(32 * ADJ_TY, 16 / ADJ_TY)
 adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_next,
                     float *__restrict__ lam, float *__restrict__ cst, double *dparams,
                     const DevParams P) {
-    __shared__ float sphi[ADJ_WX * ADJ_WY];
+    __shared__ float sphi[ADJ_WMAX];
+    constexpr int R = BIASED ? 2 : 1;
     const int nx = P.n[0], ny = P.n[1];
     const int tiles_x = (nx + 31) / 32;
     const int x0 = (int)(blockIdx.x % tiles_x) * 32, y0 = (int)(blockIdx.x / tiles_x) * ADJ_TY;
-    const bool fast = x0 >= 1 && x0 + 33 <= nx && y0 >= 1 && y0 + ADJ_TY + 1 <= ny;
+    const bool fast = x0 >= R && x0 + 32 + R <= nx && y0 >= R && y0 + ADJ_TY + R <= ny;
     float dL = 0.0f, dM = 0.0f, dS = 0.0f;        // this cell's terms (FP32)
-    if (fast) adj_a_tile<true>(st, lam_next, lam, cst, P, sphi, x0, y0, dL, dM, dS);
-    else adj_a_tile<false>(st, lam_next, lam, cst, P, sphi, x0, y0, dL, dM, dS);
+    if (fast) adj_a_tile<true, BIASED>(st, lam_next, lam, cst, P, sphi, x0, y0, dL, dM, dS);
+    else adj_a_tile<false, BIASED>(st, lam_next, lam, cst, P, sphi, x0, y0, dL, dM, dS);
     block_sum3f_atomic(dL, dM, dS, dparams);
 }
 
@@ -473,7 +503,25 @@ adj_step2d_b_kernel(const float *__restrict__ cst, float *__restrict__ lam, cons
     // c_j = 3 w_j e_j.(l_gx, l_gy) + 6 w_j l_lap from the four planes of A
     const float *lgx = cst + N, *lgy = cst + 2 * N, *llap = cst + 3 * N;
     float lphi = cst[c];
-    if (x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny) {
+    if (P.opts & OPT_BIASED) {
+        // biased gradient: a cell's gradient adjoint reaches the cells one
+        // (6 w_j e_j.l_grad) and two (-3/2 w_j e_j.l_grad) links away; the
+        // Laplacian's share stays 6 w_j l_lap on the near ones
+#pragma unroll
+        for (int j = 1; j < 9; ++j) {
+            const float w = L::w(j);
+#pragma unroll
+            for (int k = 1; k <= 2; ++k) {
+                int sx = x - k * L::ex(j), sy = y - k * L::ey(j);
+                const int kx = wrap_coord_far(sx, nx, P.periodic[0]);
+                const int ky = wrap_coord_far(sy, ny, P.periodic[1]);
+                if (kx >= 2 || ky >= 2) continue;        // no such cell
+                const size_t sc = (size_t)sy * nx + sx;
+                const float eg = edot2(L::ex(j), L::ey(j), __ldg(lgx + sc), __ldg(lgy + sc));
+                lphi += k == 1 ? fmaf(6.0f * w, eg, 6.0f * w * __ldg(llap + sc)) : (-1.5f * w) * eg;
+            }
+        }
+    } else if (x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny) {
         // all eight sources exist: c_j(y - e_j) with fixed offsets; the axis
         // and diagonal weights factored out
         const size_t up = c + nx, dn = c - nx;
@@ -528,8 +576,27 @@ adj_init2d_kernel(const float *__restrict__ phi0, const float *__restrict__ T0,
         const float ph = nb[0];
         const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
         const float dA = nb[5] - nb[7], dB = nb[8] - nb[6];
-        const float gx = 3.0f * (w1 * (nb[1] - nb[3]) + w5 * (dA + dB));
-        const float gy = 3.0f * (w1 * (nb[2] - nb[4]) + w5 * (dA - dB));
+        float gx, gy;
+        if (P.opts & OPT_BIASED) {
+            // the initialisation's biased gradient (two ghost layers)
+            float q2[9];
+#pragma unroll
+            for (int j = 1; j < 9; ++j) {
+                int cx = x + 2 * L::ex(j), cy = y + 2 * L::ey(j);
+                const int kx = wrap_coord_far(cx, nx, P.periodic[0]);
+                const int ky = wrap_coord_far(cy, ny, P.periodic[1]);
+                q2[j] = kx >= 2 ? P.phi_wall[kx - 2] : (ky >= 2 ? P.phi_wall[ky - 2] : phi0[(size_t)cy * nx + cx]);
+            }
+            const float bx = 0.5f * fmaf(4.0f, nb[1] - nb[3], -(q2[1] - q2[3]));
+            const float by = 0.5f * fmaf(4.0f, nb[2] - nb[4], -(q2[2] - q2[4]));
+            const float bA = 0.5f * fmaf(4.0f, dA, -(q2[5] - q2[7]));
+            const float bB = 0.5f * fmaf(4.0f, dB, -(q2[8] - q2[6]));
+            gx = 3.0f * fmaf(w1, bx, w5 * (bA + bB));
+            gy = 3.0f * fmaf(w1, by, w5 * (bA - bB));
+        } else {
+            gx = 3.0f * (w1 * (nb[1] - nb[3]) + w5 * (dA + dB));
+            gy = 3.0f * (w1 * (nb[2] - nb[4]) + w5 * (dA - dB));
+        }
         const float lap = 6.0f * (w1 * ((nb[1] + nb[3]) + (nb[2] + nb[4]) - 4.0f * ph)
                                 + w5 * ((nb[5] + nb[7]) + (nb[6] + nb[8]) - 4.0f * ph));
         const float pc = unit_phi(ph);
@@ -593,7 +660,10 @@ cudaError_t launch_adj_terminal2d(const float *st, const float *target, float *a
 cudaError_t launch_adj_step2d(const float *st, const float *lam_next, float *lam, float *cst,
                               double *dparams, const DevParams &P, cudaStream_t stream) {
     const int tiles = ((P.n[0] + 31) / 32) * ((P.n[1] + ADJ_TY - 1) / ADJ_TY);
-    adj_step2d_a_kernel<<<tiles, 32 * ADJ_TY, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
+    if (P.opts & OPT_BIASED)
+        adj_step2d_a_kernel<true><<<tiles, 32 * ADJ_TY, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
+    else
+        adj_step2d_a_kernel<false><<<tiles, 32 * ADJ_TY, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
     adj_step2d_b_kernel<<<dim3((P.n[0] + 255) / 256, P.n[1]), 256, 0, stream>>>(cst, lam, P);
     return cudaGetLastError();
 }

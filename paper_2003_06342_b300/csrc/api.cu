@@ -733,8 +733,7 @@ int lbm_get_kernel(const lbm_handle *h, int32_t *kernel) {
 static int adjoint_supported(const lbm_handle *h) {
     if (!h) return LBM_EINVAL;
     if (h->dim != 2 || h->params.storage != LBM_STORE_FP32 ||
-        h->params.model != LBM_MODEL_COUPLED || h->params.collision != LBM_COLLISION_BGK ||
-        h->params.grad_scheme != LBM_GRAD_CENTRAL)
+        h->params.model != LBM_MODEL_COUPLED || h->params.collision != LBM_COLLISION_BGK)
         return LBM_EUNSUPPORTED;
     return LBM_OK;
 }

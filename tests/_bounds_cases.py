@@ -94,9 +94,13 @@ def run_cac_case(n, storage, speed, period, steps):
     return st
 
 
-def run_adjoint_case():
+def run_adjoint_case(biased=False):
     from paper_2003_06342_b300.adjoint import gradients
     w = W.film_boiling_2d(40, 18, rho_ratio=5.0, y0=7.0, amplitude=1.5, phi_wall=(1.0, 0.0), theta_I=0.05)
+    if biased:
+        # wide enough for interior tiles of the two-ring window
+        w = W.film_boiling_2d(96, 24, rho_ratio=5.0, y0=8.0, amplitude=1.5, phi_wall=(1.0, 0.0),
+                              theta_I=0.05, grad_scheme="biased2")
     J, g = gradients(w.n, w.periodic, w.params, w.phi0, w.T0, w.phi0.copy(), 8, K=3, p0=w.p0)
     torch.cuda.synchronize()
     return np.concatenate([[J, g["L"], g["M_phi"], g["sigma"]], g["T0"].double().cpu().numpy().ravel()])
@@ -126,6 +130,7 @@ def run_all():
     for name, n, storage, speed, period, steps in CAC_CASES:
         out[name] = run_cac_case(n, storage, speed, period, steps)
     out["adjoint"] = run_adjoint_case()
+    out["adjoint_biased"] = run_adjoint_case(biased=True)
     out["noalloc"] = run_noalloc_case()
     return out
 

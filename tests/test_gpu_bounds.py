@@ -49,9 +49,10 @@ def test_phase_field_kernel_checked_and_bit_identical(debug_results, case):
     assert np.array_equal(rel, debug_results[name]), name
 
 
-def test_adjoint_kernels_checked(debug_results):
-    rel = BC.run_adjoint_case()
-    dbg = debug_results["adjoint"]
+@pytest.mark.parametrize("biased", [False, True], ids=["central", "biased"])
+def test_adjoint_kernels_checked(debug_results, biased):
+    rel = BC.run_adjoint_case(biased)
+    dbg = debug_results["adjoint_biased" if biased else "adjoint"]
     assert np.all(np.isfinite(dbg))
     assert np.allclose(rel, dbg, rtol=1e-6, atol=1e-12 * np.abs(rel).max())
 
