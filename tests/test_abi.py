@@ -201,7 +201,8 @@ def test_calls_reject_bad_arguments_before_device_work():
     # the adjoint exists for 2D FP32 only
     a, sc = ctypes.c_size_t(), ctypes.c_size_t()
     assert B.lib.lbm_adjoint_bytes(h, ctypes.byref(a), ctypes.byref(sc)) == B.LBM_OK
-    assert a.value == 29 * 16 * 16 * 4 and sc.value == 9 * 16 * 16 * 4
+    # the adjoint state: the 29 state planes and the phi adjoint; scratch: four stencil planes
+    assert a.value == 30 * 16 * 16 * 4 and sc.value == 4 * 16 * 16 * 4
     B.lib.lbm_destroy(h)
     p16 = make_params(w.params, "fp16")
     h2 = ctypes.c_void_p()
