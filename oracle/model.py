@@ -427,58 +427,98 @@ def _relax_trt(pops, eq_bar, S, tau, magic, lat, transport_odd):
 
 
 def mrt_basis(lat):
-    """Moment basis of the D2Q9 multiple-relaxation-time collision, built from
-    the lattice vectors (rows: rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy):
-    e = 3|c|^2 - 4, eps = 4 - 21|c|^2/2 + 9|c|^4/2, q_a = (3|c|^2 - 5) c_a,
-    p_xx = c_x^2 - c_y^2, p_xy = c_x c_y.  The rows are orthogonal."""
+    """Orthogonal moment basis of the multiple-relaxation-time collisions,
+    built from the lattice vectors (rows: moments, columns: directions; the
+    rows are orthogonal under the plain sum over directions).
+
+    D2Q9: rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy with e = 3|c|^2 - 4,
+    eps = 4 - 21|c|^2/2 + 9|c|^4/2, q_a = (3|c|^2 - 5) c_a,
+    p_xx = c_x^2 - c_y^2, p_xy = c_x c_y.
+
+    D3Q19: rho, e = 19|c|^2 - 30, eps = (21|c|^4 - 53|c|^2 + 24)/2, j_x,
+    q_x = (5|c|^2 - 9) c_x, j_y, q_y, j_z, q_z, p_xx = 3c_x^2 - |c|^2,
+    pi_xx = (3|c|^2 - 5)(3c_x^2 - |c|^2), p_ww = c_y^2 - c_z^2,
+    pi_ww = (3|c|^2 - 5)(c_y^2 - c_z^2), p_xy, p_yz, p_xz,
+    m_x = (c_y^2 - c_z^2) c_x, m_y = (c_z^2 - c_x^2) c_y, m_z = (c_x^2 - c_y^2) c_z.
+
+    D3Q7: rho, j_x, j_y, j_z, e = 7|c|^2 - 6, p_xx = 3c_x^2 - |c|^2,
+    p_ww = c_y^2 - c_z^2."""
     rows = []
     for i in range(lat.Q):
-        cx, cy = float(lat.e[i][0]), float(lat.e[i][1])
-        c2 = cx * cx + cy * cy
-        rows.append([1.0, 3.0 * c2 - 4.0, 4.0 - 10.5 * c2 + 4.5 * c2 * c2, cx, (3.0 * c2 - 5.0) * cx,
-                     cy, (3.0 * c2 - 5.0) * cy, cx * cx - cy * cy, cx * cy])
+        c = [float(v) for v in lat.e[i]]
+        if lat.name == "D2Q9":
+            cx, cy = c
+            c2 = cx * cx + cy * cy
+            rows.append([1.0, 3.0 * c2 - 4.0, 4.0 - 10.5 * c2 + 4.5 * c2 * c2, cx, (3.0 * c2 - 5.0) * cx,
+                         cy, (3.0 * c2 - 5.0) * cy, cx * cx - cy * cy, cx * cy])
+        elif lat.name == "D3Q19":
+            cx, cy, cz = c
+            c2 = cx * cx + cy * cy + cz * cz
+            pxx, pww = 3.0 * cx * cx - c2, cy * cy - cz * cz
+            rows.append([1.0, 19.0 * c2 - 30.0, (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0,
+                         cx, (5.0 * c2 - 9.0) * cx, cy, (5.0 * c2 - 9.0) * cy, cz, (5.0 * c2 - 9.0) * cz,
+                         pxx, (3.0 * c2 - 5.0) * pxx, pww, (3.0 * c2 - 5.0) * pww,
+                         cx * cy, cy * cz, cx * cz,
+                         (cy * cy - cz * cz) * cx, (cz * cz - cx * cx) * cy, (cx * cx - cy * cy) * cz])
+        elif lat.name == "D3Q7":
+            cx, cy, cz = c
+            c2 = cx * cx + cy * cy + cz * cz
+            rows.append([1.0, cx, cy, cz, 7.0 * c2 - 6.0, 3.0 * cx * cx - c2, cy * cy - cz * cz])
+        else:
+            raise ValueError(f"no moment basis for {lat.name}")
     return torch.tensor(rows, dtype=F64).T          # (moment, direction)
 
 
 def _relax_moments(pops, eq_bar, S, rates, lat):
     """Collision in the moment space of mrt_basis: with d = theta - eq_bar and
     m = M d, theta*_i = theta_i - (M^-1 diag(s) M d)_i + S_i, where `rates`
-    holds the nine rates s_k (scalars or per-cell tensors) in basis order
-    rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy."""
+    holds one rate s_k per moment (scalars or per-cell tensors) in basis
+    order."""
     Mb = mrt_basis(lat)
     d = torch.stack([pops[i] - eq_bar[i] for i in range(lat.Q)])          # (Q, *grid)
-    m = torch.tensordot(Mb, d, dims=1)                                    # (9, *grid)
+    m = torch.tensordot(Mb, d, dims=1)                                    # (Q, *grid)
     norms = (Mb * Mb).sum(dim=1)
     shape = (-1,) + (1,) * (m.dim() - 1)
     s = [r if torch.is_tensor(r) else torch.full_like(m[0], r) for r in rates]
-    relaxed = torch.stack([s[k] * m[k] for k in range(9)]) / norms.reshape(shape)
+    relaxed = torch.stack([s[k] * m[k] for k in range(len(s))]) / norms.reshape(shape)
     r = torch.tensordot(Mb.T, relaxed, dims=1)                            # M^-1 = M^T diag(1/norms)
     return [pops[i] - r[i] + S[i] for i in range(lat.Q)]
 
 
 def _relax_mrt(pops, eq_bar, S, tau, rates, lat):
     """Multiple-relaxation-time collision of the flow set (the "next" MRT
-    row; not in the paper).  The conserved moments and the stress moments
-    relax with the BGK rate 1/(tau + 1/2) (the viscosity), e and eps with
-    s_e and s_eps, and the odd moments j and q with s_q; with every rate
-    equal to the BGK rate this is Eq. LBE, and with s_e = s_eps =
-    1/(tau + 1/2) it is the TRT collision whose antisymmetric rate is s_q."""
+    row; not in the paper).  The conserved moment rho and the stress moments
+    relax with the BGK rate 1/(tau + 1/2) (the viscosity), e with s_e, the
+    fourth-order even moments (eps; in 3D also pi_xx, pi_ww) with s_eps, and
+    the odd moments (j, q; in 3D also m) with s_q.  With every rate equal to
+    the BGK rate this is Eq. LBE; with s_e = s_eps = 1/(tau + 1/2) every even
+    moment relaxes at the BGK rate and every odd one at s_q, which is the TRT
+    collision whose antisymmetric rate is s_q."""
     om = 1.0 / (tau + 0.5)
     s_e, s_eps, s_q = rates
-    return _relax_moments(pops, eq_bar, S, [om, s_e, s_eps, s_q, s_q, s_q, s_q, om, om], lat)
+    if lat.name == "D2Q9":
+        r = [om, s_e, s_eps, s_q, s_q, s_q, s_q, om, om]
+    else:   # D3Q19
+        r = [om, s_e, s_eps, s_q, s_q, s_q, s_q, s_q, s_q, om, s_eps, om, s_eps, om, om, om, s_q, s_q, s_q]
+    return _relax_moments(pops, eq_bar, S, r, lat)
 
 
 def _relax_mrt_g(pops, eq_bar, S, tau, rates, lat):
     """Multiple-relaxation-time collision of the phase-field set (not in the
     paper): phi and the fluxes j relax with the BGK rate 1/(tau_g + 1/2),
     which carries the mobility M_phi, so the model's transport coefficient
-    is that of Eq. LBE; e, eps, q and the stress moments p_xx, p_xy take
-    s_e, s_eps, s_q and s_p (a rate of 0 stands for the BGK rate).  With
-    s_q = the BGK rate and s_e = s_eps = s_p = w+ this is the TRT collision
-    of g (odd moments at the mobility rate, even ones at w+)."""
+    is that of Eq. LBE; the other moments take s_e (e), s_eps (eps), s_q (q)
+    and s_p (the stress moments), a rate of 0 standing for the BGK rate.
+    D3Q7 has no eps and no q: e takes s_e, p_xx and p_ww s_p.  With s_q = the
+    BGK rate and s_e = s_eps = s_p = w+ this is the TRT collision of g (odd
+    moments at the mobility rate, even ones at w+)."""
     om = 1.0 / (tau + 0.5)
     s_e, s_eps, s_q, s_p = [om if r == 0.0 else r for r in rates]
-    return _relax_moments(pops, eq_bar, S, [om, s_e, s_eps, om, s_q, om, s_q, s_p, s_p], lat)
+    if lat.name == "D2Q9":
+        r = [om, s_e, s_eps, om, s_q, om, s_q, s_p, s_p]
+    else:   # D3Q7
+        r = [om, om, om, om, s_e, s_p, s_p]
+    return _relax_moments(pops, eq_bar, S, r, lat)
 
 
 def collide(st, M, q, P, grid):
@@ -504,8 +544,6 @@ def collide(st, M, q, P, grid):
     s_eq, s_S, tau_s = E["s"]
     s_bar = [s_eq[i] - 0.5 * s_S[i] for i in range(Lf.Q)]
     if P.collision == "mrt":
-        if grid.dim != 2:
-            raise ValueError("the MRT collision is defined for D2Q9")
         f_out = _relax_mrt(st["f"], f_bar, f_S, tau_f, P.mrt_rates, Lf)
         g_out = _relax_mrt_g(st["g"], g_bar, g_src, tau_g, P.mrt_rates_g, Lg)
         s_out = [_relax(st["s"][i], s_bar[i], s_S[i], tau_s) for i in range(Lf.Q)]
