@@ -395,6 +395,21 @@ def run_device(args, world, rank, local):
             "workload": w3.name + ", TRT collision", "kernel": v.kernel(), "MLUPS": w3.cells / ms_v / 1e3,
             "ms_per_step": ms_v, **roof(rk, w3.cells, ms_v, peak), "finite": bool(np.isfinite(m_v))}
         del v
+        # MRT in 3D (D3Q19 flow set, D3Q7 phase-field set; TMA-staged kernel)
+        w3m = dict(w3.params, collision="mrt", mrt_rates=(1.4, 1.4, 1.2), mrt_rates_g=(1.3, 0.0, 0.0, 1.25))
+        for storage in ("fp32", "fp16"):
+            v = Solver(w3.n, w3.periodic, w3m, storage=storage, device=dev, stream=stream)
+            v.set_kernel("tma")
+            v.init(w3.phi0, w3.T0, p0=w3.p0)
+            v.step(5)
+            ms_v = step_kernel_ms(v, 100)
+            m_v = safe_reduce(v)
+            rk = ("3d", storage)
+            variants[f"3d_{storage}_tma_mrt"] = {
+                "workload": w3.name + ", MRT collision of f and g", "kernel": v.kernel(),
+                "MLUPS": w3.cells / ms_v / 1e3, "ms_per_step": ms_v, **roof(rk, w3.cells, ms_v, peak),
+                "finite": bool(np.isfinite(m_v))}
+            del v
         torch.cuda.empty_cache()
         # the 512 x 512 x 768 FP16 film (201 M cells, 36 GB of populations)
         w5 = W.c5_film_boiling_3d_large()

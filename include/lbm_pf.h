@@ -111,22 +111,28 @@ typedef struct {
 #define LBM_COLLISION_TRT 1
 /* MRT: multiple relaxation times for the flow set f and the phase-field set
  * g (not in the paper; the multiple-relaxation-time extension its outlook
- * names); s keeps BGK.  With d = theta - theta_eq_bar expressed in the
- * orthogonal D2Q9 moment basis (rho, e = 3|c|^2 - 4, eps = 4 - 21|c|^2/2 +
- * 9|c|^4/2, j_x, q_x = (3|c|^2 - 5) c_x, j_y, q_y, p_xx = c_x^2 - c_y^2,
- * p_xy = c_x c_y):
- *   f: rho, p_xx and p_xy relax at the BGK rate 1/(tau_f + 1/2) (the
- *      viscosity), e and eps at mrt_rates[0] and [1], j and q at
- *      mrt_rates[2]; each rate in (0, 2), else LBM_EINVAL.  Equal rates give
- *      BGK; s_e = s_eps = 1/(tau_f + 1/2) gives the TRT collision of f with
- *      antisymmetric rate s_q; s_q = 8 (2 - s_nu)/(8 - s_nu) puts the
- *      half-way bounce-back wall at the middle of the link for Poiseuille
- *      flow.
- *   g: phi and j relax at the BGK rate 1/(tau_g + 1/2) (the mobility), e,
- *      eps, q and p_xx, p_xy at mrt_rates_g[0..3]; each rate 0 (meaning the
- *      BGK rate, so all zeros keep g on BGK) or in (0, 2), else LBM_EINVAL.
- * MRT is implemented for LBM_MODEL_COUPLED on D2Q9 (tiled and TMA kernels);
- * D3Q19_D3Q7 and the phase-field model return LBM_EUNSUPPORTED; the adjoint
+ * names); s keeps BGK.  d = theta - theta_eq_bar is taken to an orthogonal
+ * moment basis.  D2Q9: rho, e = 3|c|^2 - 4, eps = 4 - 21|c|^2/2 + 9|c|^4/2,
+ * j_x, q_x = (3|c|^2 - 5) c_x, j_y, q_y, p_xx = c_x^2 - c_y^2, p_xy = c_x c_y.
+ * D3Q19 (f): the d'Humieres basis rho, e = 19|c|^2 - 30, eps = (21|c|^4 -
+ * 53|c|^2 + 24)/2, j, q = (5|c|^2 - 9) c, p_xx = 3c_x^2 - |c|^2, pi_xx =
+ * (3|c|^2 - 5) p_xx, p_ww = c_y^2 - c_z^2, pi_ww = (3|c|^2 - 5) p_ww, p_xy,
+ * p_yz, p_xz, m_x = (c_y^2 - c_z^2) c_x and its cyclic m_y, m_z.  D3Q7 (g):
+ * rho, j, e = 7|c|^2 - 6, p_xx = 3c_x^2 - |c|^2, p_ww = c_y^2 - c_z^2.
+ *   f: rho and the stress moments (p_*) relax at the BGK rate 1/(tau_f +
+ *      1/2) (the viscosity); e at mrt_rates[0]; eps (in 3D also pi_xx,
+ *      pi_ww) at mrt_rates[1]; j and q (in 3D also m) at mrt_rates[2]; each
+ *      rate in (0, 2), else LBM_EINVAL.  Equal rates give BGK; s_e = s_eps =
+ *      1/(tau_f + 1/2) gives the TRT collision of f with antisymmetric rate
+ *      s_q; s_q = 8 (2 - s_nu)/(8 - s_nu) puts the half-way bounce-back wall
+ *      at the middle of the link for Poiseuille flow.
+ *   g: phi and j relax at the BGK rate 1/(tau_g + 1/2) (the mobility); e,
+ *      eps, q and the stress moments at mrt_rates_g[0..3] (D3Q7 has no eps
+ *      and no q: mrt_rates_g[1] and [2] are checked but unused there); each
+ *      rate 0 (meaning the BGK rate, so all zeros keep g on BGK) or in (0, 2),
+ *      else LBM_EINVAL.
+ * MRT is implemented for LBM_MODEL_COUPLED in 2D and 3D (tiled and TMA
+ * kernels); the phase-field model returns LBM_EUNSUPPORTED; the adjoint
  * covers BGK only. */
 #define LBM_COLLISION_MRT 2
 

@@ -102,7 +102,7 @@ int validate(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
         for (int k = 0; k < 4; ++k)
             if (!(p->mrt_rates_g[k] == 0.0 || (p->mrt_rates_g[k] > 0.0 && p->mrt_rates_g[k] < 2.0)))
                 return LBM_EINVAL;
-        if (dim != 2 || p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
+        if (p->model != LBM_MODEL_COUPLED) return LBM_EUNSUPPORTED;
     }
     const double vals[] = {p->rho_l, p->rho_g, p->nu_l, p->nu_g, p->alpha_l, p->alpha_g, p->sigma,
                            p->W, p->M_phi, p->A, p->theta_I, p->L, p->Cp, p->T_sat,

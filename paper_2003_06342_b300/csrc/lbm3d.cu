@@ -8,7 +8,7 @@
 // its own cell of plane z+1 in registers for the next iteration.  The halo
 // ring's gbar and q are re-read from L2, so populations cross HBM once.
 // Everything else mirrors the 2D kernel (see lbm2d.cu): moments, closures,
-// production rate, three BGK (or TRT) collisions and push streaming with wall
+// production rate, three BGK (or TRT / MRT) collisions and push streaming with wall
 // links.
 #include "lbm_common.cuh"
 #include "lbm_kernels.h"
@@ -17,7 +17,7 @@
 
 namespace lbm {
 
-template <typename S, bool TRT, bool BIASED>
+template <typename S, int COLL, bool BIASED>
 __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
 step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
@@ -26,13 +26,13 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int cls = tile_class3d(x0, y0, P);
     if (BIASED) {
-        if (cls == XY_IN) step3d_column_biased<S, XY_IN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
-        else if (cls == XY_WRAP) step3d_column_biased<S, XY_WRAP, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
-        else step3d_column_biased<S, XY_GEN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        if (cls == XY_IN) step3d_column_biased<S, XY_IN, COLL>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        else if (cls == XY_WRAP) step3d_column_biased<S, XY_WRAP, COLL>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        else step3d_column_biased<S, XY_GEN, COLL>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
     } else {
-        if (cls == XY_IN) step3d_column<S, XY_IN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
-        else if (cls == XY_WRAP) step3d_column<S, XY_WRAP, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
-        else step3d_column<S, XY_GEN, TRT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        if (cls == XY_IN) step3d_column<S, XY_IN, COLL>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        else if (cls == XY_WRAP) step3d_column<S, XY_WRAP, COLL>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        else step3d_column<S, XY_GEN, COLL>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
     }
 }
 
@@ -207,11 +207,18 @@ cudaError_t launch_step3d(const void *pin, void *pout, float *phi_prev, const fl
     const S *in = (const S *)pin;
     S *out = (S *)pout;
     const Planes3d<S> PL = planes3d<S>(pin, pout, P);
-    switch (P.opts & (OPT_TRT | OPT_BIASED)) {
-    case 0: step3d_kernel<S, false, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
-    case OPT_TRT: step3d_kernel<S, true, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
-    case OPT_BIASED: step3d_kernel<S, false, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
-    default: step3d_kernel<S, true, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    switch (P.opts & (OPT_TRT | OPT_MRT | OPT_BIASED)) {
+    case 0: step3d_kernel<S, COLL_BGK, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_TRT: step3d_kernel<S, COLL_TRT, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_MRT: step3d_kernel<S, COLL_MRT, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_BIASED: step3d_kernel<S, COLL_BGK, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_TRT | OPT_BIASED:
+        step3d_kernel<S, COLL_TRT, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL);
+        break;
+    case OPT_MRT | OPT_BIASED:
+        step3d_kernel<S, COLL_MRT, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL);
+        break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

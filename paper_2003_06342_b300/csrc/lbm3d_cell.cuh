@@ -307,6 +307,89 @@ __device__ __forceinline__ float rep3(int i, float x) {
     return IsNarrow<S>::value ? x : weighted<Lt>(i, x);
 }
 
+// ---- MRT collisions in 3D (an extension outside the paper)
+// With d_i = theta_i - theta_eq_bar_i (population units) and an orthogonal
+// moment basis M (rows m_k with squared norms N_k), the MRT update is the
+// BGK update plus -(M^T diag((s_k - om) / N_k) M d)_i.
+//
+// D3Q19, flow set, d'Humieres basis: rho and the stress moments p_xx, p_ww,
+// p_xy, p_yz, p_xz keep om; e (N = 2394) takes s_e; eps (252), pi_xx (72)
+// and pi_ww (24) take s_eps; the nine odd moments j, q, m take s_q.  Those
+// nine span every function odd in e, so their share of the correction is
+// -(s_q - om) (d_i - d_o) / 2 (o = opposite).  The even share depends only
+// on the link's class (rest; x, y, z axis; xy, xz, yz edge) through
+//   e     = -30 d_0 - 11 sum_a A_a + 8 sum_ab E_ab
+//   eps   =  12 d_0 -  4 sum_a A_a +   sum_ab E_ab
+//   pi_xx = -4 A_x + 2 (A_y + A_z) + E_xy + E_xz - 2 E_yz
+//   pi_ww = -2 A_y + 2 A_z + E_xy - E_xz
+// with A_a the sum of d over the two a-axis links and E_ab over the four
+// ab-edge links.  Every product is rounded on its own (__fmul_rn, explicit
+// fmaf), so each kernel that runs the correction produces the same bits.
+struct Mrt19Even { float r0, ax, ay, az, exy, exz, eyz; };
+
+__device__ __forceinline__ Mrt19Even mrt19_even(float d0, float Ax, float Ay, float Az, float Exy,
+                                                float Exz, float Eyz, float de, float dp) {
+    const float sA = (Ax + Ay) + Az, sE = (Exy + Exz) + Eyz;
+    const float me = fmaf(-30.0f, d0, fmaf(-11.0f, sA, __fmul_rn(8.0f, sE)));
+    const float meps = fmaf(12.0f, d0, fmaf(-4.0f, sA, sE));
+    const float mxx = fmaf(-4.0f, Ax, fmaf(2.0f, Ay + Az, fmaf(-2.0f, Eyz, Exy + Exz)));
+    const float mww = fmaf(2.0f, Az - Ay, Exy - Exz);
+    const float Te = __fmul_rn(__fmul_rn(de, 1.0f / 2394.0f), me);
+    const float Tp = __fmul_rn(__fmul_rn(dp, 1.0f / 252.0f), meps);
+    const float Tx = __fmul_rn(__fmul_rn(dp, 1.0f / 72.0f), mxx);
+    const float Tw = __fmul_rn(__fmul_rn(dp, 1.0f / 24.0f), mww);
+    Mrt19Even r;
+    r.r0 = fmaf(30.0f, Te, __fmul_rn(-12.0f, Tp));
+    const float axb = fmaf(11.0f, Te, __fmul_rn(4.0f, Tp));    // common to the axis links
+    r.ax = fmaf(4.0f, Tx, axb);
+    const float ayz = fmaf(-2.0f, Tx, axb);
+    r.ay = fmaf(2.0f, Tw, ayz);
+    r.az = fmaf(-2.0f, Tw, ayz);
+    const float eb = -fmaf(8.0f, Te, Tp);                      // common to the edge links
+    r.exy = eb - (Tx + Tw);
+    r.exz = eb - (Tx - Tw);
+    r.eyz = fmaf(2.0f, Tx, eb);
+    return r;
+}
+
+// the even share of the link pair half19(k) (k = 0..8)
+__device__ __forceinline__ float mrt19_class(const Mrt19Even &r, int k) {
+    return k == 0 ? r.ax : k == 1 ? r.ay : k == 2 ? r.az : k <= 4 ? r.exy : k <= 6 ? r.exz : r.eyz;
+}
+
+// D3Q7, phase-field set: rho and j keep om_g (the mobility); e = 7|c|^2 - 6
+// (N = 42) takes s_e, the stress moments p_xx = 3c_x^2 - |c|^2 (12) and
+// p_ww = c_y^2 - c_z^2 (4) take s_p.  The correction is even: r0 for the
+// rest link, r[a] for both links of axis a (A_a as above).
+__device__ __forceinline__ void mrt7_even(float d0, float Ax, float Ay, float Az, float de,
+                                          float dp, float &r0, float r[3]) {
+    const float me = fmaf(-6.0f, d0, (Ax + Ay) + Az);
+    const float mxx = fmaf(2.0f, Ax, -(Ay + Az));
+    const float mww = Ay - Az;
+    const float Te = __fmul_rn(__fmul_rn(de, 1.0f / 42.0f), me);
+    const float Tx = __fmul_rn(__fmul_rn(dp, 1.0f / 12.0f), mxx);
+    const float Tw = __fmul_rn(__fmul_rn(dp, 0.25f), mww);
+    r0 = __fmul_rn(6.0f, Te);
+    r[0] = -fmaf(2.0f, Tx, Te);
+    const float yz = Tx - Te;
+    r[1] = yz - Tw;
+    r[2] = yz + Tw;
+}
+
+// d_i from the working value v and eqw = theta_eq_bar_i / w_i - ref
+template <typename S, class Lt>
+__device__ __forceinline__ float mrt_dev3(int i, float v, float eqw, float inv_sc) {
+    return IsNarrow<S>::value ? __fmul_rn(Lt::w(i), fmaf(v, inv_sc, -eqw)) : fmaf(-Lt::w(i), eqw, v);
+}
+
+// a correction c in population units, in the working representation: c for
+// FP32 deviations, c scale / w_i for 16-bit values
+template <typename S, class Lt>
+__device__ __forceinline__ float mrt_rep3(int i, float c, float sc) {
+    const float iw = Lt::Q == 19 ? (i == 0 ? 3.0f : (i <= 6 ? 18.0f : 36.0f)) : (i == 0 ? 4.0f : 8.0f);
+    return IsNarrow<S>::value ? __fmul_rn(__fmul_rn(sc, iw), c) : c;
+}
+
 // Push from cell c = (x, y, z).  MODE XY_IN: the link stays inside the grid;
 // XY_WRAP: it may cross a periodic x / y boundary but not a z edge or a wall;
 // XY_GEN: anything.  Through a wall a value comes back to c in the opposite
@@ -400,18 +483,21 @@ __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int 
 // (algebraically Eq. LBE with theta_eq_bar = theta_eq - S/2 and the sources of
 // Eqs. Forcing, MicroProduction, SourceTerm_AllenCahn, Def_SourceTerms_Temp).
 // MODE (see push3d): how the links of this cell are pushed.
-// TRT: see cell_update2d; the rest direction relaxes with the symmetric
+// COLL_TRT: see cell_update2d; the rest direction relaxes with the symmetric
 // rate, every other output is a1 v_i + a2 v_o + ... (o = opposite).
+// COLL_MRT: the BGK update of f and g plus the moment-space correction of
+// mrt19_even / mrt7_even (rates mrt_rates, mrt_rates_g; s keeps BGK).
 // BIASED: sphi holds five planes of two-ring windows (plane p in slot
 // (p + 2) % 5) and the gradient of Eq. Grad uses the second-order biased
 // difference [-phi(x + 2e) + 4 phi(x + e) - 3 phi(x)] / 2 (Sec. 3.4).
-template <typename S, int MODE, bool TRT = false, bool BIASED = false>
+template <typename S, int MODE, int COLL = COLL_BGK, bool BIASED = false>
 __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
                                                const float f[QF], const float s[QF],
                                                const float g[QG], float qp, float phip,
                                                S *__restrict__ pout, float *__restrict__ phi_prev,
                                                float *__restrict__ q_out, const DevParams &P,
                                                const Planes3d<S> &PL) {
+    constexpr bool TRT = COLL == COLL_TRT, MRT = COLL == COLL_MRT;
     const int tx = threadIdx.x, ty = threadIdx.y;
     Macro3 m;
     float phd, gx = 0.0f, gy = 0.0f, gz = 0.0f, la = 0.0f, ld = 0.0f;
@@ -506,6 +592,10 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float a1_g = 1.0f - 0.5f * (omp_g + omm_g), a2_g = 0.5f * (omm_g - omp_g);
     const float a1_s = 1.0f - 0.5f * (omp_s + omm_s), a2_s = 0.5f * (omm_s - omp_s);
 
+    // an output plus its MRT correction (the correction is never formed for
+    // BGK and TRT)
+    auto plus = [&](float v, float cm) { return MRT ? __fadd_rn(v, cm) : v; };
+
     // phase field on D3Q7: poly = 4 e.u + 8 (e.u)^2 - 2 u^2
     {
         const float iface = P.four_over_W * ph * (1.0f - ph);
@@ -517,7 +607,31 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Vg[3] = {fmaf(4.0f * Bgo, ux, bgi * n0), fmaf(4.0f * Bgo, uy, bgi * n1),
                              fmaf(4.0f * Bgo, uz, bgi * n2)};
         const float usq2 = 2.0f * usq;
-        push3d_g<S, MODE>(0, fmaf(a_g, g[0], rep3<S, LG>(0, fmaf(Bg, -usq2, Ag))),
+        // MRT: the correction of the rest link and of each axis pair
+        float cg0 = 0.0f, cgA[3] = {0.0f, 0.0f, 0.0f};
+        if constexpr (MRT) {
+            // g_eq_bar / w - phi_ref: the coefficients above at om = 1, b = -1/2
+            const float Agb = fmaf(-0.5f, q, phd);
+            const float hif = __fmul_rn(-0.5f, iface);
+            const float nn[3] = {n0, n1, n2};
+            const float isc = P.set_isc[1];
+            const float d0 = mrt_dev3<S, LG>(0, g[0], fmaf(ph, -usq2, Agb), isc);
+            float A[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float ua = m.u[a];
+                const float Eb = fmaf(ph, fmaf(8.0f * ua, ua, -usq2), Agb);
+                const float Vb = fmaf(4.0f * ph, ua, __fmul_rn(hif, nn[a]));
+                A[a] = mrt_dev3<S, LG>(a + 1, g[a + 1], Eb + Vb, isc) +
+                       mrt_dev3<S, LG>(a + 4, g[a + 4], Eb - Vb, isc);
+            }
+            float r0, r[3];
+            mrt7_even(d0, A[0], A[1], A[2], P.mrt_rates_g[0] - om_g, P.mrt_rates_g[3] - om_g, r0, r);
+            cg0 = mrt_rep3<S, LG>(0, r0, P.set_sc[1]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cgA[a] = mrt_rep3<S, LG>(a + 1, r[a], P.set_sc[1]);
+        }
+        push3d_g<S, MODE>(0, plus(fmaf(a_g, g[0], rep3<S, LG>(0, fmaf(Bg, -usq2, Ag))), cg0),
                             x, y, z, c, pout, P, PL);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -525,8 +639,10 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
             const float Eg = fmaf(Bg, fmaf(8.0f * ua, ua, -usq2), Ag);
             auto rg = [&](float v) { return rep3<S, LG>(a + 1, v); };
             if (!TRT) {
-                push3d_g<S, MODE>(a + 1, fmaf(a_g, g[a + 1], rg(Eg + Vg[a])), x, y, z, c, pout, P, PL);
-                push3d_g<S, MODE>(a + 4, fmaf(a_g, g[a + 4], rg(Eg - Vg[a])), x, y, z, c, pout, P, PL);
+                push3d_g<S, MODE>(a + 1, plus(fmaf(a_g, g[a + 1], rg(Eg + Vg[a])), cgA[a]), x, y, z, c,
+                                  pout, P, PL);
+                push3d_g<S, MODE>(a + 4, plus(fmaf(a_g, g[a + 4], rg(Eg - Vg[a])), cgA[a]), x, y, z, c,
+                                  pout, P, PL);
             } else {
                 push3d_g<S, MODE>(a + 1, fmaf(a1_g, g[a + 1], fmaf(a2_g, g[a + 4], rg(Eg + Vg[a]))),
                                   x, y, z, c, pout, P, PL);
@@ -561,7 +677,41 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     const float Bso = TRT ? scs * (omm_s * m.T) : Bs;
     // __fmul_rn: W enters E +- e.W as a finished product, never fused into the sum
     const float Wx = __fmul_rn(3.0f * Bso, ux), Wy = __fmul_rn(3.0f * Bso, uy), Wz = __fmul_rn(3.0f * Bso, uz);
-    push3d_fs<S, MODE>(0, fmaf(a_f, f[0], rep3<S, LF>(0, fmaf(K1, -usq15, K0))),
+    // MRT: the even share of f's correction by link class and the odd parts
+    // d_i - d_o of the pairs
+    Mrt19Even cfe{};
+    float fdif[9], hq = 0.0f;
+    if constexpr (MRT) {
+        // f_eq_bar / w - ref: the coefficients above at om = 1, b = -1/2
+        const float K0b = fmaf(-0.5f, fmaf(rcs2 * q, P.kappa, -uB), m.p - P.set_ref[0]);
+        const float K1b = fmaf(0.5f, hU, rcs2);
+        const float Hbx = __fmul_rn(-0.5f, hx), Hby = __fmul_rn(-0.5f, hy), Hbz = __fmul_rn(-0.5f, hz);
+        const float Vbx = fmaf(3.0f * K1b, ux, __fmul_rn(-0.5f, m.F[0]));
+        const float Vby = fmaf(3.0f * K1b, uy, __fmul_rn(-0.5f, m.F[1]));
+        const float Vbz = fmaf(3.0f * K1b, uz, __fmul_rn(-0.5f, m.F[2]));
+        const float isc = P.set_isc[0];
+        const float d0 = mrt_dev3<S, LF>(0, f[0], fmaf(K1b, -usq15, K0b), isc);
+        float cls[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = half19(k), o = LF::opp(i);
+            const int ex = LF::ex(i), ey = LF::ey(i), ez = LF::ez(i);
+            const float cu = edot3(ex, ey, ez, ux, uy, uz);
+            const float Pe = fmaf(4.5f * cu, cu, -usq15);
+            const float eHb = edot3(ex, ey, ez, Hbx, Hby, Hbz);
+            const float Eb = fmaf(3.0f * cu, eHb, fmaf(K1b, Pe, K0b));
+            const float Ob = fmaf(Pe, eHb, edot3(ex, ey, ez, Vbx, Vby, Vbz));
+            const float di = mrt_dev3<S, LF>(i, f[i], Eb + Ob, isc);
+            const float dO = mrt_dev3<S, LF>(o, f[o], Eb - Ob, isc);
+            cls[k] = di + dO;
+            fdif[k] = di - dO;
+        }
+        cfe = mrt19_even(d0, cls[0], cls[1], cls[2], cls[3] + cls[4], cls[5] + cls[6], cls[7] + cls[8],
+                         P.mrt_rates[0] - om_f, P.mrt_rates[1] - om_f);
+        hq = -0.5f * (P.mrt_rates[2] - om_f);
+    }
+    push3d_fs<S, MODE>(0, plus(fmaf(a_f, f[0], rep3<S, LF>(0, fmaf(K1, -usq15, K0))),
+                               mrt_rep3<S, LF>(0, cfe.r0, P.set_sc[0])),
                             fmaf(a_s, s[0], rep3<S, LF>(0, fmaf(Bs, -usq15, As))), x, y, z, c,
                             pout, P, PL);
 #pragma unroll
@@ -579,10 +729,14 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         // w_i = w_o: the increments of i and o share the weight of i
         auto rf = [&](float v) { return rep3<S, LF>(i, v); };
         if (!TRT) {
-            push3d_fs<S, MODE>(i, fmaf(a_f, f[i], rf(Ef + Of)), fmaf(a_s, s[i], rf(Es + Os)),
-                               x, y, z, c, pout, P, PL);
-            push3d_fs<S, MODE>(o, fmaf(a_f, f[o], rf(Ef - Of)), fmaf(a_s, s[o], rf(Es - Os)),
-                               x, y, z, c, pout, P, PL);
+            float vi = fmaf(a_f, f[i], rf(Ef + Of)), vo = fmaf(a_f, f[o], rf(Ef - Of));
+            if constexpr (MRT) {
+                const float ck = mrt19_class(cfe, k), od = __fmul_rn(hq, fdif[k]);
+                vi = __fadd_rn(vi, mrt_rep3<S, LF>(i, ck + od, P.set_sc[0]));
+                vo = __fadd_rn(vo, mrt_rep3<S, LF>(o, ck - od, P.set_sc[0]));
+            }
+            push3d_fs<S, MODE>(i, vi, fmaf(a_s, s[i], rf(Es + Os)), x, y, z, c, pout, P, PL);
+            push3d_fs<S, MODE>(o, vo, fmaf(a_s, s[o], rf(Es - Os)), x, y, z, c, pout, P, PL);
         } else {
             push3d_fs<S, MODE>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], rf(Ef + Of))),
                                fmaf(a1_s, s[i], fmaf(a2_s, s[o], rf(Es + Os))), x, y, z, c, pout, P, PL);
@@ -594,7 +748,7 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
 
 // One z-column of a 32x4 tile over layers [blockIdx.z * ZBLK, +ZBLK), every
 // value read with plain loads (see lbm3d.cu).
-template <typename S, int XY, bool TRT = false, int ZBLK = ZB>
+template <typename S, int XY, int COLL = COLL_BGK, int ZBLK = ZB>
 __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__restrict__ pout,
                                               float *__restrict__ phi_prev,
                                               const float *__restrict__ q_in,
@@ -648,9 +802,9 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
             const float phip = phi_prev[c];
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY, TRT>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY, COLL>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN, TRT>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY_GEN, COLL>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
         }
 #pragma unroll
         for (int i = 0; i < QG; ++i) g[i] = gn[i];
@@ -679,7 +833,7 @@ __device__ __forceinline__ float window_phid_b(int cx, int cy, int cz, const S *
 // each of the tile and two rings, every value formed from plain loads.
 // XY: the tile class, used for the push of interior layers as in
 // step3d_column.
-template <typename S, int XY, bool TRT>
+template <typename S, int XY, int COLL>
 __device__ __forceinline__ void step3d_column_biased(const S *__restrict__ pin, S *__restrict__ pout,
                                                      float *__restrict__ phi_prev,
                                                      const float *__restrict__ q_in,
@@ -712,9 +866,9 @@ __device__ __forceinline__ void step3d_column_biased(const S *__restrict__ pin, 
             for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
             const float qp = q_in[c], phip = phi_prev[c];
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY, TRT, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY, COLL, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN, TRT, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY_GEN, COLL, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
         }
         __syncthreads();   // slot (z - 2 + 2) % 5 is refilled next iteration
     }

@@ -269,7 +269,7 @@ __device__ __forceinline__ void bwin_store(float *pl, const uint32_t *buf, int p
 // z + 1; the copies of f/s(z + 1) and g(z + 2) are in flight, and when layer
 // z is done its stages receive f/s(z + 2) and g(z + 3): every copy is issued
 // at least one whole layer before it is awaited.
-template <typename S, int XY, bool TRT, bool BIASED>
+template <typename S, int XY, int COLL, bool BIASED>
 __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S *__restrict__ pin,
                                            S *__restrict__ pout, float *__restrict__ phi_prev,
                                            const float *__restrict__ q_in, float *__restrict__ q_out,
@@ -348,10 +348,10 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
                 const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
                 const size_t c = (size_t)z * plane_cells + cxy;
                 if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                    layer_update3d<S, XY, TRT, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out,
+                    layer_update3d<S, XY, COLL, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out,
                                                      P, PL);
                 else
-                    layer_update3d<S, XY_GEN, TRT, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev,
+                    layer_update3d<S, XY_GEN, COLL, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev,
                                                          q_out, P, PL);
             }
             __syncthreads();      // the stages of layer z and window slot of plane z - 2 are free
@@ -421,9 +421,9 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const size_t c = (size_t)z * plane_cells + cxy;
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY, TRT>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY, COLL>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN, TRT>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY_GEN, COLL>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
         }
         __syncthreads();      // the stages of layer z and window slot (z - 1) % 3 are free
         if (z + Gm::NFS < zend) {
@@ -440,7 +440,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
     }
 }
 
-template <typename S, bool TRT, bool BIASED>
+template <typename S, int COLL, bool BIASED>
 __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
 step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ pin,
                   S *__restrict__ pout, float *__restrict__ phi_prev,
@@ -461,7 +461,7 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
             if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(err, 2);
             return;
         }
-        step3d_column<S, XY_GEN, TRT, Tma3Geom<S>::ZBT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
+        step3d_column<S, XY_GEN, COLL, Tma3Geom<S>::ZBT>(pin, pout, phi_prev, q_in, q_out, P, sphi, PL);
         return;
     }
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -475,9 +475,9 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     // enough for the instruction cache (measured: FP32 +1.9%, FP16 +3.9%)
     const int cls = tile_class3d(x0, y0, P);
     if (cls != XY_GEN)
-        tma_column<S, XY_WRAP, TRT, BIASED>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
+        tma_column<S, XY_WRAP, COLL, BIASED>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
     else
-        tma_column<S, XY_GEN, TRT, BIASED>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
+        tma_column<S, XY_GEN, COLL, BIASED>(maps, par, pin, pout, phi_prev, q_in, q_out, err, P, smem, barF, barG, sphi, rbuf, PL);
 }
 
 // ------------------------------------------------------------------ host side
@@ -527,25 +527,28 @@ int make_tma_maps3d(TmaMaps3d *M, const DevParams &P, int elem_bytes, void *cons
     return 0;
 }
 
-template <typename S, bool TRT, bool BIASED>
+template <typename S, int COLL, bool BIASED>
 static int blocks_per_sm_one() {
     int n = 0;
     const int dyn = Tma3Geom<S>::DYN;
-    if (cudaFuncSetAttribute(step3d_tma_kernel<S, TRT, BIASED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(step3d_tma_kernel<S, COLL, BIASED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              dyn) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step3d_tma_kernel<S, TRT, BIASED>, TX * TY, dyn) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step3d_tma_kernel<S, COLL, BIASED>, TX * TY, dyn) !=
         cudaSuccess)
         return 0;
     return n;
 }
 
 // every collision and gradient instantiation gets the shared-memory limit;
-// the central-gradient ones decide whether the kernel runs at all
+// the BGK and TRT central-gradient ones set the occupancy, every other one
+// must fit at least one block
 template <typename S>
 static int blocks_per_sm_for() {
-    const int a = blocks_per_sm_one<S, false, false>(), b = blocks_per_sm_one<S, true, false>();
-    if (blocks_per_sm_one<S, false, true>() < 1 || blocks_per_sm_one<S, true, true>() < 1) return 0;
+    const int a = blocks_per_sm_one<S, COLL_BGK, false>(), b = blocks_per_sm_one<S, COLL_TRT, false>();
+    if (blocks_per_sm_one<S, COLL_MRT, false>() < 1 || blocks_per_sm_one<S, COLL_BGK, true>() < 1 ||
+        blocks_per_sm_one<S, COLL_TRT, true>() < 1 || blocks_per_sm_one<S, COLL_MRT, true>() < 1)
+        return 0;
     return a < b ? a : b;
 }
 
@@ -565,20 +568,19 @@ cudaError_t launch_step3d_tma(const TmaMaps3d &M, int par, const void *pin, void
     const Planes3d<S> PL = planes3d<S>(pin, pout, P);
     const S *in = (const S *)pin;
     S *out = (S *)pout;
-    switch (P.opts & (OPT_TRT | OPT_BIASED)) {
-    case 0:
-        step3d_tma_kernel<S, false, false><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, q_out, par, err, P, PL);
-        break;
-    case OPT_TRT:
-        step3d_tma_kernel<S, true, false><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, q_out, par, err, P, PL);
-        break;
-    case OPT_BIASED:
-        step3d_tma_kernel<S, false, true><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, q_out, par, err, P, PL);
-        break;
-    default:
-        step3d_tma_kernel<S, true, true><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, q_out, par, err, P, PL);
-        break;
+#define LBM_TMA3_LAUNCH(C, B)                                                                   \
+    step3d_tma_kernel<S, C, B><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, \
+                                                                      q_out, par, err, P, PL)
+    switch (P.opts & (OPT_TRT | OPT_MRT | OPT_BIASED)) {
+    case 0: LBM_TMA3_LAUNCH(COLL_BGK, false); break;
+    case OPT_TRT: LBM_TMA3_LAUNCH(COLL_TRT, false); break;
+    case OPT_MRT: LBM_TMA3_LAUNCH(COLL_MRT, false); break;
+    case OPT_BIASED: LBM_TMA3_LAUNCH(COLL_BGK, true); break;
+    case OPT_TRT | OPT_BIASED: LBM_TMA3_LAUNCH(COLL_TRT, true); break;
+    case OPT_MRT | OPT_BIASED: LBM_TMA3_LAUNCH(COLL_MRT, true); break;
+    default: return cudaErrorInvalidValue;
     }
+#undef LBM_TMA3_LAUNCH
     return cudaGetLastError();
 }
 

@@ -120,7 +120,7 @@ struct DevParams {
     // (read by the TRT instantiations of the step kernels only)
     float trt_magic[3];
     // multiple-relaxation-time collision of the flow set: rates s_e, s_eps
-    // and s_q (read by the MRT instantiations of the 2D step kernels only)
+    // and s_q (read by the MRT instantiations of the step kernels only)
     float mrt_rates[3];
     // and of the phase-field set: s_e, s_eps, s_q, s_p (om_g stored for a 0)
     float mrt_rates_g[4];

@@ -59,6 +59,9 @@ STEP_CASES = [
     ("3d_tiled_trt_fp16", lambda: _opt(_film3d(44, 13, 37, 12.0), **TRT), "fp16", "tiled", 6),
     ("3d_tma_biased", lambda: _opt(_film3d(64, 12, 37, 12.0), **BIASED), "fp32", "tma", 6),
     ("3d_tma_biased_fp16", lambda: _opt(_film3d(64, 8, 70, 20.0), **BIASED), "fp16", "tma", 6),
+    ("3d_tma_mrt_ragged", lambda: _opt(_film3d(44, 13, 37, 12.0), **MRT_G), "fp32", "tma", 6),
+    ("3d_tiled_mrt_bf16", lambda: _opt(_film3d(44, 13, 37, 12.0), **MRT_G), "bf16", "tiled", 6),
+    ("3d_tma_mrt_biased_fp16", lambda: _opt(_film3d(64, 8, 70, 20.0), **MRT_G, **BIASED), "fp16", "tma", 6),
 ]
 
 # name, grid size, storage, velocity factor, reversal period, steps

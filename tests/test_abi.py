@@ -84,7 +84,7 @@ def test_collision_option_validated():
         assert _ws(w)[0] == B.LBM_EINVAL, bad
     w.params.update(collision=3, trt_magic=(0.25, 0.25, 0.25))
     assert _ws(w)[0] == B.LBM_EINVAL
-    # MRT of the flow set: rates in (0, 2), D2Q9 and the coupled model only
+    # MRT of the flow set: rates in (0, 2), the coupled model only (2D and 3D)
     w.params.update(collision=2, mrt_rates=(1.4, 1.4, 1.2))
     assert _ws(w)[0] == B.LBM_OK
     for bad in ((0.0, 1.4, 1.2), (1.4, 2.0, 1.2), (1.4, 1.4, float("nan"))):
@@ -99,7 +99,9 @@ def test_collision_option_validated():
     w.params["mrt_rates_g"] = (0.0, 0.0, 0.0, 0.0)
     w3 = W.film_boiling_3d(8, 8, 8, modes=1, z0=3.0)
     w3.params.update(collision=2, mrt_rates=(1.4, 1.4, 1.2))
-    assert _ws(w3)[0] == B.LBM_EUNSUPPORTED
+    assert _ws(w3)[0] == B.LBM_OK
+    w3.params["mrt_rates_g"] = (1.2, 0.0, 0.0, 2.0)
+    assert _ws(w3)[0] == B.LBM_EINVAL
     vm = W.vortex_disk(n=33)
     vm.params.update(collision=2, mrt_rates=(1.4, 1.4, 1.2))
     assert _ws(vm)[0] == B.LBM_EUNSUPPORTED

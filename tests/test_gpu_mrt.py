@@ -1,11 +1,12 @@
 """The multiple-relaxation-time collision of the flow and phase-field sets
-(LBM_COLLISION_MRT, D2Q9) on the GPU against the FP64 oracle's MRT step
-(oracle.model with collision = "mrt"): parity within 1e-5 on walled,
-periodic and ragged 2D grids, with g on BGK or on its own MRT rates; the
-16-bit storages within their own bound; the TMA-staged kernel equal to the
-tiled one bit for bit; phi mass conserved with the source off; the exact
-Poiseuille profile at the magic rate s_q = 8 (2 - s_nu)/(8 - s_nu); and the
-unsupported cases."""
+(LBM_COLLISION_MRT; D2Q9, and D3Q19 / D3Q7 in 3D) on the GPU against the
+FP64 oracle's MRT step (oracle.model with collision = "mrt"): parity within
+1e-5 on walled, periodic and ragged 2D and 3D grids, with g on BGK or on its
+own MRT rates and with the biased gradient; the 16-bit storages within their
+own bound; the TMA-staged kernels equal to the tiled ones bit for bit; equal
+rates equal to the BGK kernel; phi mass conserved with the source off; the
+exact Poiseuille profile at the magic rate s_q = 8 (2 - s_nu)/(8 - s_nu) in
+2D and 3D; and the unsupported cases."""
 import numpy as np
 import pytest
 import torch
@@ -30,6 +31,15 @@ def _film(nx, ny, **kw):
     return W.film_boiling_2d(nx, ny, rho_ratio=10.0, y0=ny / 3.0, amplitude=2.0, phi_wall=(1.0, 0.0), **kw)
 
 
+def _film3d(nx, ny, nz, periodic_z=False, grad_scheme=None):
+    w = W.film_boiling_3d(nx, ny, nz, modes=2, z0=nz / 3.0, phi_wall=(1.0, 0.0))
+    if periodic_z:
+        w.periodic = (True, True, True)
+    if grad_scheme:
+        w.params.update(grad_scheme=grad_scheme)
+    return w
+
+
 CASES = [
     ("film_ragged", lambda: _mrt(_film(100, 70)), 40),
     ("droplet_periodic", lambda: _mrt(W.droplet_2d(48, 12.0, T_offset=0.05), (1.1, 1.6, 1.8)), 40),
@@ -40,6 +50,11 @@ CASES = [
     ("droplet_periodic_g", lambda: _mrt(W.droplet_2d(48, 12.0, T_offset=0.05), (1.1, 1.6, 1.8),
                                         (0.0, 1.3, 1.6, 0.0)), 40),
     ("film_biased_g", lambda: _mrt(_film(70, 45, grad_scheme="biased2"), rates_g=G_RATES), 30),
+    # 3D: D3Q19 flow set, D3Q7 phase-field set (g: s_e and s_p; s_eps, s_q unused)
+    ("film3d_ragged", lambda: _mrt(_film3d(37, 10, 21)), 15),
+    ("film3d_ragged_g", lambda: _mrt(_film3d(37, 10, 21), (1.1, 1.6, 1.8), G_RATES), 15),
+    ("film3d_periodic_g", lambda: _mrt(_film3d(24, 16, 20, periodic_z=True), rates_g=(1.5, 0.0, 0.0, 1.2)), 15),
+    ("film3d_biased_g", lambda: _mrt(_film3d(33, 12, 19, grad_scheme="biased2"), rates_g=G_RATES), 12),
 ]
 
 
@@ -137,12 +152,16 @@ def test_mrt_magic_rate_poiseuille_on_gpu():
 
 def test_mrt_unsupported_cases():
     from paper_2003_06342_b300 import Solver
-    w3 = _mrt(W.film_boiling_3d(16, 8, 12, modes=1, z0=4.0, phi_wall=(1.0, 0.0)))
+    wc = W.cac_params()
+    wc.update(collision="mrt", mrt_rates=(1.4, 1.3, 1.2))
     with pytest.raises(RuntimeError):
-        Solver(w3.n, w3.periodic, w3.params)
+        Solver((32, 32), (True, True), wc)
     w = _mrt(_film(32, 24), rates=(1.4, 2.0, 1.2))
     with pytest.raises(RuntimeError):
         Solver(w.n, w.periodic, w.params)
+    w3 = _mrt(_film3d(16, 8, 12), rates_g=(1.2, 0.0, 0.0, 2.5))
+    with pytest.raises(RuntimeError):
+        Solver(w3.n, w3.periodic, w3.params)
 
 
 def test_mrt_g_conserves_phi_mass_with_the_source_off():
@@ -154,3 +173,100 @@ def test_mrt_g_conserves_phi_mass_with_the_source_off():
     m1, _ = s.reduce()
     print("phi mass", m0, m1)
     assert abs(m1 - m0) / m0 < 1e-5
+
+
+# ---- 3D
+
+TMA3_CASES = [("3d_fp32", "fp32", (0.0,) * 4, None), ("3d_fp16", "fp16", (0.0,) * 4, None),
+              ("3d_bf16", "bf16", (0.0,) * 4, None), ("3d_fp32_g", "fp32", G_RATES, None),
+              ("3d_fp16_g", "fp16", G_RATES, None), ("3d_bf16_g", "bf16", G_RATES, None),
+              ("3d_fp32_biased_g", "fp32", G_RATES, "biased2"), ("3d_fp16_biased_g", "fp16", G_RATES, "biased2")]
+
+
+@pytest.mark.parametrize("name,storage,rates_g,grad", TMA3_CASES, ids=[c[0] for c in TMA3_CASES])
+def test_mrt3d_tma_matches_tiled_bit_for_bit(name, storage, rates_g, grad):
+    # 64 x 24 x 70: whole 32 x 4 tiles in x and y (the biased TMA path needs
+    # them), a ragged last z block
+    w = _mrt(_film3d(64, 24, 70, grad_scheme=grad), rates_g=rates_g)
+    a = gpu_solver(w, storage=storage)
+    b = gpu_solver(w, storage=storage)
+    a.set_kernel("tma")
+    b.set_kernel("tiled")
+    a.step(8)
+    b.step(8)
+    sa, sb = a.get_state(), b.get_state()
+    torch.cuda.synchronize()
+    assert torch.equal(sa, sb), name
+
+
+def test_mrt3d_parity_on_the_tma_kernel():
+    w = _mrt(_film3d(64, 24, 30), (1.1, 1.6, 1.8), G_RATES)
+    ref = oracle_fields(w, 10)
+    s = gpu_solver(w)
+    s.set_kernel("tma")
+    s.step(10)
+    err = max_errors(gpu_fields(s), ref)
+    print("tma", err)
+    assert all(v < TOL for v in err.values()), err
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_mrt3d_16bit_storage_near_oracle(storage):
+    w = _mrt(_film3d(32, 12, 24), rates_g=G_RATES)
+    ref = oracle_fields(w, 10)
+    err = max_errors(gpu_fields(_stepped(gpu_solver(w, storage=storage), 10)), ref)
+    bgk = _film3d(32, 12, 24)
+    ref_b = oracle_fields(bgk, 10)
+    err_b = max_errors(gpu_fields(_stepped(gpu_solver(bgk, storage=storage), 10)), ref_b)
+    print(storage, "mrt", err, "bgk", err_b)
+    assert all(err[k] < 4.0 * err_b[k] + 1e-5 for k in err), (err, err_b)
+
+
+def test_mrt3d_equal_rates_match_bgk():
+    om = 1.0 / (3.0 * 0.1 + 0.5)
+    wl = _film3d(32, 12, 24)
+    wl.params.update(nu_l=0.1, nu_g=0.1)
+    wm = _film3d(32, 12, 24)
+    wm.params.update(nu_l=0.1, nu_g=0.1, collision="mrt", mrt_rates=(om, om, om))
+    c, d = gpu_solver(wl), gpu_solver(wm)
+    c.step(15)
+    d.step(15)
+    err = max_errors(gpu_fields(c), gpu_fields(d))
+    assert all(v < 1e-6 for v in err.values()), err
+    e = gpu_solver(_mrt(_film3d(32, 12, 24), (1.1, 1.6, 1.8), G_RATES))
+    e.step(15)
+    assert np.abs(gpu_fields(e)["phi"] - gpu_fields(c)["phi"]).max() > 1e-7
+
+
+def test_mrt3d_g_conserves_phi_mass_with_the_source_off():
+    w = _mrt(_film3d(24, 16, 20, periodic_z=True), (1.3, 1.1, 1.6), G_RATES)
+    w.params.update(source_on=0)
+    s = gpu_solver(w)
+    m0, _ = s.reduce()
+    s.step(100)
+    m1, _ = s.reduce()
+    print("phi mass 3d", m0, m1)
+    assert abs(m1 - m0) / m0 < 1e-5
+
+
+def _poiseuille3d_error(rates, nu=0.5, H=8, G=1e-5, steps=1500):
+    params = W.base_params(rho_l=1.0, rho_g=1.0, nu_l=nu, nu_g=nu, alpha_l=0.05, alpha_g=0.05, sigma=0.0,
+                           gravity=(0.0, 0.0, 0.0), body_force=(G, 0.0, 0.0), source_on=0,
+                           phi_wall=(0.0, 0.0), T_wall=(1.0, 1.0), collision="mrt", mrt_rates=rates)
+    from paper_2003_06342_b300 import Solver
+    s = Solver((4, 4, H), (True, True, False), params)
+    s.init(np.zeros((H, 4, 4)), np.ones((H, 4, 4)))
+    s.step(steps)
+    u = s.fields()["u"][0].double().cpu().numpy()[:, 0, 0]
+    z = np.arange(H)
+    exact = G / (2 * nu) * (z + 0.5) * (H - 0.5 - z)
+    return float(np.abs(u - exact).max() / exact.max())
+
+
+def test_mrt3d_magic_rate_poiseuille_on_gpu():
+    s_nu = 1.0 / (0.5 * 3.0 + 0.5)
+    s_q = 8.0 * (2.0 - s_nu) / (8.0 - s_nu)
+    err_magic, err_off = _poiseuille3d_error((1.1, 1.3, s_q)), _poiseuille3d_error((1.1, 1.3, 1.9))
+    print("3d poiseuille rel err MRT magic", err_magic, "off", err_off)
+    assert err_magic < 1e-4
+    assert err_off > 1e-3
