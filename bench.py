@@ -77,6 +77,7 @@ KERNEL_SOURCES = {
     "step3d_tma": ["lbm3d_tma.cu", "lbm3d_cell.cuh", "lbm_common.cuh", "tma_util.cuh"],
     "adjoint2d": ["adjoint2d.cu", "adjoint.h", "lbm_common.cuh"],
     "cac2d": ["cac2d.cu", "lbm2d_cell.cuh", "lbm_common.cuh"],
+    "cac3d": ["cac3d.cu", "lbm3d_cell.cuh", "lbm_common.cuh", "tma_util.cuh"],
 }
 
 
@@ -648,6 +649,19 @@ def ncu_case(case):
         torch.cuda.synchronize()
         print(json.dumps({"ncu_case": case, "workload": wv.name, "cells": wv.cells}))
         return
+    if case.startswith("3d_phase_field"):
+        # the thin 3D vortex of the phase-field variant (33.5 M cells, 2 GB of
+        # FP32 populations)
+        wv = W.vortex_disk(n=1024)
+        nz3 = 32
+        phi3 = np.repeat(wv.phi0[None], nz3, axis=0)
+        u3 = [np.repeat(uu[None], nz3, axis=0) for uu in wv.extra["u"]] + [np.zeros_like(phi3)]
+        s = Solver((1024, 1024, nz3), (True, True, True), wv.params, storage=case.split("_")[-1])
+        s.set_velocity(u3, wv.extra["period"]).init(phi3, np.ones_like(phi3))
+        s.step(4)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": case, "workload": "vortex_1024x1024x32", "cells": phi3.size}))
+        return
     dim, storage = case.split("_")[:2]
     w = workload_c2() if dim == "2d" else W.c3_film_boiling_3d(256, 256, 128)
     s = Solver(w.n, w.periodic, w.params, storage=storage)
@@ -695,7 +709,8 @@ def main():
     ap.add_argument("--ncu-case", default=None,
                     choices=["2d_fp32", "2d_fp16", "2d_bf16", "3d_fp32", "3d_fp16",
                              "2d_fp32_tma", "2d_fp16_tma", "3d_fp32_tma", "3d_fp16_tma",
-                             "2d_adjoint", "2d_phase_field"],
+                             "2d_adjoint", "2d_phase_field", "3d_phase_field_fp32",
+                             "3d_phase_field_fp16"],
                     help="only initialise one kernel case and run 4 steps (for ncu captures)")
     args = ap.parse_args()
     if args.ncu_case:

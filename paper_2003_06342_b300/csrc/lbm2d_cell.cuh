@@ -145,6 +145,20 @@ __device__ __forceinline__ float set_sum2d(const float v[9], float inv_sc) {
     return fmaf(4.0f / 9.0f, v[0], fmaf(1.0f / 9.0f, ax, (1.0f / 36.0f) * dg)) * inv_sc;
 }
 
+// set_sum2d of the flow (x) and temperature (y) sets at once, with the same
+// sum tree (packed FP32x2), so each lane equals set_sum2d of its set
+template <typename S>
+__device__ __forceinline__ float2 set_sum2dx2(const float f[9], const float s[9], float2 inv_sc) {
+    float2 v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = make_float2(f[i], s[i]);
+    const float2 ax = fadd2(fadd2(v[1], v[3]), fadd2(v[2], v[4]));
+    const float2 dg = fadd2(fadd2(v[5], v[7]), fadd2(v[6], v[8]));
+    if (!IsNarrow<S>::value) return fadd2(v[0], fadd2(ax, dg));
+    return fmul2(ffma2(splat2(4.0f / 9.0f), v[0], ffma2(splat2(1.0f / 9.0f), ax, fmul2(splat2(1.0f / 36.0f), dg))),
+                 inv_sc);
+}
+
 template <typename S>
 __device__ __forceinline__ void set_flux2d(const float v[9], float inv_sc, float &jx, float &jy) {
     const float ax = v[1] - v[3], ay = v[2] - v[4];
@@ -332,8 +346,9 @@ __device__ __forceinline__ void cell_core2d(const float *sp, int pitch, const fl
     // moments (Eqs. Velocity, Pressure, Moment_Temp)
     float jx, jy;
     set_flux2d<S>(f, P.set_isc[0], jx, jy);
-    const float sf = set_sum2d<S>(f, P.set_isc[0]) + P.set_ref[0];
-    const float ss = set_sum2d<S>(s, P.set_isc[2]);                  // T - T_ref
+    const float2 sfs = set_sum2dx2<S>(f, s, make_float2(P.set_isc[0], P.set_isc[2]));
+    const float sf = sfs.x + P.set_ref[0];
+    const float ss = sfs.y;                                          // T - T_ref
     const float inv_rho = rcp_approx(m.rho);
     m.ux = fmaf(0.5f, m.Fx, 3.0f * jx) * inv_rho;
     m.uy = fmaf(0.5f, m.Fy, 3.0f * jy) * inv_rho;
@@ -484,6 +499,8 @@ __device__ __forceinline__ void cell_core2d(const float *sp, int pitch, const fl
         MRT ? __fadd_rn(fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)), cg[0])
             : fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)),
         fmaf(k.a_s, s[0], to_rep<S>(0, 2, fmaf(k.Bs, P0, k.As), P)));
+    const float2 a_fs = make_float2(k.a_f, k.a_s);
+    const float2 a1_fs = make_float2(a1_f, a1_s), a2_fs = make_float2(a2_f, a2_s);
     // a direction i with e = (ex, ey) and its opposite o
     auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eHo, float eVf,
                     float eW) {
@@ -492,28 +509,28 @@ __device__ __forceinline__ void cell_core2d(const float *sp, int pitch, const fl
         const float Of = fmaf(Pe, eHo, eVf);
         const float Es = fmaf(k.Bs, Pe, k.As);
         // w_i = w_o: the increments of i and o share the weight of i
-        auto rf = [&](float v) { return to_rep<S>(i, 0, v, P); };
         auto rg = [&](float v) { return to_rep<S>(i, 1, v, P); };
-        auto rs = [&](float v) { return to_rep<S>(i, 2, v, P); };
+        // f and s as one FP32x2 pair (x: f, y: s): E + O and E - O of both
+        // sets, taken to the working representation (to_rep on each lane)
+        auto rfs = [&](float2 v) {
+            return IsNarrow<S>::value ? fmul2(make_float2(P.set_sc[0], P.set_sc[2]), v) : weighted2<L>(i, v);
+        };
+        const float2 ri = rfs(fadd2(make_float2(Ef, Es), make_float2(Of, eW)));
+        const float2 ro = rfs(fadd2(make_float2(Ef, Es), make_float2(-Of, -eW)));
+        const float2 fsi = make_float2(f[i], s[i]), fso = make_float2(f[o], s[o]);
         if (MRT) {
-            sink.put(i, __fadd_rn(fmaf(k.a_f, f[i], rf(Ef + Of)), cf[i]),
-                            __fadd_rn(fmaf(k.a_g, g[i], rg(Eg + eVg)), cg[i]),
-                            fmaf(k.a_s, s[i], rs(Es + eW)));
-            sink.put(o, __fadd_rn(fmaf(k.a_f, f[o], rf(Ef - Of)), cf[o]),
-                            __fadd_rn(fmaf(k.a_g, g[o], rg(Eg - eVg)), cg[o]),
-                            fmaf(k.a_s, s[o], rs(Es - eW)));
+            const float2 vi = ffma2(a_fs, fsi, ri), vo = ffma2(a_fs, fso, ro);
+            sink.put(i, __fadd_rn(vi.x, cf[i]), __fadd_rn(fmaf(k.a_g, g[i], rg(Eg + eVg)), cg[i]), vi.y);
+            sink.put(o, __fadd_rn(vo.x, cf[o]), __fadd_rn(fmaf(k.a_g, g[o], rg(Eg - eVg)), cg[o]), vo.y);
         } else if (!TRT) {
-            sink.put(i, fmaf(k.a_f, f[i], rf(Ef + Of)), fmaf(k.a_g, g[i], rg(Eg + eVg)),
-                            fmaf(k.a_s, s[i], rs(Es + eW)));
-            sink.put(o, fmaf(k.a_f, f[o], rf(Ef - Of)), fmaf(k.a_g, g[o], rg(Eg - eVg)),
-                            fmaf(k.a_s, s[o], rs(Es - eW)));
+            const float2 vi = ffma2(a_fs, fsi, ri), vo = ffma2(a_fs, fso, ro);
+            sink.put(i, vi.x, fmaf(k.a_g, g[i], rg(Eg + eVg)), vi.y);
+            sink.put(o, vo.x, fmaf(k.a_g, g[o], rg(Eg - eVg)), vo.y);
         } else {
-            sink.put(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], rf(Ef + Of))),
-                            fmaf(a1_g, g[i], fmaf(a2_g, g[o], rg(Eg + eVg))),
-                            fmaf(a1_s, s[i], fmaf(a2_s, s[o], rs(Es + eW))));
-            sink.put(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], rf(Ef - Of))),
-                            fmaf(a1_g, g[o], fmaf(a2_g, g[i], rg(Eg - eVg))),
-                            fmaf(a1_s, s[o], fmaf(a2_s, s[i], rs(Es - eW))));
+            const float2 vi = ffma2(a1_fs, fsi, ffma2(a2_fs, fso, ri));
+            const float2 vo = ffma2(a1_fs, fso, ffma2(a2_fs, fsi, ro));
+            sink.put(i, vi.x, fmaf(a1_g, g[i], fmaf(a2_g, g[o], rg(Eg + eVg))), vi.y);
+            sink.put(o, vo.x, fmaf(a1_g, g[o], fmaf(a2_g, g[i], rg(Eg - eVg))), vo.y);
         }
     };
     pair(1, 3, ux, Pxa, k.Vgx, k.Hx, Hox, k.Vfx, k.Wx);                          // (1, 0)

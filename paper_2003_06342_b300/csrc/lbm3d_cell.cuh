@@ -140,6 +140,23 @@ __device__ __forceinline__ float set_sum19(const float v[QF], float inv_sc) {
     return fmaf(1.0f / 3.0f, v[0], fmaf(1.0f / 18.0f, ax, (1.0f / 36.0f) * dg)) * inv_sc;
 }
 
+// set_sum19 of the flow (x) and temperature (y) sets at once, with the
+// same sum tree, so each lane equals set_sum19 of its set
+template <typename S>
+__device__ __forceinline__ float2 set_sum19x2(const float f[QF], const float s[QF], float2 inv_sc) {
+    float2 v[QF];
+#pragma unroll
+    for (int i = 0; i < QF; ++i) v[i] = make_float2(f[i], s[i]);
+    const float2 ax = fadd2(fadd2(fadd2(v[1], v[4]), fadd2(v[2], v[5])), fadd2(v[3], v[6]));
+    const float2 dg = fadd2(fadd2(fadd2(fadd2(v[7], v[10]), fadd2(v[8], v[9])),
+                                  fadd2(fadd2(v[11], v[14]), fadd2(v[12], v[13]))),
+                            fadd2(fadd2(v[15], v[18]), fadd2(v[16], v[17])));
+    if (!IsNarrow<S>::value) return fadd2(v[0], fadd2(ax, dg));
+    return fmul2(ffma2(splat2(1.0f / 3.0f), v[0],
+                       ffma2(splat2(1.0f / 18.0f), ax, fmul2(splat2(1.0f / 36.0f), dg))),
+                 inv_sc);
+}
+
 __device__ __forceinline__ float sgnv(int e, float v) { return e > 0 ? v : -v; }
 // e.(a, b, c) for e in {-1, 0, 1}^3 without multiplications; __fadd_rn keeps
 // a product among a, b, c from being fused into the sum
@@ -306,6 +323,10 @@ template <typename S, class Lt>
 __device__ __forceinline__ float rep3(int i, float x) {
     return IsNarrow<S>::value ? x : weighted<Lt>(i, x);
 }
+template <typename S, class Lt>
+__device__ __forceinline__ float2 rep3x2(int i, float2 x) {
+    return IsNarrow<S>::value ? x : weighted2<Lt>(i, x);
+}
 
 // ---- MRT collisions in 3D (an extension outside the paper)
 // With d_i = theta_i - theta_eq_bar_i (population units) and an orthogonal
@@ -397,6 +418,21 @@ __device__ __forceinline__ float mrt_rep3(int i, float c, float sc) {
 // s (anti-bounce-back), in the working representation.  Fast-path stores
 // address their plane through PL (base + cell).
 
+// Offset of the cell that link e = (ex, ey, ez) of cell (x, y) reaches, on
+// the fast paths: in the grid (XY_IN), or across a periodic x / y edge
+// (wrap); the grid holds fewer than 2^31 cells, so it fits an int.
+__device__ __forceinline__ int push_off3(int ex, int ey, int ez, int x, int y, bool wrap,
+                                         const DevParams &P) {
+    const int nx = P.n[0], ny = P.n[1];
+    if (!wrap) return (ez * ny + ey) * nx + ex;
+    int oxy = 0;
+    if (ex > 0) oxy = x == nx - 1 ? 1 - nx : 1;
+    if (ex < 0) oxy = x == 0 ? nx - 1 : -1;
+    if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
+    if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
+    return ez * (ny * nx) + oxy;
+}
+
 // Push of direction i's g value (D3Q7).
 template <typename S, int MODE>
 __device__ __forceinline__ void push3d_g(int i, float v, int x, int y, int z, size_t c,
@@ -406,18 +442,9 @@ __device__ __forceinline__ void push3d_g(int i, float v, int x, int y, int z, si
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const size_t N = (size_t)P.N;
     if (MODE == XY_IN || MODE == XY_WRAP) {
-        long long off;
-        if (MODE == XY_IN) off = ((long long)ez * ny + ey) * nx + ex;
-        else {
-            int oxy = 0;
-            if (ex > 0) oxy = x == nx - 1 ? 1 - nx : 1;
-            if (ex < 0) oxy = x == 0 ? nx - 1 : -1;
-            if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
-            if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
-            off = (long long)ez * ny * nx + oxy;
-        }
+        const int off = push_off3(ex, ey, ez, x, y, MODE == XY_WRAP, P);
         if (!in_bounds((long long)c + off, (long long)N, P)) return;
-        PL.out[G0 + i][(long long)c + off] = narrow<S>(v);
+        PL.out[G0 + i][(cidx)c + (cidx)off] = narrow<S>(v);
         return;
     }
     int dx = x + ex, dy = y + ey, dz = z + ez;
@@ -443,18 +470,9 @@ __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int 
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const size_t N = (size_t)P.N;
     if (MODE == XY_IN || MODE == XY_WRAP) {
-        long long off;
-        if (MODE == XY_IN) off = ((long long)ez * ny + ey) * nx + ex;
-        else {
-            int oxy = 0;
-            if (ex > 0) oxy = x == nx - 1 ? 1 - nx : 1;
-            if (ex < 0) oxy = x == 0 ? nx - 1 : -1;
-            if (ey > 0) oxy += y == ny - 1 ? (1 - ny) * nx : nx;
-            if (ey < 0) oxy += y == 0 ? (ny - 1) * nx : -nx;
-            off = (long long)ez * ny * nx + oxy;
-        }
+        const int off = push_off3(ex, ey, ez, x, y, MODE == XY_WRAP, P);
         if (!in_bounds((long long)c + off, (long long)N, P)) return;
-        store_pair<S>(PL.out[i], (long long)c + off, vf, vs);
+        store_pair<S>(PL.out[i], (cidx)c + (cidx)off, vf, vs);
         return;
     }
     int dx = x + ex, dy = y + ey, dz = z + ez;
@@ -490,7 +508,7 @@ __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int 
 // BIASED: sphi holds five planes of two-ring windows (plane p in slot
 // (p + 2) % 5) and the gradient of Eq. Grad uses the second-order biased
 // difference [-phi(x + 2e) + 4 phi(x + e) - 3 phi(x)] / 2 (Sec. 3.4).
-template <typename S, int MODE, int COLL = COLL_BGK, bool BIASED = false>
+template <typename S, int MODE, int COLL = COLL_BGK, bool BIASED = false, int NW = 3>
 __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
                                                const float f[QF], const float s[QF],
                                                const float g[QG], float qp, float phip,
@@ -503,8 +521,9 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     float phd, gx = 0.0f, gy = 0.0f, gz = 0.0f, la = 0.0f, ld = 0.0f;
     if constexpr (!BIASED) {
         const int centre = (ty + 1) * SX + tx + 1;
-        const float *pl[3] = {sphi + (z % 3) * PLANE + centre, sphi + ((z + 1) % 3) * PLANE + centre,
-                              sphi + ((z + 2) % 3) * PLANE + centre};   // planes z-1, z, z+1
+        // planes z-1, z, z+1 (plane p in window slot (p + 1) % NW)
+        const float *pl[3] = {sphi + (z % NW) * PLANE + centre, sphi + ((z + 1) % NW) * PLANE + centre,
+                              sphi + ((z + 2) % NW) * PLANE + centre};
         phd = pl[1][0];                      // the window holds phi - phi_ref
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -545,8 +564,9 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     closures3d(m, P);
     float j[3];
     set_flux19<S>(f, P.set_isc[0], j);
-    const float sf = set_sum19<S>(f, P.set_isc[0]) + P.set_ref[0];
-    const float ss = set_sum19<S>(s, P.set_isc[2]);                  // T - T_ref
+    const float2 sfs = set_sum19x2<S>(f, s, make_float2(P.set_isc[0], P.set_isc[2]));
+    const float sf = sfs.x + P.set_ref[0];
+    const float ss = sfs.y;                                          // T - T_ref
     const float inv_rho = rcp_approx(m.rho);
 #pragma unroll
     for (int a = 0; a < 3; ++a) m.u[a] = fmaf(0.5f, m.F[a], 3.0f * j[a]) * inv_rho;
@@ -710,10 +730,15 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
                          P.mrt_rates[0] - om_f, P.mrt_rates[1] - om_f);
         hq = -0.5f * (P.mrt_rates[2] - om_f);
     }
-    push3d_fs<S, MODE>(0, plus(fmaf(a_f, f[0], rep3<S, LF>(0, fmaf(K1, -usq15, K0))),
-                               mrt_rep3<S, LF>(0, cfe.r0, P.set_sc[0])),
-                            fmaf(a_s, s[0], rep3<S, LF>(0, fmaf(Bs, -usq15, As))), x, y, z, c,
-                            pout, P, PL);
+    // f and s of a direction as one FP32x2 pair (x: f, y: s), as stored
+    const float2 a_fs = make_float2(a_f, a_s);
+    {
+        float2 v0 = ffma2(a_fs, make_float2(f[0], s[0]),
+                          rep3x2<S, LF>(0, make_float2(fmaf(K1, -usq15, K0), fmaf(Bs, -usq15, As))));
+        v0.x = plus(v0.x, mrt_rep3<S, LF>(0, cfe.r0, P.set_sc[0]));
+        push3d_fs<S, MODE>(0, v0.x, v0.y, x, y, z, c, pout, P, PL);
+    }
+    const float2 a1_fs = make_float2(a1_f, a1_s), a2_fs = make_float2(a2_f, a2_s);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = half19(k), o = LF::opp(i);
@@ -726,23 +751,26 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const float Of = fmaf(Pe, eHo, edot3(ex, ey, ez, Vfx, Vfy, Vfz));
         const float Es = fmaf(Bs, Pe, As);
         const float Os = edot3(ex, ey, ez, Wx, Wy, Wz);
-        // w_i = w_o: the increments of i and o share the weight of i
-        auto rf = [&](float v) { return rep3<S, LF>(i, v); };
+        // (E + O, E - O) of both sets; w_i = w_o: i and o share the weight of i
+        const float2 E = make_float2(Ef, Es), O = make_float2(Of, Os);
+        const float2 ri = rep3x2<S, LF>(i, fadd2(E, O));
+        const float2 ro = rep3x2<S, LF>(i, fadd2(E, make_float2(-Of, -Os)));
+        const float2 fsi = make_float2(f[i], s[i]), fso = make_float2(f[o], s[o]);
+        float2 vi, vo;
         if (!TRT) {
-            float vi = fmaf(a_f, f[i], rf(Ef + Of)), vo = fmaf(a_f, f[o], rf(Ef - Of));
+            vi = ffma2(a_fs, fsi, ri);
+            vo = ffma2(a_fs, fso, ro);
             if constexpr (MRT) {
                 const float ck = mrt19_class(cfe, k), od = __fmul_rn(hq, fdif[k]);
-                vi = __fadd_rn(vi, mrt_rep3<S, LF>(i, ck + od, P.set_sc[0]));
-                vo = __fadd_rn(vo, mrt_rep3<S, LF>(o, ck - od, P.set_sc[0]));
+                vi.x = __fadd_rn(vi.x, mrt_rep3<S, LF>(i, ck + od, P.set_sc[0]));
+                vo.x = __fadd_rn(vo.x, mrt_rep3<S, LF>(o, ck - od, P.set_sc[0]));
             }
-            push3d_fs<S, MODE>(i, vi, fmaf(a_s, s[i], rf(Es + Os)), x, y, z, c, pout, P, PL);
-            push3d_fs<S, MODE>(o, vo, fmaf(a_s, s[o], rf(Es - Os)), x, y, z, c, pout, P, PL);
         } else {
-            push3d_fs<S, MODE>(i, fmaf(a1_f, f[i], fmaf(a2_f, f[o], rf(Ef + Of))),
-                               fmaf(a1_s, s[i], fmaf(a2_s, s[o], rf(Es + Os))), x, y, z, c, pout, P, PL);
-            push3d_fs<S, MODE>(o, fmaf(a1_f, f[o], fmaf(a2_f, f[i], rf(Ef - Of))),
-                               fmaf(a1_s, s[o], fmaf(a2_s, s[i], rf(Es - Os))), x, y, z, c, pout, P, PL);
+            vi = ffma2(a1_fs, fsi, ffma2(a2_fs, fso, ri));
+            vo = ffma2(a1_fs, fso, ffma2(a2_fs, fsi, ro));
         }
+        push3d_fs<S, MODE>(i, vi.x, vi.y, x, y, z, c, pout, P, PL);
+        push3d_fs<S, MODE>(o, vo.x, vo.y, x, y, z, c, pout, P, PL);
     }
 }
 
@@ -788,7 +816,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             if (ok) {
                 const size_t c = (size_t)(z + 1) * plane_cells + cxy;
 #pragma unroll
-                for (int i = 0; i < QG; ++i) gn[i] = load_raw(PL.in[G0 + i] + c);
+                for (int i = 0; i < QG; ++i) gn[i] = load_raw(PL.in[G0 + i] + (cidx)c);
                 qnext = q_in[c];
                 ph = fmaf(0.5f, qnext, set_sum7<S>(gn, P.set_isc[1]));
             }
@@ -799,7 +827,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             const size_t c = (size_t)z * plane_cells + cxy;
             float f[QF], s[QF];
 #pragma unroll
-            for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
+            for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (cidx)c, f[i], s[i]);
             const float phip = phi_prev[c];
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
                 layer_update3d<S, XY, COLL>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
@@ -863,7 +891,7 @@ __device__ __forceinline__ void step3d_column_biased(const S *__restrict__ pin, 
 #pragma unroll
             for (int i = 0; i < QG; ++i) g[i] = load_raw(PL.in[G0 + i] + c);
 #pragma unroll
-            for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (long long)c, f[i], s[i]);
+            for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (cidx)c, f[i], s[i]);
             const float qp = q_in[c], phip = phi_prev[c];
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
                 layer_update3d<S, XY, COLL, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);

@@ -370,10 +370,14 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
         return;
     }
 
+    // window of NWIN slots, plane p in slot (p + 1) % NWIN: with four, the
+    // plane built while the slowest threads still update layer z - 1 never
+    // overwrites one they read, so one barrier per layer suffices
+    constexpr int NWIN = 4;
     // window: plane zbeg - 1 with plain loads, plane zbeg from its g stage
-    fill_plane<S, XY_GEN>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
+    fill_plane<S, XY_GEN>(sphi, zbeg % NWIN, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
     bool ok = G.wait(barG, 0, first_wait_limit);
-    fill_plane<S, XY>(sphi, (zbeg + 1) % 3, zbeg, true, true, staged_phid<S>(g_base, tid, P), pin,
+    fill_plane<S, XY>(sphi, (zbeg + 1) % NWIN, zbeg, true, true, staged_phid<S>(g_base, tid, P), pin,
                        q_in, x0, y0, tid, tx, ty, P);
     if (PRE && zbeg + 1 < nz)
         ring_prefetch<S, XY>(rbuf + ((zbeg + 1) & 1) * RING_WORDS, pin, q_in, zbeg + 1, x0, y0, tid, P);
@@ -388,21 +392,35 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             phn = staged_phid<S>(g_base + gn * Gm::G_STAGE, tid, P);
         }
         if (PRE && has_next) {
-            float *plane = sphi + ((z + 2) % 3) * PLANE;
+            float *plane = sphi + ((z + 2) % NWIN) * PLANE;
             plane[(ty + 1) * SX + tx + 1] = phn;
             cp_async_wait_all();                     // this thread's ring words have landed
             ring_store<S, XY>(plane, rbuf + ((z + 1) & 1) * RING_WORDS, z + 1, x0, y0, tid, P);
         } else {
-            fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, has_next, phn, pin, q_in, x0, y0, tid,
+            fill_plane<S, XY>(sphi, (z + 2) % NWIN, z + 1, true, has_next, phn, pin, q_in, x0, y0, tid,
                                tx, ty, P);
         }
         ok = F.wait(barF, fb) && ok;
+        // every thread is done with layer z - 1 and has built plane z + 1
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicOr(err, 1);
             cp_async_wait_all();
             F.drain(barF, Gm::NFS);                  // copies that may still land
             G.drain(barG, Gm::NG);
             return;
+        }
+        // the stages of layer z - 1 are free: refill them
+        if (z > zbeg) {
+            const int fp = fb ^ 1, gp = gb == 0 ? Gm::NG - 1 : gb - 1;
+            if (z - 1 + Gm::NFS < zend) {
+                if (tid == 0)
+                    issue_fs<S>(fs_base + fp * Gm::FS_STAGE, &barF[fp], M, par, x0, y0, z - 1 + Gm::NFS);
+                F.pend |= 1u << fp;
+            }
+            if (z - 1 + Gm::NG <= zlast) {
+                if (tid == 0) issue_g<S>(g_base + gp * Gm::G_STAGE, &barG[gp], M, par, x0, y0, z - 1 + Gm::NG);
+                G.pend |= 1u << gp;
+            }
         }
         // the ring of plane z + 2 goes into the buffer plane z's ring used
         if (PRE && z + 2 < nz && z + 1 < zend)
@@ -421,19 +439,9 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             const float phip = ((const float *)(b + Gm::OFF_PP))[tid];
             const size_t c = (size_t)z * plane_cells + cxy;
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY, COLL>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY, COLL, false, NWIN>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN, COLL>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
-        }
-        __syncthreads();      // the stages of layer z and window slot (z - 1) % 3 are free
-        if (z + Gm::NFS < zend) {
-            if (tid == 0)
-                issue_fs<S>(fs_base + fb * Gm::FS_STAGE, &barF[fb], M, par, x0, y0, z + Gm::NFS);
-            F.pend |= 1u << fb;
-        }
-        if (z + Gm::NG <= zlast) {
-            if (tid == 0) issue_g<S>(g_base + gb * Gm::G_STAGE, &barG[gb], M, par, x0, y0, z + Gm::NG);
-            G.pend |= 1u << gb;
+                layer_update3d<S, XY_GEN, COLL, false, NWIN>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
         }
         fb ^= 1;
         gb = gn;
@@ -451,7 +459,7 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t barF[Tma3Geom<S>::NFS], barG[Tma3Geom<S>::NG];
     // the biased gradient: a five-plane two-ring window, two fetched planes
-    __shared__ float sphi[BIASED ? 5 * PLANEB : 3 * PLANE];
+    __shared__ float sphi[BIASED ? 5 * PLANEB : 4 * PLANE];
     __shared__ uint32_t rbuf[BIASED ? 2 * BWIN_WORDS : 2 * RING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if (x0 + TX > P.n[0] || y0 + TY > P.n[1]) {          // ragged tile: plain loads

@@ -201,6 +201,18 @@ template <typename S>
 __device__ __forceinline__ void load_pair(const S *plane, long long c, float &f, float &s) {
     unpack_pair(__ldg(reinterpret_cast<const typename PairOf<S>::T *>(plane) + c), f, s);
 }
+// Fast-path cell index: the grid holds fewer than 2^31 cells (checked when
+// the handle is created), so a cell index fits 32 bits and a plane element's
+// address is one wide multiply-add from the plane base.
+using cidx = uint32_t;
+template <typename S>
+__device__ __forceinline__ void load_pair(const S *plane, cidx c, float &f, float &s) {
+    unpack_pair(__ldg(reinterpret_cast<const typename PairOf<S>::T *>(plane) + c), f, s);
+}
+template <typename S>
+__device__ __forceinline__ void store_pair(S *plane, cidx c, float f, float s) {
+    reinterpret_cast<typename PairOf<S>::T *>(plane)[c] = pack_pair<S>(f, s);
+}
 template <typename S>
 __device__ __forceinline__ void store_pair(S *plane, long long c, float f, float s) {
     reinterpret_cast<typename PairOf<S>::T *>(plane)[c] = pack_pair<S>(f, s);
@@ -306,6 +318,22 @@ template <class Lat>
 __device__ __forceinline__ float weighted(int i, float x) {
     if (Lat::wlo(i) == 0.0f) return Lat::w(i) * x;
     return fmaf(x, Lat::w(i), __fmul_rn(x, Lat::wlo(i)));
+}
+
+// Packed FP32x2 arithmetic (sm_100 and later): one instruction works on two
+// lanes, each rounded exactly as fmaf / __fadd_rn / __fmul_rn, so a paired
+// expression gives the bits of the two scalar ones.  The step kernels pair
+// the flow value of a direction with the temperature value stored beside it.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+
+// weighted() on both lanes (one weight)
+template <class Lat>
+__device__ __forceinline__ float2 weighted2(int i, float2 x) {
+    if (Lat::wlo(i) == 0.0f) return fmul2(splat2(Lat::w(i)), x);
+    return ffma2(x, splat2(Lat::w(i)), fmul2(x, splat2(Lat::wlo(i))));
 }
 
 // Approximate reciprocal and reciprocal square root, one instruction each
