@@ -4,14 +4,14 @@
 // coupled 3D model (cs^2 = 1/4), without phase change (q = 0) and with the
 // velocity u(x) c(n) prescribed -- the CAC validations of Sec. 4.1 run on
 // thin 3D domains.  Each block marches a 32x4 column tile through ZB layers
-// with the rolling three-plane phi window of step3d_kernel: before layer z is
-// updated, plane z+1 is formed.  With FP32 storage, on tiles that need no wall
-// test, the loads run a layer ahead: while layer z is updated, the own cells' g of plane z+2 and
-// the imposed velocity of layer z+1 are in flight in registers and the halo
-// ring of plane z+2 is being copied into shared memory with cp.async (the
-// per-layer work is small, so without the lookahead every layer waited for
-// its loads).  There is no phase change, so phi = sum_i g_i and no lagged
-// source is read.  Per cell:
+// with a rolling phi window (four plane slots, one barrier per layer): before
+// layer z is updated, plane z+1 is formed.  On tiles that need no wall test
+// the loads run a layer ahead: while layer z is updated, the own cells' g of
+// plane z+2 and the imposed velocity of layer z+1 are in flight in registers
+// and the halo ring of plane z+2 is being copied into shared memory with
+// cp.async (the per-layer work is small, so without the lookahead every
+// layer waited for its loads).  There is no phase change, so phi = sum_i g_i
+// and no lagged source is read.  Per cell:
 // grad(phi) by Eqs. DerivDirec_Grad and Grad over the D3Q19 neighbours, the
 // normal, Gamma(u) (Eq. FunctionGamma) and the collision of Eq. LBE with the
 // source F^g of Eq. SourceTerm_AllenCahn in the even / odd form of the
@@ -27,6 +27,12 @@
 namespace lbm {
 
 namespace {
+
+// Slots of the phi window: plane p in slot (p + 1) % CW.  With four, the
+// plane built for layer z + 1 never overwrites one that the slowest threads
+// still read for layer z - 1, so one barrier per layer suffices (each
+// thread reads back only the ring words it fetched itself).
+constexpr int CW = 4;
 
 // Halo ring of the phi window (one cell per thread r < CRING), fetched a
 // layer ahead with 4-byte cp.async copies into shared memory: the 7 g values
@@ -104,7 +110,7 @@ __device__ __forceinline__ void cac_ring_store(float *plane, const uint32_t *buf
 }  // namespace
 
 // update of one cell of layer z from the phi window (planes z-1, z, z+1 in
-// slots z % 3, (z+1) % 3, (z+2) % 3) and its g values (working representation)
+// slots z % CW, (z+1) % CW, (z+2) % CW) and its g values (working representation)
 template <typename S, int MODE>
 __device__ __forceinline__ void cac3d_cell(const float *sphi, int z, int x, int y, size_t c,
                                            const float g[QG], const float *__restrict__ vel, float factor,
@@ -113,8 +119,8 @@ __device__ __forceinline__ void cac3d_cell(const float *sphi, int z, int x, int 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const size_t N = (size_t)P.N;
     const int centre = (ty + 1) * SX + tx + 1;
-    const float *pl[3] = {sphi + (z % 3) * PLANE + centre, sphi + ((z + 1) % 3) * PLANE + centre,
-                          sphi + ((z + 2) % 3) * PLANE + centre};
+    const float *pl[3] = {sphi + (z % CW) * PLANE + centre, sphi + ((z + 1) % CW) * PLANE + centre,
+                          sphi + ((z + 2) % CW) * PLANE + centre};
     const float phd = pl[1][0];
     const float ph = phd + P.g_ref;
     float gx = 0.0f, gy = 0.0f, gz = 0.0f;
@@ -169,10 +175,8 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
     const size_t plane_cells = (size_t)nx * ny;
     const size_t N = (size_t)P.N;
     const float isc = P.set_isc[1];
-    // lookahead on tiles that need no wall test (q = 0: phi = sum_i g_i), FP32
-    // storage: with 16-bit storage it measured 3% slower than without
-    // (609 against 589 us on 1024 x 1024 x 32), so those keep the plain march
-    constexpr bool PRE = XY != XY_GEN && !IsNarrow<S>::value;
+    // lookahead on tiles that need no wall test (q = 0: phi = sum_i g_i)
+    constexpr bool PRE = XY != XY_GEN;
 
     // gn: the own g of plane z + 1 as stored (a 16-bit value is widened only
     // where it is used, so the load it came from is not waited for early)
@@ -187,8 +191,8 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
             ph = PRE ? set_sum7<S>(g, isc) : fmaf(0.5f, q_zero[c], set_sum7<S>(g, isc));
             if (PRE) for (int a = 0; a < 3; ++a) u[a] = vel[a * N + c];
         }
-        fill_plane<S, XY>(sphi, (zbeg + 1) % 3, zbeg, true, col, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
-        fill_plane<S, XY_GEN>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
+        fill_plane<S, XY>(sphi, (zbeg + 1) % CW, zbeg, true, col, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
+        fill_plane<S, XY_GEN>(sphi, zbeg % CW, zbeg - 1, false, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
         if (PRE && zbeg + 1 < nz) {
             const size_t c = (size_t)(zbeg + 1) * plane_cells + cxy;
 #pragma unroll
@@ -213,7 +217,7 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
             }
             // plane z + 1 (in range: its own values and ring arrived a layer ago)
             if (z + 1 < nz) {
-                float *plane = sphi + ((z + 2) % 3) * PLANE;
+                float *plane = sphi + ((z + 2) % CW) * PLANE;
                 float v[QG];
 #pragma unroll
                 for (int i = 0; i < QG; ++i) v[i] = widen(gn[i]);
@@ -222,7 +226,7 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
                 else asm volatile("cp.async.wait_group 0;" ::: "memory");
                 cac_ring_store<S, XY>(plane, rbuf[(z + 1) & 1], z + 1, x0, y0, tid, P);
             } else {
-                fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
+                fill_plane<S, XY>(sphi, (z + 2) % CW, z + 1, true, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
             }
         } else {
             float ph = 0.0f;
@@ -234,7 +238,7 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
                 for (int i = 0; i < QG; ++i) { gn[i] = __ldg(PL.in[G0 + i] + c); v[i] = widen(gn[i]); }
                 ph = fmaf(0.5f, q_zero[c], set_sum7<S>(v, isc));
             }
-            fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, ok, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
+            fill_plane<S, XY>(sphi, (z + 2) % CW, z + 1, true, ok, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
         }
         __syncthreads();
         if (col) {
@@ -247,7 +251,6 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
 #pragma unroll
         for (int i = 0; i < QG; ++i) { g[i] = widen(gn[i]); if (PRE) gn[i] = gnn[i]; }
         if (PRE) for (int a = 0; a < 3; ++a) u[a] = un[a];
-        __syncthreads();   // plane (z - 1) % 3 and ring buffer z & 1 are reused next iteration
     }
     if (PRE) asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(TX * TY, 8)
 cac3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, const float *__restrict__ q_zero,
              const float *__restrict__ vel, float factor, const DevParams P,
              const __grid_constant__ Planes3d<S> PL) {
-    __shared__ float sphi[3 * PLANE];
+    __shared__ float sphi[CW * PLANE];
     __shared__ uint32_t rbuf[2][CRING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int cls = tile_class3d(x0, y0, P);

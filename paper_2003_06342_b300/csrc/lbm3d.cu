@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
 step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
               const __grid_constant__ Planes3d<S> PL) {
-    __shared__ float sphi[BIASED ? 5 * PLANEB : 3 * PLANE];
+    __shared__ float sphi[BIASED ? NWB * PLANEB : NW3 * PLANE];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int cls = tile_class3d(x0, y0, P);
     if (BIASED) {

@@ -13,6 +13,11 @@ constexpr int TX = 32, TY = 4, SX = TX + 2, SY = TY + 2, PLANE = SX * SY;
 constexpr int ZB = 32;                       // z planes per block
 // window of the biased gradient: two rings around the tile, five planes
 constexpr int SXB = TX + 4, SYB = TY + 4, PLANEB = SXB * SYB;
+// Slots of the biased gradient's five-plane window (plane p in slot
+// (p + 2) % NWB): with six, the plane formed for layer z + 2 never
+// overwrites one that the slowest threads still read for layer z - 1, so one
+// barrier per layer suffices.
+constexpr int NWB = 6;
 constexpr int QF = 19, QG = 7;
 constexpr int G0 = QF, S0 = QF + QG;         // flat plane number of g_0 and of s_0
 
@@ -505,10 +510,12 @@ __device__ __forceinline__ void push3d_fs(int i, float vf, float vs, int x, int 
 // rate, every other output is a1 v_i + a2 v_o + ... (o = opposite).
 // COLL_MRT: the BGK update of f and g plus the moment-space correction of
 // mrt19_even / mrt7_even (rates mrt_rates, mrt_rates_g; s keeps BGK).
-// BIASED: sphi holds five planes of two-ring windows (plane p in slot
-// (p + 2) % 5) and the gradient of Eq. Grad uses the second-order biased
-// difference [-phi(x + 2e) + 4 phi(x + e) - 3 phi(x)] / 2 (Sec. 3.4).
-template <typename S, int MODE, int COLL = COLL_BGK, bool BIASED = false, int NW = 3>
+// BIASED: sphi holds the two-ring window planes (plane p in slot
+// (p + 2) % NW, the five planes z - 2 .. z + 2 read) and the gradient of
+// Eq. Grad uses the second-order biased difference
+// [-phi(x + 2e) + 4 phi(x + e) - 3 phi(x)] / 2 (Sec. 3.4).  Otherwise plane
+// p of the one-ring window is in slot (p + 1) % NW.
+template <typename S, int MODE, int COLL = COLL_BGK, bool BIASED = false, int NW = BIASED ? NWB : 3>
 __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, int y, size_t c,
                                                const float f[QF], const float s[QF],
                                                const float g[QG], float qp, float phip,
@@ -540,7 +547,7 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
         const int centre = (ty + 2) * SXB + tx + 2;
         const float *pl[5];                  // planes z-2 .. z+2
 #pragma unroll
-        for (int k = 0; k < 5; ++k) pl[k] = sphi + ((z + k) % 5) * PLANEB + centre;
+        for (int k = 0; k < 5; ++k) pl[k] = sphi + ((z + k) % NW) * PLANEB + centre;
         phd = pl[2][0];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -774,6 +781,12 @@ __device__ __forceinline__ void layer_update3d(const float *sphi, int z, int x, 
     }
 }
 
+// Slots of the phi window of step3d_column: plane p in slot (p + 1) % NW3.
+// With four, the plane formed for layer z + 1 never overwrites one that the
+// slowest threads still read for layer z - 1, so one barrier per layer
+// suffices.
+constexpr int NW3 = 4;
+
 // One z-column of a 32x4 tile over layers [blockIdx.z * ZBLK, +ZBLK), every
 // value read with plain loads (see lbm3d.cu).
 template <typename S, int XY, int COLL = COLL_BGK, int ZBLK = ZB>
@@ -794,7 +807,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
 
     float g[QG], qcur = 0.0f;
     // prologue: plane zbeg (own cells kept in registers) and plane zbeg-1;
-    // plane p lives in window slot (p + 1) % 3
+    // plane p lives in window slot (p + 1) % NW3
     {
         float ph = 0.0f;
         if (col) {
@@ -804,8 +817,8 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             qcur = q_in[c];
             ph = fmaf(0.5f, qcur, set_sum7<S>(g, P.set_isc[1]));
         }
-        fill_plane<S, XY>(sphi, (zbeg + 1) % 3, zbeg, true, col, ph, pin, q_in, x0, y0, tid, tx, ty, P);
-        fill_plane<S, XY_GEN>(sphi, zbeg % 3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
+        fill_plane<S, XY>(sphi, (zbeg + 1) % NW3, zbeg, true, col, ph, pin, q_in, x0, y0, tid, tx, ty, P);
+        fill_plane<S, XY_GEN>(sphi, zbeg % NW3, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
     }
 
     for (int z = zbeg; z < zend; ++z) {
@@ -820,7 +833,7 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
                 qnext = q_in[c];
                 ph = fmaf(0.5f, qnext, set_sum7<S>(gn, P.set_isc[1]));
             }
-            fill_plane<S, XY>(sphi, (z + 2) % 3, z + 1, true, ok, ph, pin, q_in, x0, y0, tid, tx, ty, P);
+            fill_plane<S, XY>(sphi, (z + 2) % NW3, z + 1, true, ok, ph, pin, q_in, x0, y0, tid, tx, ty, P);
         }
         __syncthreads();
         if (col) {
@@ -830,14 +843,13 @@ __device__ __forceinline__ void step3d_column(const S *__restrict__ pin, S *__re
             for (int i = 0; i < QF; ++i) load_pair<S>(PL.in[i], (cidx)c, f[i], s[i]);
             const float phip = phi_prev[c];
             if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                layer_update3d<S, XY, COLL>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY, COLL, false, NW3>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
             else
-                layer_update3d<S, XY_GEN, COLL>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
+                layer_update3d<S, XY_GEN, COLL, false, NW3>(sphi, z, x, y, c, f, s, g, qcur, phip, pout, phi_prev, q_out, P, PL);
         }
 #pragma unroll
         for (int i = 0; i < QG; ++i) g[i] = gn[i];
         qcur = qnext;
-        __syncthreads();   // plane (z - 1) % 3 is overwritten next iteration
     }
 }
 
@@ -876,8 +888,8 @@ __device__ __forceinline__ void step3d_column_biased(const S *__restrict__ pin, 
     const bool col = (x < nx) && (y < ny);
     const size_t cxy = col ? (size_t)y * nx + x : 0;
     const size_t plane_cells = (size_t)nx * ny;
-    auto fill = [&](int p) {                 // plane p into slot (p + 2) % 5
-        float *pl = sphi + ((p + 2 + 5 * 4) % 5) * PLANEB;
+    auto fill = [&](int p) {                 // plane p into slot (p + 2) % NWB
+        float *pl = sphi + ((p + 2 + NWB * 4) % NWB) * PLANEB;
         for (int sidx = tid; sidx < PLANEB; sidx += TX * TY)
             pl[sidx] = window_phid_b<S>(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, pin, q_in, P);
     };
@@ -898,7 +910,6 @@ __device__ __forceinline__ void step3d_column_biased(const S *__restrict__ pin, 
             else
                 layer_update3d<S, XY_GEN, COLL, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev, q_out, P, PL);
         }
-        __syncthreads();   // slot (z - 2 + 2) % 5 is refilled next iteration
     }
 }
 

@@ -266,9 +266,11 @@ __device__ __forceinline__ void bwin_store(float *pl, const uint32_t *buf, int p
 
 // Layer z uses f/s stage (z - zbeg) % 2 and g stage (z - zbeg) % 3.  In
 // iteration z the block needs the f/s stage of z and the g stages of z and
-// z + 1; the copies of f/s(z + 1) and g(z + 2) are in flight, and when layer
-// z is done its stages receive f/s(z + 2) and g(z + 3): every copy is issued
-// at least one whole layer before it is awaited.
+// z + 1; the copies of f/s(z + 1) and g(z + 2) are in flight.  Once every
+// thread has passed the barrier of iteration z + 1 (so is done with layer
+// z), the stages of layer z receive f/s(z + 2) and g(z + 3): every copy is
+// issued about one whole layer before it is awaited, and one barrier per
+// layer orders both the stages and the window slots.
 template <typename S, int XY, int COLL, bool BIASED>
 __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S *__restrict__ pin,
                                            S *__restrict__ pout, float *__restrict__ phi_prev,
@@ -303,11 +305,29 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             if ((F.pend >> k) & 1u) issue_fs<S>(fs_base + k * Gm::FS_STAGE, &barF[k], M, par, x0, y0, zbeg + k);
     }
 
+    // After the barrier of layer z every thread is done with layer z - 1:
+    // its f/s stage takes layer z - 1 + NFS and its g stage layer z - 1 + NG
+    // (the layers of a stage are NFS, NG apart).  fb and gb are the stages of
+    // layer z ((z - zbeg) mod NFS and mod NG).
+    static_assert(Gm::NFS == 2, "the f/s stages alternate");
+    auto refill = [&](int z, int fb, int gb) {
+        if (z == zbeg) return;
+        const int fp = fb ^ 1, gp = gb == 0 ? Gm::NG - 1 : gb - 1;
+        if (z - 1 + Gm::NFS < zend) {
+            if (tid == 0) issue_fs<S>(fs_base + fp * Gm::FS_STAGE, &barF[fp], M, par, x0, y0, z - 1 + Gm::NFS);
+            F.pend |= 1u << fp;
+        }
+        if (z - 1 + Gm::NG <= zlast) {
+            if (tid == 0) issue_g<S>(g_base + gp * Gm::G_STAGE, &barG[gp], M, par, x0, y0, z - 1 + Gm::NG);
+            G.pend |= 1u << gp;
+        }
+    };
+
     if (BIASED) {
         // the two-ring window: planes zbeg - 2 .. zbeg + 1 with plain loads
-        // (slot of plane p: (p + 2) mod 5), plane zbeg + 2 fetched
+        // (slot of plane p: (p + 2) mod NWB), plane zbeg + 2 fetched
         for (int p = zbeg - 2; p <= zbeg + 1; ++p) {
-            float *pl = sphi + ((p + 2 + 5 * 4) % 5) * PLANEB;
+            float *pl = sphi + ((p + 2 + NWB * 4) % NWB) * PLANEB;
             for (int sidx = tid; sidx < PLANEB; sidx += TX * TY)
                 pl[sidx] = window_phid_b<S>(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, pin, q_in, P);
         }
@@ -325,8 +345,9 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             } else {
                 cp_async_wait_all();
             }
-            bwin_store<S>(sphi + ((z + 4) % 5) * PLANEB, rbuf + ((z - zbeg) & 1) * BWIN_WORDS, z + 2, x0, y0,
+            bwin_store<S>(sphi + ((z + 4) % NWB) * PLANEB, rbuf + ((z - zbeg) & 1) * BWIN_WORDS, z + 2, x0, y0,
                           tid, P);
+            // every thread is done with layer z - 1 and has stored its part of plane z + 2
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) atomicOr(err, 1);
                 cp_async_wait_all();
@@ -334,6 +355,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
                 G.drain(barG, Gm::NG);
                 return;
             }
+            refill(z, fb, gb);
             {
                 const unsigned char *b = fs_base + fb * Gm::FS_STAGE;
                 const unsigned char *bg = g_base + gb * Gm::G_STAGE;
@@ -354,16 +376,6 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
                     layer_update3d<S, XY_GEN, COLL, true>(sphi, z, x, y, c, f, s, g, qp, phip, pout, phi_prev,
                                                          q_out, P, PL);
             }
-            __syncthreads();      // the stages of layer z and window slot of plane z - 2 are free
-            if (z + Gm::NFS < zend) {
-                if (tid == 0)
-                    issue_fs<S>(fs_base + fb * Gm::FS_STAGE, &barF[fb], M, par, x0, y0, z + Gm::NFS);
-                F.pend |= 1u << fb;
-            }
-            if (z + Gm::NG <= zlast) {
-                if (tid == 0) issue_g<S>(g_base + gb * Gm::G_STAGE, &barG[gb], M, par, x0, y0, z + Gm::NG);
-                G.pend |= 1u << gb;
-            }
             fb ^= 1;
             gb = gn;
         }
@@ -373,7 +385,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
     // window of NWIN slots, plane p in slot (p + 1) % NWIN: with four, the
     // plane built while the slowest threads still update layer z - 1 never
     // overwrites one they read, so one barrier per layer suffices
-    constexpr int NWIN = 4;
+    constexpr int NWIN = NW3;
     // window: plane zbeg - 1 with plain loads, plane zbeg from its g stage
     fill_plane<S, XY_GEN>(sphi, zbeg % NWIN, zbeg - 1, false, false, 0.0f, pin, q_in, x0, y0, tid, tx, ty, P);
     bool ok = G.wait(barG, 0, first_wait_limit);
@@ -409,19 +421,7 @@ __device__ __forceinline__ void tma_column(const TmaMaps3d &M, int par, const S 
             G.drain(barG, Gm::NG);
             return;
         }
-        // the stages of layer z - 1 are free: refill them
-        if (z > zbeg) {
-            const int fp = fb ^ 1, gp = gb == 0 ? Gm::NG - 1 : gb - 1;
-            if (z - 1 + Gm::NFS < zend) {
-                if (tid == 0)
-                    issue_fs<S>(fs_base + fp * Gm::FS_STAGE, &barF[fp], M, par, x0, y0, z - 1 + Gm::NFS);
-                F.pend |= 1u << fp;
-            }
-            if (z - 1 + Gm::NG <= zlast) {
-                if (tid == 0) issue_g<S>(g_base + gp * Gm::G_STAGE, &barG[gp], M, par, x0, y0, z - 1 + Gm::NG);
-                G.pend |= 1u << gp;
-            }
-        }
+        refill(z, fb, gb);
         // the ring of plane z + 2 goes into the buffer plane z's ring used
         if (PRE && z + 2 < nz && z + 1 < zend)
             ring_prefetch<S, XY>(rbuf + (z & 1) * RING_WORDS, pin, q_in, z + 2, x0, y0, tid, P);
@@ -459,7 +459,7 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t barF[Tma3Geom<S>::NFS], barG[Tma3Geom<S>::NG];
     // the biased gradient: a five-plane two-ring window, two fetched planes
-    __shared__ float sphi[BIASED ? 5 * PLANEB : 4 * PLANE];
+    __shared__ float sphi[BIASED ? NWB * PLANEB : NW3 * PLANE];
     __shared__ uint32_t rbuf[BIASED ? 2 * BWIN_WORDS : 2 * RING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if (x0 + TX > P.n[0] || y0 + TY > P.n[1]) {          // ragged tile: plain loads
