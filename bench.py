@@ -438,7 +438,8 @@ def run_device(args, world, rank, local):
             rk = ("cac2d", storage)
             variants[f"phase_field_2d_{storage}"] = {
                 "workload": wv.name + " (imposed reversing vortex)", "MLUPS": wv.cells / ms_v / 1e3,
-                "ms_per_step": ms_v, **roof(rk, wv.cells, ms_v, peak), "finite": bool(np.isfinite(m_v))}
+                "ms_per_step": ms_v, **roof(rk, wv.cells, ms_v, peak), "finite": bool(np.isfinite(m_v)),
+                "traffic": profiled_traffic(f"cac2d_{storage}_vortex_4096x4096")}
             del v
         del wv
         torch.cuda.empty_cache()
@@ -459,7 +460,8 @@ def run_device(args, world, rank, local):
             variants[f"phase_field_3d_{storage}"] = {
                 "workload": "vortex_1024x1024x32 (imposed reversing vortex, thin 3D domain)",
                 "MLUPS": cells3 / ms_v / 1e3, "ms_per_step": ms_v, **roof(rk, cells3, ms_v, peak),
-                "finite": bool(np.isfinite(m_v))}
+                "finite": bool(np.isfinite(m_v)),
+                "traffic": profiled_traffic(f"cac3d_{storage}_vortex_1024x1024x32")}
             del v
         del wv, phi3, u3
         torch.cuda.empty_cache()
