@@ -313,6 +313,34 @@ def run_device(args, world, rank, local):
                 **roof(rk, w.cells, ms_v, peak), "finite": bool(np.isfinite(m_v)),
                 "traffic": profiled_traffic(f"step2d_{storage}_2048x4096")}
             del v
+        # the 2048 x 4096 grid at density ratio 100 (the C1 values otherwise),
+        # which is not stable beyond a few hundred steps with this model (see
+        # the design notes): a bounded window is timed and its end state
+        # checked; and the 3D film with the paper's Table physics (the 3D
+        # variants below run density ratio 10); the per-step work does not
+        # depend on the physics
+        for name, mk, fam, kern, nsteps in (
+                ("2d_fp32_ratio100",
+                 lambda: W.film_boiling_2d(2048, 4096, rho_ratio=100.0, modes=8, seed=1, y0=64.0,
+                                           phi_wall=(1.0, 0.0)), "step2d_fp32_2048x4096", "tiled", 100),
+                ("3d_fp32_tma_paper_ratio",
+                 lambda: W.film_boiling_3d(256, 256, 512, modes=4, seed=2, paper=True,
+                                           phi_wall=(1.0, 0.0)), "step3d_tma_fp32_256x256x512", "tma", 60)):
+            wr = mk()
+            v = Solver(wr.n, wr.periodic, wr.params, storage="fp32", device=dev, stream=stream)
+            v.set_kernel(kern)
+            v.init(wr.phi0, wr.T0, p0=wr.p0)
+            v.step(5)
+            ms_v = step_kernel_ms(v, nsteps)
+            m_v = safe_reduce(v)
+            rk = ("2d" if wr.dim == 2 else "3d", "fp32")
+            variants[name] = {
+                "workload": f"{wr.name}, density ratio {wr.params['rho_l'] / wr.params['rho_g']:g} "
+                            f"(steps 5..{5 + nsteps} timed)", "kernel": v.kernel(),
+                "MLUPS": wr.cells / ms_v / 1e3, "ms_per_step": ms_v, **roof(rk, wr.cells, ms_v, peak),
+                "finite": bool(np.isfinite(m_v)), "traffic": profiled_traffic(fam)}
+            del v, wr
+            torch.cuda.empty_cache()
         # the two-relaxation-time collision option on the same 2D workload
         wt = dict(w.params, collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25))
         for storage in ("fp32", "fp16"):
@@ -352,6 +380,7 @@ def run_device(args, world, rank, local):
             **roof(rk, w.cells, ms_v, peak), "finite": bool(np.isfinite(m_v))}
         del v
         w3 = W.c3_film_boiling_3d()
+        w3.name += " (density ratio 10)"
         best16 = ("tiled", 0.0)
         for storage in ("fp32", "fp16"):
             for kern in ("tiled", "tma"):
@@ -414,6 +443,7 @@ def run_device(args, world, rank, local):
         torch.cuda.empty_cache()
         # the 512 x 512 x 768 FP16 film (201 M cells, 36 GB of populations)
         w5 = W.c5_film_boiling_3d_large()
+        w5.name += " (density ratio 10)"
         v = Solver(w5.n, w5.periodic, w5.params, storage="fp16", device=dev, stream=stream)
         v.set_kernel(best16[0])
         v.init(w5.phi0, w5.T0, p0=w5.p0)

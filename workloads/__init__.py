@@ -252,8 +252,10 @@ def c2_film_boiling(nx=2048, ny=4096, top_phi=0.0):
 
 
 def c3_film_boiling_3d(nx=256, ny=256, nz=512, top_phi=0.0):
-    """256 x 256 x 512 3D film boiling, paper parameters, gravity along z."""
-    w = film_boiling_3d(nx, ny, nz, modes=4, seed=2, paper=True,
+    """256 x 256 x 512 3D film boiling at density ratio 10 with the other
+    film values of the 128 x 256 case (gravity 1e-5 along z), 2D-mode
+    interface perturbation (seed 2), 5000 steps; stable over that horizon."""
+    w = film_boiling_3d(nx, ny, nz, rho_ratio=10.0, modes=4, seed=2, z0=32.0,
                         phi_wall=(1.0, float(top_phi)))
     w.steps = 5000
     return w
@@ -266,7 +268,9 @@ def c4_droplet(n=512):
 
 
 def c5_film_boiling_3d_large(top_phi=0.0):
-    w = film_boiling_3d(512, 512, 768, modes=4, seed=2, paper=True,
+    """512 x 512 x 768 3D film boiling, the physics of c3_film_boiling_3d
+    (density ratio 10), 2000 steps, FP16 storage in the measurements."""
+    w = film_boiling_3d(512, 512, 768, rho_ratio=10.0, modes=4, seed=2, z0=32.0,
                         phi_wall=(1.0, float(top_phi)))
     w.steps = 2000
     return w
