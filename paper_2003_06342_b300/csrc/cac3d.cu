@@ -91,12 +91,15 @@ __device__ __forceinline__ void cac_ring_store(float *plane, const uint32_t *buf
     const size_t cc = cac_ring_cell<XY>(tid, z, x0, y0, P, slot);
     const size_t N = (size_t)P.N;
     float v[QG];
+    // element off_g(QF, i, cc, N) = (2 QF + i) N + cc sits in the high half of
+    // its word when odd
+    const uint32_t pc = (uint32_t)cc & 1u, pn = (uint32_t)N & 1u;
 #pragma unroll
     for (int i = 0; i < QG; ++i) {
         const uint32_t w = buf[i * CRING + tid];
         if (IsNarrow<S>::value) {
-            const size_t e = off_g(QF, i, cc, N);
-            const unsigned short h = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
+            const uint32_t odd = pc ^ (pn & (uint32_t)((2 * QF + i) & 1));
+            const unsigned short h = (unsigned short)(odd ? (w >> 16) : (w & 0xffffu));
             S val;
             memcpy(&val, &h, 2);
             v[i] = widen(val);
