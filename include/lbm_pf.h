@@ -257,9 +257,13 @@ int lbm_set_kernel(lbm_handle *h, int32_t kernel);
 int lbm_get_kernel(const lbm_handle *h, int32_t *kernel);
 
 /* n time steps, saving the state after each: after step k (k = 0..n-1) the
- * state (lbm_get_state layout) is copied to buf + k*stride, device memory.
- * Used to recompute a checkpointed segment for the adjoint in one call.
- * stride >= lbm_state_bytes; LBM_ENOMEM for a short stride. */
+ * state (lbm_get_state layout) is in buf + k*stride, device memory, and the
+ * handle holds the last one.  Used to recompute a checkpointed segment for
+ * the adjoint in one call.  stride >= lbm_state_bytes; LBM_ENOMEM for a
+ * short stride.  For the 2D coupled model on the tiled kernel without the
+ * periodic state check, with buf and stride multiples of 16 bytes, each
+ * step reads the previous slot and writes the next one directly (one state
+ * copy per call instead of one per step); the states are the same. */
 int lbm_step_record(lbm_handle *h, int32_t n, void *buf, size_t stride);
 
 /* Number of time steps since lbm_init / lbm_set_state. */

@@ -537,12 +537,52 @@ int lbm_set_health_check(lbm_handle *h, int32_t every, float phi_excess) {
 
 static int copy_state(lbm_handle *h, void *buf, size_t bytes, int32_t on_device, bool save);
 
+// One 2D step of the coupled model on the tiled kernel from the state (in
+// populations, phi^{n-1}, lagged source) to another; phi^{n-1} is copied
+// into the output first, since the kernel reads and rewrites it in place.
+static int step2d_between(lbm_handle *h, const void *in_pops, const float *in_pp, const float *in_q,
+                          void *out_pops, float *out_pp, float *out_q) {
+    if (cudaMemcpyAsync(out_pp, in_pp, h->N * sizeof(float), cudaMemcpyDeviceToDevice, h->stream) !=
+        cudaSuccess)
+        return LBM_ECUDA;
+    cudaError_t e;
+    switch (h->params.storage) {
+    case LBM_STORE_FP32: e = launch_step2d<float>(in_pops, out_pops, out_pp, in_q, out_q, h->dp, h->stream); break;
+    case LBM_STORE_FP16: e = launch_step2d<__half>(in_pops, out_pops, out_pp, in_q, out_q, h->dp, h->stream); break;
+    default: e = launch_step2d<__nv_bfloat16>(in_pops, out_pops, out_pp, in_q, out_q, h->dp, h->stream); break;
+    }
+    return cuda_status(e);
+}
+
 int lbm_step_record(lbm_handle *h, int32_t n, void *buf, size_t stride) {
     if (!h || n < 0 || (!buf && n > 0)) return LBM_EINVAL;
     size_t need;
     lbm_state_bytes(h, &need);
     if (stride < need) return LBM_ENOMEM;
     h->last_launches = 0;
+    // 2D coupled model on the tiled kernel without the periodic check: step
+    // k reads record slot k - 1 (the handle's state for k = 0) and writes
+    // slot k directly, and only the last slot is copied back into the
+    // handle, instead of a state copy after every step
+    const size_t pb = (size_t)h->Qtot * h->N * h->elem, sb = h->N * sizeof(float);
+    if (n > 0 && h->dim == 2 && h->params.model == LBM_MODEL_COUPLED &&
+        h->kernel_choice != LBM_KERNEL_TMA && h->health_every <= 0 && (uintptr_t)buf % 16 == 0 &&
+        stride % 16 == 0 && pb % 16 == 0) {
+        char *b = (char *)buf;
+        for (int32_t k = 0; k < n; ++k) {
+            char *out = b + (size_t)k * stride;
+            const char *in = b + (size_t)(k - 1) * stride;
+            const int r = k == 0
+                ? step2d_between(h, h->pops[h->cur], h->phi_prev, h->q[h->cur], out, (float *)(out + pb),
+                                 (float *)(out + pb + sb))
+                : step2d_between(h, in, (const float *)(in + pb), (const float *)(in + pb + sb), out,
+                                 (float *)(out + pb), (float *)(out + pb + sb));
+            if (r != LBM_OK) return r;
+            ++h->steps;
+            ++h->last_launches;
+        }
+        return copy_state(h, b + (size_t)(n - 1) * stride, stride, 1, false);
+    }
     for (int32_t k = 0; k < n; ++k) {
         int r = do_step(h);
         if (r != LBM_OK) return r;

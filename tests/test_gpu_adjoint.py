@@ -110,6 +110,19 @@ def test_segment_calls_match_single_steps():
         b.step(1)
         assert torch.equal(rec[k], b.get_state())
     assert a.steps_done() == n
+    assert torch.equal(a.get_state(), b.get_state())     # the handle holds the last state
+    # 16-bit storage records the same way, and so does the copying path
+    # (an unaligned stride)
+    for storage, pad in (("fp16", 0), ("fp32", 4)):
+        c = Solver(w.n, w.periodic, w.params, storage=storage).init(w.phi0, w.T0)
+        d = Solver(w.n, w.periodic, w.params, storage=storage).init(w.phi0, w.T0)
+        nbc = c.state_bytes()
+        rc = torch.zeros((n, nbc + pad), dtype=torch.uint8, device="cuda")
+        Bd.check(Bd.lib.lbm_step_record(c._h, n, vp(rc), rc.stride(0)), "lbm_step_record")
+        for k in range(n):
+            d.step(1)
+            assert torch.equal(rc[k, :nbc], d.get_state()), (storage, pad, k)
+        assert torch.equal(c.get_state(), d.get_state()) and c.steps_done() == n
     # reverse over the recorded states both ways
     ab, sb = ctypes.c_size_t(), ctypes.c_size_t()
     Bd.check(Bd.lib.lbm_adjoint_bytes(a._h, ctypes.byref(ab), ctypes.byref(sb)), "bytes")
