@@ -376,12 +376,6 @@ __device__ __forceinline__ float density(float phi, const DevParams &P) {
     return fmaf(phi, P.rho_g, (1.0f - phi) * P.rho_l);
 }
 
-__device__ __forceinline__ float viscosity(float phi, const DevParams &P) {
-    phi = unit_phi(phi);
-    return P.visc_interp == 0 ? P.nu_l * P.nu_g / (phi * P.nu_l + (1.0f - phi) * P.nu_g)
-                              : (1.0f - phi) * P.nu_l + phi * P.nu_g;
-}
-
 __device__ __forceinline__ float diffusivity(float phi, const DevParams &P) {
     phi = unit_phi(phi);
     return P.alpha_interp == 0 ? fmaf(phi, P.alpha_g, (1.0f - phi) * P.alpha_l)
