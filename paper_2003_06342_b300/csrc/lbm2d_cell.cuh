@@ -189,18 +189,21 @@ __device__ __forceinline__ float to_rep(int i, int set, float x, const DevParams
 
 // Push of direction i's three post-collision values (working representation)
 // from cell c = (x, y).  FAST: the link neither wraps nor meets a wall.
-template <typename S, bool FAST>
+// PART: all three values, g alone (PUSH_G) or the (f, s) pair alone (PUSH_FS).
+constexpr int PUSH_ALL = 0, PUSH_G = 1, PUSH_FS = 2;
+template <typename S, bool FAST, int PART = PUSH_ALL>
 __device__ __forceinline__ void push2d(int i, float vf, float vg, float vs, int x, int y, size_t c,
                                        S *__restrict__ pout, const DevParams &P,
                                        const Planes2d<S> &PL) {
+    constexpr bool DO_FS = PART != PUSH_G, DO_G = PART != PUSH_FS;
     const int ex = L::ex(i), ey = L::ey(i);
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     if (FAST) {
         const long long d = (long long)c + ((long long)ey * nx + ex);
         if (in_bounds(d, (long long)N, P)) {
-            store_pair<S>(PL.out[i], d, vf, vs);
-            PL.out[9 + i][d] = narrow<S>(vg);
+            if (DO_FS) store_pair<S>(PL.out[i], d, vf, vs);
+            if (DO_G) PL.out[9 + i][d] = narrow<S>(vg);
         }
         return;
     }
@@ -214,14 +217,16 @@ __device__ __forceinline__ void push2d(int i, float vf, float vg, float vs, int 
         const int side = (kx >= 2 ? kx : ky) - 2;
         const int o = L::opp(i);
         if (!in_bounds((long long)c, (long long)N, P)) return;
-        store_pair<S>(pout + off_f(o, 0, N), (long long)c, vf,
-                      fmaf(2.0f * rep_mul<S>(i, 2, P), P.T_wall[side] - P.s_ref, -vs));
-        pout[off_g(9, o, c, N)] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 1, P), P.phi_wall[side] - P.g_ref, -vg));
+        if (DO_FS)
+            store_pair<S>(pout + off_f(o, 0, N), (long long)c, vf,
+                          fmaf(2.0f * rep_mul<S>(i, 2, P), P.T_wall[side] - P.s_ref, -vs));
+        if (DO_G)
+            pout[off_g(9, o, c, N)] = narrow<S>(fmaf(2.0f * rep_mul<S>(i, 1, P), P.phi_wall[side] - P.g_ref, -vg));
     } else {
         const size_t d = (size_t)dy * nx + dx;
         if (!in_bounds((long long)d, (long long)N, P)) return;
-        store_pair<S>(pout + off_f(i, 0, N), (long long)d, vf, vs);
-        pout[off_g(9, i, d, N)] = narrow<S>(vg);
+        if (DO_FS) store_pair<S>(pout + off_f(i, 0, N), (long long)d, vf, vs);
+        if (DO_G) pout[off_g(9, i, d, N)] = narrow<S>(vg);
     }
 }
 
@@ -432,78 +437,14 @@ __device__ __forceinline__ void cell_core2d(const float *sp, int pitch, const fl
     const float Pxa = fmaf(3.0f, uxx, -1.5f * uyy), Pya = fmaf(3.0f, uyy, -1.5f * uxx);
     const float Pd0 = 3.0f * usq;
 
-    // MRT: correction per direction of the flow and phase-field sets, in the
-    // working representation (zero and never formed for BGK and TRT)
-    float cf[9], cg[9];
-    if (MRT) {
-        // f_eq_bar - w ref per weight: the coefficient form above at om = 1 and
-        // b = -1/2, since om f_eq + (1 - om/2) S = f_eq - S/2 there
-        const float K0b = fmaf(-0.5f, fmaf(rcs2 * q, P.kappa, -uB), m.p - P.set_ref[0]);
-        const float K1b = fmaf(0.5f, hU, rcs2);
-        const float Hbx = __fmul_rn(-0.5f, hx), Hby = __fmul_rn(-0.5f, hy);
-        const float Vbx = fmaf(3.0f * K1b, ux, -0.5f * m.Fx), Vby = fmaf(3.0f * K1b, uy, -0.5f * m.Fy);
-        // d_i = f_i - f_eq_bar_i (population units)
-        float dd[9];
-        auto devf = [&](int i, float eqw) {
-            return IsNarrow<S>::value ? __fmul_rn(L::w(i), fmaf(f[i], P.set_isc[0], -eqw))
-                                      : fmaf(-L::w(i), eqw, f[i]);
-        };
-        dd[0] = devf(0, fmaf(K1b, P0, K0b));
-        auto dpair = [&](int i, int o, float cu, float Pe, float eHb, float eVb) {
-            const float Eb = fmaf(3.0f * cu, eHb, fmaf(K1b, Pe, K0b));
-            const float Ob = fmaf(Pe, eHb, eVb);
-            dd[i] = devf(i, Eb + Ob);
-            dd[o] = devf(o, Eb - Ob);
-        };
-        dpair(1, 3, ux, Pxa, Hbx, Vbx);
-        dpair(2, 4, uy, Pya, Hby, Vby);
-        dpair(5, 7, __fadd_rn(ux, uy), fmaf(9.0f, uxy, Pd0), __fadd_rn(Hbx, Hby), __fadd_rn(Vbx, Vby));
-        dpair(6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(Hby, Hbx), __fsub_rn(Vby, Vbx));
-        // e, eps, j and q relax at their own rates; rho, p_xx, p_xy at om_f
-        mrt_correction2d<S, true, false>(dd, P.mrt_rates[0] - om_f, P.mrt_rates[1] - om_f,
-                                         P.mrt_rates[2] - om_f, 0.0f, P.set_sc[0], cf);
-
-        // g_eq_bar - w phi_ref per weight: (phd - q/2) + phi P_e + e.(3 phi u - iface n / 2)
-        const float Agb = fmaf(-0.5f, q, phd);
-        const float hif = __fmul_rn(-0.5f, iface);
-        const float Vgbx = fmaf(3.0f * ph, ux, __fmul_rn(hif, nx_));
-        const float Vgby = fmaf(3.0f * ph, uy, __fmul_rn(hif, ny_));
-        auto devg = [&](int i, float eqw) {
-            return IsNarrow<S>::value ? __fmul_rn(L::w(i), fmaf(g[i], P.set_isc[1], -eqw))
-                                      : fmaf(-L::w(i), eqw, g[i]);
-        };
-        dd[0] = devg(0, fmaf(ph, P0, Agb));
-        auto gpair = [&](int i, int o, float Pe, float eV) {
-            const float Eb = fmaf(ph, Pe, Agb);
-            dd[i] = devg(i, Eb + eV);
-            dd[o] = devg(o, Eb - eV);
-        };
-        gpair(1, 3, Pxa, Vgbx);
-        gpair(2, 4, Pya, Vgby);
-        gpair(5, 7, fmaf(9.0f, uxy, Pd0), __fadd_rn(Vgbx, Vgby));
-        gpair(6, 8, fmaf(-9.0f, uxy, Pd0), __fsub_rn(Vgby, Vgbx));
-        // phi and j relax at om_g (the mobility); e, eps, q, p_xx, p_xy at
-        // their own rates (the host stores om_g for a rate given as 0)
-        mrt_correction2d<S, false, true>(dd, P.mrt_rates_g[0] - om_g, P.mrt_rates_g[1] - om_g,
-                                         P.mrt_rates_g[2] - om_g, P.mrt_rates_g[3] - om_g,
-                                         P.set_sc[1], cg);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) cf[i] = cg[i] = 0.0f;
-    }
-
-    // rest
-    sink.put(0,
-        MRT ? __fadd_rn(fmaf(k.a_f, f[0], to_rep<S>(0, 0, fmaf(k.K1, P0, k.K0), P)), cf[0])
-            : fmaf(k.a_f, f[0], to_rep<S>(0, 0, fmaf(k.K1, P0, k.K0), P)),
-        MRT ? __fadd_rn(fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)), cg[0])
-            : fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)),
-        fmaf(k.a_s, s[0], to_rep<S>(0, 2, fmaf(k.Bs, P0, k.As), P)));
     const float2 a_fs = make_float2(k.a_f, k.a_s);
     const float2 a1_fs = make_float2(a1_f, a1_s), a2_fs = make_float2(a2_f, a2_s);
-    // a direction i with e = (ex, ey) and its opposite o
-    auto pair = [&](int i, int o, float cu, float Pe, float eVg, float eH, float eHo, float eVf,
-                    float eW) {
+    // a direction i with e = (ex, ey) and its opposite o.  With MRT the sets
+    // go out in two passes, each with its own correction c (working
+    // representation), so only one set's correction is live at a time:
+    // part 1 pushes g, part 2 pushes f and s.
+    auto pair = [&](int part, const float *c, int i, int o, float cu, float Pe, float eVg, float eH,
+                    float eHo, float eVf, float eW) {
         const float Eg = fmaf(k.Bg, Pe, k.Ag);
         const float Ef = fmaf(3.0f * cu, eH, fmaf(k.K1, Pe, k.K0));
         const float Of = fmaf(Pe, eHo, eVf);
@@ -519,9 +460,14 @@ __device__ __forceinline__ void cell_core2d(const float *sp, int pitch, const fl
         const float2 ro = rfs(fadd2(make_float2(Ef, Es), make_float2(-Of, -eW)));
         const float2 fsi = make_float2(f[i], s[i]), fso = make_float2(f[o], s[o]);
         if (MRT) {
-            const float2 vi = ffma2(a_fs, fsi, ri), vo = ffma2(a_fs, fso, ro);
-            sink.put(i, __fadd_rn(vi.x, cf[i]), __fadd_rn(fmaf(k.a_g, g[i], rg(Eg + eVg)), cg[i]), vi.y);
-            sink.put(o, __fadd_rn(vo.x, cf[o]), __fadd_rn(fmaf(k.a_g, g[o], rg(Eg - eVg)), cg[o]), vo.y);
+            if (part == 1) {
+                sink.put_g(i, __fadd_rn(fmaf(k.a_g, g[i], rg(Eg + eVg)), c[i]));
+                sink.put_g(o, __fadd_rn(fmaf(k.a_g, g[o], rg(Eg - eVg)), c[o]));
+            } else {
+                const float2 vi = ffma2(a_fs, fsi, ri), vo = ffma2(a_fs, fso, ro);
+                sink.put_fs(i, __fadd_rn(vi.x, c[i]), vi.y);
+                sink.put_fs(o, __fadd_rn(vo.x, c[o]), vo.y);
+            }
         } else if (!TRT) {
             const float2 vi = ffma2(a_fs, fsi, ri), vo = ffma2(a_fs, fso, ro);
             sink.put(i, vi.x, fmaf(k.a_g, g[i], rg(Eg + eVg)), vi.y);
@@ -533,23 +479,96 @@ __device__ __forceinline__ void cell_core2d(const float *sp, int pitch, const fl
             sink.put(o, vo.x, fmaf(a1_g, g[o], fmaf(a2_g, g[i], rg(Eg - eVg))), vo.y);
         }
     };
-    pair(1, 3, ux, Pxa, k.Vgx, k.Hx, Hox, k.Vfx, k.Wx);                          // (1, 0)
-    pair(2, 4, uy, Pya, k.Vgy, k.Hy, Hoy, k.Vfy, k.Wy);                          // (0, 1)
-    // the diagonal components are sums of products: __fadd_rn / __fsub_rn keep
-    // the compiler from fusing one of the products into the sum
-    pair(5, 7, __fadd_rn(ux, uy), fmaf(9.0f, uxy, Pd0), __fadd_rn(k.Vgx, k.Vgy),
-         __fadd_rn(k.Hx, k.Hy), __fadd_rn(Hox, Hoy), __fadd_rn(k.Vfx, k.Vfy),
-         __fadd_rn(k.Wx, k.Wy));                                                 // (1, 1)
-    pair(6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(k.Vgy, k.Vgx),
-         __fsub_rn(k.Hy, k.Hx), __fsub_rn(Hoy, Hox), __fsub_rn(k.Vfy, k.Vfx),
-         __fsub_rn(k.Wy, k.Wx));                                                 // (-1, 1)
+    auto pairs = [&](int part, const float *c) {
+        pair(part, c, 1, 3, ux, Pxa, k.Vgx, k.Hx, Hox, k.Vfx, k.Wx);                 // (1, 0)
+        pair(part, c, 2, 4, uy, Pya, k.Vgy, k.Hy, Hoy, k.Vfy, k.Wy);                 // (0, 1)
+        // the diagonal components are sums of products: __fadd_rn / __fsub_rn
+        // keep the compiler from fusing one of the products into the sum
+        pair(part, c, 5, 7, __fadd_rn(ux, uy), fmaf(9.0f, uxy, Pd0), __fadd_rn(k.Vgx, k.Vgy),
+             __fadd_rn(k.Hx, k.Hy), __fadd_rn(Hox, Hoy), __fadd_rn(k.Vfx, k.Vfy),
+             __fadd_rn(k.Wx, k.Wy));                                                 // (1, 1)
+        pair(part, c, 6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(k.Vgy, k.Vgx),
+             __fsub_rn(k.Hy, k.Hx), __fsub_rn(Hoy, Hox), __fsub_rn(k.Vfy, k.Vfx),
+             __fsub_rn(k.Wy, k.Wx));                                                 // (-1, 1)
+    };
+
+    if constexpr (MRT) {
+        // the phase-field set: g_eq_bar - w phi_ref per weight is
+        // (phd - q/2) + phi P_e + e.(3 phi u - iface n / 2) (the coefficient
+        // form above at om = 1 and b = -1/2)
+        {
+            float dd[9], cg[9];
+            const float Agb = fmaf(-0.5f, q, phd);
+            const float hif = __fmul_rn(-0.5f, iface);
+            const float Vgbx = fmaf(3.0f * ph, ux, __fmul_rn(hif, nx_));
+            const float Vgby = fmaf(3.0f * ph, uy, __fmul_rn(hif, ny_));
+            auto devg = [&](int i, float eqw) {
+                return IsNarrow<S>::value ? __fmul_rn(L::w(i), fmaf(g[i], P.set_isc[1], -eqw))
+                                          : fmaf(-L::w(i), eqw, g[i]);
+            };
+            dd[0] = devg(0, fmaf(ph, P0, Agb));
+            auto gpair = [&](int i, int o, float Pe, float eV) {
+                const float Eb = fmaf(ph, Pe, Agb);
+                dd[i] = devg(i, Eb + eV);
+                dd[o] = devg(o, Eb - eV);
+            };
+            gpair(1, 3, Pxa, Vgbx);
+            gpair(2, 4, Pya, Vgby);
+            gpair(5, 7, fmaf(9.0f, uxy, Pd0), __fadd_rn(Vgbx, Vgby));
+            gpair(6, 8, fmaf(-9.0f, uxy, Pd0), __fsub_rn(Vgby, Vgbx));
+            // phi and j relax at om_g (the mobility); e, eps, q, p_xx, p_xy at
+            // their own rates (the host stores om_g for a rate given as 0)
+            mrt_correction2d<S, false, true>(dd, P.mrt_rates_g[0] - om_g, P.mrt_rates_g[1] - om_g,
+                                             P.mrt_rates_g[2] - om_g, P.mrt_rates_g[3] - om_g,
+                                             P.set_sc[1], cg);
+            sink.put_g(0, __fadd_rn(fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)), cg[0]));
+            pairs(1, cg);
+        }
+        // the flow set (s keeps BGK): f_eq_bar - w ref per weight, the same
+        // coefficient form at om = 1 and b = -1/2
+        {
+            float dd[9], cf[9];
+            const float K0b = fmaf(-0.5f, fmaf(rcs2 * q, P.kappa, -uB), m.p - P.set_ref[0]);
+            const float K1b = fmaf(0.5f, hU, rcs2);
+            const float Hbx = __fmul_rn(-0.5f, hx), Hby = __fmul_rn(-0.5f, hy);
+            const float Vbx = fmaf(3.0f * K1b, ux, -0.5f * m.Fx), Vby = fmaf(3.0f * K1b, uy, -0.5f * m.Fy);
+            // d_i = f_i - f_eq_bar_i (population units)
+            auto devf = [&](int i, float eqw) {
+                return IsNarrow<S>::value ? __fmul_rn(L::w(i), fmaf(f[i], P.set_isc[0], -eqw))
+                                          : fmaf(-L::w(i), eqw, f[i]);
+            };
+            dd[0] = devf(0, fmaf(K1b, P0, K0b));
+            auto dpair = [&](int i, int o, float cu, float Pe, float eHb, float eVb) {
+                const float Eb = fmaf(3.0f * cu, eHb, fmaf(K1b, Pe, K0b));
+                const float Ob = fmaf(Pe, eHb, eVb);
+                dd[i] = devf(i, Eb + Ob);
+                dd[o] = devf(o, Eb - Ob);
+            };
+            dpair(1, 3, ux, Pxa, Hbx, Vbx);
+            dpair(2, 4, uy, Pya, Hby, Vby);
+            dpair(5, 7, __fadd_rn(ux, uy), fmaf(9.0f, uxy, Pd0), __fadd_rn(Hbx, Hby), __fadd_rn(Vbx, Vby));
+            dpair(6, 8, __fsub_rn(uy, ux), fmaf(-9.0f, uxy, Pd0), __fsub_rn(Hby, Hbx), __fsub_rn(Vby, Vbx));
+            // e, eps, j and q relax at their own rates; rho, p_xx, p_xy at om_f
+            mrt_correction2d<S, true, false>(dd, P.mrt_rates[0] - om_f, P.mrt_rates[1] - om_f,
+                                             P.mrt_rates[2] - om_f, 0.0f, P.set_sc[0], cf);
+            sink.put_fs(0, __fadd_rn(fmaf(k.a_f, f[0], to_rep<S>(0, 0, fmaf(k.K1, P0, k.K0), P)), cf[0]),
+                        fmaf(k.a_s, s[0], to_rep<S>(0, 2, fmaf(k.Bs, P0, k.As), P)));
+            pairs(2, cf);
+        }
+    } else {
+        // rest
+        sink.put(0, fmaf(k.a_f, f[0], to_rep<S>(0, 0, fmaf(k.K1, P0, k.K0), P)),
+                 fmaf(k.a_g, g[0], to_rep<S>(0, 1, fmaf(k.Bg, P0, k.Ag), P)),
+                 fmaf(k.a_s, s[0], to_rep<S>(0, 2, fmaf(k.Bs, P0, k.As), P)));
+        pairs(0, nullptr);
+    }
 }
 
 
 // Where a cell update's results go: PushSink2 pushes them into the other
 // population buffer and writes phi^{n-1} and the lagged source (the tiled and
 // TMA kernels); a sink gets scalars(phd, q) once and put(i, f, g, s) for every
-// direction i.
+// direction i, or with MRT put_g(i, g) for every i and then put_fs(i, f, s).
 template <typename S, bool FAST>
 struct PushSink2 {
     int x, y;
@@ -567,6 +586,12 @@ struct PushSink2 {
     }
     __device__ __forceinline__ void put(int i, float vf, float vg, float vs) {
         push2d<S, FAST>(i, vf, vg, vs, x, y, c, pout, P, PL);
+    }
+    __device__ __forceinline__ void put_g(int i, float vg) {
+        push2d<S, FAST, PUSH_G>(i, 0.0f, vg, 0.0f, x, y, c, pout, P, PL);
+    }
+    __device__ __forceinline__ void put_fs(int i, float vf, float vs) {
+        push2d<S, FAST, PUSH_FS>(i, vf, 0.0f, vs, x, y, c, pout, P, PL);
     }
 };
 
