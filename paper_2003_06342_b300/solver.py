@@ -142,21 +142,41 @@ class Solver:
         self._keep = keep     # inputs stay alive until the init kernel has run
         return self
 
-    def init_host(self, phi0, T0, u0=None, p0=None):
-        """Same as init() from host float64 numpy arrays (synchronous copy)."""
-        arrs = [np.ascontiguousarray(phi0, dtype=np.float64), np.ascontiguousarray(T0, dtype=np.float64)]
+    @staticmethod
+    def _host_array(a, dtype):
+        """A C-contiguous host array (numpy or CPU tensor) of `dtype`, kept
+        without a copy when it already is one (a pinned float32 tensor stays
+        pinned, so its copy to the device runs at the bus rate)."""
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda:
+                raise ValueError("host path: expected a CPU array")
+            want = torch.float32 if dtype == np.float32 else torch.float64
+            return a if (a.dtype == want and a.is_contiguous()) else a.to(want).contiguous()
+        return np.ascontiguousarray(a, dtype=dtype)
+
+    @staticmethod
+    def _host_ptr(a):
+        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+    def init_host(self, phi0, T0, u0=None, p0=None, dtype=np.float64):
+        """Same as init() from host arrays through the host-pointer path of
+        lbm_init: float64 (converted on the host) or float32 (copied as is;
+        pass pinned CPU tensors for the fastest transfer)."""
+        if dtype not in (np.float32, np.float64):
+            raise ValueError("dtype must be float32 or float64")
+        arrs = [self._host_array(phi0, dtype), self._host_array(T0, dtype)]
         u = [None, None, None]
         if u0 is not None:
             for a in range(self.dim):
-                u[a] = np.ascontiguousarray(u0[a], dtype=np.float64)
-        p = None if p0 is None else np.ascontiguousarray(p0, dtype=np.float64)
+                u[a] = self._host_array(u0[a], dtype)
+        p = None if p0 is None else self._host_array(p0, dtype)
         f = B.lbm_fields()
-        f.phi, f.T = arrs[0].ctypes.data, arrs[1].ctypes.data
-        f.ux = u[0].ctypes.data if u[0] is not None else None
-        f.uy = u[1].ctypes.data if u[1] is not None else None
-        f.uz = u[2].ctypes.data if u[2] is not None else None
-        f.p = p.ctypes.data if p is not None else None
-        f.on_device, f.dtype = 0, 1
+        f.phi, f.T = self._host_ptr(arrs[0]), self._host_ptr(arrs[1])
+        f.ux = self._host_ptr(u[0]) if u[0] is not None else None
+        f.uy = self._host_ptr(u[1]) if u[1] is not None else None
+        f.uz = self._host_ptr(u[2]) if u[2] is not None else None
+        f.p = self._host_ptr(p) if p is not None else None
+        f.on_device, f.dtype = 0, (0 if dtype == np.float32 else 1)
         B.check(B.lib.lbm_init(self._h, ctypes.byref(f)), "lbm_init")
         return self
 
@@ -197,14 +217,22 @@ class Solver:
         u = [out["ux"], out["uy"]] + ([out["uz"]] if self.dim == 3 else [])
         return dict(phi=out["phi"], T=out["T"], u=u, p=out["p"])
 
-    def fields_host(self):
-        """dict of float64 numpy arrays through the host-pointer path."""
-        out = {k: np.empty(self.shape, dtype=np.float64) for k in ("phi", "T", "ux", "uy", "uz", "p")}
+    def fields_host(self, out=None):
+        """dict(phi, T, u=[...], p) on the host through the host-pointer path:
+        float64 numpy arrays by default, or written into `out`, a dict of
+        float32 CPU buffers (keys phi, T, ux, uy, uz, p; pinned tensors copy
+        at the bus rate)."""
+        if out is None:
+            out = {k: np.empty(self.shape, dtype=np.float64) for k in ("phi", "T", "ux", "uy", "uz", "p")}
+            dt = 1
+        else:
+            dt = 0
         f = B.lbm_fields()
-        f.phi, f.T = out["phi"].ctypes.data, out["T"].ctypes.data
-        f.ux, f.uy, f.uz = out["ux"].ctypes.data, out["uy"].ctypes.data, out["uz"].ctypes.data
-        f.p = out["p"].ctypes.data
-        f.on_device, f.dtype = 0, 1
+        f.phi, f.T = self._host_ptr(out["phi"]), self._host_ptr(out["T"])
+        f.ux, f.uy = self._host_ptr(out["ux"]), self._host_ptr(out["uy"])
+        f.uz = self._host_ptr(out["uz"]) if self.dim == 3 else None
+        f.p = self._host_ptr(out["p"])
+        f.on_device, f.dtype = 0, dt
         B.check(B.lib.lbm_get_fields(self._h, ctypes.byref(f)), "lbm_get_fields")
         u = [out["ux"], out["uy"]] + ([out["uz"]] if self.dim == 3 else [])
         return dict(phi=out["phi"], T=out["T"], u=u, p=out["p"])

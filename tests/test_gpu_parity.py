@@ -146,6 +146,15 @@ def test_host_paths_match_device_paths():
     Hb = b.fields_host()
     for k in ("phi", "T", "p"):
         assert np.array_equal(Fa[k], Hb[k])
+    # float32 host buffers (pinned tensors): the same bits in and out
+    c = gpu_solver(w)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).pin_memory()
+    c.init_host(pin(w.phi0), pin(w.T0), p0=pin(w.p0), dtype=np.float32)
+    c.step(5)
+    out = {k: torch.empty(c.shape, dtype=torch.float32).pin_memory() for k in ("phi", "T", "ux", "uy", "p")}
+    Hc = c.fields_host(out=out)
+    for k in ("phi", "T", "p"):
+        assert np.array_equal(Fa[k], Hc[k].double().numpy())
 
 
 def test_mass_conservation_source_off_gpu():
