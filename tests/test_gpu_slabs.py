@@ -31,7 +31,16 @@ CASES = [
     ("2d_droplet_periodic_4slabs", lambda: W.droplet_2d(64, 12.0, T_offset=0.05), "fp32", 4),
     ("3d_fp32_2slabs", lambda: W.film_boiling_3d(64, 20, 30, modes=1, z0=10.0, phi_wall=(1.0, 0.0)), "fp32", 2),
     ("3d_fp16_3slabs", lambda: W.film_boiling_3d(48, 12, 26, modes=1, z0=8.0, phi_wall=(1.0, 0.0)), "fp16", 3),
+    ("3d_mrt_biased_2slabs", lambda: _film3d_opts(collision="mrt", mrt_rates=(1.4, 1.4, 1.2),
+                                                  mrt_rates_g=(1.3, 0.0, 0.0, 1.25), grad_scheme="biased2"),
+     "fp32", 2),
 ]
+
+
+def _film3d_opts(**extra):
+    w = W.film_boiling_3d(64, 16, 24, modes=1, z0=8.0, phi_wall=(1.0, 0.0))
+    w.params.update(**extra)
+    return w
 
 
 @pytest.mark.parametrize("name,make,storage,nslabs", CASES, ids=[c[0] for c in CASES])
