@@ -215,52 +215,72 @@ __device__ __forceinline__ long long bwin_cell(int cx, int cy, int cz, const Dev
 // i * PLANEB + k, its lagged source in word 7 PLANEB + k
 constexpr int BWIN_WORDS = (QG + 1) * PLANEB;
 
-// issue the copies of window plane p for the slots this thread handles (one
-// commit group); a 16-bit value comes as the aligned 32-bit word holding it
+// The window's slots go in pairs of x-adjacent cells: SXB = 36 is even and
+// the pairs start at column x0 - 2, even on a grid of even n_x (the biased
+// TMA path runs on n_x a multiple of 32).  The two cells of a pair are both
+// grid cells, cc and cc + 1 (x wrapped by a whole period on a periodic
+// axis), or both beyond the same wall.  cc is even and so is N, so a pair's
+// values of one g plane fill one aligned 8-byte (FP32) or 4-byte (16-bit,
+// low half = cell cc) word, and one cp.async fetches both.
+constexpr int BWIN_PAIRS = PLANEB / 2;
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// issue the copies of window plane p for the slot pairs this thread
+// handles (one commit group): pair k (slots 2k, 2k + 1) has its plane-i word
+// at buf[i * PLANEB + 2k] (FP32: and 2k + 1), its lagged sources at
+// buf[7 PLANEB + 2k], + 1
 template <typename S>
 __device__ __forceinline__ void bwin_prefetch(uint32_t *buf, const S *__restrict__ pin,
                                               const float *__restrict__ q_in, int p, int x0, int y0,
                                               int tid, const DevParams &P) {
     const size_t N = (size_t)P.N;
-    for (int sidx = tid; sidx < PLANEB; sidx += TX * TY) {
+    for (int k = tid; k < BWIN_PAIRS; k += TX * TY) {
+        const int sidx = 2 * k;
         float wv;
         const long long cc = bwin_cell(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, P, wv);
-        if (cc < 0 || !in_bounds(cc, (long long)N, P)) continue;
+        if (cc < 0 || !in_bounds(cc + 1, (long long)N, P)) continue;
+        const S *g0 = pin + off_g(QF, 0, (size_t)cc, N);
 #pragma unroll
         for (int i = 0; i < QG; ++i) {
-            const size_t e = off_g(QF, i, (size_t)cc, N);
-            cp_async4(&buf[i * PLANEB + sidx], pin + (IsNarrow<S>::value ? (e & ~(size_t)1) : e));
+            if (IsNarrow<S>::value) cp_async4(&buf[i * PLANEB + sidx], g0 + (size_t)i * N);
+            else cp_async8(&buf[i * PLANEB + sidx], g0 + (size_t)i * N);
         }
-        cp_async4(&buf[QG * PLANEB + sidx], q_in + cc);
+        cp_async8(&buf[QG * PLANEB + sidx], q_in + cc);
     }
     cp_async_commit();
 }
 
-// phi - phi_ref of window plane p's slots handled by this thread, from the
-// words it fetched (same arithmetic as phid_at)
+// phi - phi_ref of window plane p's slot pairs handled by this thread, from
+// the words it fetched (same arithmetic as phid_at)
 template <typename S>
 __device__ __forceinline__ void bwin_store(float *pl, const uint32_t *buf, int p, int x0, int y0, int tid,
                                            const DevParams &P) {
-    const size_t N = (size_t)P.N;
-    for (int sidx = tid; sidx < PLANEB; sidx += TX * TY) {
+    for (int k = tid; k < BWIN_PAIRS; k += TX * TY) {
+        const int sidx = 2 * k;
         float wv;
         const long long cc = bwin_cell(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, P, wv);
-        if (cc < 0) { pl[sidx] = wv; continue; }
-        float v[QG];
+        if (cc < 0) { pl[sidx] = wv; pl[sidx + 1] = wv; continue; }
+        float va[QG], vb[QG];
 #pragma unroll
         for (int i = 0; i < QG; ++i) {
             const uint32_t w = buf[i * PLANEB + sidx];
             if (IsNarrow<S>::value) {
-                const size_t e = off_g(QF, i, (size_t)cc, N);
-                const unsigned short h = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
-                S val;
-                memcpy(&val, &h, 2);
-                v[i] = widen(val);
+                const unsigned short lo = (unsigned short)(w & 0xffffu), hi = (unsigned short)(w >> 16);
+                S a, b;
+                memcpy(&a, &lo, 2);
+                memcpy(&b, &hi, 2);
+                va[i] = widen(a);
+                vb[i] = widen(b);
             } else {
-                v[i] = __uint_as_float(w);
+                va[i] = __uint_as_float(w);
+                vb[i] = __uint_as_float(buf[i * PLANEB + sidx + 1]);
             }
         }
-        pl[sidx] = fmaf(0.5f, __uint_as_float(buf[QG * PLANEB + sidx]), set_sum7<S>(v, P.set_isc[1]));
+        pl[sidx] = fmaf(0.5f, __uint_as_float(buf[QG * PLANEB + sidx]), set_sum7<S>(va, P.set_isc[1]));
+        pl[sidx + 1] = fmaf(0.5f, __uint_as_float(buf[QG * PLANEB + sidx + 1]), set_sum7<S>(vb, P.set_isc[1]));
     }
 }
 
@@ -460,7 +480,7 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     __shared__ __align__(8) uint64_t barF[Tma3Geom<S>::NFS], barG[Tma3Geom<S>::NG];
     // the biased gradient: a five-plane two-ring window, two fetched planes
     __shared__ float sphi[BIASED ? NWB * PLANEB : NW3 * PLANE];
-    __shared__ uint32_t rbuf[BIASED ? 2 * BWIN_WORDS : 2 * RING_WORDS];
+    __shared__ __align__(16) uint32_t rbuf[BIASED ? 2 * BWIN_WORDS : 2 * RING_WORDS];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     if (x0 + TX > P.n[0] || y0 + TY > P.n[1]) {          // ragged tile: plain loads
         if (BIASED) {
