@@ -211,76 +211,91 @@ __device__ __forceinline__ long long bwin_cell(int cx, int cy, int cz, const Dev
     return ((long long)cz * ny + cy) * nx + cx;
 }
 
-// words of one fetched window plane: slot k's 7 g values in words
-// i * PLANEB + k, its lagged source in word 7 PLANEB + k
-constexpr int BWIN_WORDS = (QG + 1) * PLANEB;
-
-// The window's slots go in pairs of x-adjacent cells: SXB = 36 is even and
-// the pairs start at column x0 - 2, even on a grid of even n_x (the biased
-// TMA path runs on n_x a multiple of 32).  The two cells of a pair are both
-// grid cells, cc and cc + 1 (x wrapped by a whole period on a periodic
-// axis), or both beyond the same wall.  cc is even and so is N, so a pair's
-// values of one g plane fill one aligned 8-byte (FP32) or 4-byte (16-bit,
-// low half = cell cc) word, and one cp.async fetches both.
-constexpr int BWIN_PAIRS = PLANEB / 2;
+// The window plane is fetched in quads of x-adjacent cells, columns x0 - 4
+// .. x0 + 35 (ten quads a row, eight rows; the window's 36 columns are
+// x0 - 2 .. x0 + 33): x0 is a multiple of 32 and the biased TMA path runs on
+// n_x a multiple of 32, so the four cells of a quad are grid cells cc .. cc
+// + 3 with cc a multiple of 4 (x wrapped by a whole period on a periodic
+// axis), or all beyond the same wall.  N is a multiple of 4 too, so a quad's
+// values of one g plane fill one aligned 16-byte (FP32) or 8-byte (16-bit)
+// block and one cp.async fetches them.
+constexpr int BWQ_COLS = 40, BWQ_QUADS = BWQ_COLS / 4 * SYB;        // 80 quads a plane
+// words of one fetched plane: FP32 plane i in [i * BWQ_W, +BWQ_W), the
+// lagged source after the 7 g planes; 16-bit: g quads take 2 words
+constexpr int BWQ_W = BWQ_COLS * SYB;                                // 320
+constexpr int BWIN_WORDS = (QG + 1) * BWQ_W;
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 
-// issue the copies of window plane p for the slot pairs this thread
-// handles (one commit group): pair k (slots 2k, 2k + 1) has its plane-i word
-// at buf[i * PLANEB + 2k] (FP32: and 2k + 1), its lagged sources at
-// buf[7 PLANEB + 2k], + 1
+// word offset of quad q's plane-i block in a fetched plane (the 16-bit g
+// planes pack a quad into 2 words)
+template <typename S>
+__device__ __forceinline__ int bwq_off(int i, int q) {
+    return IsNarrow<S>::value && i < QG ? i * BWQ_W + 2 * q : i * BWQ_W + 4 * q;
+}
+
+// issue the copies of window plane p for the quads this thread handles (one
+// commit group): quad q = row * 10 + k covers columns x0 - 4 + 4k .. + 3 of
+// window row `row` (y0 - 2 + row)
 template <typename S>
 __device__ __forceinline__ void bwin_prefetch(uint32_t *buf, const S *__restrict__ pin,
                                               const float *__restrict__ q_in, int p, int x0, int y0,
                                               int tid, const DevParams &P) {
     const size_t N = (size_t)P.N;
-    for (int k = tid; k < BWIN_PAIRS; k += TX * TY) {
-        const int sidx = 2 * k;
+    for (int q = tid; q < BWQ_QUADS; q += TX * TY) {
         float wv;
-        const long long cc = bwin_cell(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, P, wv);
-        if (cc < 0 || !in_bounds(cc + 1, (long long)N, P)) continue;
+        const long long cc = bwin_cell(x0 - 4 + 4 * (q % 10), y0 + q / 10 - 2, p, P, wv);
+        if (cc < 0 || !in_bounds(cc + 3, (long long)N, P)) continue;
         const S *g0 = pin + off_g(QF, 0, (size_t)cc, N);
 #pragma unroll
         for (int i = 0; i < QG; ++i) {
-            if (IsNarrow<S>::value) cp_async4(&buf[i * PLANEB + sidx], g0 + (size_t)i * N);
-            else cp_async8(&buf[i * PLANEB + sidx], g0 + (size_t)i * N);
+            if (IsNarrow<S>::value) cp_async8(&buf[bwq_off<S>(i, q)], g0 + (size_t)i * N);
+            else cp_async16(&buf[bwq_off<S>(i, q)], g0 + (size_t)i * N);
         }
-        cp_async8(&buf[QG * PLANEB + sidx], q_in + cc);
+        cp_async16(&buf[bwq_off<S>(QG, q)], q_in + cc);
     }
     cp_async_commit();
 }
 
-// phi - phi_ref of window plane p's slot pairs handled by this thread, from
-// the words it fetched (same arithmetic as phid_at)
+// phi - phi_ref of the window slots of the quads this thread fetched (same
+// arithmetic as phid_at); a quad's cells are window columns 4k - 2 .. 4k + 1
 template <typename S>
 __device__ __forceinline__ void bwin_store(float *pl, const uint32_t *buf, int p, int x0, int y0, int tid,
                                            const DevParams &P) {
-    for (int k = tid; k < BWIN_PAIRS; k += TX * TY) {
-        const int sidx = 2 * k;
+    for (int q = tid; q < BWQ_QUADS; q += TX * TY) {
+        const int k = q % 10, row = q / 10;
         float wv;
-        const long long cc = bwin_cell(x0 + sidx % SXB - 2, y0 + sidx / SXB - 2, p, P, wv);
-        if (cc < 0) { pl[sidx] = wv; pl[sidx + 1] = wv; continue; }
-        float va[QG], vb[QG];
+        const long long cc = bwin_cell(x0 - 4 + 4 * k, y0 + row - 2, p, P, wv);
 #pragma unroll
-        for (int i = 0; i < QG; ++i) {
-            const uint32_t w = buf[i * PLANEB + sidx];
-            if (IsNarrow<S>::value) {
-                const unsigned short lo = (unsigned short)(w & 0xffffu), hi = (unsigned short)(w >> 16);
-                S a, b;
-                memcpy(&a, &lo, 2);
-                memcpy(&b, &hi, 2);
-                va[i] = widen(a);
-                vb[i] = widen(b);
+        for (int j = 0; j < 4; ++j) {
+            const int sx = 4 * k - 2 + j;
+            if (sx < 0 || sx >= SXB) continue;
+            float v;
+            if (cc < 0) {
+                v = wv;
             } else {
-                va[i] = __uint_as_float(w);
-                vb[i] = __uint_as_float(buf[i * PLANEB + sidx + 1]);
+                float g[QG];
+#pragma unroll
+                for (int i = 0; i < QG; ++i) {
+                    if (IsNarrow<S>::value) {
+                        const uint32_t w = buf[bwq_off<S>(i, q) + (j >> 1)];
+                        const unsigned short h = (unsigned short)((j & 1) ? (w >> 16) : (w & 0xffffu));
+                        S val;
+                        memcpy(&val, &h, 2);
+                        g[i] = widen(val);
+                    } else {
+                        g[i] = __uint_as_float(buf[bwq_off<S>(i, q) + j]);
+                    }
+                }
+                v = fmaf(0.5f, __uint_as_float(buf[bwq_off<S>(QG, q) + j]), set_sum7<S>(g, P.set_isc[1]));
             }
+            pl[row * SXB + sx] = v;
         }
-        pl[sidx] = fmaf(0.5f, __uint_as_float(buf[QG * PLANEB + sidx]), set_sum7<S>(va, P.set_isc[1]));
-        pl[sidx + 1] = fmaf(0.5f, __uint_as_float(buf[QG * PLANEB + sidx + 1]), set_sum7<S>(vb, P.set_isc[1]));
     }
 }
 
