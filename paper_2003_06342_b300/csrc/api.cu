@@ -142,7 +142,7 @@ bool tma3_gradient_ok(const lbm_handle *h) {
 
 // What AUTO selects in 3D: the TMA kernel, except with the biased gradient
 // and FP32 storage, where the tiled kernel measured faster on 256 x 256 x 512
-// (13.3k against 11.3k MLUPS; FP16: TMA 17.3k against tiled 15.4k).
+// (13.3k against 12.9k MLUPS; FP16: TMA 20.6k against tiled 15.4k).
 bool tma3_auto(const lbm_handle *h) {
     if (!tma3_gradient_ok(h)) return false;
     return h->params.grad_scheme == LBM_GRAD_CENTRAL || h->params.storage != LBM_STORE_FP32;
