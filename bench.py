@@ -369,16 +369,17 @@ def run_device(args, world, rank, local):
             del v
         # the second-order biased gradient option (two-ring phi window)
         wb = dict(w.params, grad_scheme="biased2")
-        v = Solver(w.n, w.periodic, wb, storage="fp32", device=dev, stream=stream)
-        v.init(w.phi0, w.T0, p0=w.p0)
-        v.step(20)
-        ms_v = step_kernel_ms(v, 500)
-        m_v = safe_reduce(v)
-        rk = ("2d", "fp32")
-        variants["2d_fp32_biased"] = {
-            "workload": w.name + ", biased gradient", "MLUPS": w.cells / ms_v / 1e3, "ms_per_step": ms_v,
-            **roof(rk, w.cells, ms_v, peak), "finite": bool(np.isfinite(m_v))}
-        del v
+        for storage in ("fp32", "fp16"):
+            v = Solver(w.n, w.periodic, wb, storage=storage, device=dev, stream=stream)
+            v.init(w.phi0, w.T0, p0=w.p0)
+            v.step(20)
+            ms_v = step_kernel_ms(v, 500)
+            m_v = safe_reduce(v)
+            rk = ("2d", storage)
+            variants[f"2d_{storage}_biased"] = {
+                "workload": w.name + ", biased gradient", "MLUPS": w.cells / ms_v / 1e3,
+                "ms_per_step": ms_v, **roof(rk, w.cells, ms_v, peak), "finite": bool(np.isfinite(m_v))}
+            del v
         w3 = W.c3_film_boiling_3d()
         w3.name += " (density ratio 10)"
         best16 = ("tiled", 0.0)
