@@ -3,7 +3,7 @@
 // The conservative Allen-Cahn scheme of Sec. 3.2 on the D3Q7 lattice of the
 // coupled 3D model (cs^2 = 1/4), without phase change (q = 0) and with the
 // velocity u(x) c(n) prescribed -- the CAC validations of Sec. 4.1 run on
-// thin 3D domains.  Each block marches a 32x4 column tile through ZB layers
+// thin 3D domains.  Each block marches a 32x8 column tile through ZB layers
 // with a rolling phi window (four plane slots, one barrier per layer): before
 // layer z is updated, plane z+1 is formed.  On tiles that need no wall test
 // the loads run a layer ahead: while layer z is updated, the own cells' g of
@@ -34,11 +34,16 @@ namespace {
 // thread reads back only the ring words it fetched itself).
 constexpr int CW = 4;
 
+// Column tile of this kernel: 32 x CTY cells (the coupled kernels use 32 x 4).
+// The per-cell update is short, so the halo ring (84 cells for 256 owners
+// here, 76 for 128 at a height of 4) is a large share of the work.
+constexpr int CTY = 8, CSY = CTY + 2, CPLANE = SX * CSY, CTHREADS = TX * CTY;
+
 // Halo ring of the phi window (one cell per thread r < CRING), fetched a
 // layer ahead with 4-byte cp.async copies into shared memory: the 7 g values
 // of ring cell r in words buf[i * CRING + r].  A 16-bit value is fetched as
 // the aligned 32-bit word that holds it (the workspace is 256-byte aligned).
-constexpr int CRING = 2 * SX + 2 * TY;
+constexpr int CRING = 2 * SX + 2 * CTY;
 constexpr int CRING_WORDS = QG * CRING;
 
 __device__ __forceinline__ void cac_cp_async4(void *dst, const void *src) {
@@ -50,9 +55,9 @@ __device__ __forceinline__ size_t cac_ring_cell(int r, int z, int x0, int y0, co
     const int nx = P.n[0], ny = P.n[1];
     int sx, sy;
     if (r < SX) { sx = r; sy = 0; }
-    else if (r < 2 * SX) { sx = r - SX; sy = SY - 1; }
-    else if (r < 2 * SX + TY) { sx = 0; sy = 1 + r - 2 * SX; }
-    else { sx = SX - 1; sy = 1 + r - 2 * SX - TY; }
+    else if (r < 2 * SX) { sx = r - SX; sy = CSY - 1; }
+    else if (r < 2 * SX + CTY) { sx = 0; sy = 1 + r - 2 * SX; }
+    else { sx = SX - 1; sy = 1 + r - 2 * SX - CTY; }
     slot = sy * SX + sx;
     int cx = x0 + sx - 1, cy = y0 + sy - 1;
     if (XY == XY_WRAP) {
@@ -110,6 +115,21 @@ __device__ __forceinline__ void cac_ring_store(float *plane, const uint32_t *buf
     plane[slot] = set_sum7<S>(v, P.set_isc[1]);
 }
 
+// Fast-path push of direction i's g value (tile class MODE = XY_IN or
+// XY_WRAP): the x / y link as in the coupled kernel, and the z link moved by
+// zup (ez = +1) or zdn (ez = -1) cells, +-N on the last / first layer of a
+// periodic z axis and 0 elsewhere (N < 2^31, so the offsets fit an int).
+template <typename S, int MODE>
+__device__ __forceinline__ void cac_push_g(int i, float v, int x, int y, size_t c, int zup, int zdn,
+                                           const DevParams &P, const Planes3d<S> &PL) {
+    const int ex = LG::ex(i), ey = LG::ey(i), ez = LG::ez(i);
+    int off = push_off3(ex, ey, ez, x, y, MODE == XY_WRAP, P);
+    if (ez > 0) off += zup;
+    if (ez < 0) off += zdn;
+    if (!in_bounds((long long)c + off, (long long)P.N, P)) return;
+    PL.out[G0 + i][(cidx)c + (cidx)off] = narrow<S>(v);
+}
+
 }  // namespace
 
 // update of one cell of layer z from the phi window (planes z-1, z, z+1 in
@@ -117,13 +137,13 @@ __device__ __forceinline__ void cac_ring_store(float *plane, const uint32_t *buf
 template <typename S, int MODE>
 __device__ __forceinline__ void cac3d_cell(const float *sphi, int z, int x, int y, size_t c,
                                            const float g[QG], const float *__restrict__ vel, float factor,
-                                           const float uin[3], bool have_u, S *__restrict__ pout,
-                                           const DevParams &P, const Planes3d<S> &PL) {
+                                           const float uin[3], bool have_u, int zup, int zdn,
+                                           S *__restrict__ pout, const DevParams &P, const Planes3d<S> &PL) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const size_t N = (size_t)P.N;
     const int centre = (ty + 1) * SX + tx + 1;
-    const float *pl[3] = {sphi + (z % CW) * PLANE + centre, sphi + ((z + 1) % CW) * PLANE + centre,
-                          sphi + ((z + 2) % CW) * PLANE + centre};
+    const float *pl[3] = {sphi + (z % CW) * CPLANE + centre, sphi + ((z + 1) % CW) * CPLANE + centre,
+                          sphi + ((z + 2) % CW) * CPLANE + centre};
     const float phd = pl[1][0];
     const float ph = phd + P.g_ref;
     float gx = 0.0f, gy = 0.0f, gz = 0.0f;
@@ -152,13 +172,17 @@ __device__ __forceinline__ void cac3d_cell(const float *sphi, int z, int x, int 
     const float Vg[3] = {fmaf(4.0f * Bg, u[0], bgi * n[0]), fmaf(4.0f * Bg, u[1], bgi * n[1]),
                          fmaf(4.0f * Bg, u[2], bgi * n[2])};
     const float usq2 = 2.0f * usq;
-    push3d_g<S, MODE>(0, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)), x, y, z, c, pout, P, PL);
+    auto push = [&](int i, float v) {
+        if (MODE == XY_GEN) push3d_g<S, MODE>(i, v, x, y, z, c, pout, P, PL);
+        else cac_push_g<S, MODE>(i, v, x, y, c, zup, zdn, P, PL);
+    };
+    push(0, fmaf(a_g, g[0], rep_mul3<S, LG>(0) * fmaf(Bg, -usq2, Ag)));
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float Eg = fmaf(Bg, fmaf(8.0f * u[a], u[a], -usq2), Ag);
         const float mg = rep_mul3<S, LG>(a + 1);
-        push3d_g<S, MODE>(a + 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])), x, y, z, c, pout, P, PL);
-        push3d_g<S, MODE>(a + 4, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])), x, y, z, c, pout, P, PL);
+        push(a + 1, fmaf(a_g, g[a + 1], mg * (Eg + Vg[a])));
+        push(a + 4, fmaf(a_g, g[a + 4], mg * (Eg - Vg[a])));
     }
 }
 
@@ -169,7 +193,7 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
                                              uint32_t (*rbuf)[CRING_WORDS], const Planes3d<S> &PL) {
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * CTY;
     const int zbeg = blockIdx.z * ZB;
     const int zend = min(zbeg + ZB, nz);
     const int x = x0 + tx, y = y0 + ty;
@@ -194,8 +218,8 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
             ph = PRE ? set_sum7<S>(g, isc) : fmaf(0.5f, q_zero[c], set_sum7<S>(g, isc));
             if (PRE) for (int a = 0; a < 3; ++a) u[a] = vel[a * N + c];
         }
-        fill_plane<S, XY>(sphi, (zbeg + 1) % CW, zbeg, true, col, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
-        fill_plane<S, XY_GEN>(sphi, zbeg % CW, zbeg - 1, false, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
+        fill_plane<S, XY, CTY>(sphi, (zbeg + 1) % CW, zbeg, true, col, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
+        fill_plane<S, XY_GEN, CTY>(sphi, zbeg % CW, zbeg - 1, false, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
         if (PRE && zbeg + 1 < nz) {
             const size_t c = (size_t)(zbeg + 1) * plane_cells + cxy;
 #pragma unroll
@@ -220,7 +244,7 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
             }
             // plane z + 1 (in range: its own values and ring arrived a layer ago)
             if (z + 1 < nz) {
-                float *plane = sphi + ((z + 2) % CW) * PLANE;
+                float *plane = sphi + ((z + 2) % CW) * CPLANE;
                 float v[QG];
 #pragma unroll
                 for (int i = 0; i < QG; ++i) v[i] = widen(gn[i]);
@@ -229,7 +253,7 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
                 else asm volatile("cp.async.wait_group 0;" ::: "memory");
                 cac_ring_store<S, XY>(plane, rbuf[(z + 1) & 1], z + 1, x0, y0, tid, P);
             } else {
-                fill_plane<S, XY>(sphi, (z + 2) % CW, z + 1, true, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
+                fill_plane<S, XY, CTY>(sphi, (z + 2) % CW, z + 1, true, false, 0.0f, pin, q_zero, x0, y0, tid, tx, ty, P);
             }
         } else {
             float ph = 0.0f;
@@ -241,15 +265,19 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
                 for (int i = 0; i < QG; ++i) { gn[i] = __ldg(PL.in[G0 + i] + c); v[i] = widen(gn[i]); }
                 ph = fmaf(0.5f, q_zero[c], set_sum7<S>(v, isc));
             }
-            fill_plane<S, XY>(sphi, (z + 2) % CW, z + 1, true, ok, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
+            fill_plane<S, XY, CTY>(sphi, (z + 2) % CW, z + 1, true, ok, ph, pin, q_zero, x0, y0, tid, tx, ty, P);
         }
         __syncthreads();
         if (col) {
             const size_t c = (size_t)z * plane_cells + cxy;
-            if (XY != XY_GEN && z >= 1 && z + 1 < nz)
-                cac3d_cell<S, XY>(sphi, z, x, y, c, g, vel, factor, u, PRE, pout, P, PL);
-            else
-                cac3d_cell<S, XY_GEN>(sphi, z, x, y, c, g, vel, factor, u, PRE, pout, P, PL);
+            // the first and last layers of a periodic z axis take the fast
+            // push too, with the z link wrapped; beside a z wall the generic one
+            if (XY != XY_GEN && ((z >= 1 && z + 1 < nz) || P.periodic[2])) {
+                const int zup = z + 1 == nz ? -(int)N : 0, zdn = z == 0 ? (int)N : 0;
+                cac3d_cell<S, XY>(sphi, z, x, y, c, g, vel, factor, u, PRE, zup, zdn, pout, P, PL);
+            } else {
+                cac3d_cell<S, XY_GEN>(sphi, z, x, y, c, g, vel, factor, u, PRE, 0, 0, pout, P, PL);
+            }
         }
 #pragma unroll
         for (int i = 0; i < QG; ++i) { g[i] = widen(gn[i]); if (PRE) gn[i] = gnn[i]; }
@@ -259,14 +287,14 @@ __device__ __forceinline__ void cac3d_column(const S *__restrict__ pin, S *__res
 }
 
 template <typename S>
-__global__ void __launch_bounds__(TX * TY, 8)
+__global__ void __launch_bounds__(CTHREADS, 4)
 cac3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, const float *__restrict__ q_zero,
              const float *__restrict__ vel, float factor, const DevParams P,
              const __grid_constant__ Planes3d<S> PL) {
-    __shared__ float sphi[CW * PLANE];
+    __shared__ float sphi[CW * CPLANE];
     __shared__ uint32_t rbuf[2][CRING_WORDS];
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int cls = tile_class3d(x0, y0, P);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * CTY;
+    const int cls = tile_class3d<CTY>(x0, y0, P);
     if (cls == XY_IN) cac3d_column<S, XY_IN>(pin, pout, q_zero, vel, factor, P, sphi, rbuf, PL);
     else if (cls == XY_WRAP) cac3d_column<S, XY_WRAP>(pin, pout, q_zero, vel, factor, P, sphi, rbuf, PL);
     else cac3d_column<S, XY_GEN>(pin, pout, q_zero, vel, factor, P, sphi, rbuf, PL);
@@ -275,8 +303,8 @@ cac3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, const float *__res
 template <typename S>
 cudaError_t launch_cac3d(const void *pin, void *pout, const float *q_zero, const float *vel, float factor,
                          const DevParams &P, cudaStream_t st) {
-    dim3 block(TX, TY);
-    dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, (P.n[2] + ZB - 1) / ZB);
+    dim3 block(TX, CTY);
+    dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + CTY - 1) / CTY, (P.n[2] + ZB - 1) / ZB);
     cac3d_kernel<S><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, q_zero, vel, factor, P,
                                             planes3d<S>(pin, pout, P));
     return cudaGetLastError();

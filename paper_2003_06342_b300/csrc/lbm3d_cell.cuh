@@ -215,17 +215,18 @@ __device__ __forceinline__ float phi_at(const S *__restrict__ pin, const float *
     return phid_at<S>(pin, q_in, cc, N, P) + P.g_ref;
 }
 
-// Classes of a 32x4 column tile.  XY_IN: the tile and its halo ring lie
+// Classes of a 32 x TYv column tile (TYv = 4 unless a kernel picks another).  XY_IN: the tile and its halo ring lie
 // inside the grid in x and y.  XY_WRAP: the tile lies inside the grid and its
 // ring crosses only periodic x / y boundaries (so every x / y link of its
 // cells lands on a grid cell after the periodic wrap).  XY_GEN: anything
 // else (a ragged tile, or a wall next to the tile), handled generically.
 constexpr int XY_GEN = 0, XY_IN = 1, XY_WRAP = 2;
 
+template <int TYv = TY>
 __device__ __forceinline__ int tile_class3d(int x0, int y0, const DevParams &P) {
     const int nx = P.n[0], ny = P.n[1];
-    if (x0 + TX > nx || y0 + TY > ny) return XY_GEN;
-    const bool xin = x0 >= 1 && x0 + TX + 1 <= nx, yin = y0 >= 1 && y0 + TY + 1 <= ny;
+    if (x0 + TX > nx || y0 + TYv > ny) return XY_GEN;
+    const bool xin = x0 >= 1 && x0 + TX + 1 <= nx, yin = y0 >= 1 && y0 + TYv + 1 <= ny;
     if (xin && yin) return XY_IN;
     if ((xin || P.periodic[0]) && (yin || P.periodic[1])) return XY_WRAP;
     return XY_GEN;
@@ -237,24 +238,25 @@ __device__ __forceinline__ int tile_class3d(int x0, int y0, const DevParams &P) 
 // other slot is computed here: phi of the wrapped cell, or the wall's
 // Dirichlet value beyond a wall.  XY (a tile class): for XY_IN / XY_WRAP an
 // in-range plane needs no wall test, one thread per ring cell.
-template <typename S, int XY>
+template <typename S, int XY, int TYv = TY>
 __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool owners_write,
                                            bool own_ok, float own_phi, const S *__restrict__ pin,
                                            const float *__restrict__ q_in, int x0, int y0, int tid,
                                            int tx, int ty, const DevParams &P) {
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const size_t N = (size_t)P.N;
-    float *plane = sphi + slot * PLANE;
+    constexpr int SYv = TYv + 2, PLANEv = SX * SYv;
+    float *plane = sphi + slot * PLANEv;
     const bool z_in = z >= 0 && z < nz;
     if (owners_write && own_ok) plane[(ty + 1) * SX + tx + 1] = own_phi;
     if (XY != XY_GEN && z_in && owners_write) {
-        constexpr int RING = 2 * SX + 2 * TY;
+        constexpr int RING = 2 * SX + 2 * TYv;
         if (tid < RING) {
             int sx, sy;
             if (tid < SX) { sx = tid; sy = 0; }
-            else if (tid < 2 * SX) { sx = tid - SX; sy = SY - 1; }
-            else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
-            else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
+            else if (tid < 2 * SX) { sx = tid - SX; sy = SYv - 1; }
+            else if (tid < 2 * SX + TYv) { sx = 0; sy = 1 + tid - 2 * SX; }
+            else { sx = SX - 1; sy = 1 + tid - 2 * SX - TYv; }
             int cx = x0 + sx - 1, cy = y0 + sy - 1;
             if (XY == XY_WRAP) {
                 cx = cx < 0 ? cx + nx : (cx >= nx ? cx - nx : cx);
@@ -265,10 +267,10 @@ __device__ __forceinline__ void fill_plane(float *sphi, int slot, int z, bool ow
         }
         return;
     }
-    for (int sidx = tid; sidx < PLANE; sidx += TX * TY) {
+    for (int sidx = tid; sidx < PLANEv; sidx += TX * TYv) {
         const int sx = sidx % SX, sy = sidx / SX;
         int cx = x0 + sx - 1, cy = y0 + sy - 1, cz = z;
-        const bool inner = sx >= 1 && sx <= TX && sy >= 1 && sy <= TY;
+        const bool inner = sx >= 1 && sx <= TX && sy >= 1 && sy <= TYv;
         if (owners_write && z_in && inner && cx < nx && cy < ny) continue;   // owner wrote it
         if (cx < -1 || cx > nx || cy < -1 || cy > ny || cz < -1 || cz > nz) { plane[sidx] = 0.0f; continue; }
         const int kx = wrap_coord(cx, nx, P.periodic[0]);

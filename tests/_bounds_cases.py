@@ -64,10 +64,14 @@ STEP_CASES = [
     ("3d_tma_mrt_biased_fp16", lambda: _opt(_film3d(64, 8, 70, 20.0), **MRT_G, **BIASED), "fp16", "tma", 6),
 ]
 
-# name, grid size, storage, velocity factor, reversal period, steps
+# name, grid size (n, or (nx, ny, nz) for a thin periodic 3D box), storage,
+# velocity factor, reversal period, steps
 CAC_CASES = [
     ("cac_fp32_ragged", 49, "fp32", 5.0, 30.0, 12),
     ("cac_fp16_ragged", 41, "fp16", 5.0, 0.0, 12),
+    # interior, wrapped and ragged 32x8 column tiles of the 3D kernel
+    ("cac3d_fp32_interior_ragged", (100, 45, 5), "fp32", 5.0, 30.0, 8),
+    ("cac3d_fp16_interior_ragged", (100, 45, 5), "fp16", 5.0, 0.0, 8),
 ]
 
 
@@ -86,6 +90,19 @@ def run_step_case(make, storage, kernel, steps):
 
 def run_cac_case(n, storage, speed, period, steps):
     from paper_2003_06342_b300 import Solver
+    if isinstance(n, tuple):
+        # the vortex disk of the x-y plane repeated along z, uz = 0
+        nx, ny, nz = n
+        w = W.vortex_disk(n=nx)
+        phi0 = np.repeat(w.phi0[None, :ny, :], nz, axis=0)
+        u = [np.repeat(uu[None, :ny, :] * speed, nz, axis=0) for uu in w.extra["u"]] + [np.zeros_like(phi0)]
+        s = Solver((nx, ny, nz), (True, True, True), w.params, storage=storage)
+        s.set_velocity(u, period)
+        s.init(phi0, np.ones_like(phi0))
+        s.step(steps)
+        st = s.get_state().cpu().numpy().copy()
+        s.sync()
+        return st
     w = W.vortex_disk(n=n)
     u = [uu * speed for uu in w.extra["u"]]
     s = Solver(w.n, w.periodic, w.params, storage=storage)

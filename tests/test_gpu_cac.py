@@ -158,6 +158,10 @@ def _sphere_in_rotation(nx, ny, nz, speed):
 CASES_3D = [
     ("vortex_thin_z", lambda: _extruded_vortex(41, 4, 5.0), 30.0, 30),
     ("sphere_walls_z", lambda: _sphere_in_rotation(37, 21, 18, 2e-3), 0.0, 30),
+    # wide enough for tiles whose halo ring lies inside the grid (the fast
+    # lookahead path), with ragged last tiles in x and y
+    ("vortex_thin_z_interior_tiles", lambda: _extruded_vortex(100, 3, 5.0), 30.0, 20),
+    ("sphere_walls_z_interior_tiles", lambda: _sphere_in_rotation(70, 27, 12, 2e-3), 0.0, 20),
 ]
 
 
