@@ -1,6 +1,6 @@
 """Parity at the full benchmark sizes, in the launch configuration bench.py
-times (2048 x 4096 2D film on the tiled kernel; 256 x 256 x 512 3D film on
-the TMA-staged kernel), on sampled cells.
+times (2048 x 4096 2D film on the tiled kernel; 256 x 256 x 512 and
+512 x 512 x 768 3D films on the TMA-staged kernel), on sampled cells.
 
 The oracle cannot step 8 M or 34 M cells in a test, but a cell's update over
 k steps depends only on the initial fields within a few cells of it (the push
@@ -127,3 +127,12 @@ def test_3d_256x256x512_tma_fp32_sampled():
 
 def test_3d_256x256x512_tma_fp16_sampled():
     _check(W.c3_film_boiling_3d(), "tma", 2, storage="fp16", tol=5e-3, seed=2)
+
+
+def test_3d_512x512x768_tma_fp16_sampled():
+    """The largest film (201 M cells, 36 GB of FP16 populations), in the
+    configuration the bench times it: TMA kernel, FP16 storage."""
+    w = W.c5_film_boiling_3d_large()
+    _check(w, "tma", 2, storage="fp16", tol=5e-3, seed=3)
+    del w
+    torch.cuda.empty_cache()
