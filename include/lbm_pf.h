@@ -359,16 +359,15 @@ int lbm_set_velocity(lbm_handle *h, const lbm_fields *u, double period);
  * memory for two doubles.  Queued on `stream` (a cudaStream_t, NULL = legacy
  * default stream).  The per-block partial sums use a 1 MiB array in static
  * device memory that every GPU loading the library holds until exit; hence
- * n_cells is limited to 16,777,216 and larger sizes return LBM_ENOMEM.  The
- * first call on a device looks up that array's device address (with the
- * device current) and caches it for the life of the process; make that first
- * call before any stream capture.  A device reset (cudaDeviceReset, or a
- * primary context released and created again) reloads the module and leaves
- * the cached address stale: do not call this entry point on a device after
- * resetting it.  All calls share the array: calls whose kernels overlap on
- * the GPU race and must be ordered by the caller.  Errors: LBM_EINVAL (NULL
- * pointer, n_cells < 1, non-positive density), LBM_ENOMEM, LBM_EUNSUPPORTED
- * (current device ordinal 64 or above), LBM_ECUDA. */
+ * n_cells is limited to 16,777,216 and larger sizes return LBM_ENOMEM.  Every
+ * call looks up that array's device address on the current device (no
+ * allocation), so the entry point stays valid after a device reset
+ * (cudaDeviceReset, or a primary context released and created again); the
+ * first call on a device may load the library's device code, so make it
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU race and must be ordered by the caller.  Errors:
+ * LBM_EINVAL (NULL pointer, n_cells < 1, non-positive density), LBM_ENOMEM,
+ * LBM_ECUDA. */
 int lbm_field_sums_noalloc(const float *phi, const float *T, int64_t n_cells, double rho_l,
                            double rho_g, double Cp, double L, double *d_out, void *stream);
 

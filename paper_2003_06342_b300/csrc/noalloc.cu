@@ -4,10 +4,10 @@
 // caller's workspace, live here in a file-scope device array instead, so
 // this entry point needs no workspace and allocates nothing.  Host code only
 // sees a host-side stand-in for that array under its name; the device
-// address is obtained once per device with cudaGetSymbolAddress (with that
-// device current) on the first call made on it, and cached.
+// address is looked up with cudaGetSymbolAddress (with the caller's device
+// current) on every call, so it stays right after a device reset or a
+// recreated primary context reloads the module.
 #include <cmath>
-#include <mutex>
 
 #include "../../include/lbm_pf.h"
 #include "lbm_kernels.h"
@@ -20,10 +20,6 @@ constexpr long long NA_MAX_CELLS = (long long)NA_MAX_BLOCKS * NA_THREADS;
 
 // two doubles per block: 1 MiB, held by every GPU that loads the library
 static __device__ __align__(256) double na_scratch[2 * NA_MAX_BLOCKS];
-
-constexpr int NA_MAX_DEVICES = 64;
-double *na_ptr[NA_MAX_DEVICES] = {nullptr};
-std::mutex na_mutex;
 
 // Same per-cell terms and the same 256-cell blocking as the moment kernels'
 // reduction: phi and rho(phi) (Cp T + phi L), rho on phi clipped to [0, 1].
@@ -43,16 +39,9 @@ field_sums_kernel(const float *__restrict__ phi, const float *__restrict__ T, lo
 }
 
 int device_scratch(double **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
-    if (dev < 0 || dev >= NA_MAX_DEVICES) return LBM_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lock(na_mutex);
-    if (!na_ptr[dev]) {
-        double *p = nullptr;
-        if (cudaGetSymbolAddress((void **)&p, na_scratch) != cudaSuccess || !p) return LBM_ECUDA;
-        na_ptr[dev] = p;
-    }
-    *out = na_ptr[dev];
+    double *p = nullptr;
+    if (cudaGetSymbolAddress((void **)&p, na_scratch) != cudaSuccess || !p) return LBM_ECUDA;
+    *out = p;
     return LBM_OK;
 }
 
