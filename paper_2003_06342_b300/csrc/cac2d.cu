@@ -28,8 +28,9 @@ __device__ __forceinline__ void cac_push2d(int i, float v, int x, int y, size_t 
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     if (FAST) {
-        const long long d = (long long)c + ((long long)ey * nx + ex);
-        if (in_bounds(d, (long long)N, P)) PL.out[9 + i][d] = narrow<S>(v);
+        // 32-bit cell offsets (fewer than 2^31 cells)
+        const int off = ey * nx + ex;
+        if (in_bounds((long long)c + off, (long long)N, P)) PL.out[9 + i][(cidx)c + (cidx)off] = narrow<S>(v);
         return;
     }
     int dx = x + ex, dy = y + ey;
@@ -76,7 +77,7 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
             else if (tid < 2 * SX + TY) { sx = 0; sy = 1 + tid - 2 * SX; }
             else { sx = SX - 1; sy = 1 + tid - 2 * SX - TY; }
             rslot = sy * SX + sx;
-            const size_t cc = (size_t)(y0 + sy - 1) * nx + (x0 + sx - 1);
+            const cidx cc = (cidx)((y0 + sy - 1) * nx + (x0 + sx - 1));
 #pragma unroll
             for (int i = 0; i < 9; ++i) rv[i] = load_raw(PL.in[9 + i] + cc);
             (void)in_bounds((long long)cc, (long long)N, P);
@@ -86,7 +87,7 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
     float g[9];
     if (active) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = load_raw(PL.in[9 + i] + c);
+        for (int i = 0; i < 9; ++i) g[i] = load_raw(PL.in[9 + i] + (cidx)c);
         sphi[(ty + 1) * SX + tx + 1] = set_sum2d<S>(g, isc);          // phi - phi_ref
     }
     if (!RING_FIRST) load_ring();
@@ -127,7 +128,7 @@ __device__ __forceinline__ void cac_tile2d(const S *__restrict__ pin, S *__restr
     const float inv_d = rsqrt_approx(fmaxf(fmaf(gx, gx, gy * gy), P.eps2));
     const float nx_ = gx * inv_d, ny_ = gy * inv_d;
     // imposed velocity
-    const float ux = vel[c] * factor, uy = vel[N + c] * factor;
+    const float ux = vel[(cidx)c] * factor, uy = (vel + N)[(cidx)c] * factor;
 
     const float om = P.om_g, a_g = 1.0f - om, b_g = fmaf(-0.5f, om, 1.0f);
     const float Ag = om * phd, Bg = om * ph;
