@@ -709,9 +709,10 @@ def ncu_case(case):
     from paper_2003_06342_b300 import Solver
     if case == "2d_adjoint":
         return ncu_case_adjoint()
-    if case == "2d_phase_field":
+    if case.startswith("2d_phase_field"):
+        # FP32 unless the case names 16-bit storage (2d_phase_field_fp16)
         wv = W.vortex_disk(n=4096)
-        s = Solver(wv.n, wv.periodic, wv.params)
+        s = Solver(wv.n, wv.periodic, wv.params, storage="fp16" if case.endswith("_fp16") else "fp32")
         s.set_velocity(wv.extra["u"], wv.extra["period"]).init(wv.phi0, wv.T0)
         s.step(4)
         torch.cuda.synchronize()
@@ -777,7 +778,7 @@ def main():
     ap.add_argument("--ncu-case", default=None,
                     choices=["2d_fp32", "2d_fp16", "2d_bf16", "3d_fp32", "3d_fp16",
                              "2d_fp32_tma", "2d_fp16_tma", "3d_fp32_tma", "3d_fp16_tma",
-                             "2d_adjoint", "2d_phase_field", "3d_phase_field_fp32",
+                             "2d_adjoint", "2d_phase_field", "2d_phase_field_fp16", "3d_phase_field_fp32",
                              "3d_phase_field_fp16"],
                     help="only initialise one kernel case and run 4 steps (for ncu captures)")
     args = ap.parse_args()
