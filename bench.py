@@ -43,24 +43,24 @@ BYTES_PER_CELL = {("2d", "fp32"): 27 * 4 * 2 + 16, ("2d", "fp16"): 27 * 2 * 2 + 
                   ("cac2d", "fp32"): 9 * 4 * 2 + 8, ("cac2d", "fp16"): 9 * 2 * 2 + 8,
                   # 3D: the 7 g planes each way and the imposed (ux, uy, uz)
                   ("cac3d", "fp32"): 7 * 4 * 2 + 12, ("cac3d", "fp16"): 7 * 2 * 2 + 12}
-# the hot-path survey's algorithmic bytes per cell and step (each population
-# read and written once plus 20 B of scalar state: phi written and read,
-# phi^{n-1} read, lagged source written and read); the rooflines are quoted on
-# these.  The kernels never store phi (each tile recomputes it from g), so
+# algorithmic bytes per cell and step with phi counted as a stored field
+# (each population read and written once plus 20 B of scalar state: phi
+# written and read, phi^{n-1} read, lagged source written and read); the
+# rooflines are quoted on these.  The kernels never store phi (each tile recomputes it from g), so
 # they move BYTES_PER_CELL, 4 B less; both fractions are reported.
-SURVEY_BYTES_PER_CELL = {("2d", "fp32"): 236, ("2d", "fp16"): 128, ("2d", "bf16"): 128,
-                         ("3d", "fp32"): 380, ("3d", "fp16"): 200, ("3d", "bf16"): 200}
+PHI_STORED_BYTES_PER_CELL = {("2d", "fp32"): 236, ("2d", "fp16"): 128, ("2d", "bf16"): 128,
+                             ("3d", "fp32"): 380, ("3d", "fp16"): 200, ("3d", "bf16"): 200}
 
 
 def roofline_bytes(kind, storage):
     """(bytes per cell the fraction is quoted on, the kernel's own minimum)."""
     own = BYTES_PER_CELL[(kind, storage)]
-    return SURVEY_BYTES_PER_CELL.get((kind, storage), own), own
+    return PHI_STORED_BYTES_PER_CELL.get((kind, storage), own), own
 
 
 def roof(rk, cells, ms, peak):
-    """Roofline fields of a variant: bytes and fraction on the survey's byte
-    count (the kernel's own count where the survey gives none), and on the
+    """Roofline fields of a variant: bytes and fraction on the count with phi
+    stored (the kernel's own count where there is none), and on the
     kernel's own minimum."""
     bpc, own = roofline_bytes(*rk)
     gbs = bpc * cells / ms / 1e6
@@ -556,10 +556,10 @@ def run_device(args, world, rank, local):
     return result
 
 
-# adjoint step, the survey's algorithmic bytes per cell: the primal state read
+# adjoint step, algorithmic bytes per cell: the primal state read
 # (120 B), the adjoint populations read and written (216 B) and 16 B of
 # adjoint scalars
-ADJ_SURVEY_BYTES_PER_CELL = 352
+ADJ_ALG_BYTES_PER_CELL = 352
 # what the two-kernel adjoint step moves: kernel A reads the state (29
 # planes) and the next adjoint state (30: 29 planes and the phi adjoint) and
 # writes the adjoint state's 29 planes and four stencil-contribution planes;
@@ -621,9 +621,9 @@ def adjoint_variant(dev, peak, steps=2000, K=100):
             "what": "forward with checkpoints + reverse with segment recomputation, per forward step",
             "J": J, "dJ_dL": g["L"], "dJ_dM_phi": g["M_phi"], "dJ_dsigma": g["sigma"],
             "dJ_dT0_norm": float(g["T0"].norm()),
-            "adjoint_step_ms": ms, "adjoint_step_bytes_per_cell": ADJ_SURVEY_BYTES_PER_CELL,
-            "adjoint_step_achieved_GBs": ADJ_SURVEY_BYTES_PER_CELL * w.cells / ms / 1e6,
-            "adjoint_step_frac": ADJ_SURVEY_BYTES_PER_CELL * w.cells / ms / 1e6 / peak,
+            "adjoint_step_ms": ms, "adjoint_step_bytes_per_cell": ADJ_ALG_BYTES_PER_CELL,
+            "adjoint_step_achieved_GBs": ADJ_ALG_BYTES_PER_CELL * w.cells / ms / 1e6,
+            "adjoint_step_frac": ADJ_ALG_BYTES_PER_CELL * w.cells / ms / 1e6 / peak,
             "adjoint_step_moved_bytes_per_cell": ADJ_BYTES_PER_CELL,
             "adjoint_step_frac_moved_bytes": ADJ_BYTES_PER_CELL * w.cells / ms / 1e6 / peak}
 
