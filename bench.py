@@ -514,10 +514,15 @@ def run_device(args, world, rank, local):
         red_dev = torch.zeros((2, 2), dtype=torch.float64, device=dev)
         red_host = torch.zeros((2, 2), dtype=torch.float64).pin_memory()
         red_ev = [torch.cuda.Event(), torch.cuda.Event()]
+        # device-side breakdown of the same region (events on the stream):
+        # fields in + initialisation, the steps with their sums, fields out
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        ev[0].record(stream)
         e.init_host(h_in[0], h_in[1], p0=h_in[2], dtype=np.float32)
+        ev[1].record(stream)
         done, d2h, nred, red_ok = 0, 0, 0, True
         while done < K:
             k = min(REDUCE_EVERY, K - done)
@@ -535,9 +540,11 @@ def run_device(args, world, rank, local):
                 red_ok = red_ok and bool(torch.isfinite(red_host[1 - slot]).all())
             nred += 1
             d2h += 16
+        ev[2].record(stream)
         red_ev[(nred - 1) % 2].synchronize()
         red_ok = red_ok and bool(torch.isfinite(red_host[(nred - 1) % 2]).all())
         F = e.fields_host(out=h_out)
+        ev[3].record(stream)
         torch.cuda.synchronize(dev)
         t_e2e = time.perf_counter() - t0
         barrier()
@@ -547,6 +554,9 @@ def run_device(args, world, rank, local):
         result["e2e"] = {"value": w.cells * K * world / t_e2e / 1e6, "unit": "MLUPS",
                          "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                          "wall_s": t_e2e, "host_buffers": "pinned float32",
+                         "device_ms": {"fields_in_and_init": ev[0].elapsed_time(ev[1]),
+                                       "steps_and_sums": ev[1].elapsed_time(ev[2]),
+                                       "fields_out": ev[2].elapsed_time(ev[3])},
                          "finite": bool(red_ok and torch.isfinite(F["phi"]).all())}
         del e
     if world > 1:
