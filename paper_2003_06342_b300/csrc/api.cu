@@ -124,7 +124,7 @@ Layout layout(const lbm_grid *g, int32_t lattice, const lbm_params *p) {
     L.phi = align_up(N * sizeof(float));
     L.q = align_up(N * sizeof(float));
     L.scratch = align_up(6 * N * sizeof(float));
-    L.red_blocks = (int)((N + 255) / 256);
+    L.red_blocks = moment_blocks((long long)N);
     L.partial = align_up((size_t)L.red_blocks * 2 * sizeof(double));
     L.red = align_up(2 * sizeof(double));
     L.err = align_up(sizeof(int));

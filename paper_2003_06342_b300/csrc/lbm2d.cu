@@ -130,9 +130,8 @@ macro2d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
                double *partial, double Cp, double Lh, const DevParams P) {
     const int nx = P.n[0];
     const size_t N = (size_t)P.N;
-    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     double mass = 0.0, energy = 0.0;
-    if (c < N) {
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)(c / nx);
         float nb[9], f[9], s[9];
         gather_nb2d(phi_f, x, y, nb, P);
@@ -151,8 +150,8 @@ macro2d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
         if (o_ux) o_ux[c] = m.ux;
         if (o_uy) o_uy[c] = m.uy;
         if (o_p) o_p[c] = m.p;
-        mass = (double)m.phi;
-        energy = (double)m.rho * (Cp * (double)m.T + (double)m.phi * Lh);
+        mass += (double)m.phi;
+        energy += (double)m.rho * (Cp * (double)m.T + (double)m.phi * Lh);
     }
     if (partial) block_sum2(mass, energy, partial);
 }
@@ -253,8 +252,8 @@ cudaError_t launch_macro2d(const void *pin, float *phi_tmp, const float *phi_pre
                            cudaStream_t st) {
     const int nb = (int)((P.N + 255) / 256);
     phi2d_kernel<S><<<nb, 256, 0, st>>>((const S *)pin, q_in, phi_tmp, P);
-    macro2d_kernel<S><<<nb, 256, 0, st>>>((const S *)pin, phi_tmp, phi_prev, q_in, o_phi, o_T,
-                                          o_ux, o_uy, o_p, partial, Cp, Lh, P);
+    macro2d_kernel<S><<<moment_blocks(P.N), 256, 0, st>>>((const S *)pin, phi_tmp, phi_prev, q_in, o_phi,
+                                                          o_T, o_ux, o_uy, o_p, partial, Cp, Lh, P);
     return cudaGetLastError();
 }
 

@@ -99,9 +99,8 @@ macro3d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
                double *partial, double Cp, double Lh, const DevParams P) {
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
-    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     double mass = 0.0, energy = 0.0;
-    if (c < N) {
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((size_t)nx * ny));
         float nb[QF], f[QF], s[QF];
         gather_nb3d(phi_f, x, y, z, nb, P);
@@ -121,8 +120,8 @@ macro3d_kernel(const S *__restrict__ pin, const float *__restrict__ phi_f,
         if (o_uy) o_uy[c] = m.u[1];
         if (o_uz) o_uz[c] = m.u[2];
         if (o_p) o_p[c] = m.p;
-        mass = (double)m.phi;
-        energy = (double)m.rho * (Cp * (double)m.T + (double)m.phi * Lh);
+        mass += (double)m.phi;
+        energy += (double)m.rho * (Cp * (double)m.T + (double)m.phi * Lh);
     }
     if (partial) block_sum2(mass, energy, partial);
 }
@@ -230,8 +229,9 @@ cudaError_t launch_macro3d(const void *pin, float *phi_tmp, const float *phi_pre
                            cudaStream_t st) {
     const int nb = (int)((P.N + 255) / 256);
     phi3d_kernel<S><<<nb, 256, 0, st>>>((const S *)pin, q_in, phi_tmp, P);
-    macro3d_kernel<S><<<nb, 256, 0, st>>>((const S *)pin, phi_tmp, phi_prev, q_in, o_phi, o_T,
-                                          o_u[0], o_u[1], o_u[2], o_p, partial, Cp, Lh, P);
+    macro3d_kernel<S><<<moment_blocks(P.N), 256, 0, st>>>((const S *)pin, phi_tmp, phi_prev, q_in, o_phi,
+                                                          o_T, o_u[0], o_u[1], o_u[2], o_p, partial, Cp,
+                                                          Lh, P);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,17 @@ namespace lbm {
 // per-warp sums) and store the pair at partial[2*blockIdx.x].  Every thread
 // of the block must call it.  The summation order is fixed, so results are
 // reproducible run to run.
+// Blocks of 256 threads of the moment kernels, which also form the FP64
+// mass and energy partial sums: one thread per cell up to two waves of 148 x
+// 4 blocks, then a grid-stride loop, so each thread adds several cells into
+// its FP64 accumulators before the (FP64) warp-shuffle block reduction.  B300
+// runs FP64 at a small fraction of its FP32 rate, and the block reduction's
+// shuffles and adds dominated a one-cell-per-thread sum.
+inline int moment_blocks(long long n_cells) {
+    const long long b = (n_cells + 255) / 256;
+    return (int)(b < 148 * 8 ? (b < 1 ? 1 : b) : 148 * 8);
+}
+
 __device__ __forceinline__ void block_sum2(double a, double b, double *partial) {
     __shared__ double sa[32], sb[32];
     const unsigned full = 0xffffffffu;

@@ -21,8 +21,10 @@ constexpr long long NA_MAX_CELLS = (long long)NA_MAX_BLOCKS * NA_THREADS;
 // two doubles per block: 1 MiB, held by every GPU that loads the library
 static __device__ __align__(256) double na_scratch[2 * NA_MAX_BLOCKS];
 
-// Same per-cell terms and the same 256-cell blocking as the moment kernels'
-// reduction: phi and rho(phi) (Cp T + phi L), rho on phi clipped to [0, 1].
+// Same per-cell terms as the moment kernels' reduction: phi and rho(phi)
+// (Cp T + phi L), rho on phi clipped to [0, 1]; one cell per thread (the
+// moment kernels add several cells per thread), so the FP64 sums agree with
+// lbm_reduce to rounding.
 __global__ void __launch_bounds__(NA_THREADS)
 field_sums_kernel(const float *__restrict__ phi, const float *__restrict__ T, long long n,
                   float rho_l, float rho_g, double Cp, double Lh, double *partial) {
