@@ -86,6 +86,13 @@ __global__ void phi2d_kernel(const S *__restrict__ pin, const float *__restrict_
 __device__ __forceinline__ void gather_nb2d(const float *__restrict__ phi, int x, int y, float nb[9],
                                             const DevParams &P) {
     const int nx = P.n[0], ny = P.n[1];
+    if (x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny) {
+        // no neighbour wraps or lies beyond a wall
+        const float *pc = phi + ((size_t)y * nx + x);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) nb[i] = pc[L::ey(i) * nx + L::ex(i)];
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         int cx = x + L::ex(i), cy = y + L::ey(i);

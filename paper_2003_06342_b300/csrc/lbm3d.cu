@@ -48,6 +48,14 @@ __global__ void phi3d_kernel(const S *__restrict__ pin, const float *__restrict_
 __device__ __forceinline__ void gather_nb3d(const float *__restrict__ phi, int x, int y, int z,
                                             float nb[QF], const DevParams &P) {
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    if (x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny && z >= 1 && z + 1 < nz) {
+        // no neighbour wraps or lies beyond a wall
+        const float *pc = phi + (((size_t)z * ny + y) * nx + x);
+        const long long plane = (long long)nx * ny;
+#pragma unroll
+        for (int i = 0; i < QF; ++i) nb[i] = pc[LF::ez(i) * plane + LF::ey(i) * nx + LF::ex(i)];
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < QF; ++i) {
         int cx = x + LF::ex(i), cy = y + LF::ey(i), cz = z + LF::ez(i);
