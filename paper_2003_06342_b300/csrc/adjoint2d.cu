@@ -476,6 +476,7 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
                     float *__restrict__ lam, float *__restrict__ cst, double *dparams,
                     const DevParams P) {
     __shared__ float sphi[ADJ_WMAX];
+    pdl_wait();
     constexpr int R = BIASED ? 2 : 1;
     const int nx = P.n[0], ny = P.n[1];
     const int tiles_x = (nx + 31) / 32;
@@ -493,6 +494,7 @@ adj_step2d_a_kernel(const float *__restrict__ st, const float *__restrict__ lam_
 // others wrap periodic axes and skip neighbours beyond a wall.
 __global__ void __launch_bounds__(256)
 adj_step2d_b_kernel(const float *__restrict__ cst, float *__restrict__ lam, const DevParams P) {
+    pdl_wait();
     const int nx = P.n[0], ny = P.n[1];
     const size_t N = (size_t)P.N;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
@@ -660,11 +662,17 @@ cudaError_t launch_adj_terminal2d(const float *st, const float *target, float *a
 cudaError_t launch_adj_step2d(const float *st, const float *lam_next, float *lam, float *cst,
                               double *dparams, const DevParams &P, cudaStream_t stream) {
     const int tiles = ((P.n[0] + 31) / 32) * ((P.n[1] + ADJ_TY - 1) / ADJ_TY);
+    cudaError_t e;
     if (P.opts & OPT_BIASED)
-        adj_step2d_a_kernel<true><<<tiles, 32 * ADJ_TY, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
+        e = pdl_launch(adj_step2d_a_kernel<true>, dim3(tiles), dim3(32 * ADJ_TY), 0, stream, st, lam_next, lam,
+                       cst, dparams, P);
     else
-        adj_step2d_a_kernel<false><<<tiles, 32 * ADJ_TY, 0, stream>>>(st, lam_next, lam, cst, dparams, P);
-    adj_step2d_b_kernel<<<dim3((P.n[0] + 255) / 256, P.n[1]), 256, 0, stream>>>(cst, lam, P);
+        e = pdl_launch(adj_step2d_a_kernel<false>, dim3(tiles), dim3(32 * ADJ_TY), 0, stream, st, lam_next, lam,
+                       cst, dparams, P);
+    if (e != cudaSuccess) return e;
+    e = pdl_launch(adj_step2d_b_kernel, dim3((P.n[0] + 255) / 256, P.n[1]), dim3(256), 0, stream,
+                   (const float *)cst, lam, P);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -166,6 +166,7 @@ cac2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, const float *__res
              float factor, const DevParams P, const __grid_constant__ Planes2d<S> PL) {
     using T = typename CacTile<S>::T;
     __shared__ float sphi[T::SY * T::SX];
+    pdl_wait();
     const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
     const bool fast = x0 >= 1 && x0 + T::TX + 1 <= P.n[0] && y0 >= 1 && y0 + T::TY + 1 <= P.n[1];
     if (fast) cac_tile2d<S, true, T>(pin, pout, vel, factor, P, sphi, x0, y0, PL);
@@ -178,8 +179,8 @@ cudaError_t launch_cac2d(const void *pin, void *pout, const float *vel, float fa
     using T = typename CacTile<S>::T;
     dim3 block(T::TX, T::TY);
     dim3 grid((P.n[0] + T::TX - 1) / T::TX, (P.n[1] + T::TY - 1) / T::TY);
-    cac2d_kernel<S><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, vel, factor, P,
-                                            planes2d<S>(pin, pout, P));
+    pdl_launch(cac2d_kernel<S>, grid, block, 0, st, (const S *)pin, (S *)pout, vel, factor, P,
+               planes2d<S>(pin, pout, P));
     return cudaGetLastError();
 }
 

@@ -293,6 +293,7 @@ cac3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, const float *__res
              const __grid_constant__ Planes3d<S> PL) {
     __shared__ float sphi[CW * CPLANE];
     __shared__ uint32_t rbuf[2][CRING_WORDS];
+    pdl_wait();
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * CTY;
     const int cls = tile_class3d<CTY>(x0, y0, P);
     if (cls == XY_IN) cac3d_column<S, XY_IN>(pin, pout, q_zero, vel, factor, P, sphi, rbuf, PL);
@@ -305,8 +306,8 @@ cudaError_t launch_cac3d(const void *pin, void *pout, const float *q_zero, const
                          const DevParams &P, cudaStream_t st) {
     dim3 block(TX, CTY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + CTY - 1) / CTY, (P.n[2] + ZB - 1) / ZB);
-    cac3d_kernel<S><<<grid, block, 0, st>>>((const S *)pin, (S *)pout, q_zero, vel, factor, P,
-                                            planes3d<S>(pin, pout, P));
+    pdl_launch(cac3d_kernel<S>, grid, block, 0, st, (const S *)pin, (S *)pout, q_zero, vel, factor, P,
+               planes3d<S>(pin, pout, P));
     return cudaGetLastError();
 }
 

@@ -49,6 +49,7 @@ step2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
               const __grid_constant__ Planes2d<S> PL) {
     using T = typename StepTile<S, BIASED>::T;
     __shared__ float sphi[BIASED ? (T::TY + 4) * (T::TX + 4) : T::SY * T::SX];
+    pdl_wait();
     const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
     const bool fast = x0 >= 1 && x0 + T::TX + 1 <= P.n[0] && y0 >= 1 && y0 + T::TY + 1 <= P.n[1];
     if (BIASED) {
@@ -66,7 +67,7 @@ static void launch_step2d_one(const S *in, S *out, float *phi_prev, const float 
     using T = typename StepTile<S, BIASED>::T;
     const dim3 block(T::TX, T::TY);
     const dim3 grid((P.n[0] + T::TX - 1) / T::TX, (P.n[1] + T::TY - 1) / T::TY);
-    step2d_kernel<S, COLL, BIASED><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL);
+    pdl_launch(step2d_kernel<S, COLL, BIASED>, grid, block, 0, st, in, out, phi_prev, q_in, q_out, P, PL);
 }
 
 // ------------------------------------------------------------------ phi moment

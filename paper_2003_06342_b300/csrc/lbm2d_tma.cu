@@ -182,6 +182,7 @@ step2d_tma_kernel(const __grid_constant__ TmaMaps2d maps, const S *__restrict__ 
     // bulk tensor copies want 128-byte aligned destinations
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t barF[Gm::NFS], barG[Gm::NG];
+    pdl_wait();
     __shared__ float win[2][SY * SX];
     __shared__ uint32_t rbuf[2][RWORDS];
     const int nx = P.n[0], ny = P.n[1];
@@ -394,14 +395,14 @@ cudaError_t launch_step2d_tma(const TmaMaps2d &M, int par, const void *pin, void
     dim3 block(TX, TY);
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY * YC - 1) / (TY * YC));
     if (P.opts & OPT_TRT)
-        step2d_tma_kernel<S, COLL_TRT><<<grid, block, March2Geom<S>::DYN, st>>>(
-            M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
+        pdl_launch(step2d_tma_kernel<S, COLL_TRT>, grid, block, March2Geom<S>::DYN, st, M, (const S *)pin,
+                   (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
     else if (P.opts & OPT_MRT)
-        step2d_tma_kernel<S, COLL_MRT><<<grid, block, March2Geom<S>::DYN, st>>>(
-            M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
+        pdl_launch(step2d_tma_kernel<S, COLL_MRT>, grid, block, March2Geom<S>::DYN, st, M, (const S *)pin,
+                   (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
     else
-        step2d_tma_kernel<S, COLL_BGK><<<grid, block, March2Geom<S>::DYN, st>>>(
-            M, (const S *)pin, (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
+        pdl_launch(step2d_tma_kernel<S, COLL_BGK>, grid, block, March2Geom<S>::DYN, st, M, (const S *)pin,
+                   (S *)pout, phi_prev, q_in, q_out, par, err, P, planes2d<S>(pin, pout, P));
     return cudaGetLastError();
 }
 

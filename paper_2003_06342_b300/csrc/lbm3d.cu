@@ -23,6 +23,7 @@ step3d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
               const __grid_constant__ Planes3d<S> PL) {
     __shared__ float sphi[BIASED ? NWB * PLANEB : NW3 * PLANE];
+    pdl_wait();
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int cls = tile_class3d(x0, y0, P);
     if (BIASED) {
@@ -215,15 +216,15 @@ cudaError_t launch_step3d(const void *pin, void *pout, float *phi_prev, const fl
     S *out = (S *)pout;
     const Planes3d<S> PL = planes3d<S>(pin, pout, P);
     switch (P.opts & (OPT_TRT | OPT_MRT | OPT_BIASED)) {
-    case 0: step3d_kernel<S, COLL_BGK, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
-    case OPT_TRT: step3d_kernel<S, COLL_TRT, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
-    case OPT_MRT: step3d_kernel<S, COLL_MRT, false><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
-    case OPT_BIASED: step3d_kernel<S, COLL_BGK, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL); break;
+    case 0: pdl_launch(step3d_kernel<S, COLL_BGK, false>, grid, block, 0, st, in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_TRT: pdl_launch(step3d_kernel<S, COLL_TRT, false>, grid, block, 0, st, in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_MRT: pdl_launch(step3d_kernel<S, COLL_MRT, false>, grid, block, 0, st, in, out, phi_prev, q_in, q_out, P, PL); break;
+    case OPT_BIASED: pdl_launch(step3d_kernel<S, COLL_BGK, true>, grid, block, 0, st, in, out, phi_prev, q_in, q_out, P, PL); break;
     case OPT_TRT | OPT_BIASED:
-        step3d_kernel<S, COLL_TRT, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL);
+        pdl_launch(step3d_kernel<S, COLL_TRT, true>, grid, block, 0, st, in, out, phi_prev, q_in, q_out, P, PL);
         break;
     case OPT_MRT | OPT_BIASED:
-        step3d_kernel<S, COLL_MRT, true><<<grid, block, 0, st>>>(in, out, phi_prev, q_in, q_out, P, PL);
+        pdl_launch(step3d_kernel<S, COLL_MRT, true>, grid, block, 0, st, in, out, phi_prev, q_in, q_out, P, PL);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -493,6 +493,7 @@ step3d_tma_kernel(const __grid_constant__ TmaMaps3d maps, const S *__restrict__ 
     // bulk tensor copies want 128-byte aligned destinations
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     __shared__ __align__(8) uint64_t barF[Tma3Geom<S>::NFS], barG[Tma3Geom<S>::NG];
+    pdl_wait();
     // the biased gradient: a five-plane two-ring window, two fetched planes
     __shared__ float sphi[BIASED ? NWB * PLANEB : NW3 * PLANE];
     __shared__ __align__(16) uint32_t rbuf[BIASED ? 2 * BWIN_WORDS : 2 * RING_WORDS];
@@ -612,8 +613,8 @@ cudaError_t launch_step3d_tma(const TmaMaps3d &M, int par, const void *pin, void
     const S *in = (const S *)pin;
     S *out = (S *)pout;
 #define LBM_TMA3_LAUNCH(C, B)                                                                   \
-    step3d_tma_kernel<S, C, B><<<grid, block, Tma3Geom<S>::DYN, st>>>(M, in, out, phi_prev, q_in, \
-                                                                      q_out, par, err, P, PL)
+    pdl_launch(step3d_tma_kernel<S, C, B>, grid, block, Tma3Geom<S>::DYN, st, M, in, out, phi_prev, q_in, \
+               q_out, par, err, P, PL)
     switch (P.opts & (OPT_TRT | OPT_MRT | OPT_BIASED)) {
     case 0: LBM_TMA3_LAUNCH(COLL_BGK, false); break;
     case OPT_TRT: LBM_TMA3_LAUNCH(COLL_TRT, false); break;

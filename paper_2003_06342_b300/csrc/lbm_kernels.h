@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <utility>
 #include "lbm_common.cuh"
 
 namespace lbm {
@@ -11,6 +12,33 @@ namespace lbm {
 // per-warp sums) and store the pair at partial[2*blockIdx.x].  Every thread
 // of the block must call it.  The summation order is fixed, so results are
 // reproducible run to run.
+// Programmatic dependent launch.  A kernel launched by pdl_launch may have
+// its blocks scheduled while the kernel before it on the stream drains; it
+// calls pdl_wait first, which returns once that kernel has completed and its
+// writes are visible, and then lets the kernel after it be scheduled the same
+// way.  Nothing before pdl_wait touches global memory.  Launched without the
+// attribute (or after a copy), the wait returns at once.
+__device__ __forceinline__ void pdl_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Blocks of 256 threads of the moment kernels, which also form the FP64
 // mass and energy partial sums: one thread per cell up to two waves of 148 x
 // 4 blocks, then a grid-stride loop, so each thread adds several cells into
