@@ -38,9 +38,13 @@ namespace lbm {
 // Tile of the tiled kernel per storage and gradient scheme, chosen by
 // measurement on the 2048 x 4096 film (one thread per cell, 64 registers,
 // 1024 threads per SM): FP32 32 x 4 (25.6k MLUPS against 24.9k for 32 x 8),
-// 16-bit 64 x 4 (FP16 36.5k against 34.5k), the biased gradient 64 x 4.
+// 16-bit 64 x 4 (FP16 36.8k against 34.5k for 32 x 8, 33.0k for 64 x 8,
+// 32.5k for 128 x 4), the biased gradient 64 x 4 for 16-bit storage and
+// 64 x 8 for FP32 (23.7k against 23.1k: its two-ring window has a smaller
+// share of halo cells).
 template <typename S, bool BIASED> struct StepTile { using T = Tile2<64, 4>; };
 template <> struct StepTile<float, false> { using T = Tile2<32, 4>; };
+template <> struct StepTile<float, true> { using T = Tile2<64, 8>; };
 
 template <typename S, int COLL, bool BIASED>
 __global__ void __launch_bounds__(StepTile<S, BIASED>::T::NT, 1024 / StepTile<S, BIASED>::T::NT)

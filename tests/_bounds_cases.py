@@ -49,6 +49,8 @@ STEP_CASES = [
     # the separately instantiated collision and gradient options
     ("2d_tiled_biased_ragged_walls", lambda: _opt(_film(100, 70), **BIASED), "fp32", "tiled", 12),
     ("2d_tiled_biased_one_cell_axis", lambda: _opt(W.stefan_1d(nx=40, ny=1), **BIASED), "fp16", "tiled", 12),
+    ("2d_tiled_biased_interior_fp32", lambda: _opt(_film(200, 45), **BIASED), "fp32", "tiled", 12),
+    ("2d_tiled_biased_interior_fp16", lambda: _opt(_film(200, 45), **BIASED), "fp16", "tiled", 12),
     ("3d_tiled_biased_ragged", lambda: _opt(_film3d(44, 13, 37, 12.0), **BIASED), "fp32", "tiled", 6),
     ("3d_tiled_biased_tiny_z", lambda: _opt(_film3d(9, 9, 5, 2.0), **BIASED), "fp32", "tiled", 6),
     ("2d_tiled_mrt_ragged", lambda: _opt(_film(100, 70), **MRT_G), "fp32", "tiled", 12),

@@ -33,6 +33,9 @@ CASES = [
     ("stefan_walls_x", lambda: _b(W.stefan_1d(nx=90, ny=2)), 80),
     ("one_cell_axis", lambda: _b(W.stefan_1d(nx=40, ny=1)), 40),
     ("film_trt", lambda: _b(_film(67, 45), collision="trt", trt_magic=(3.0 / 16.0, 0.25, 0.25)), 30),
+    # wide enough for tiles whose two rings lie inside the grid (the fast
+    # path of the 64-wide tiles), with ragged last tiles
+    ("film_interior_tiles", lambda: _b(_film(200, 45)), 20),
     # 3D: walls on z, ragged x / y tiles, several z blocks of 32 layers
     ("film_3d_ragged", lambda: _b(W.film_boiling_3d(37, 10, 41, modes=2, z0=12.0, phi_wall=(1.0, 0.0))), 12),
     # a periodic axis of three cells, shorter than the two rings
