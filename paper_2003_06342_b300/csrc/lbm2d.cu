@@ -39,19 +39,22 @@ namespace lbm {
 // measurement on the 2048 x 4096 film (one thread per cell, 64 registers,
 // 1024 threads per SM): FP32 32 x 4 (25.6k MLUPS against 24.9k for 32 x 8),
 // 16-bit 64 x 4 (FP16 36.8k against 34.5k for 32 x 8, 33.0k for 64 x 8,
-// 32.5k for 128 x 4), the biased gradient 64 x 4 for 16-bit storage and
-// 64 x 8 for FP32 (23.7k against 23.1k: its two-ring window has a smaller
-// share of halo cells).
-template <typename S, bool BIASED> struct StepTile { using T = Tile2<64, 4>; };
-template <> struct StepTile<float, false> { using T = Tile2<32, 4>; };
-template <> struct StepTile<float, true> { using T = Tile2<64, 8>; };
+// 32.5k for 128 x 4) except with the MRT collision, which spills at 64
+// registers and runs 32 x 4 (FP16 31.9k against 29.6k), the biased gradient
+// 64 x 4 for 16-bit storage and 64 x 8 for FP32 (23.7k against 23.1k: its
+// two-ring window has a smaller share of halo cells).
+template <typename S, bool BIASED, int COLL> struct StepTile { using T = Tile2<64, 4>; };
+template <int COLL> struct StepTile<float, false, COLL> { using T = Tile2<32, 4>; };
+template <int COLL> struct StepTile<float, true, COLL> { using T = Tile2<64, 8>; };
+template <> struct StepTile<__half, false, COLL_MRT> { using T = Tile2<32, 4>; };
+template <> struct StepTile<__nv_bfloat16, false, COLL_MRT> { using T = Tile2<32, 4>; };
 
 template <typename S, int COLL, bool BIASED>
-__global__ void __launch_bounds__(StepTile<S, BIASED>::T::NT, 1024 / StepTile<S, BIASED>::T::NT)
+__global__ void __launch_bounds__(StepTile<S, BIASED, COLL>::T::NT, 1024 / StepTile<S, BIASED, COLL>::T::NT)
 step2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict__ phi_prev,
               const float *__restrict__ q_in, float *__restrict__ q_out, const DevParams P,
               const __grid_constant__ Planes2d<S> PL) {
-    using T = typename StepTile<S, BIASED>::T;
+    using T = typename StepTile<S, BIASED, COLL>::T;
     __shared__ float sphi[BIASED ? (T::TY + 4) * (T::TX + 4) : T::SY * T::SX];
     pdl_wait();
     const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
@@ -68,7 +71,7 @@ step2d_kernel(const S *__restrict__ pin, S *__restrict__ pout, float *__restrict
 template <typename S, int COLL, bool BIASED>
 static void launch_step2d_one(const S *in, S *out, float *phi_prev, const float *q_in, float *q_out,
                               const DevParams &P, const Planes2d<S> &PL, cudaStream_t st) {
-    using T = typename StepTile<S, BIASED>::T;
+    using T = typename StepTile<S, BIASED, COLL>::T;
     const dim3 block(T::TX, T::TY);
     const dim3 grid((P.n[0] + T::TX - 1) / T::TX, (P.n[1] + T::TY - 1) / T::TY);
     pdl_launch(step2d_kernel<S, COLL, BIASED>, grid, block, 0, st, in, out, phi_prev, q_in, q_out, P, PL);
