@@ -40,14 +40,17 @@ namespace lbm {
 // 1024 threads per SM): FP32 32 x 4 (25.6k MLUPS against 24.9k for 32 x 8),
 // 16-bit 64 x 4 (FP16 36.8k against 34.5k for 32 x 8, 33.0k for 64 x 8,
 // 32.5k for 128 x 4) except with the MRT collision, which spills at 64
-// registers and runs 32 x 4 (FP16 31.9k against 29.6k), the biased gradient
-// 64 x 4 for 16-bit storage and 64 x 8 for FP32 (23.7k against 23.1k: its
-// two-ring window has a smaller share of halo cells).
+// registers and runs 32 x 4 (FP16 31.9k against 29.6k); the biased gradient
+// 32 x 4 for 16-bit storage (FP16 32.7k against 31.0k for 64 x 4, 32.5k
+// for 32 x 8) and 64 x 8 for FP32 (23.7k against 23.1k for 64 x 4, 22.5k
+// for 32 x 8, 22.9k for 128 x 4).
 template <typename S, bool BIASED, int COLL> struct StepTile { using T = Tile2<64, 4>; };
 template <int COLL> struct StepTile<float, false, COLL> { using T = Tile2<32, 4>; };
 template <int COLL> struct StepTile<float, true, COLL> { using T = Tile2<64, 8>; };
 template <> struct StepTile<__half, false, COLL_MRT> { using T = Tile2<32, 4>; };
 template <> struct StepTile<__nv_bfloat16, false, COLL_MRT> { using T = Tile2<32, 4>; };
+template <int COLL> struct StepTile<__half, true, COLL> { using T = Tile2<32, 4>; };
+template <int COLL> struct StepTile<__nv_bfloat16, true, COLL> { using T = Tile2<32, 4>; };
 
 template <typename S, int COLL, bool BIASED>
 __global__ void __launch_bounds__(StepTile<S, BIASED, COLL>::T::NT, 1024 / StepTile<S, BIASED, COLL>::T::NT)
