@@ -33,6 +33,27 @@ def _noalloc_sums(F, params, stream):
     return out.tolist()
 
 
+@pytest.mark.parametrize("make", [
+    lambda: W.film_boiling_2d(1024, 512, modes=3, seed=2, y0=120.0, paper=True, phi_wall=(1.0, 0.0)),
+    lambda: W.film_boiling_3d(96, 96, 40, modes=1, z0=14.0, phi_wall=(1.0, 0.0)),
+], ids=["2d_1024x512", "3d_96x96x40"])
+def test_reduce_over_several_cells_per_thread(make):
+    """Grids larger than the moment kernel's grid of 148 x 8 blocks of 256
+    threads, so each of its threads adds several cells into its FP64
+    accumulators: the sums equal the one-cell-per-thread sums of the same
+    fields, and the mass equals the host's FP64 sum of phi."""
+    w = make()
+    s = gpu_solver(w)
+    s.step(5)
+    mass, energy = s.reduce()
+    F = s.fields()
+    m2, e2 = _noalloc_sums(F, w.params, s.stream)
+    assert abs(m2 - mass) <= 1e-12 * abs(mass)
+    assert abs(e2 - energy) <= 1e-12 * abs(energy)
+    m_host = float(F["phi"].double().sum().item())
+    assert abs(m_host - mass) <= 1e-12 * abs(mass)
+
+
 def test_noalloc_sums_match_reduce_two_calls():
     w = W.film_boiling_2d(300, 170, modes=3, seed=1, y0=40.0, paper=True, phi_wall=(1.0, 0.0))
     s = gpu_solver(w)
