@@ -9,9 +9,11 @@ the fields at x after k steps depend on the initial fields within 2k + 2
 cells).  For each sampled cell the oracle therefore steps the window of
 radius r = 2k + 3 around it, cut from the same initial fields: periodic axes
 wrap, a window that meets a wall keeps that wall, and the window's own edges
-(wrapped or cut) are more than 2k + 2 cells from the sample.  The sampled
-cells include the interface band, cells next to both walls, periodic edges
-and the borders of the 32 x 8 tiles."""
+(wrapped or cut) are more than 2k + 2 cells from the sample.  With the
+biased gradient the phi stencil reaches two cells, so the window radius is
+3k + 3.  The sampled cells include the interface band, cells next to both
+walls, periodic edges and tile borders.  The MRT and biased-gradient
+variants the bench times on the 2D grid are checked the same way."""
 import numpy as np
 import pytest
 import torch
@@ -67,8 +69,10 @@ def _window(w, cell, r):
     return cut(w.phi0), cut(w.T0), cut(w.p0), tuple(2 * r + 1 for _ in w.n), tuple(per), tuple(pos)
 
 
-def _oracle_at(w, cell, steps):
-    r = 2 * steps + 3
+def _oracle_at(w, cell, steps, reach=2):
+    """reach: cells a step's value depends on in each direction (the push
+    plus the phi stencil: 2 for the central gradient, 3 for the biased one)."""
+    r = reach * steps + 3
     phi0, T0, p0, n, per, pos = _window(w, cell, r)
     P, G = M.Params.from_dict(w.params), M.Grid(n, per)
     st = M.run(M.init_state(phi0, T0, P, G, p0=p0), P, G, steps)
@@ -85,7 +89,7 @@ def _gpu_at(F, cells):
     return dict(phi=pick(F["phi"]), T=pick(F["T"]), p=pick(F["p"]), u=[pick(F["u"][a]) for a in range(dim)])
 
 
-def _check(w, kernel, steps, storage="fp32", tol=TOL, seed=0):
+def _check(w, kernel, steps, storage="fp32", tol=TOL, seed=0, reach=2):
     from paper_2003_06342_b300 import Solver
     s = Solver(w.n, w.periodic, w.params, storage=storage)
     s.set_kernel(kernel)
@@ -101,7 +105,7 @@ def _check(w, kernel, steps, storage="fp32", tol=TOL, seed=0):
     got = _gpu_at(s.fields(), cells)
     worst = {k: 0.0 for k in ("phi", "T", "p", "u")}
     for j, cell in enumerate(cells):
-        ref = _oracle_at(w, cell, steps)
+        ref = _oracle_at(w, cell, steps, reach)
         for k in ("phi", "T", "p"):
             worst[k] = max(worst[k], abs(got[k][j] - ref[k]))
         worst["u"] = max(worst["u"], max(abs(got["u"][a][j] - ref["u"][a]) for a in range(dim)))
@@ -119,6 +123,27 @@ def test_2d_2048x4096_tiled_fp32_sampled_20_steps():
 
 def test_2d_2048x4096_tiled_fp16_sampled():
     _check(W.c2_film_boiling(), "tiled", 3, storage="fp16", tol=5e-3)
+
+
+def _with(w, **extra):
+    w.params.update(**extra)
+    return w
+
+
+def test_2d_2048x4096_tiled_mrt_fp32_sampled():
+    """The MRT collision of both sets on the full grid (the bench's MRT
+    variant), FP32 and FP16 storage."""
+    mrt = dict(collision="mrt", mrt_rates=(1.4, 1.4, 1.2))
+    _check(_with(W.c2_film_boiling(), **mrt), "tiled", 3, seed=4)
+    _check(_with(W.c2_film_boiling(), **mrt), "tiled", 3, storage="fp16", tol=5e-3, seed=5)
+
+
+def test_2d_2048x4096_tiled_biased_sampled():
+    """The biased gradient on the full grid (its two-ring window: a step
+    reaches three cells), FP32 and FP16 storage."""
+    _check(_with(W.c2_film_boiling(), grad_scheme="biased2"), "tiled", 3, seed=6, reach=3)
+    _check(_with(W.c2_film_boiling(), grad_scheme="biased2"), "tiled", 3, storage="fp16", tol=5e-3, seed=7,
+           reach=3)
 
 
 def test_3d_256x256x512_tma_fp32_sampled():
