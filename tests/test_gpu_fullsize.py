@@ -150,6 +150,17 @@ def test_3d_256x256x512_tma_fp32_sampled():
     _check(W.c3_film_boiling_3d(), "tma", 2)
 
 
+def test_3d_256x256x512_mrt_and_biased_sampled():
+    """The 3D MRT collision (TMA kernel, FP32 and FP16) and the biased
+    gradient (the kernels AUTO takes: tiled for FP32, TMA for FP16)."""
+    mrt = dict(collision="mrt", mrt_rates=(1.4, 1.4, 1.2), mrt_rates_g=(1.3, 0.0, 0.0, 1.25))
+    _check(_with(W.c3_film_boiling_3d(), **mrt), "tma", 2, seed=8)
+    _check(_with(W.c3_film_boiling_3d(), **mrt), "tma", 2, storage="fp16", tol=5e-3, seed=9)
+    _check(_with(W.c3_film_boiling_3d(), grad_scheme="biased2"), "tiled", 2, seed=10, reach=3)
+    _check(_with(W.c3_film_boiling_3d(), grad_scheme="biased2"), "tma", 2, storage="fp16", tol=5e-3, seed=11,
+           reach=3)
+
+
 def test_3d_256x256x512_tma_fp16_sampled():
     _check(W.c3_film_boiling_3d(), "tma", 2, storage="fp16", tol=5e-3, seed=2)
 
