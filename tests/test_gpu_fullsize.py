@@ -172,3 +172,57 @@ def test_3d_512x512x768_tma_fp16_sampled():
     _check(w, "tma", 2, storage="fp16", tol=5e-3, seed=3)
     del w
     torch.cuda.empty_cache()
+
+
+def _cac_sampled(n, periodic, params, phi0, u, period, steps, storage, tol, seed):
+    """The phase field alone at full size: sampled cells against the oracle
+    of oracle.cac on windows of radius 2k + 3 cut (every axis periodic) from
+    the initial field and the imposed velocity."""
+    from oracle import cac as C
+    from paper_2003_06342_b300 import Solver
+    s = Solver(n, periodic, params, storage=storage)
+    s.set_velocity(u, period)
+    s.init(phi0, np.ones_like(phi0))
+    s.step(steps)
+    got = s.fields()["phi"]
+    rng = np.random.default_rng(seed)
+    dim = len(n)
+    # cells of the interface band (0.05 < phi < 0.95), random cells, corners
+    # and tile borders
+    band = np.argwhere((phi0 > 0.05) & (phi0 < 0.95))
+    pick = band[rng.choice(len(band), size=min(24, len(band)), replace=False)]
+    cells = [[int(v) for v in reversed(b)] for b in pick]
+    cells += [[int(rng.integers(0, n[a])) for a in range(dim)] for _ in range(8)]
+    cells += [[0] * dim, [n[a] - 1 for a in range(dim)], [31] + [7] * (dim - 1), [32] + [8] * (dim - 1)]
+    r = 2 * steps + 3
+    worst = 0.0
+    for cell in cells:
+        idx = [[(c - r + k) % m for k in range(2 * r + 1)] for c, m in zip(cell, n)]
+        ix = np.ix_(*reversed(idx))
+        win = tuple(2 * r + 1 for _ in n)
+        P, G = M.Params.from_dict(params), M.Grid(win, (True,) * dim)
+        uw = [np.ascontiguousarray(ua[ix]) for ua in u]
+        g = C.run(C.init_state(np.ascontiguousarray(phi0[ix]), uw, P, G, period), uw, P, G, steps, period)
+        ref = float(C.phase_field(g).numpy()[(r,) * dim])
+        val = float(got[tuple(reversed(cell))].item())
+        worst = max(worst, abs(val - ref))
+    print("phase field", n, storage, steps, len(cells), "cells", worst)
+    assert worst < tol, worst
+
+
+def test_phase_field_2d_4096_sampled():
+    """The 4096^2 vortex of the bench's phase-field variant, FP32 and FP16."""
+    w = W.vortex_disk(n=4096)
+    for storage, tol, seed in (("fp32", TOL, 12), ("fp16", 5e-3, 13)):
+        _cac_sampled(w.n, w.periodic, w.params, w.phi0, w.extra["u"], w.extra["period"], 3, storage, tol, seed)
+
+
+def test_phase_field_3d_1024x1024x32_sampled():
+    """The thin periodic 3D vortex of the bench's 3D phase-field variant."""
+    wv = W.vortex_disk(n=1024)
+    nz = 32
+    phi = np.repeat(wv.phi0[None], nz, axis=0)
+    u = [np.repeat(uu[None], nz, axis=0) for uu in wv.extra["u"]] + [np.zeros_like(phi)]
+    for storage, tol, seed in (("fp32", TOL, 14), ("fp16", 5e-3, 15)):
+        _cac_sampled((1024, 1024, nz), (True, True, True), wv.params, phi, u, wv.extra["period"], 3, storage, tol,
+                     seed)
